@@ -1,0 +1,415 @@
+"""Benchmark: global XPBD iterations per second of the MGPBD solve.
+
+Workload (default): ``block100`` -- 100x33x100 hex cells of 0.005 m, 5 tets
+per cell (1.65M tets, 346,834 vertices), edge distance plus tet volume
+constraints (3,680,033 rows, 376,541,249 nonzeros in A), alpha = 1e-10,
+bottom face pinned, dt = 1/60, 20 global iterations per frame, lazy setup
+every 20 global iterations, PCG rtol 1e-6 capped at 200 iterations.
+
+A step is one global iteration of Algorithm 1 (constraints, assembly, lazy
+setup when due, Galerkin re-form, coarsest factorisation, MGPCG with one
+V-cycle per PCG iteration, dx/lambda/x update); the frame prologue and
+epilogue fall inside the timed region at their natural rate (every 20
+steps).  The headline `value` is the mixed-precision form; the FP64 form is
+reported under "fp64".  Inputs are resident on the device; A alone is
+3-4.6 GB, far larger than L2, so no L2 flush is needed between steps.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload (a 10x33x4-cell block of the same
+recipe) and scales the time per iteration to the full workload by the
+nonzero count of A.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FULL_NNZ = 376_541_249  # nonzeros of A for block100 (checked at run time)
+SAMPLE = (10, 33, 4)    # oracle sample: cells along x, y (vertical), z
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="block100")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only: no collective on the data path)
+# ---------------------------------------------------------------------------
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.proc = None
+        self.path = None
+        self.uuid = uuid
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+class Runner:
+    """Steps global iterations and keeps the frame bookkeeping of Alg. 1."""
+
+    def __init__(self, solver, max_iter):
+        self.g = solver
+        self.max_iter = max_iter
+        self.k = 0
+        self.g.begin_frame()
+        self.pcg = []
+
+    def step(self):
+        d = self.g.iterate()
+        self.pcg.append(d["pcg_iters"])
+        self.k += 1
+        if self.k % self.max_iter == 0:
+            self.g.end_frame()
+            self.g.begin_frame()
+        return d
+
+
+def measure(mesh, params, steps, warmup, ws, profile=True):
+    import torch
+
+    from paper_2505_13390_gb300.mgpbd import Solver, launch_count
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    g = Solver(mesh, params, stream=stream)
+    create_s = time.perf_counter() - t0
+    run = Runner(g, params["max_iter"])
+    for _ in range(warmup):
+        run.step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    if profile:
+        g.profile(True)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = Clocks(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    n0 = launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    pcg0 = len(run.pcg)
+    ev0.record(stream)
+    for _ in range(steps):
+        run.step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    launches = launch_count() - n0
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = g.profile_read() if profile else None
+    if profile:
+        g.profile(False)
+    st = g.stats()
+    out = dict(ms=ms, launches=launches, clocks=ck, prof=prof, stats=st, create_s=create_s,
+               pcg=run.pcg[pcg0:], solver=g, runner=run)
+    return out
+
+
+def e2e(g, run, steps):
+    """Same metric through the C ABI with host buffers: per step the state goes
+    host->device from pinned memory, one global iteration runs, and the new
+    positions and velocities come back device->host."""
+    import numpy as np
+    import torch
+
+    x, v = g.get_state()
+    xp = torch.from_numpy(x).pin_memory()
+    vp = torch.from_numpy(v).pin_memory()
+    xh, vh = xp.numpy(), vp.numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        g.set_state(xh, vh)  # MEM_HOST: synchronous H2D copies
+        run.step()
+        from paper_2505_13390_gb300 import mgpbd as M
+        M._check(M.load().mgpbd_get_state(g.h, xh.ctypes.data, vh.ctypes.data, M.MEM_HOST),
+                 "get_state")
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    nbytes = int(xh.nbytes + vh.nbytes)
+    assert np.isfinite(xh).all()
+    return steps / dt, nbytes
+
+
+def cpu_sample_baseline(iters=3, warm=1):
+    """The FP64 oracle on the host cores (1 thread) on the bounded sample."""
+    from oracle.oracle import Oracle
+    from paper_2505_13390_gb300.meshgen import default_params, hex_block
+    mesh = hex_block(*SAMPLE, h=0.005, jitter=0.1, alpha=1e-10, pin="y0", seed=1,
+                     name="block-sample")
+    p = default_params(omega_x=0.1, setup_interval=20)
+    o = Oracle(mesh, p)
+    nnz = int(o.matrix(0)[0][-1])
+    o.begin_frame()
+    for _ in range(warm):
+        o.iterate()
+    t0 = time.perf_counter()
+    pcg = []
+    for _ in range(iters):
+        pcg.append(o.iterate()["pcg_iters"])
+    dt = (time.perf_counter() - t0) / iters
+    scale = FULL_NNZ / nnz
+    return {"value": 1.0 / (dt * scale), "unit": "global_iters/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 C oracle, {iters} global iterations (after {warm} with setup) on a "
+                       f"{SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]}-cell block of the same recipe "
+                       f"({mesh.n_rows} rows, {nnz} nnz), {dt:.2f} s/iteration, scaled by the "
+                       f"nnz ratio {scale:.1f} to 376.5M nnz; PCG iterations {pcg}")}, dt, scale
+
+
+def run_ours(args, ws, rank):
+    import torch
+
+    import __graft_entry__ as ge
+    from paper_2505_13390_gb300.meshgen import workload
+    if not os.path.exists(os.path.join(ROOT, "paper_2505_13390_gb300", "libmgpbd.so")):
+        ge.build()
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu, _, _ = cpu_sample_baseline()
+    mesh, params = workload(args.workload)
+    params = dict(params, precision=1)
+    res = measure(mesh, params, args.steps, args.warmup, ws)
+    ms = max_over_ranks(ws, res["ms"])
+    value = ws * args.steps / (ms / 1e3)
+    prof = res["prof"]
+    g = res["solver"]
+    nnz = res["stats"]
+    li = g.level_info(0)
+    if li["nnz"] != FULL_NNZ and args.workload == "block100":
+        raise RuntimeError(f"unexpected nnz {li['nnz']}")
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    avg_ms = prof["total_ms"] / max(prof["launches"], 1)
+    achieved = prof["bytes_per_launch"] / (avg_ms / 1e3) / 1e9
+    e2e_val = None
+    e2e_bytes = 0
+    if not args.no_e2e:
+        e2e_val, e2e_bytes = e2e(g, res["runner"], max(3, args.steps // 2))
+        e2e_val = e2e_val * ws
+    fp64 = None
+    levels = [g.level_info(l) for l in range(g.levels)]
+    g.close()
+    del res["solver"], res["runner"]
+    torch.cuda.empty_cache()
+    if not args.no_fp64:
+        p64 = dict(params, precision=0)
+        r64 = measure(mesh, p64, args.steps, args.warmup, ws)
+        ms64 = max_over_ranks(ws, r64["ms"])
+        pr = r64["prof"]
+        a64 = pr["bytes_per_launch"] / (pr["total_ms"] / max(pr["launches"], 1) / 1e3) / 1e9
+        fp64 = {"value": ws * args.steps / (ms64 / 1e3), "ms_per_step": ms64 / args.steps,
+                "pcg_iters": r64["pcg"], "clocks": r64["clocks"],
+                "smoother_sweep_gbs": a64, "smoother_sweep_frac": a64 / hbm}
+        r64["solver"].close()
+    if rank != 0:
+        return
+    line = {
+        "metric": "global XPBD iters/s at 1.65M tets (mixed precision; FP64 under fp64)",
+        "value": value,
+        "unit": "global_iters/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "rows": li["n"], "nnz": li["nnz"],
+                   "tets": mesh.n_tet, "verts": mesh.n_verts, "iters_per_frame": 20,
+                   "setup_interval": params["setup_interval"], "pcg_rtol": 1e-6,
+                   "pcg_maxiter": params["pcg_maxiter"], "parallelism": f"replicas{ws}",
+                   "l2": "inputs larger than L2 (A is 3.1 GB in FP32, 4.6 GB in FP64)",
+                   "levels": [(l["n"], l["nnz"]) for l in levels]},
+        "pcg_iters": res["pcg"],
+        "roofline": {"bound": "hbm", "kernel": "k_jacobi (level-0 weighted-Jacobi sweep, FP32)",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_source": peak_src,
+                     "traffic": None,
+                     "bytes_per_launch": prof["bytes_per_launch"], "avg_launch_ms": avg_ms,
+                     "launches": prof["launches"]},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "global_iters/s", "h2d_bytes_per_step": e2e_bytes,
+                "d2h_bytes_per_step": e2e_bytes} if e2e_val else None,
+        "gpu_launches": res["launches"],
+        "clocks": res["clocks"],
+        "fp64": fp64,
+        "create_s": res["create_s"],
+        "stats": {k: res["stats"][k] for k in ("levels", "op_complexity", "device_bytes")},
+    }
+    print(json.dumps(line))
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from oracle.oracle import Oracle
+    from paper_2505_13390_gb300.meshgen import default_params, hex_block
+    mesh = hex_block(*SAMPLE, h=0.005, jitter=0.1, alpha=1e-10, pin="y0", seed=1)
+    p = default_params(omega_x=0.1, setup_interval=20)
+    o = Oracle(mesh, p)
+    nnz = int(o.matrix(0)[0][-1])
+    scale = FULL_NNZ / nnz
+    o.begin_frame()
+    k = 0
+
+    def step():
+        nonlocal k
+        o.iterate()
+        k += 1
+        if k % p["max_iter"] == 0:
+            o.end_frame()
+            o.begin_frame()
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = args.steps / (dt * scale)
+    sample = (f"FP64 C oracle (1 thread) on a {SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]}-cell block of "
+              f"the same recipe ({mesh.n_rows} rows, {nnz} nnz); time per global iteration "
+              f"scaled by the nnz ratio {scale:.1f} to 376.5M nnz")
+    line = {
+        "impl": "reference",
+        "metric": "global XPBD iters/s at 1.65M tets (mixed precision; FP64 under fp64)",
+        "value": value, "unit": "global_iters/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * scale * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload},
+        "cpu_baseline": {"value": value, "unit": "global_iters/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "global_iters/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * mgpbd.h -- C ABI of the GB300 (sm_103a) global XPBD solver of MGPBD
+ * (Li et al., "MGPBD: A Multigrid Accelerated Global XPBD Solver",
+ * SIGGRAPH 2025).
+ *
+ * One handle holds one simulation instance resident in device memory.  Every
+ * call is asynchronous on the CUDA stream given at create time unless its
+ * comment says that it synchronises.  All device pointers are plain CUDA
+ * global-memory addresses; host pointers are ordinary (pageable or pinned)
+ * memory.  No call retains a caller pointer after it returns.
+ *
+ * Errors: every call returns an mgpbd_status; a negative value is an error,
+ * a positive value a warning.  mgpbd_last_error() gives a thread-local text
+ * for the most recent error of the calling thread.  No call throws.
+ */
+#ifndef MGPBD_H
+#define MGPBD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque instance handle, owned by the library. */
+typedef struct mgpbd_handle mgpbd_handle_t;
+
+typedef int mgpbd_status;
+enum {
+  MGPBD_OK = 0,
+  MGPBD_W_NOT_CONVERGED = 1,  /* PCG stopped at pcg_maxiter above pcg_rtol */
+  MGPBD_E_INVALID = -1,       /* bad argument or mesh */
+  MGPBD_E_OOM = -2,           /* device allocation failed */
+  MGPBD_E_BREAKDOWN = -3,     /* PCG: p^T A p <= 0, r^T z <= 0, or NaN */
+  MGPBD_E_SINGULAR = -4,      /* coarsest Cholesky pivot <= 0 */
+  MGPBD_E_DEVICE_TIMEOUT = -5,/* a bounded device wait ran out */
+  MGPBD_E_CUDA = -6,          /* a CUDA runtime call failed */
+  MGPBD_E_BUDGET = -7,        /* device-memory budget exceeded */
+  MGPBD_E_SETUP = -8          /* AMG setup could not coarsen to a solvable size */
+};
+
+enum { MGPBD_MEM_HOST = 0, MGPBD_MEM_DEVICE = 1 };
+enum { MGPBD_SMOOTH_JACOBI = 0, MGPBD_SMOOTH_MCGS = 1 };
+enum { MGPBD_FP64 = 0, MGPBD_MIXED = 1 };
+
+/* Problem definition (eq. 1-3 of the paper).  Host pointers, copied at
+ * create.  Rows of the constraint system are all distance rows (in the order
+ * of `dist`) followed by all volume rows (in the order of `tet`).
+ *   rest_pos  [n_verts*3]  rest shape (AoS xyz), defines L0 and V0
+ *   inv_mass  [n_verts]    M^-1 per vertex; 0 pins the vertex
+ *   dist      [n_dist*2]   distance pairs, C = |x_a - x_b| - L0
+ *   tet       [n_tet*4]    tetrahedra, C = V(x) - V0 with V = det[x1-x0,x2-x0,x3-x0]/6
+ *   alpha     [n_dist+n_tet] compliance per row; alpha~ = alpha/dt^2 (eq. 2) */
+typedef struct {
+  int n_verts;
+  const double *rest_pos;
+  const double *inv_mass;
+  int n_dist;
+  const int32_t *dist;
+  int n_tet;
+  const int32_t *tet;
+  const double *alpha;
+} mgpbd_mesh_desc;
+
+/* Solver parameters.  mgpbd_default_params() fills the paper's defaults:
+ * theta_s = 0.1 (Sec. 4.1), 2 smoothing sweeps (Sec. 4.5), lambda_min
+ * estimate 0.1 (Sec. 4.5), coarsest below 400 rows (Fig. 2), omega_x 0.25. */
+typedef struct {
+  double dt;            /* time step */
+  double gravity[3];    /* f_ext / m */
+  double omega_x;       /* position relaxation of Alg. 1 */
+  int max_iter;         /* global iterations per frame (Alg. 1) */
+  double eps_b;         /* stop the frame when |b| < eps_b (0 disables) */
+  double pcg_rtol;      /* PCG stop: |r|/|b| <= pcg_rtol */
+  int pcg_maxiter;      /* PCG iteration cap */
+  int setup_interval;   /* lazy setup every k global iterations (Sec. 4.2) */
+  int nk_sweeps;        /* near-kernel Jacobi sweeps on A x = 0 (Sec. 4.3) */
+  double nk_omega;      /* their weight */
+  double theta_s;       /* strength threshold (Sec. 4.1) */
+  int smoother;         /* MGPBD_SMOOTH_JACOBI (MCGS: see mgpbd_create) */
+  int smooth_sweeps;    /* pre- and post-smoothing sweeps (Sec. 4.5) */
+  double lambda_min_est;/* lambda_min estimate in omega_opt (Sec. 4.5) */
+  int power_iters;      /* power-method iterations for lambda_max */
+  double power_safety;  /* factor on the lambda_max estimate */
+  int coarse_max;       /* stop coarsening below this many rows (Fig. 2) */
+  int max_levels;       /* hard cap on the number of levels */
+  int precision;        /* MGPBD_FP64 or MGPBD_MIXED */
+  uint64_t seed_nk, seed_agg, seed_col, seed_pow;
+} mgpbd_params;
+
+typedef struct {
+  int pcg_iters;
+  int status;           /* MGPBD_OK, MGPBD_W_NOT_CONVERGED or an error */
+  double bnorm;         /* |b|_2 of the solved system */
+  double rel_res;       /* recursive |r|/|b| at exit */
+  double true_rel_res;  /* |b - A dlambda| / |b| recomputed in FP64 */
+} mgpbd_solve_info;
+
+typedef struct {
+  int levels;           /* number of AMG levels (1 = direct solve) */
+  int n_setups;         /* setups run so far */
+  int64_t global_iters; /* global iterations run so far */
+  double op_complexity; /* sum nnz_l / nnz_0 (Table 1 column C) */
+  size_t device_bytes;  /* device memory held by the handle */
+  double ms_setup, ms_galerkin, ms_solve, ms_other; /* accumulated phase times */
+} mgpbd_stats_t;
+
+typedef struct {
+  int n;                /* rows */
+  int64_t nnz;
+  int n_agg;            /* aggregates (0 on the coarsest level) */
+  int n_colors;         /* colours of the multicolour ordering (0 if none) */
+  double lmax, omega;   /* power-method lambda_max(D^-1 A) and Jacobi weight */
+} mgpbd_level_info;
+
+/* Fills p with the defaults listed above.  Never fails for p != NULL. */
+mgpbd_status mgpbd_default_params(mgpbd_params *p);
+
+/* Creates an instance (Alg. 1 problem set-up; fixed CSR pattern, Sec. 4.2).
+ * Uploads the mesh, computes rest lengths/volumes, builds the vertex
+ * incidence, the diagonal-last CSR pattern of A and its assembly map on the
+ * device.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ * Positions start at rest_pos, velocities at 0.  Synchronises the stream.
+ * Errors: MGPBD_E_INVALID (index out of range, nnz >= 2^31, bad params),
+ * MGPBD_E_OOM, MGPBD_E_CUDA.  *out is NULL on error. */
+mgpbd_status mgpbd_create(const mgpbd_mesh_desc *mesh, const mgpbd_params *p, void *stream,
+                          mgpbd_handle_t **out);
+
+/* Frees everything the handle holds.  Synchronises its stream. NULL is a no-op. */
+void mgpbd_destroy(mgpbd_handle_t *h);
+
+/* Positions and velocities, AoS [n_verts*3] doubles, host or device memory
+ * per `mem`.  Either pointer may be NULL to leave that array unchanged.
+ * Host-memory transfers synchronise the stream. */
+mgpbd_status mgpbd_set_state(mgpbd_handle_t *h, const double *x, const double *v, int mem);
+mgpbd_status mgpbd_get_state(mgpbd_handle_t *h, double *x, double *v, int mem);
+
+/* Alg. 1 for n_frames frames: per frame semi-implicit Euler and lambda = 0,
+ * max_iter global iterations (C and grad C, assembly, b, lazy setup or
+ * Galerkin re-form, coarsest Cholesky, MGPCG, dx, lambda and x update,
+ * |b| < eps_b test), then the velocity update.  Synchronises at lazy-setup
+ * points and at PCG convergence polls.  Returns the worst PCG status seen
+ * (MGPBD_W_NOT_CONVERGED when any solve hit pcg_maxiter) or an error. */
+mgpbd_status mgpbd_step(mgpbd_handle_t *h, int n_frames);
+
+/* The pieces of mgpbd_step: the frame prologue (semi-Euler, lambda = 0),
+ * one global iteration (info may be NULL) and the frame epilogue (velocity). */
+mgpbd_status mgpbd_begin_frame(mgpbd_handle_t *h);
+mgpbd_status mgpbd_iterate(mgpbd_handle_t *h, mgpbd_solve_info *info);
+mgpbd_status mgpbd_end_frame(mgpbd_handle_t *h);
+
+/* Evaluates C, grad C, b = -C - alpha~ lambda and the values of A at the
+ * current positions (Alg. 1, eq. 3), without solving. */
+mgpbd_status mgpbd_eval_assemble(mgpbd_handle_t *h);
+
+/* Runs the full AMG setup (Sec. 4.1-4.3, Fig. 2) on the current A. */
+mgpbd_status mgpbd_setup(mgpbd_handle_t *h);
+
+/* Readies the current A for solving: setup if none exists, else the
+ * Galerkin re-form of every coarse operator (Sec. 4.4); then the coarsest
+ * Cholesky.  Synchronises. */
+mgpbd_status mgpbd_prepare_solve(mgpbd_handle_t *h);
+
+/* MGPCG (Sec. 4.4) on the current hierarchy: solves A dl = b from dl = 0.
+ * d_b, d_dl: device arrays of n_rows doubles (d_b is not modified).
+ * Synchronises; fills info if not NULL. */
+mgpbd_status mgpbd_solve(mgpbd_handle_t *h, const double *d_b, double *d_dl,
+                         mgpbd_solve_info *info);
+
+/* One V-cycle z = V(r) of the current hierarchy (the preconditioner of
+ * Sec. 4.4); device arrays of n_rows doubles. */
+mgpbd_status mgpbd_vcycle(mgpbd_handle_t *h, const double *d_r, double *d_z);
+
+/* Counters and phase times.  Synchronises. */
+mgpbd_status mgpbd_stats(mgpbd_handle_t *h, mgpbd_stats_t *s);
+
+/* ---- inspection (host or device destinations per `mem`; synchronise) ---- */
+mgpbd_status mgpbd_sizes(mgpbd_handle_t *h, int *n_verts, int *n_rows, int64_t *nnz);
+mgpbd_status mgpbd_level_info_get(mgpbd_handle_t *h, int level, mgpbd_level_info *info);
+/* CSR of level `level`: ptr [n+1] int64, col [nnz] int32, val [nnz] double
+ * (diagonal last in each row); any pointer may be NULL. */
+mgpbd_status mgpbd_get_matrix(mgpbd_handle_t *h, int level, int64_t *ptr, int32_t *col,
+                              double *val, int mem);
+/* assembly map of level 0: per nnz, bits 0-1 the number of shared vertices,
+ * pair p at bits 2+4p (slot in row i) and 4+4p (slot in row j) */
+mgpbd_status mgpbd_get_map(mgpbd_handle_t *h, uint16_t *map, int mem);
+/* vertex -> incident rows, ascending: vptr [n_verts+1], vrow [2*n_dist+4*n_tet] */
+mgpbd_status mgpbd_get_incidence(mgpbd_handle_t *h, int64_t *vptr, int32_t *vrow, int mem);
+/* aggregates, MIS-2 roots, P values and near-kernel B of level `level` */
+mgpbd_status mgpbd_get_aggregates(mgpbd_handle_t *h, int level, int32_t *agg, uint8_t *root,
+                                  double *P, double *B, int mem);
+mgpbd_status mgpbd_get_colors(mgpbd_handle_t *h, int level, int32_t *color, int mem);
+/* C [m], b [m], distance gradients n [n_dist*3], tet gradients [n_tet*12] */
+mgpbd_status mgpbd_get_constraints(mgpbd_handle_t *h, double *C, double *b, double *gd,
+                                   double *gt, int mem);
+mgpbd_status mgpbd_get_lambda(mgpbd_handle_t *h, double *lambda, double *dlambda, int mem);
+
+/* ---- measurement ----
+ * mgpbd_profile(h, 1) starts recording a CUDA event pair around every launch
+ * of the level-0 smoother sweep (the dominant kernel of the V-cycle, Sec. 5.2
+ * of the paper: the V-cycle takes most of an iteration and the smoother most
+ * of the V-cycle); mgpbd_profile(h, 0) stops.  Both reset the totals and
+ * synchronise.  mgpbd_profile_read returns the summed kernel time, the number
+ * of timed launches (launches skipped after PCG convergence are excluded)
+ * and the algorithmic bytes of one launch (CSR values and columns once, row
+ * pointers, and four row vectors).  mgpbd_launch_count is the number of
+ * kernels this library has launched in the process so far. */
+mgpbd_status mgpbd_profile(mgpbd_handle_t *h, int enable);
+mgpbd_status mgpbd_profile_read(mgpbd_handle_t *h, double *total_ms, int64_t *launches,
+                                double *bytes_per_launch);
+unsigned long long mgpbd_launch_count(void);
+
+/* Thread-local text of the calling thread's last error ("" if none). */
+const char *mgpbd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,626 @@
+// C ABI of the GB300 MGPBD library: handle lifecycle, state I/O, the
+// Algorithm 1 driver (frame prologue, global iterations, epilogue) and the
+// inspection getters.  Compute happens in the kernels of pattern.cu,
+// physics.cu, setup.cu and solve.cu.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "common.cuh"
+
+namespace mg {
+
+static thread_local std::string g_err;
+unsigned long long g_launches = 0;
+
+mgpbd_status prof_begin(Handle *h) {
+  if (!h->prof) return MGPBD_OK;
+  if (h->pev_used + 1 > (int)h->pev.size() / 2) {
+    size_t old = h->pev.size();
+    size_t want = std::max<size_t>(2048, 2 * old);
+    h->pev.resize(want);
+    h->pev_iter.resize(want / 2);
+    for (size_t k = old; k < want; ++k) MG_CUDA(cudaEventCreate(&h->pev[k]));
+  }
+  MG_CUDA(cudaEventRecord(h->pev[2 * h->pev_used], h->stream));
+  return MGPBD_OK;
+}
+
+mgpbd_status prof_end(Handle *h) {
+  if (!h->prof) return MGPBD_OK;
+  MG_CUDA(cudaEventRecord(h->pev[2 * h->pev_used + 1], h->stream));
+  h->pev_iter[h->pev_used] = h->pcg_k;
+  h->pev_used++;
+  return MGPBD_OK;
+}
+
+mgpbd_status prof_harvest(Handle *h, int iters) {
+  if (!h->prof) return MGPBD_OK;
+  for (int k = 0; k < h->pev_used; ++k) {
+    // the V-cycle of PCG iteration k ran only if the solve had not finished
+    if (h->pev_iter[k] > iters - 2) continue;
+    float ms = 0.f;
+    MG_CUDA(cudaEventSynchronize(h->pev[2 * k + 1]));
+    MG_CUDA(cudaEventElapsedTime(&ms, h->pev[2 * k], h->pev[2 * k + 1]));
+    h->prof_ms += ms;
+    h->prof_n++;
+  }
+  h->pev_used = 0;
+  return MGPBD_OK;
+}
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+mgpbd_status cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  set_error(buf);
+  return e == cudaErrorMemoryAllocation ? MGPBD_E_OOM : MGPBD_E_CUDA;
+}
+
+mgpbd_status Arena::alloc(void **p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 16;
+  cudaError_t e = cudaMalloc(p, n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    char buf[128];
+    snprintf(buf, sizeof(buf), "cudaMalloc of %zu bytes failed: %s", n, cudaGetErrorString(e));
+    set_error(buf);
+    return MGPBD_E_OOM;
+  }
+  bytes += n;
+  live.push_back(*p);
+  return MGPBD_OK;
+}
+
+void Arena::release(void *p) {
+  if (!p) return;
+  auto it = std::find(live.begin(), live.end(), p);
+  if (it != live.end()) live.erase(it);
+  cudaFree(p);
+}
+
+void Arena::release_all() {
+  for (void *p : live) cudaFree(p);
+  live.clear();
+  bytes = 0;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+mgpbd_status ensure_tmp(Handle *h, size_t bytes) {
+  if (h->tmp_bytes >= bytes) return MGPBD_OK;
+  if (h->tmp) {
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    h->arena.release(h->tmp);
+    h->tmp = nullptr;
+    h->tmp_bytes = 0;
+  }
+  size_t want = std::max(bytes, (size_t)1 << 20);
+  MG_TRY(h->arena.alloc(&h->tmp, want));
+  h->tmp_bytes = want;
+  return MGPBD_OK;
+}
+
+mgpbd_status read_i64(Handle *h, const int64_t *d, int64_t *out) {
+  MG_CUDA(cudaMemcpyAsync(out, d, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  return MGPBD_OK;
+}
+
+static mgpbd_status copy_out(Handle *h, void *dst, const void *src, size_t bytes, int mem) {
+  if (!dst || bytes == 0) return MGPBD_OK;
+  if (!src) {
+    set_error("requested array is not available (no setup yet?)");
+    return MGPBD_E_INVALID;
+  }
+  MG_CUDA(cudaMemcpyAsync(dst, src, bytes,
+                          mem == MGPBD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                          h->stream));
+  if (mem == MGPBD_MEM_HOST) MG_CUDA(cudaStreamSynchronize(h->stream));
+  return MGPBD_OK;
+}
+
+static mgpbd_status check_params(const mgpbd_params *p) {
+  if (!(p->dt > 0.0) || p->max_iter < 0 || p->pcg_maxiter < 1 || p->nk_sweeps < 0 ||
+      p->smooth_sweeps < 1 || p->power_iters < 1 || p->coarse_max < 1 || p->max_levels < 1 ||
+      p->max_levels > kMaxLevels || (p->precision != MGPBD_FP64 && p->precision != MGPBD_MIXED) ||
+      (p->smoother != MGPBD_SMOOTH_JACOBI) || !(p->theta_s >= 0.0) ||
+      !(p->pcg_rtol >= 0.0) || !(p->power_safety > 0.0)) {
+    set_error("invalid mgpbd_params (or unsupported smoother on this build)");
+    return MGPBD_E_INVALID;
+  }
+  return MGPBD_OK;
+}
+
+static void destroy(Handle *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  h->arena.release_all();
+  if (h->sc_host) cudaFreeHost(h->sc_host);
+  if (h->flag_host) cudaFreeHost(h->flag_host);
+  for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete h;
+}
+
+static mgpbd_status create(const mgpbd_mesh_desc *md, const mgpbd_params *p, void *stream,
+                           Handle **out) {
+  *out = nullptr;
+  if (!md || !p || md->n_verts <= 0 || md->n_dist < 0 || md->n_tet < 0 || !md->rest_pos ||
+      !md->inv_mass || (md->n_dist > 0 && !md->dist) || (md->n_tet > 0 && !md->tet) ||
+      (md->n_dist + md->n_tet > 0 && !md->alpha)) {
+    set_error("invalid mesh descriptor");
+    return MGPBD_E_INVALID;
+  }
+  if ((int64_t)md->n_dist + md->n_tet >= (int64_t)1 << 31) {
+    set_error("too many constraint rows");
+    return MGPBD_E_INVALID;
+  }
+  MG_TRY(check_params(p));
+  // host-side validation of indices (rows must reference distinct vertices)
+  for (int64_t j = 0; j < md->n_dist; ++j) {
+    int a = md->dist[2 * j], b = md->dist[2 * j + 1];
+    if (a < 0 || a >= md->n_verts || b < 0 || b >= md->n_verts || a == b) {
+      set_error("distance pair out of range or degenerate");
+      return MGPBD_E_INVALID;
+    }
+  }
+  for (int64_t t = 0; t < md->n_tet; ++t) {
+    const int32_t *q = md->tet + 4 * t;
+    for (int k = 0; k < 4; ++k) {
+      if (q[k] < 0 || q[k] >= md->n_verts) {
+        set_error("tet vertex out of range");
+        return MGPBD_E_INVALID;
+      }
+      for (int k2 = 0; k2 < k; ++k2)
+        if (q[k] == q[k2]) {
+          set_error("degenerate tet (repeated vertex)");
+          return MGPBD_E_INVALID;
+        }
+    }
+  }
+  for (int64_t v = 0; v < md->n_verts; ++v)
+    if (!(md->inv_mass[v] >= 0.0)) {
+      set_error("inverse mass must be >= 0");
+      return MGPBD_E_INVALID;
+    }
+
+  Handle *h = new Handle();
+  h->stream = (cudaStream_t)stream;
+  h->p = *p;
+  h->N = md->n_verts;
+  h->E = md->n_dist;
+  h->T = md->n_tet;
+  h->m = h->E + h->T;
+  auto fail = [&](mgpbd_status s) {
+    destroy(h);
+    return s;
+  };
+  mgpbd_status s;
+#define CK(expr)             \
+  do {                       \
+    s = (expr);              \
+    if (s < 0) return fail(s); \
+  } while (0)
+  const int N = h->N, E = h->E, T = h->T, m = h->m;
+  CK(alloc_n(h->arena, &h->rest, 3 * (size_t)N));
+  CK(alloc_n(h->arena, &h->w, (size_t)N));
+  CK(alloc_n(h->arena, &h->alpha_t, (size_t)m));
+  CK(alloc_n(h->arena, &h->L0, (size_t)E));
+  CK(alloc_n(h->arena, &h->V0, (size_t)T));
+  CK(alloc_n(h->arena, &h->edge, 2 * (size_t)E));
+  CK(alloc_n(h->arena, &h->tet, 4 * (size_t)T));
+  CK(alloc_n(h->arena, &h->x, 3 * (size_t)N));
+  CK(alloc_n(h->arena, &h->v, 3 * (size_t)N));
+  CK(alloc_n(h->arena, &h->xold, 3 * (size_t)N));
+  CK(alloc_n(h->arena, &h->lambda, (size_t)m));
+  CK(alloc_n(h->arena, &h->C, (size_t)m));
+  CK(alloc_n(h->arena, &h->b, (size_t)m));
+  CK(alloc_n(h->arena, &h->dl, (size_t)m));
+  CK(alloc_n(h->arena, &h->gd, 3 * (size_t)E));
+  CK(alloc_n(h->arena, &h->gt, 12 * (size_t)T));
+  CK(alloc_n(h->arena, &h->pr, (size_t)m));
+  CK(alloc_n(h->arena, &h->pz, (size_t)m));
+  CK(alloc_n(h->arena, &h->pp, (size_t)m));
+  CK(alloc_n(h->arena, &h->pq, (size_t)m));
+  CK(alloc_n(h->arena, &h->sc, 1));
+  CK(alloc_n(h->arena, &h->partials, 4096 + 16));
+  CK(alloc_n(h->arena, &h->counter, 16));
+  CK(alloc_n(h->arena, &h->flag, 16));
+  CK(alloc_n(h->arena, &h->cstat, 4));
+  if (cudaMallocHost((void **)&h->sc_host, sizeof(PcgScalars)) != cudaSuccess ||
+      cudaMallocHost((void **)&h->flag_host, 16 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("pinned host allocation failed");
+    return fail(MGPBD_E_OOM);
+  }
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+    set_error("cudaEventCreate failed");
+    return fail(MGPBD_E_CUDA);
+  }
+  cudaStream_t st = h->stream;
+  auto up = [&](void *d, const void *src, size_t bytes) -> mgpbd_status {
+    if (!bytes) return MGPBD_OK;
+    MG_CUDA(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, st));
+    return MGPBD_OK;
+  };
+  CK(up(h->rest, md->rest_pos, sizeof(double) * 3 * N));
+  CK(up(h->x, md->rest_pos, sizeof(double) * 3 * N));
+  CK(up(h->w, md->inv_mass, sizeof(double) * N));
+  CK(up(h->edge, md->dist, sizeof(int32_t) * 2 * E));
+  CK(up(h->tet, md->tet, sizeof(int32_t) * 4 * T));
+  {
+    // alpha~ = alpha / dt^2 (eq. 2), computed on the host in IEEE double
+    std::vector<double> at((size_t)m);
+    double dt2 = p->dt * p->dt;
+    for (int j = 0; j < m; ++j) at[j] = md->alpha[j] / dt2;
+    CK(up(h->alpha_t, at.data(), sizeof(double) * m));
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(MGPBD_E_CUDA);
+  }
+  if (cudaMemsetAsync(h->v, 0, sizeof(double) * 3 * N, st) != cudaSuccess ||
+      cudaMemsetAsync(h->lambda, 0, sizeof(double) * m, st) != cudaSuccess ||
+      cudaMemsetAsync(h->counter, 0, 16 * sizeof(unsigned), st) != cudaSuccess)
+    return fail(MGPBD_E_CUDA);
+  CK(rest_shape(h));
+  CK(build_incidence(h));
+  CK(build_pattern(h));
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error("create: stream error");
+    return fail(MGPBD_E_CUDA);
+  }
+#undef CK
+  *out = h;
+  return MGPBD_OK;
+}
+
+static mgpbd_status timed_begin(Handle *h) {
+  MG_CUDA(cudaEventRecord(h->ev0, h->stream));
+  return MGPBD_OK;
+}
+static mgpbd_status timed_end(Handle *h, double *acc) {
+  MG_CUDA(cudaEventRecord(h->ev1, h->stream));
+  MG_CUDA(cudaEventSynchronize(h->ev1));
+  float ms = 0.f;
+  MG_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  *acc += ms;
+  return MGPBD_OK;
+}
+
+// One global iteration of Alg. 1.
+static mgpbd_status iterate(Handle *h, mgpbd_solve_info *info) {
+  MG_TRY(launch_eval(h));
+  MG_TRY(launch_assemble(h));
+  bool due = !h->have_setup ||
+             (h->p.setup_interval > 0 && h->it_global % h->p.setup_interval == 0);
+  if (due) {
+    MG_TRY(timed_begin(h));
+    MG_TRY(amg_setup(h));
+    MG_TRY(timed_end(h, &h->ms_setup));
+  } else {
+    MG_TRY(galerkin_reform(h));
+  }
+  MG_TRY(coarsest_factor(h));
+  mgpbd_solve_info inf{};
+  mgpbd_status st = pcg_solve(h, h->b, h->dl, &inf);
+  h->last = inf;
+  h->it_global++;
+  if (info) *info = inf;
+  if (st < 0) return st;
+  MG_TRY(launch_update(h));
+  return inf.status;
+}
+
+}  // namespace mg
+
+using namespace mg;
+
+struct mgpbd_handle : public Handle {};
+
+static inline Handle *H(mgpbd_handle_t *h) { return reinterpret_cast<Handle *>(h); }
+
+extern "C" {
+
+const char *mgpbd_last_error(void) { return g_err.c_str(); }
+
+mgpbd_status mgpbd_default_params(mgpbd_params *p) {
+  if (!p) return MGPBD_E_INVALID;
+  memset(p, 0, sizeof(*p));
+  p->dt = 1.0 / 60.0;
+  p->gravity[0] = 0.0;
+  p->gravity[1] = -9.8;
+  p->gravity[2] = 0.0;
+  p->omega_x = 0.25;
+  p->max_iter = 20;
+  p->eps_b = 0.0;
+  p->pcg_rtol = 1e-6;
+  p->pcg_maxiter = 200;
+  p->setup_interval = 400;
+  p->nk_sweeps = 3;
+  p->nk_omega = 2.0 / 3.0;
+  p->theta_s = 0.1;
+  p->smoother = MGPBD_SMOOTH_JACOBI;
+  p->smooth_sweeps = 2;
+  p->lambda_min_est = 0.1;
+  p->power_iters = 15;
+  p->power_safety = 1.25;
+  p->coarse_max = 400;
+  p->max_levels = 8;
+  p->precision = MGPBD_FP64;
+  p->seed_nk = 3;
+  p->seed_agg = 4;
+  p->seed_col = 5;
+  p->seed_pow = 7;
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_create(const mgpbd_mesh_desc *mesh, const mgpbd_params *p, void *stream,
+                          mgpbd_handle_t **out) {
+  if (!out) {
+    set_error("out is NULL");
+    return MGPBD_E_INVALID;
+  }
+  Handle *h = nullptr;
+  mgpbd_status s = create(mesh, p, stream, &h);
+  *out = reinterpret_cast<mgpbd_handle_t *>(h);
+  return s;
+}
+
+void mgpbd_destroy(mgpbd_handle_t *h) { destroy(H(h)); }
+
+mgpbd_status mgpbd_set_state(mgpbd_handle_t *hh, const double *x, const double *v, int mem) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  cudaMemcpyKind k = mem == MGPBD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  size_t bytes = sizeof(double) * 3 * (size_t)h->N;
+  if (x) MG_CUDA(cudaMemcpyAsync(h->x, x, bytes, k, h->stream));
+  if (v) MG_CUDA(cudaMemcpyAsync(h->v, v, bytes, k, h->stream));
+  if (mem == MGPBD_MEM_HOST) MG_CUDA(cudaStreamSynchronize(h->stream));
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_get_state(mgpbd_handle_t *hh, double *x, double *v, int mem) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  size_t bytes = sizeof(double) * 3 * (size_t)h->N;
+  MG_TRY(copy_out(h, x, h->x, bytes, mem));
+  MG_TRY(copy_out(h, v, h->v, bytes, mem));
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_begin_frame(mgpbd_handle_t *hh) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  return launch_begin_frame(h);
+}
+
+mgpbd_status mgpbd_end_frame(mgpbd_handle_t *hh) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  return launch_end_frame(h);
+}
+
+mgpbd_status mgpbd_iterate(mgpbd_handle_t *hh, mgpbd_solve_info *info) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  return iterate(h, info);
+}
+
+mgpbd_status mgpbd_step(mgpbd_handle_t *hh, int n_frames) {
+  Handle *h = H(hh);
+  if (!h || n_frames < 0) return MGPBD_E_INVALID;
+  mgpbd_status worst = MGPBD_OK;
+  for (int f = 0; f < n_frames; ++f) {
+    MG_TRY(launch_begin_frame(h));
+    for (int it = 0; it < h->p.max_iter; ++it) {
+      mgpbd_solve_info inf{};
+      mgpbd_status s = iterate(h, &inf);
+      if (s < 0) return s;
+      if (s > worst) worst = s;
+      if (inf.bnorm < h->p.eps_b) break;
+    }
+    MG_TRY(launch_end_frame(h));
+  }
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  return worst;
+}
+
+mgpbd_status mgpbd_eval_assemble(mgpbd_handle_t *hh) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  MG_TRY(launch_eval(h));
+  return launch_assemble(h);
+}
+
+mgpbd_status mgpbd_setup(mgpbd_handle_t *hh) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  return amg_setup(h);
+}
+
+mgpbd_status mgpbd_prepare_solve(mgpbd_handle_t *hh) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  if (!h->have_setup) MG_TRY(amg_setup(h));
+  else MG_TRY(galerkin_reform(h));
+  MG_TRY(coarsest_factor(h));
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_solve(mgpbd_handle_t *hh, const double *d_b, double *d_dl,
+                         mgpbd_solve_info *info) {
+  Handle *h = H(hh);
+  if (!h || !d_b || !d_dl) return MGPBD_E_INVALID;
+  if (!h->have_setup) {
+    set_error("mgpbd_solve: no hierarchy (call mgpbd_prepare_solve first)");
+    return MGPBD_E_INVALID;
+  }
+  mgpbd_solve_info inf{};
+  mgpbd_status s = pcg_solve(h, d_b, d_dl, &inf);
+  if (info) *info = inf;
+  return s;
+}
+
+mgpbd_status mgpbd_vcycle(mgpbd_handle_t *hh, const double *d_r, double *d_z) {
+  Handle *h = H(hh);
+  if (!h || !d_r || !d_z || !h->have_setup) return MGPBD_E_INVALID;
+  MG_TRY(vcycle_apply(h, d_r, d_z));
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_stats(mgpbd_handle_t *hh, mgpbd_stats_t *s) {
+  Handle *h = H(hh);
+  if (!h || !s) return MGPBD_E_INVALID;
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  memset(s, 0, sizeof(*s));
+  s->levels = h->L;
+  s->n_setups = h->n_setups;
+  s->global_iters = h->it_global;
+  double tot = 0;
+  for (int l = 0; l < h->L; ++l) tot += (double)h->lev[l].nnz;
+  s->op_complexity = h->L && h->lev[0].nnz ? tot / (double)h->lev[0].nnz : 0.0;
+  s->device_bytes = h->arena.bytes;
+  s->ms_setup = h->ms_setup;
+  s->ms_galerkin = h->ms_galerkin;
+  s->ms_solve = h->ms_solve;
+  s->ms_other = h->ms_other;
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_profile(mgpbd_handle_t *hh, int enable) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  h->prof = enable != 0;
+  h->pev_used = 0;
+  h->prof_ms = 0.0;
+  h->prof_n = 0;
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_profile_read(mgpbd_handle_t *hh, double *total_ms, int64_t *launches,
+                                double *bytes_per_launch) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  if (total_ms) *total_ms = h->prof_ms;
+  if (launches) *launches = h->prof_n;
+  if (bytes_per_launch) {
+    // algorithmic bytes of one level-0 smoother sweep: the CSR values and
+    // column indices once, row pointers, and four vectors (x, b, 1/A_ii, x_new)
+    const Level &L = h->lev[0];
+    double vb = h->p.precision == MGPBD_MIXED ? 4.0 : 8.0;
+    *bytes_per_launch = (double)L.nnz * (vb + 4.0) + (double)L.n * (8.0 + 4.0 * vb);
+  }
+  return MGPBD_OK;
+}
+
+unsigned long long mgpbd_launch_count(void) { return g_launches; }
+
+mgpbd_status mgpbd_sizes(mgpbd_handle_t *hh, int *n_verts, int *n_rows, int64_t *nnz) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  if (n_verts) *n_verts = h->N;
+  if (n_rows) *n_rows = h->m;
+  if (nnz) *nnz = h->lev[0].nnz;
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_level_info_get(mgpbd_handle_t *hh, int level, mgpbd_level_info *info) {
+  Handle *h = H(hh);
+  if (!h || !info || level < 0 || level >= std::max(h->L, 1)) return MGPBD_E_INVALID;
+  const Level &L = h->lev[level];
+  info->n = L.n;
+  info->nnz = L.nnz;
+  info->n_agg = level + 1 < h->L ? L.n_agg : 0;
+  info->n_colors = L.n_colors;
+  info->lmax = L.lmax;
+  info->omega = L.omega;
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_get_matrix(mgpbd_handle_t *hh, int level, int64_t *ptr, int32_t *col,
+                              double *val, int mem) {
+  Handle *h = H(hh);
+  if (!h || level < 0 || level >= std::max(h->L, 1)) return MGPBD_E_INVALID;
+  const Level &L = h->lev[level];
+  MG_TRY(copy_out(h, ptr, L.ptr, sizeof(int64_t) * ((size_t)L.n + 1), mem));
+  MG_TRY(copy_out(h, col, L.col, sizeof(int32_t) * (size_t)L.nnz, mem));
+  MG_TRY(copy_out(h, val, L.val, sizeof(double) * (size_t)L.nnz, mem));
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_get_map(mgpbd_handle_t *hh, uint16_t *map, int mem) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  return copy_out(h, map, h->map, sizeof(uint16_t) * (size_t)h->lev[0].nnz, mem);
+}
+
+mgpbd_status mgpbd_get_incidence(mgpbd_handle_t *hh, int64_t *vptr, int32_t *vrow, int mem) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  MG_TRY(copy_out(h, vptr, h->vptr, sizeof(int64_t) * ((size_t)h->N + 1), mem));
+  MG_TRY(copy_out(h, vrow, h->vrow, sizeof(int32_t) * (2 * (size_t)h->E + 4 * (size_t)h->T), mem));
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_get_aggregates(mgpbd_handle_t *hh, int level, int32_t *agg, uint8_t *root,
+                                  double *P, double *B, int mem) {
+  Handle *h = H(hh);
+  if (!h || !h->have_setup || level < 0 || level >= h->L) return MGPBD_E_INVALID;
+  const Level &L = h->lev[level];
+  size_t n = (size_t)L.n;
+  if (level + 1 < h->L) {
+    MG_TRY(copy_out(h, agg, L.agg, sizeof(int32_t) * n, mem));
+    MG_TRY(copy_out(h, root, L.root, n, mem));
+    MG_TRY(copy_out(h, P, L.P, sizeof(double) * n, mem));
+  }
+  if (L.B) MG_TRY(copy_out(h, B, L.B, sizeof(double) * n, mem));
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_get_colors(mgpbd_handle_t *hh, int level, int32_t *color, int mem) {
+  Handle *h = H(hh);
+  if (!h || !h->have_setup || level < 0 || level >= h->L) return MGPBD_E_INVALID;
+  const Level &L = h->lev[level];
+  if (!L.color) return MGPBD_E_INVALID;
+  return copy_out(h, color, L.color, sizeof(int32_t) * (size_t)L.n, mem);
+}
+
+mgpbd_status mgpbd_get_constraints(mgpbd_handle_t *hh, double *C, double *b, double *gd,
+                                   double *gt, int mem) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  MG_TRY(copy_out(h, C, h->C, sizeof(double) * (size_t)h->m, mem));
+  MG_TRY(copy_out(h, b, h->b, sizeof(double) * (size_t)h->m, mem));
+  MG_TRY(copy_out(h, gd, h->gd, sizeof(double) * 3 * (size_t)h->E, mem));
+  MG_TRY(copy_out(h, gt, h->gt, sizeof(double) * 12 * (size_t)h->T, mem));
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_get_lambda(mgpbd_handle_t *hh, double *lambda, double *dlambda, int mem) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  MG_TRY(copy_out(h, lambda, h->lambda, sizeof(double) * (size_t)h->m, mem));
+  MG_TRY(copy_out(h, dlambda, h->dl, sizeof(double) * (size_t)h->m, mem));
+  return MGPBD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,239 @@
+// Internal declarations of the GB300 MGPBD library (not part of the ABI).
+//
+// Compiled with --fmad=false: a*b+c is never contracted, and every fused
+// multiply-add is an explicit fma()/fmaf().  Constraint evaluation, assembly,
+// near-kernel sweeps, strength, aggregation, injection and the canonical
+// Galerkin product therefore reproduce a plain IEEE-754 FP64 program exactly.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mgpbd.h"
+
+namespace mg {
+
+constexpr int kMaxLevels = 16;
+constexpr int kWarp = 32;
+
+// ---------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+mgpbd_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define MG_CUDA(call)                                                     \
+  do {                                                                    \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess) return mg::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+// every kernel launch is followed by MG_LAUNCH, which also counts it
+extern unsigned long long g_launches;
+#define MG_LAUNCH(what)                                                   \
+  do {                                                                    \
+    ++mg::g_launches;                                                     \
+    cudaError_t e_ = cudaGetLastError();                                  \
+    if (e_ != cudaSuccess) return mg::cuda_fail(e_, what, __FILE__, __LINE__); \
+  } while (0)
+#define MG_TRY(expr)                                                      \
+  do {                                                                    \
+    mgpbd_status s_ = (expr);                                             \
+    if (s_ < 0) return s_;                                                \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device memory owned by a handle
+// ---------------------------------------------------------------------------
+struct Arena {
+  size_t bytes = 0;
+  std::vector<void *> live;
+  mgpbd_status alloc(void **p, size_t n);
+  void release(void *p);
+  void release_all();
+};
+
+template <class T>
+inline mgpbd_status alloc_n(Arena &a, T **p, size_t n) {
+  return a.alloc(reinterpret_cast<void **>(p), n * sizeof(T));
+}
+
+// ---------------------------------------------------------------------------
+// PCG scalars that live on the device (no host round trip per iteration)
+// ---------------------------------------------------------------------------
+struct PcgScalars {
+  double bnorm2;   // |b|^2
+  double rz;       // r.z of the current iteration
+  double rz_new;
+  double pq;       // p.q
+  double rr;       // r.r
+  double alpha, beta;
+  double tr2;      // |b - A x|^2 (true residual)
+  int done;        // 1 once converged or failed
+  int iters;       // PCG iterations taken
+  int status;      // MGPBD_OK / MGPBD_W_NOT_CONVERGED / MGPBD_E_BREAKDOWN
+  int pad;
+};
+
+// ---------------------------------------------------------------------------
+// one AMG level
+// ---------------------------------------------------------------------------
+struct Level {
+  int n = 0;
+  int64_t nnz = 0;
+  int64_t *ptr = nullptr;
+  int32_t *col = nullptr;
+  double *val = nullptr;   // FP64 values (canonical)
+  float *val32 = nullptr;  // FP32 mirror (mixed precision)
+  double *dinv = nullptr;  // 1/A_ii
+  float *dinv32 = nullptr;
+  // capacity of the coarse-level buffers (levels >= 1)
+  int cap_n = 0;
+  int64_t cap_nnz = 0;
+  // prolongation to level+1 (absent on the coarsest)
+  int n_agg = 0;
+  int32_t *agg = nullptr;
+  uint8_t *root = nullptr;
+  double *P = nullptr;
+  float *P32 = nullptr;
+  double *B = nullptr;       // near-kernel of this level
+  int64_t *mptr = nullptr;   // members of each aggregate (ascending rows)
+  int32_t *mrow = nullptr;
+  int max_members = 0;
+  int max_coarse_row = 0;    // longest row of level+1 (Galerkin smem size)
+  int32_t *color = nullptr;
+  int n_colors = 0;
+  double lmax = 0.0, omega = 0.0;
+  // V-cycle vectors in the working precision (double or float)
+  void *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr;
+};
+
+struct Handle {
+  cudaStream_t stream = nullptr;
+  mgpbd_params p{};
+  int N = 0, E = 0, T = 0, m = 0;
+  Arena arena;
+  // mesh (device)
+  double *rest = nullptr, *w = nullptr, *alpha_t = nullptr, *L0 = nullptr, *V0 = nullptr;
+  int32_t *edge = nullptr, *tet = nullptr;
+  // incidence
+  int64_t *vptr = nullptr;
+  int32_t *vrow = nullptr;
+  // state
+  double *x = nullptr, *v = nullptr, *xold = nullptr, *lambda = nullptr;
+  // per-iteration
+  double *C = nullptr, *b = nullptr, *gd = nullptr, *gt = nullptr, *dl = nullptr;
+  uint16_t *map = nullptr;
+  uint8_t *S = nullptr;  // strength mask, sized for level 0 and reused per level
+  // hierarchy
+  int L = 0;
+  bool have_setup = false;
+  Level lev[kMaxLevels];
+  // coarsest dense factor and inverse (FP64)
+  int nc = 0, cap_nc = 0;
+  double *cdense = nullptr;  // n_c x n_c: A, then L (lower)
+  double *cinv = nullptr;    // n_c x n_c: A^-1
+  int *cstat = nullptr;      // Cholesky status (device)
+  // PCG
+  double *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr;
+  PcgScalars *sc = nullptr;
+  PcgScalars *sc_host = nullptr;  // pinned mirror for polls
+  double *partials = nullptr;     // dot-product block partials
+  unsigned int *counter = nullptr;
+  // scratch for setup
+  void *tmp = nullptr;
+  size_t tmp_bytes = 0;
+  int *flag = nullptr;       // device int scratch (round counters)
+  int *flag_host = nullptr;  // pinned
+  // counters
+  int64_t it_global = 0;
+  int n_setups = 0;
+  double ms_setup = 0, ms_galerkin = 0, ms_solve = 0, ms_other = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int last_pcg_iters = 0;
+  mgpbd_solve_info last{};
+  // optional event timing of the level-0 smoother sweeps (the dominant kernel)
+  bool prof = false;
+  std::vector<cudaEvent_t> pev;  // pairs
+  std::vector<int> pev_iter;     // PCG iteration of each pair (-1 = initial V-cycle)
+  int pev_used = 0;
+  int pcg_k = -1;                // PCG iteration being launched
+  double prof_ms = 0.0;
+  long long prof_n = 0;
+};
+
+// event pair around one launch of the profiled kernel (no-op when disabled)
+mgpbd_status prof_begin(Handle *h);
+mgpbd_status prof_end(Handle *h);
+// sums the pairs recorded during the last solve that belong to iterations that ran
+mgpbd_status prof_harvest(Handle *h, int iters);
+
+// grid sizing
+int num_sms();
+inline int blocks_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  return (int)(b < 1 ? 1 : (b > 1048576 ? 1048576 : b));
+}
+
+// device scratch of at least `bytes`
+mgpbd_status ensure_tmp(Handle *h, size_t bytes);
+
+// ---------------------------------------------------------------------------
+// building blocks (definitions in the .cu files)
+// ---------------------------------------------------------------------------
+// exclusive scan of n int64 counts in place into out[0..n] (out[n] = total)
+mgpbd_status scan_counts(Handle *h, const int64_t *counts, int64_t *out, int64_t n);
+// read one int64 from device memory (synchronises)
+mgpbd_status read_i64(Handle *h, const int64_t *d, int64_t *out);
+
+// pattern.cu
+mgpbd_status build_incidence(Handle *h);
+mgpbd_status build_pattern(Handle *h);
+
+// physics.cu
+mgpbd_status rest_shape(Handle *h);
+mgpbd_status launch_begin_frame(Handle *h);
+mgpbd_status launch_end_frame(Handle *h);
+mgpbd_status launch_eval(Handle *h);
+mgpbd_status launch_assemble(Handle *h);
+mgpbd_status launch_update(Handle *h);
+
+// setup.cu
+mgpbd_status amg_setup(Handle *h);
+mgpbd_status galerkin_reform(Handle *h);
+mgpbd_status level_precision_copies(Handle *h, int l);
+
+// solve.cu
+mgpbd_status coarsest_factor(Handle *h);
+mgpbd_status pcg_solve(Handle *h, const double *d_b, double *d_x, mgpbd_solve_info *info);
+mgpbd_status vcycle_apply(Handle *h, const double *d_r, double *d_z);
+mgpbd_status dot_dd(Handle *h, const double *x, const double *y, int64_t n, double *d_out);
+mgpbd_status power_method(Handle *h, int l);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+// SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014)
+__host__ __device__ __forceinline__ uint64_t h64(uint64_t k) {
+  uint64_t z = k + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t hkey(uint64_t seed, int l, int i) {
+  return (seed << 40) | ((uint64_t)(uint32_t)l << 32) | (uint64_t)(uint32_t)i;
+}
+__host__ __device__ __forceinline__ double u01(uint64_t hv) {
+  return ((double)(hv >> 11) + 0.5) * 0x1p-53;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace mg

@@ -1,0 +1,336 @@
+// Per-vertex and per-constraint kernels of Algorithm 1: rest shape,
+// semi-implicit Euler prologue, constraint values and gradients, the values
+// of A on the fixed pattern, and the dx / lambda / x update (eq. 5).
+//
+// Arithmetic is spelled out operation by operation (the library is built
+// without FMA contraction), so that these kernels give the IEEE-754 result
+// of the formulas as written:
+//   distance  C = |d| - L0, |d| = sqrt(fma(dz,dz, fma(dy,dy, dx*dx))),
+//             n = d/|d| (n = 0 if |d| = 0), gradients n and -n
+//   volume    e_k = x_k - x_0, V = fma(e1z,c23z, fma(e1y,c23y, e1x*c23x))/6,
+//             g1 = (e2 x e3)/6, g2 = (e3 x e1)/6, g3 = (e1 x e2)/6,
+//             g0 = -((g1 + g2) + g3)
+//   A_ij      sum over shared vertices (ascending id) acc = fma(w_v, g_i.g_j, acc),
+//             g_i.g_j = fma(gz_i,gz_j, fma(gy_i,gy_j, gx_i*gx_j)); A_ii + alpha~ last
+#include "common.cuh"
+
+namespace mg {
+
+__device__ __forceinline__ double dist_eval(const double *xa, const double *xb, double L0,
+                                            double n[3]) {
+  double d0 = xa[0] - xb[0], d1 = xa[1] - xb[1], d2 = xa[2] - xb[2];
+  double len = sqrt(fma(d2, d2, fma(d1, d1, d0 * d0)));
+  if (len > 0.0) {
+    n[0] = d0 / len;
+    n[1] = d1 / len;
+    n[2] = d2 / len;
+  } else {
+    n[0] = n[1] = n[2] = 0.0;
+  }
+  return len - L0;
+}
+
+__device__ __forceinline__ void cross3(const double *a, const double *b, double *c) {
+  double t1, t2;
+  t1 = a[1] * b[2]; t2 = a[2] * b[1]; c[0] = t1 - t2;
+  t1 = a[2] * b[0]; t2 = a[0] * b[2]; c[1] = t1 - t2;
+  t1 = a[0] * b[1]; t2 = a[1] * b[0]; c[2] = t1 - t2;
+}
+
+__device__ __forceinline__ double tet_eval(const double *x0, const double *x1, const double *x2,
+                                           const double *x3, double V0, double g[12]) {
+  double e1[3], e2[3], e3[3], c23[3], c31[3], c12[3];
+  for (int k = 0; k < 3; ++k) {
+    e1[k] = x1[k] - x0[k];
+    e2[k] = x2[k] - x0[k];
+    e3[k] = x3[k] - x0[k];
+  }
+  cross3(e2, e3, c23);
+  cross3(e3, e1, c31);
+  cross3(e1, e2, c12);
+  for (int k = 0; k < 3; ++k) {
+    g[3 + k] = c23[k] / 6.0;
+    g[6 + k] = c31[k] / 6.0;
+    g[9 + k] = c12[k] / 6.0;
+    g[k] = -((g[3 + k] + g[6 + k]) + g[9 + k]);
+  }
+  double V = fma(e1[2], c23[2], fma(e1[1], c23[1], e1[0] * c23[0])) / 6.0;
+  return V - V0;
+}
+
+__device__ __forceinline__ void load3(const double *p, double *o) {
+  o[0] = p[0];
+  o[1] = p[1];
+  o[2] = p[2];
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_rest(int E, int T, const int32_t *edge, const int32_t *tet, const double *X,
+                       double *L0, double *V0) {
+  int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = tid; j < (int64_t)E + T; j += stride) {
+    if (j < E) {
+      double a[3], b[3], n[3];
+      load3(X + 3 * (int64_t)edge[2 * j], a);
+      load3(X + 3 * (int64_t)edge[2 * j + 1], b);
+      L0[j] = dist_eval(a, b, 0.0, n);
+    } else {
+      int64_t t = j - E;
+      const int32_t *q = tet + 4 * t;
+      double p0[3], p1[3], p2[3], p3[3], g[12];
+      load3(X + 3 * (int64_t)q[0], p0);
+      load3(X + 3 * (int64_t)q[1], p1);
+      load3(X + 3 * (int64_t)q[2], p2);
+      load3(X + 3 * (int64_t)q[3], p3);
+      V0[t] = tet_eval(p0, p1, p2, p3, 0.0, g);
+    }
+  }
+}
+
+mgpbd_status rest_shape(Handle *h) {
+  if (h->m == 0) return MGPBD_OK;
+  k_rest<<<blocks_for(h->m, 256), 256, 0, h->stream>>>(h->E, h->T, h->edge, h->tet, h->rest,
+                                                       h->L0, h->V0);
+  MG_LAUNCH("k_rest");
+  return MGPBD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 1 prologue: free vertices v += dt g, x_old = x, x += dt v;
+// pinned vertices (w = 0) keep x and get v = 0.  lambda = 0.
+__global__ void k_begin_frame(int N, double dt, double g0, double g1, double g2, const double *w,
+                              double *x, double *v, double *xold) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    double *xi = x + 3 * (int64_t)i, *vi = v + 3 * (int64_t)i, *oi = xold + 3 * (int64_t)i;
+    double gg[3] = {g0, g1, g2};
+    for (int k = 0; k < 3; ++k) oi[k] = xi[k];
+    if (w[i] == 0.0) {
+      vi[0] = vi[1] = vi[2] = 0.0;
+      continue;
+    }
+    for (int k = 0; k < 3; ++k) {
+      double t = dt * gg[k];
+      double vk = vi[k] + t;
+      vi[k] = vk;
+      double t2 = dt * vk;
+      xi[k] = xi[k] + t2;
+    }
+  }
+}
+
+mgpbd_status launch_begin_frame(Handle *h) {
+  k_begin_frame<<<blocks_for(h->N, 256), 256, 0, h->stream>>>(
+      h->N, h->p.dt, h->p.gravity[0], h->p.gravity[1], h->p.gravity[2], h->w, h->x, h->v, h->xold);
+  MG_LAUNCH("k_begin_frame");
+  if (h->m) MG_CUDA(cudaMemsetAsync(h->lambda, 0, sizeof(double) * h->m, h->stream));
+  return MGPBD_OK;
+}
+
+// Alg. 1 epilogue: v = (x - x_old) / dt
+__global__ void k_end_frame(int64_t n3, double dt, const double *x, const double *xold,
+                            double *v) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n3;
+       q += (int64_t)gridDim.x * blockDim.x)
+    v[q] = (x[q] - xold[q]) / dt;
+}
+
+mgpbd_status launch_end_frame(Handle *h) {
+  int64_t n3 = 3 * (int64_t)h->N;
+  k_end_frame<<<blocks_for(n3, 256), 256, 0, h->stream>>>(n3, h->p.dt, h->x, h->xold, h->v);
+  MG_LAUNCH("k_end_frame");
+  return MGPBD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 1: C and grad C; eq. 3: b = -C - alpha~ lambda
+__global__ void k_eval(int E, int T, const int32_t *edge, const int32_t *tet, const double *x,
+                       const double *L0, const double *V0, const double *alpha_t,
+                       const double *lambda, double *C, double *b, double *gd, double *gt) {
+  int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = tid; j < (int64_t)E + T; j += stride) {
+    double c;
+    if (j < E) {
+      double a[3], bb[3], n[3];
+      load3(x + 3 * (int64_t)edge[2 * j], a);
+      load3(x + 3 * (int64_t)edge[2 * j + 1], bb);
+      c = dist_eval(a, bb, L0[j], n);
+      gd[3 * j] = n[0];
+      gd[3 * j + 1] = n[1];
+      gd[3 * j + 2] = n[2];
+    } else {
+      int64_t t = j - E;
+      const int32_t *q = tet + 4 * t;
+      double p0[3], p1[3], p2[3], p3[3], g[12];
+      load3(x + 3 * (int64_t)q[0], p0);
+      load3(x + 3 * (int64_t)q[1], p1);
+      load3(x + 3 * (int64_t)q[2], p2);
+      load3(x + 3 * (int64_t)q[3], p3);
+      c = tet_eval(p0, p1, p2, p3, V0[t], g);
+      double *o = gt + 12 * t;
+      for (int k = 0; k < 12; ++k) o[k] = g[k];
+    }
+    C[j] = c;
+    double t = alpha_t[j] * lambda[j];
+    b[j] = (-c) - t;
+  }
+}
+
+mgpbd_status launch_eval(Handle *h) {
+  if (h->m == 0) return MGPBD_OK;
+  k_eval<<<blocks_for(h->m, 256), 256, 0, h->stream>>>(h->E, h->T, h->edge, h->tet, h->x, h->L0,
+                                                       h->V0, h->alpha_t, h->lambda, h->C, h->b,
+                                                       h->gd, h->gt);
+  MG_LAUNCH("k_eval");
+  return MGPBD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// gradient of row j at slot s
+__device__ __forceinline__ void row_grad(int j, int s, int E, const double *gd, const double *gt,
+                                         double g[3]) {
+  if (j < E) {
+    const double *n = gd + 3 * (int64_t)j;
+    if (s == 0) {
+      g[0] = n[0]; g[1] = n[1]; g[2] = n[2];
+    } else {
+      g[0] = -n[0]; g[1] = -n[1]; g[2] = -n[2];
+    }
+  } else {
+    const double *t = gt + 12 * (int64_t)(j - E) + 3 * s;
+    g[0] = t[0]; g[1] = t[1]; g[2] = t[2];
+  }
+}
+
+__device__ __forceinline__ double gdot(const double *a, const double *b) {
+  return fma(a[2], b[2], fma(a[1], b[1], a[0] * b[0]));
+}
+
+// Values of A (eq. 3, Sec. 4.2 formulas); one warp per row, lanes over the
+// row's off-diagonals; lane 0 also forms the diagonal.  Also writes 1/A_ii
+// and, in mixed precision, the FP32 mirrors.
+__global__ void k_assemble(int m, int E, const int32_t *edge, const int32_t *tet, const double *w,
+                           const double *gd, const double *gt, const double *alpha_t,
+                           const int64_t *ptr, const int32_t *col, const uint16_t *map,
+                           double *val, double *dinv, float *val32, float *dinv32) {
+  const int lane = threadIdx.x & 31;
+  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t ii = warp; ii < m; ii += nwarps) {
+    int i = (int)ii;
+    int32_t v[4];
+    int c;
+    if (i < E) {
+      v[0] = edge[2 * (int64_t)i];
+      v[1] = edge[2 * (int64_t)i + 1];
+      v[2] = v[3] = 0;
+      c = 2;
+    } else {
+      const int32_t *t = tet + 4 * (int64_t)(i - E);
+      v[0] = t[0]; v[1] = t[1]; v[2] = t[2]; v[3] = t[3];
+      c = 4;
+    }
+    double gi[4][3], wi[4];
+    for (int s = 0; s < 4; ++s) {
+      if (s < c) {
+        row_grad(i, s, E, gd, gt, gi[s]);
+        wi[s] = w[v[s]];
+      } else {
+        gi[s][0] = gi[s][1] = gi[s][2] = 0.0;
+        wi[s] = 0.0;
+      }
+    }
+    int64_t s0 = ptr[i], e = ptr[i + 1] - 1;
+    for (int64_t k = s0 + lane; k < e; k += 32) {
+      int j = col[k];
+      unsigned code = map[k];
+      int ns = code & 3;
+      double acc = 0.0;
+      for (int p = 0; p < ns; ++p) {
+        int si = (code >> (2 + 4 * p)) & 3, sj = (code >> (4 + 4 * p)) & 3;
+        double gj[3];
+        row_grad(j, sj, E, gd, gt, gj);
+        acc = fma(wi[si], gdot(gi[si], gj), acc);
+      }
+      val[k] = acc;
+      if (val32) val32[k] = (float)acc;
+    }
+    if (lane == 0) {
+      double acc = 0.0;
+      for (int s = 0; s < c; ++s) acc = fma(wi[s], gdot(gi[s], gi[s]), acc);
+      double d = acc + alpha_t[i];
+      val[e] = d;
+      dinv[i] = 1.0 / d;
+      if (val32) {
+        val32[e] = (float)d;
+        dinv32[i] = (float)(1.0 / d);
+      }
+    }
+  }
+}
+
+mgpbd_status launch_assemble(Handle *h) {
+  if (h->m == 0) return MGPBD_OK;
+  Level &L = h->lev[0];
+  const int th = 256;
+  int64_t warps = h->m;
+  int blocks = blocks_for(warps * 32, th);
+  k_assemble<<<blocks, th, 0, h->stream>>>(h->m, h->E, h->edge, h->tet, h->w, h->gd, h->gt,
+                                            h->alpha_t, L.ptr, L.col, h->map, L.val, L.dinv,
+                                            L.val32, L.dinv32);
+  MG_LAUNCH("k_assemble");
+  return MGPBD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// eq. 5: dx_v = w_v * sum_{j incident to v, ascending} fma(g_{j,v}, dl_j, .);
+// x_v = fma(omega_x, dx_v, x_v).  Then lambda += dl.
+__global__ void k_update_x(int N, int E, const int32_t *edge, const int32_t *tet,
+                           const int64_t *vptr, const int32_t *vrow, const double *gd,
+                           const double *gt, const double *dl, const double *w, double omega_x,
+                           double *x) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+    for (int64_t q = vptr[v]; q < vptr[v + 1]; ++q) {
+      int j = vrow[q];
+      int s;
+      if (j < E) {
+        s = edge[2 * (int64_t)j] == v ? 0 : 1;
+      } else {
+        const int32_t *t = tet + 4 * (int64_t)(j - E);
+        s = t[0] == v ? 0 : (t[1] == v ? 1 : (t[2] == v ? 2 : 3));
+      }
+      double g[3];
+      row_grad(j, s, E, gd, gt, g);
+      double d = dl[j];
+      acc0 = fma(g[0], d, acc0);
+      acc1 = fma(g[1], d, acc1);
+      acc2 = fma(g[2], d, acc2);
+    }
+    double wv = w[v];
+    double *xv = x + 3 * (int64_t)v;
+    xv[0] = fma(omega_x, wv * acc0, xv[0]);
+    xv[1] = fma(omega_x, wv * acc1, xv[1]);
+    xv[2] = fma(omega_x, wv * acc2, xv[2]);
+  }
+}
+
+__global__ void k_add(int64_t n, const double *a, double *y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = y[i] + a[i];
+}
+
+mgpbd_status launch_update(Handle *h) {
+  if (h->m == 0) return MGPBD_OK;
+  k_update_x<<<blocks_for(h->N, 128), 128, 0, h->stream>>>(h->N, h->E, h->edge, h->tet, h->vptr,
+                                                          h->vrow, h->gd, h->gt, h->dl, h->w,
+                                                          h->p.omega_x, h->x);
+  MG_LAUNCH("k_update_x");
+  k_add<<<blocks_for(h->m, 256), 256, 0, h->stream>>>(h->m, h->dl, h->lambda);
+  MG_LAUNCH("k_add");
+  return MGPBD_OK;
+}
+
+}  // namespace mg

@@ -1,0 +1,729 @@
+// Solve phase (Sec. 4.4-4.5): MGPCG with one V-cycle per iteration, the
+// weighted-Jacobi smoother, restriction/prolongation through the aggregates,
+// the coarsest dense Cholesky, and the power method for lambda_max(D^-1 A).
+//
+// Scalars of the PCG recurrence (r.z, p.q, alpha, beta, |r|) stay on the
+// device: every dot product is a fixed-grid two-stage reduction whose last
+// block folds the per-block partials in a fixed order and applies the next
+// recurrence step, so results are deterministic run to run and no host round
+// trip is needed inside an iteration.  Kernels of an iteration return at once
+// when the device flag `done` is set, so the host launches iterations in
+// chunks and polls the flag between chunks.
+//
+// Precision: MGPBD_FP64 runs everything in FP64.  MGPBD_MIXED runs the
+// V-cycle bulk and A.p with FP32 values, vectors and accumulation; the dot
+// products, alpha/beta, the Krylov vectors, the true residual and the
+// coarsest factorisation stay FP64.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mg {
+
+constexpr int kDotThreads = 256;
+
+enum DotMode {
+  DOT_STORE = 0,  // *out = s
+  DOT_BNORM,      // |b|^2; zero right-hand side finishes at once
+  DOT_RZ0,        // initial r.z
+  DOT_PQ,         // p.q and alpha
+  DOT_RR,         // r.r, iteration count and convergence test
+  DOT_RZ,         // new r.z and beta
+  DOT_TR          // |b - A x|^2
+};
+
+struct DotCtx {
+  double *partials;
+  unsigned int *counter;
+  PcgScalars *sc;
+  double *out;
+  int mode;
+  double rtol;
+  int maxiter;
+};
+
+__device__ void dot_finalize(const DotCtx &c, double s) {
+  PcgScalars *sc = c.sc;
+  switch (c.mode) {
+    case DOT_STORE:
+      *c.out = s;
+      break;
+    case DOT_BNORM:
+      sc->bnorm2 = s;
+      sc->iters = 0;
+      sc->rr = s;
+      if (s == 0.0) {
+        sc->done = 1;
+        sc->status = MGPBD_OK;
+      } else if (!(s == s) || isinf(s)) {
+        sc->done = 1;
+        sc->status = MGPBD_E_BREAKDOWN;
+      }
+      break;
+    case DOT_RZ0:
+      sc->rz = s;
+      if (!(s > 0.0)) {
+        sc->done = 1;
+        sc->status = MGPBD_E_BREAKDOWN;
+      }
+      break;
+    case DOT_PQ:
+      sc->pq = s;
+      if (!(s > 0.0)) {
+        sc->done = 1;
+        sc->status = MGPBD_E_BREAKDOWN;
+      } else {
+        sc->alpha = sc->rz / s;
+      }
+      break;
+    case DOT_RR:
+      sc->rr = s;
+      sc->iters += 1;
+      if (!(s == s)) {
+        sc->done = 1;
+        sc->status = MGPBD_E_BREAKDOWN;
+      } else if (sqrt(s) <= c.rtol * sqrt(sc->bnorm2)) {
+        sc->done = 1;
+        sc->status = MGPBD_OK;
+      } else if (sc->iters >= c.maxiter) {
+        sc->done = 1;
+        sc->status = MGPBD_W_NOT_CONVERGED;
+      }
+      break;
+    case DOT_RZ:
+      if (!(s > 0.0)) {
+        sc->done = 1;
+        sc->status = MGPBD_E_BREAKDOWN;
+      } else {
+        sc->beta = s / sc->rz;
+        sc->rz = s;
+      }
+      break;
+    case DOT_TR:
+      sc->tr2 = s;
+      break;
+  }
+}
+
+// block reduce of one value per thread in a fixed order, then the last block
+// folds the partials (fixed order) and finalizes
+__device__ void block_dot_finish(double v, const DotCtx &c) {
+  __shared__ double ws[32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) ws[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+    c.partials[blockIdx.x] = s;
+    __threadfence();
+    unsigned t = atomicAdd(c.counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+    s += ((volatile double *)c.partials)[b];
+  s = warp_sum(s);
+  if (lane == 0) ws[wid] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    dot_finalize(c, t);
+    *c.counter = 0;
+  }
+}
+
+__device__ __forceinline__ bool is_done(const PcgScalars *sc) {
+  return ((volatile const PcgScalars *)sc)->done != 0;
+}
+
+static int dot_grid() { return std::min(4096, 2 * num_sms()); }
+
+static DotCtx make_ctx(Handle *h, int mode, double *out = nullptr) {
+  DotCtx c;
+  c.partials = h->partials;
+  c.counter = h->counter;
+  c.sc = h->sc;
+  c.out = out;
+  c.mode = mode;
+  c.rtol = h->p.pcg_rtol;
+  c.maxiter = h->p.pcg_maxiter;
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// plain vector kernels
+// ---------------------------------------------------------------------------
+__global__ void k_dot(int64_t n, const double *x, const double *y, DotCtx c, int check_done) {
+  if (check_done && is_done(c.sc)) return;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(x[i], y[i], acc);
+  block_dot_finish(acc, c);
+}
+
+// x += alpha p; r -= alpha q; then r.r (convergence test)
+__global__ void k_xr_update(int64_t n, double *x, double *r, const double *p, const double *q,
+                            DotCtx c) {
+  if (is_done(c.sc)) return;
+  const double al = c.sc->alpha;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(al, p[i], x[i]);
+    double ri = fma(-al, q[i], r[i]);
+    r[i] = ri;
+    acc = fma(ri, ri, acc);
+  }
+  block_dot_finish(acc, c);
+}
+
+// p = z + beta p
+__global__ void k_p_update(int64_t n, double *p, const double *z, const PcgScalars *sc) {
+  if (is_done(sc)) return;
+  const double be = sc->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(be, p[i], z[i]);
+}
+
+__global__ void k_pcg_init(PcgScalars *sc) {
+  sc->done = 0;
+  sc->iters = 0;
+  sc->status = MGPBD_W_NOT_CONVERGED;
+  sc->rz = sc->pq = sc->rr = sc->alpha = sc->beta = sc->tr2 = 0.0;
+}
+
+template <class S, class D>
+__global__ void k_convert(int64_t n, const S *a, D *b, const PcgScalars *sc) {
+  if (sc && is_done(sc)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (D)a[i];
+}
+
+// ---------------------------------------------------------------------------
+// sparse kernels: G lanes per row (G in 4, 8, 16, 32)
+// ---------------------------------------------------------------------------
+template <int G, class T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// partial row dot of lane g of a G-lane group (no shuffles: callers reduce)
+template <int G, class VT, class AT, class XT>
+__device__ __forceinline__ AT row_dot(const int64_t *ptr, const int32_t *col, const VT *val,
+                                      const XT *x, int i, int g) {
+  AT acc = 0;
+  int64_t s0 = ptr[i], e = ptr[i + 1];
+  for (int64_t k = s0 + g; k < e; k += G) acc = fma((AT)val[k], (AT)x[col[k]], acc);
+  return acc;
+}
+
+// Rows handled by G-lane groups, 32/G rows per warp per trip.  The loop bound
+// is uniform across the warp, so full-mask shuffles inside are safe; `valid`
+// marks groups past the last row.
+#define GROUP_ROWS(G, n)                                                          \
+  const int lane_ = threadIdx.x & 31;                                             \
+  const int g = lane_ & ((G) - 1);                                                \
+  const int sub_ = lane_ / (G);                                                   \
+  const int64_t warp_ = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;    \
+  const int64_t nwarp_ = ((int64_t)gridDim.x * blockDim.x) >> 5;                  \
+  for (int64_t base_ = warp_ * (32 / (G)), i = base_ + sub_; base_ < (n);         \
+       base_ += nwarp_ * (32 / (G)), i = base_ + sub_)                            \
+    if (const bool valid = i < (n); true)
+
+// q = A p (PCG operator) fused with p.q
+template <int G, class VT, class AT>
+__global__ void k_spmv_pq(int n, const int64_t *ptr, const int32_t *col, const VT *val,
+                          const double *p, double *q, DotCtx c) {
+  if (is_done(c.sc)) return;
+  double acc = 0.0;
+  GROUP_ROWS(G, n) {
+    AT s = valid ? row_dot<G, VT, AT, double>(ptr, col, val, p, (int)i, g) : (AT)0;
+    s = group_sum<G>(s);
+    if (valid && g == 0) {
+      double qi = (double)s;
+      q[i] = qi;
+      acc = fma(p[i], qi, acc);
+    }
+  }
+  block_dot_finish(acc, c);
+}
+
+// r_t = b - A x in FP64, |r_t|^2
+__global__ void k_true_resid(int n, const int64_t *ptr, const int32_t *col, const double *val,
+                             const double *x, const double *b, DotCtx c) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double acc = 0.0;
+  for (int64_t i = w; i < n; i += nw) {
+    double s = warp_sum(row_dot<32, double, double, double>(ptr, col, val, x, (int)i, lane));
+    if (lane == 0) {
+      double ri = b[i] - s;
+      acc = fma(ri, ri, acc);
+    }
+  }
+  block_dot_finish(acc, c);
+}
+
+// weighted Jacobi, first sweep from x = 0: x = omega D^-1 b
+template <class T>
+__global__ void k_jacobi0(int n, const T *b, const T *dinv, T omega, T *x, const PcgScalars *sc) {
+  if (is_done(sc)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x[i] = omega * (b[i] * dinv[i]);
+}
+
+// weighted Jacobi sweep: xn = x + omega D^-1 (b - A x)
+template <int G, class T>
+__global__ void k_jacobi(int n, const int64_t *ptr, const int32_t *col, const T *val,
+                         const T *dinv, T omega, const T *b, const T *x, T *xn,
+                         const PcgScalars *sc) {
+  if (is_done(sc)) return;
+  GROUP_ROWS(G, n) {
+    T s = valid ? row_dot<G, T, T, T>(ptr, col, val, x, (int)i, g) : (T)0;
+    s = group_sum<G>(s);
+    if (valid && g == 0) xn[i] = fma(omega, (b[i] - s) * dinv[i], x[i]);
+  }
+}
+
+// r = b - A x
+template <int G, class T>
+__global__ void k_resid(int n, const int64_t *ptr, const int32_t *col, const T *val, const T *b,
+                        const T *x, T *r, const PcgScalars *sc) {
+  if (is_done(sc)) return;
+  GROUP_ROWS(G, n) {
+    T s = valid ? row_dot<G, T, T, T>(ptr, col, val, x, (int)i, g) : (T)0;
+    s = group_sum<G>(s);
+    if (valid && g == 0) r[i] = b[i] - s;
+  }
+}
+
+// b_c[a] = sum_{i in a} P_i r_i (warp per aggregate)
+template <class T>
+__global__ void k_restrict(int na, const int64_t *mptr, const int32_t *mrow, const T *P,
+                           const T *r, T *bc, const PcgScalars *sc) {
+  if (is_done(sc)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t a = w; a < na; a += nw) {
+    T acc = 0;
+    for (int64_t q = mptr[a] + lane; q < mptr[a + 1]; q += 32) {
+      int i = mrow[q];
+      acc = fma(P[i], r[i], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) bc[a] = acc;
+  }
+}
+
+// x_i += P_i x_c[agg_i]
+template <class T>
+__global__ void k_prolong(int n, const int32_t *agg, const T *P, const T *xc, T *x,
+                          const PcgScalars *sc) {
+  if (is_done(sc)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x[i] = fma(P[i], xc[agg[i]], x[i]);
+}
+
+// coarsest: x = A_c^-1 b with the explicit FP64 inverse (warp per row)
+template <class T>
+__global__ void k_coarse_apply(int n, const double *inv, const T *b, T *x, const PcgScalars *sc) {
+  if (sc && is_done(sc)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w; i < n; i += nw) {
+    double acc = 0.0;
+    for (int j = lane; j < n; j += 32) acc = fma(inv[i * (int64_t)n + j], (double)b[j], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) x[i] = (T)acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// coarsest dense Cholesky (FP64) and explicit inverse
+// ---------------------------------------------------------------------------
+__global__ void k_dense_fill(int n, const int64_t *ptr, const int32_t *col, const double *val,
+                             double *Ad) {
+  for (int i = blockIdx.x; i < n; i += gridDim.x)
+    for (int64_t k = ptr[i] + threadIdx.x; k < ptr[i + 1]; k += blockDim.x)
+      Ad[(int64_t)i * n + col[k]] = val[k];
+}
+
+// right-looking Cholesky in place (lower triangle), one block
+__global__ void k_cholesky(int n, double *A, int *status) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double d = A[(int64_t)j * n + j];
+      if (!(d > 0.0)) bad = 1;
+      else A[(int64_t)j * n + j] = sqrt(d);
+    }
+    __syncthreads();
+    if (bad) break;
+    double ljj = A[(int64_t)j * n + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(int64_t)i * n + j] /= ljj;
+    __syncthreads();
+    // trailing update of the lower triangle: A_ik -= L_ij L_kj, j < k <= i
+    int64_t m = n - j - 1;
+    int64_t tri = m * (m + 1) / 2;
+    for (int64_t t = threadIdx.x; t < tri; t += blockDim.x) {
+      // t -> (ii, kk) with 0 <= kk <= ii < m, row-major over the triangle
+      int64_t ii = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+      while (ii * (ii + 1) / 2 > t) --ii;
+      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+      int64_t kk = t - ii * (ii + 1) / 2;
+      int64_t i = j + 1 + ii, k = j + 1 + kk;
+      A[i * n + k] = fma(-A[i * n + j], A[k * n + j], A[i * n + k]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *status = bad ? MGPBD_E_SINGULAR : MGPBD_OK;
+}
+
+// column c of L^-1 (thread per column, forward substitution), row-major Li[k][c]
+__global__ void k_tri_inverse(int n, const double *Lm, double *Li, const int *status) {
+  if (*status != MGPBD_OK) return;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    for (int i = 0; i < c; ++i) Li[(int64_t)i * n + c] = 0.0;
+    for (int i = c; i < n; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) s = fma(-Lm[(int64_t)i * n + k], Li[(int64_t)k * n + c], s);
+      Li[(int64_t)i * n + c] = s / Lm[(int64_t)i * n + i];
+    }
+  }
+}
+
+// A^-1 = L^-T L^-1: inv[i][j] = sum_{k >= max(i,j)} Li[k][i] Li[k][j]
+__global__ void k_inv_gram(int n, const double *Li, double *inv, const int *status) {
+  if (*status != MGPBD_OK) return;
+  int64_t tot = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t / n), j = (int)(t % n);
+    int k0 = max(i, j);
+    double s = 0.0;
+    for (int k = k0; k < n; ++k) s = fma(Li[(int64_t)k * n + i], Li[(int64_t)k * n + j], s);
+    inv[t] = s;
+  }
+}
+
+mgpbd_status coarsest_factor(Handle *h) {
+  if (!h->have_setup || h->m == 0) return MGPBD_OK;
+  Level &L = h->lev[h->L - 1];
+  int n = L.n;
+  if (n > h->cap_nc) {
+    h->arena.release(h->cdense);
+    h->arena.release(h->cinv);
+    MG_TRY(alloc_n(h->arena, &h->cdense, (size_t)n * n));
+    MG_TRY(alloc_n(h->arena, &h->cinv, 2 * (size_t)n * n));
+    h->cap_nc = n;
+  }
+  h->nc = n;
+  MG_CUDA(cudaMemsetAsync(h->cdense, 0, sizeof(double) * (size_t)n * n, h->stream));
+  k_dense_fill<<<std::max(1, std::min(n, 4096)), 128, 0, h->stream>>>(n, L.ptr, L.col, L.val,
+                                                                      h->cdense);
+  MG_LAUNCH("k_dense_fill");
+  k_cholesky<<<1, 1024, 0, h->stream>>>(n, h->cdense, h->cstat);
+  MG_LAUNCH("k_cholesky");
+  double *Li = h->cinv + (size_t)n * n;
+  k_tri_inverse<<<blocks_for(n, 32), 32, 0, h->stream>>>(n, h->cdense, Li, h->cstat);
+  MG_LAUNCH("k_tri_inverse");
+  k_inv_gram<<<blocks_for((int64_t)n * n, 256), 256, 0, h->stream>>>(n, Li, h->cinv, h->cstat);
+  MG_LAUNCH("k_inv_gram");
+  int st = 0;
+  MG_CUDA(cudaMemcpyAsync(h->flag_host, h->cstat, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  st = *h->flag_host;
+  if (st != MGPBD_OK) {
+    set_error("coarsest Cholesky: non-positive pivot");
+    return MGPBD_E_SINGULAR;
+  }
+  return MGPBD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+static int group_for(const Level &L) {
+  double avg = L.n ? (double)L.nnz / L.n : 1.0;
+  return avg <= 12 ? 4 : (avg <= 24 ? 8 : (avg <= 48 ? 16 : 32));
+}
+
+static int row_blocks(int64_t rows, int G, int th = 256) {
+  int64_t groups_per_block = th / G;
+  int64_t b = (rows + groups_per_block - 1) / groups_per_block;
+  int cap = 64 * num_sms();
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
+}
+
+#define DISPATCH_G(G, ...)                  \
+  switch (G) {                              \
+    case 4: { constexpr int GG = 4; __VA_ARGS__; } break;   \
+    case 8: { constexpr int GG = 8; __VA_ARGS__; } break;   \
+    case 16: { constexpr int GG = 16; __VA_ARGS__; } break; \
+    default: { constexpr int GG = 32; __VA_ARGS__; } break; \
+  }
+
+template <class T>
+static const T *vals(const Level &L);
+template <>
+const double *vals<double>(const Level &L) { return L.val; }
+template <>
+const float *vals<float>(const Level &L) { return L.val32; }
+template <class T>
+static const T *dinvs(const Level &L);
+template <>
+const double *dinvs<double>(const Level &L) { return L.dinv; }
+template <>
+const float *dinvs<float>(const Level &L) { return L.dinv32; }
+template <class T>
+static const T *Ps(const Level &L);
+template <>
+const double *Ps<double>(const Level &L) { return L.P; }
+template <>
+const float *Ps<float>(const Level &L) { return L.P32; }
+
+// V-cycle on level l in precision T: L.b -> L.x (zero start)
+template <class T>
+static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in) {
+  Level &L = h->lev[l];
+  const PcgScalars *sc = h->sc;
+  const int n = L.n;
+  T *x = (T *)L.x;
+  if (l == h->L - 1) {
+    k_coarse_apply<T><<<blocks_for((int64_t)n * 32, 256), 256, 0, h->stream>>>(n, h->cinv, b_in, x,
+                                                                                sc);
+    MG_LAUNCH("k_coarse_apply");
+    return MGPBD_OK;
+  }
+  const int G = group_for(L);
+  const T om = (T)L.omega;
+  const T *val = vals<T>(L);
+  const T *dinv = dinvs<T>(L);
+  T *x2 = (T *)L.x2, *r = (T *)L.r;
+  k_jacobi0<T><<<blocks_for(n, 256), 256, 0, h->stream>>>(n, b_in, dinv, om, x, sc);
+  MG_LAUNCH("k_jacobi0");
+  for (int s = 1; s < h->p.smooth_sweeps; ++s) {
+    if (l == 0) MG_TRY(prof_begin(h));
+    DISPATCH_G(G, (k_jacobi<GG, T><<<row_blocks(n, GG), 256, 0, h->stream>>>(
+                      n, L.ptr, L.col, val, dinv, om, b_in, x, x2, sc)));
+    MG_LAUNCH("k_jacobi");
+    if (l == 0) MG_TRY(prof_end(h));
+    std::swap(x, x2);
+  }
+  DISPATCH_G(G, (k_resid<GG, T><<<row_blocks(n, GG), 256, 0, h->stream>>>(n, L.ptr, L.col, val,
+                                                                         b_in, x, r, sc)));
+  MG_LAUNCH("k_resid");
+  Level &Lc = h->lev[l + 1];
+  k_restrict<T><<<blocks_for((int64_t)L.n_agg * 32, 256), 256, 0, h->stream>>>(
+      L.n_agg, L.mptr, L.mrow, Ps<T>(L), r, (T *)Lc.b, sc);
+  MG_LAUNCH("k_restrict");
+  MG_TRY(vcycle_level<T>(h, l + 1, (const T *)Lc.b));
+  k_prolong<T><<<blocks_for(n, 256), 256, 0, h->stream>>>(n, L.agg, Ps<T>(L), (const T *)Lc.x, x,
+                                                          sc);
+  MG_LAUNCH("k_prolong");
+  for (int s = 0; s < h->p.smooth_sweeps; ++s) {
+    if (l == 0) MG_TRY(prof_begin(h));
+    DISPATCH_G(G, (k_jacobi<GG, T><<<row_blocks(n, GG), 256, 0, h->stream>>>(
+                      n, L.ptr, L.col, val, dinv, om, b_in, x, x2, sc)));
+    MG_LAUNCH("k_jacobi");
+    if (l == 0) MG_TRY(prof_end(h));
+    std::swap(x, x2);
+  }
+  if (x != (T *)L.x) {  // keep the result in L.x
+    MG_CUDA(cudaMemcpyAsync(L.x, x, sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return MGPBD_OK;
+}
+
+// z = V(r) on level 0, FP64 in and out
+static mgpbd_status vcycle_top(Handle *h, const double *r, double *z) {
+  Level &L = h->lev[0];
+  const int m = h->m;
+  if (h->p.precision == MGPBD_MIXED) {
+    k_convert<double, float><<<blocks_for(m, 256), 256, 0, h->stream>>>(m, r, (float *)L.b, h->sc);
+    MG_LAUNCH("k_convert");
+    MG_TRY(vcycle_level<float>(h, 0, (const float *)L.b));
+    k_convert<float, double><<<blocks_for(m, 256), 256, 0, h->stream>>>(m, (const float *)L.x, z,
+                                                                        h->sc);
+    MG_LAUNCH("k_convert");
+  } else {
+    MG_TRY(vcycle_level<double>(h, 0, r));
+    k_convert<double, double><<<blocks_for(m, 256), 256, 0, h->stream>>>(m, (const double *)L.x,
+                                                                         z, h->sc);
+    MG_LAUNCH("k_convert");
+  }
+  return MGPBD_OK;
+}
+
+mgpbd_status vcycle_apply(Handle *h, const double *d_r, double *d_z) {
+  k_pcg_init<<<1, 1, 0, h->stream>>>(h->sc);
+  MG_LAUNCH("k_pcg_init");
+  return vcycle_top(h, d_r, d_z);
+}
+
+static mgpbd_status launch_dot(Handle *h, const double *x, const double *y, int64_t n, int mode,
+                               int check_done, double *out = nullptr) {
+  DotCtx c = make_ctx(h, mode, out);
+  k_dot<<<dot_grid(), kDotThreads, 0, h->stream>>>(n, x, y, c, check_done);
+  MG_LAUNCH("k_dot");
+  return MGPBD_OK;
+}
+
+mgpbd_status dot_dd(Handle *h, const double *x, const double *y, int64_t n, double *d_out) {
+  return launch_dot(h, x, y, n, DOT_STORE, 0, d_out);
+}
+
+// one PCG iteration (kernels return early once `done` is set)
+static mgpbd_status pcg_iteration(Handle *h, double *x) {
+  Level &L = h->lev[0];
+  const int m = h->m;
+  double *r = h->pr, *z = h->pz, *p = h->pp, *q = h->pq;
+  const int G = group_for(L);
+  DotCtx cpq = make_ctx(h, DOT_PQ);
+  if (h->p.precision == MGPBD_MIXED) {
+    DISPATCH_G(G, (k_spmv_pq<GG, float, float><<<std::min(row_blocks(m, GG), 4096), 256, 0, h->stream>>>(
+                      m, L.ptr, L.col, L.val32, p, q, cpq)));
+  } else {
+    DISPATCH_G(G, (k_spmv_pq<GG, double, double><<<std::min(row_blocks(m, GG), 4096), 256, 0, h->stream>>>(
+                      m, L.ptr, L.col, L.val, p, q, cpq)));
+  }
+  MG_LAUNCH("k_spmv_pq");
+  k_xr_update<<<dot_grid(), kDotThreads, 0, h->stream>>>(m, x, r, p, q, make_ctx(h, DOT_RR));
+  MG_LAUNCH("k_xr_update");
+  MG_TRY(vcycle_top(h, r, z));
+  MG_TRY(launch_dot(h, r, z, m, DOT_RZ, 1));
+  k_p_update<<<blocks_for(m, 256), 256, 0, h->stream>>>(m, p, z, h->sc);
+  MG_LAUNCH("k_p_update");
+  return MGPBD_OK;
+}
+
+mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *info) {
+  const int m = h->m;
+  memset(info, 0, sizeof(*info));
+  if (m == 0) return MGPBD_OK;
+  MG_CUDA(cudaEventRecord(h->ev0, h->stream));
+  double *r = h->pr, *z = h->pz, *p = h->pp;
+  h->pcg_k = -1;
+  h->pev_used = 0;
+  k_pcg_init<<<1, 1, 0, h->stream>>>(h->sc);
+  MG_LAUNCH("k_pcg_init");
+  MG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * m, h->stream));
+  MG_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->stream));
+  MG_TRY(launch_dot(h, b, b, m, DOT_BNORM, 0));
+  MG_TRY(vcycle_top(h, r, z));
+  MG_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->stream));
+  MG_TRY(launch_dot(h, r, z, m, DOT_RZ0, 1));
+  const int chunk = 8;
+  int launched = 0;
+  while (launched < h->p.pcg_maxiter) {
+    int c = std::min(chunk, h->p.pcg_maxiter - launched);
+    for (int k = 0; k < c; ++k) {
+      h->pcg_k = launched + k;
+      MG_TRY(pcg_iteration(h, x));
+    }
+    launched += c;
+    MG_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost,
+                            h->stream));
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    if (h->sc_host->done) break;
+  }
+  // true residual in FP64
+  k_true_resid<<<std::min(blocks_for((int64_t)m * 32, 256), 4096), 256, 0, h->stream>>>(
+      m, h->lev[0].ptr, h->lev[0].col, h->lev[0].val, x, b, make_ctx(h, DOT_TR));
+  MG_LAUNCH("k_true_resid");
+  MG_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost,
+                          h->stream));
+  MG_CUDA(cudaEventRecord(h->ev1, h->stream));
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->ms_solve += ms;
+  const PcgScalars &s = *h->sc_host;
+  MG_TRY(prof_harvest(h, s.iters));
+  double bn = sqrt(s.bnorm2);
+  info->pcg_iters = s.iters;
+  info->bnorm = bn;
+  info->rel_res = bn > 0 ? sqrt(s.rr) / bn : 0.0;
+  info->true_rel_res = bn > 0 ? sqrt(s.tr2) / bn : 0.0;
+  info->status = s.done ? s.status : MGPBD_W_NOT_CONVERGED;
+  if (bn == 0.0) info->status = MGPBD_OK;
+  h->last_pcg_iters = s.iters;
+  if (info->status == MGPBD_E_BREAKDOWN) set_error("PCG breakdown (p.Ap <= 0, r.z <= 0 or NaN)");
+  return info->status;
+}
+
+// ---------------------------------------------------------------------------
+// power method for lambda_max(D^-1 A) (Sec. 4.5)
+// ---------------------------------------------------------------------------
+__global__ void k_pow_init(int n, uint64_t seed, int l, double *y) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    y[i] = u01(h64(hkey(seed, l, i)));
+}
+
+// z_i = (A y)_i / A_ii
+__global__ void k_pow_apply(int n, const int64_t *ptr, const int32_t *col, const double *val,
+                            const double *y, double *z) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w; i < n; i += nw) {
+    double s = warp_sum(row_dot<32, double, double, double>(ptr, col, val, y, (int)i, lane));
+    if (lane == 0) z[i] = s / val[ptr[i + 1] - 1];
+  }
+}
+
+// lam = |z|/|y|; y = z/|z|  (s[0] = z.z, s[1] = y.y)
+__global__ void k_pow_scale(int n, const double *z, double *y, const double *s, double *lam) {
+  double nz = sqrt(s[0]), ny = sqrt(s[1]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *lam = nz / ny;
+  if (!(nz > 0.0)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    y[i] = z[i] / nz;
+}
+
+mgpbd_status power_method(Handle *h, int l) {
+  Level &L = h->lev[l];
+  const int n = L.n;
+  double *y = h->pp, *z = h->pq;
+  double *s = h->partials + 4096;  // 3 scalars after the partial area used by dots
+  k_pow_init<<<blocks_for(n, 256), 256, 0, h->stream>>>(n, h->p.seed_pow, l, y);
+  MG_LAUNCH("k_pow_init");
+  for (int it = 0; it < h->p.power_iters; ++it) {
+    k_pow_apply<<<std::min(blocks_for((int64_t)n * 32, 256), 8192), 256, 0, h->stream>>>(
+        n, L.ptr, L.col, L.val, y, z);
+    MG_LAUNCH("k_pow_apply");
+    MG_TRY(launch_dot(h, z, z, n, DOT_STORE, 0, s));
+    MG_TRY(launch_dot(h, y, y, n, DOT_STORE, 0, s + 1));
+    k_pow_scale<<<blocks_for(n, 256), 256, 0, h->stream>>>(n, z, y, s, s + 2);
+    MG_LAUNCH("k_pow_scale");
+  }
+  double lam = 0.0;
+  MG_CUDA(cudaMemcpyAsync(&lam, s + 2, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  L.lmax = lam;
+  L.omega = 2.0 / (h->p.power_safety * lam + h->p.lambda_min_est);
+  return MGPBD_OK;
+}
+
+}  // namespace mg

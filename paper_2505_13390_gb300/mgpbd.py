@@ -1,0 +1,337 @@
+"""Thin Python binding of the C ABI in include/mgpbd.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA library (libmgpbd.so).  PyTorch is
+used for device memory and for the current CUDA stream.  There is no CPU
+fallback: importing this module raises if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmgpbd.so")
+
+OK, W_NOT_CONVERGED = 0, 1
+E_INVALID, E_OOM, E_BREAKDOWN, E_SINGULAR = -1, -2, -3, -4
+E_DEVICE_TIMEOUT, E_CUDA, E_BUDGET, E_SETUP = -5, -6, -7, -8
+MEM_HOST, MEM_DEVICE = 0, 1
+FP64, MIXED = 0, 1
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("n_verts", C.c_int), ("rest_pos", C.c_void_p), ("inv_mass", C.c_void_p),
+                ("n_dist", C.c_int), ("dist", C.c_void_p), ("n_tet", C.c_int),
+                ("tet", C.c_void_p), ("alpha", C.c_void_p)]
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("dt", C.c_double), ("gravity", C.c_double * 3), ("omega_x", C.c_double),
+        ("max_iter", C.c_int), ("eps_b", C.c_double), ("pcg_rtol", C.c_double),
+        ("pcg_maxiter", C.c_int), ("setup_interval", C.c_int), ("nk_sweeps", C.c_int),
+        ("nk_omega", C.c_double), ("theta_s", C.c_double), ("smoother", C.c_int),
+        ("smooth_sweeps", C.c_int), ("lambda_min_est", C.c_double), ("power_iters", C.c_int),
+        ("power_safety", C.c_double), ("coarse_max", C.c_int), ("max_levels", C.c_int),
+        ("precision", C.c_int),
+        ("seed_nk", C.c_uint64), ("seed_agg", C.c_uint64), ("seed_col", C.c_uint64),
+        ("seed_pow", C.c_uint64),
+    ]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("pcg_iters", C.c_int), ("status", C.c_int), ("bnorm", C.c_double),
+                ("rel_res", C.c_double), ("true_rel_res", C.c_double)]
+
+    def as_dict(self) -> Dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Stats(C.Structure):
+    _fields_ = [("levels", C.c_int), ("n_setups", C.c_int), ("global_iters", C.c_int64),
+                ("op_complexity", C.c_double), ("device_bytes", C.c_size_t),
+                ("ms_setup", C.c_double), ("ms_galerkin", C.c_double), ("ms_solve", C.c_double),
+                ("ms_other", C.c_double)]
+
+    def as_dict(self) -> Dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LevelInfo(C.Structure):
+    _fields_ = [("n", C.c_int), ("nnz", C.c_int64), ("n_agg", C.c_int), ("n_colors", C.c_int),
+                ("lmax", C.c_double), ("omega", C.c_double)]
+
+    def as_dict(self) -> Dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# every symbol the header declares, with (restype, argtypes)
+_vp, _i, _i64 = C.c_void_p, C.c_int, C.c_int64
+SIGNATURES = {
+    "mgpbd_default_params": (_i, [C.POINTER(Params)]),
+    "mgpbd_create": (_i, [C.POINTER(MeshDesc), C.POINTER(Params), _vp, C.POINTER(_vp)]),
+    "mgpbd_destroy": (None, [_vp]),
+    "mgpbd_set_state": (_i, [_vp, _vp, _vp, _i]),
+    "mgpbd_get_state": (_i, [_vp, _vp, _vp, _i]),
+    "mgpbd_step": (_i, [_vp, _i]),
+    "mgpbd_begin_frame": (_i, [_vp]),
+    "mgpbd_iterate": (_i, [_vp, C.POINTER(SolveInfo)]),
+    "mgpbd_end_frame": (_i, [_vp]),
+    "mgpbd_eval_assemble": (_i, [_vp]),
+    "mgpbd_setup": (_i, [_vp]),
+    "mgpbd_prepare_solve": (_i, [_vp]),
+    "mgpbd_solve": (_i, [_vp, _vp, _vp, C.POINTER(SolveInfo)]),
+    "mgpbd_vcycle": (_i, [_vp, _vp, _vp]),
+    "mgpbd_stats": (_i, [_vp, C.POINTER(Stats)]),
+    "mgpbd_sizes": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i64)]),
+    "mgpbd_level_info_get": (_i, [_vp, _i, C.POINTER(LevelInfo)]),
+    "mgpbd_get_matrix": (_i, [_vp, _i, _vp, _vp, _vp, _i]),
+    "mgpbd_get_map": (_i, [_vp, _vp, _i]),
+    "mgpbd_get_incidence": (_i, [_vp, _vp, _vp, _i]),
+    "mgpbd_get_aggregates": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i]),
+    "mgpbd_get_colors": (_i, [_vp, _i, _vp, _i]),
+    "mgpbd_get_constraints": (_i, [_vp, _vp, _vp, _vp, _vp, _i]),
+    "mgpbd_get_lambda": (_i, [_vp, _vp, _vp, _i]),
+    "mgpbd_profile": (_i, [_vp, _i]),
+    "mgpbd_profile_read": (_i, [_vp, C.POINTER(C.c_double), C.POINTER(_i64),
+                                C.POINTER(C.c_double)]),
+    "mgpbd_launch_count": (C.c_ulonglong, []),
+    "mgpbd_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmgpbd.so; raises if it is missing (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with paper_2505_13390_gb300.build.build()")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def launch_count() -> int:
+    return int(load().mgpbd_launch_count())
+
+
+class MgpbdError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = load().mgpbd_last_error().decode(errors="replace")
+        super().__init__(f"{what}: status {status}: {msg}")
+        self.status = status
+
+
+def _check(status: int, what: str) -> int:
+    if status < 0:
+        raise MgpbdError(status, what)
+    return status
+
+
+def make_params(d: Dict) -> Params:
+    p = Params()
+    load().mgpbd_default_params(C.byref(p))
+    for k, _ in Params._fields_:
+        if k in d:
+            if k == "gravity":
+                p.gravity = (C.c_double * 3)(*d[k])
+            else:
+                setattr(p, k, d[k])
+    return p
+
+
+def _ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+class Solver:
+    """One MGPBD instance resident on the current CUDA device."""
+
+    def __init__(self, mesh, params: Dict, stream=None):
+        import torch
+
+        L = load()
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.N, self.E, self.T = mesh.n_verts, mesh.n_dist, mesh.n_tet
+        self.m = self.E + self.T
+        keep = [np.ascontiguousarray(mesh.rest_pos, np.float64),
+                np.ascontiguousarray(mesh.inv_mass, np.float64),
+                np.ascontiguousarray(mesh.dist, np.int32).reshape(-1, 2),
+                np.ascontiguousarray(mesh.tet, np.int32).reshape(-1, 4),
+                np.ascontiguousarray(mesh.alpha, np.float64)]
+        md = MeshDesc(self.N, _ptr(keep[0]), _ptr(keep[1]), self.E, _ptr(keep[2]), self.T,
+                      _ptr(keep[3]), _ptr(keep[4]))
+        self.params = dict(params)
+        self._p = make_params(params)
+        h = C.c_void_p()
+        _check(L.mgpbd_create(C.byref(md), C.byref(self._p), C.c_void_p(self.stream.cuda_stream),
+                              C.byref(h)), "mgpbd_create")
+        self.h = h
+        self.set_state(mesh.x0, mesh.v0)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().mgpbd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- state ----------------------------------------------------------
+    def set_state(self, x, v):
+        """x, v: numpy arrays (host) or CUDA tensors (device), [N, 3] float64."""
+        if hasattr(x, "data_ptr") or hasattr(v, "data_ptr"):
+            _check(load().mgpbd_set_state(self.h, _ptr(x), _ptr(v), MEM_DEVICE), "set_state")
+        else:
+            x = None if x is None else np.ascontiguousarray(x, np.float64)
+            v = None if v is None else np.ascontiguousarray(v, np.float64)
+            _check(load().mgpbd_set_state(self.h, _ptr(x), _ptr(v), MEM_HOST), "set_state")
+
+    def get_state(self):
+        x = np.zeros((self.N, 3))
+        v = np.zeros((self.N, 3))
+        _check(load().mgpbd_get_state(self.h, _ptr(x), _ptr(v), MEM_HOST), "get_state")
+        return x, v
+
+    def get_state_device(self, x, v=None):
+        _check(load().mgpbd_get_state(self.h, _ptr(x), _ptr(v), MEM_DEVICE), "get_state")
+
+    # ---- Algorithm 1 ----------------------------------------------------
+    def step(self, n_frames: int) -> int:
+        return _check(load().mgpbd_step(self.h, n_frames), "step")
+
+    def begin_frame(self):
+        _check(load().mgpbd_begin_frame(self.h), "begin_frame")
+
+    def end_frame(self):
+        _check(load().mgpbd_end_frame(self.h), "end_frame")
+
+    def iterate(self) -> Dict:
+        inf = SolveInfo()
+        st = _check(load().mgpbd_iterate(self.h, C.byref(inf)), "iterate")
+        d = inf.as_dict()
+        d["ret"] = st
+        return d
+
+    def eval_assemble(self):
+        _check(load().mgpbd_eval_assemble(self.h), "eval_assemble")
+
+    def setup(self):
+        _check(load().mgpbd_setup(self.h), "setup")
+
+    def prepare_solve(self):
+        _check(load().mgpbd_prepare_solve(self.h), "prepare_solve")
+
+    def solve(self, b):
+        """b: CUDA float64 tensor [m]; returns (dlambda tensor, info dict)."""
+        torch = self.torch
+        x = torch.zeros(self.m, dtype=torch.float64, device=b.device)
+        inf = SolveInfo()
+        _check(load().mgpbd_solve(self.h, _ptr(b), _ptr(x), C.byref(inf)), "solve")
+        return x, inf.as_dict()
+
+    def vcycle(self, r):
+        torch = self.torch
+        z = torch.zeros(self.m, dtype=torch.float64, device=r.device)
+        _check(load().mgpbd_vcycle(self.h, _ptr(r), _ptr(z)), "vcycle")
+        return z
+
+    # ---- measurement ----------------------------------------------------
+    def profile(self, enable: bool):
+        _check(load().mgpbd_profile(self.h, 1 if enable else 0), "profile")
+
+    def profile_read(self) -> Dict:
+        ms, n, b = C.c_double(), C.c_int64(), C.c_double()
+        _check(load().mgpbd_profile_read(self.h, C.byref(ms), C.byref(n), C.byref(b)),
+               "profile_read")
+        return {"total_ms": ms.value, "launches": n.value, "bytes_per_launch": b.value}
+
+    # ---- inspection -----------------------------------------------------
+    def stats(self) -> Dict:
+        s = Stats()
+        _check(load().mgpbd_stats(self.h, C.byref(s)), "stats")
+        return s.as_dict()
+
+    def level_info(self, level: int) -> Dict:
+        li = LevelInfo()
+        _check(load().mgpbd_level_info_get(self.h, level, C.byref(li)), "level_info")
+        return li.as_dict()
+
+    @property
+    def levels(self) -> int:
+        return self.stats()["levels"]
+
+    def matrix(self, level: int = 0):
+        li = self.level_info(level)
+        ptr = np.zeros(li["n"] + 1, np.int64)
+        col = np.zeros(li["nnz"], np.int32)
+        val = np.zeros(li["nnz"], np.float64)
+        _check(load().mgpbd_get_matrix(self.h, level, _ptr(ptr), _ptr(col), _ptr(val), MEM_HOST),
+               "get_matrix")
+        return ptr, col, val
+
+    def assembly_map(self):
+        nnz = C.c_int64()
+        load().mgpbd_sizes(self.h, None, None, C.byref(nnz))
+        m = np.zeros(nnz.value, np.uint16)
+        _check(load().mgpbd_get_map(self.h, _ptr(m), MEM_HOST), "get_map")
+        return m
+
+    def incidence(self):
+        vptr = np.zeros(self.N + 1, np.int64)
+        vrow = np.zeros(2 * self.E + 4 * self.T, np.int32)
+        _check(load().mgpbd_get_incidence(self.h, _ptr(vptr), _ptr(vrow), MEM_HOST), "incidence")
+        return vptr, vrow
+
+    def level_agg(self, level: int):
+        li = self.level_info(level)
+        n = li["n"]
+        agg = np.zeros(n, np.int32)
+        root = np.zeros(n, np.uint8)
+        P = np.zeros(n)
+        B = np.zeros(n)
+        _check(load().mgpbd_get_aggregates(self.h, level, _ptr(agg), _ptr(root), _ptr(P), _ptr(B),
+                                           MEM_HOST), "get_aggregates")
+        return li["n_agg"], agg, root, P, B
+
+    def level_color(self, level: int):
+        li = self.level_info(level)
+        c = np.zeros(li["n"], np.int32)
+        _check(load().mgpbd_get_colors(self.h, level, _ptr(c), MEM_HOST), "get_colors")
+        return li["n_colors"], c
+
+    def level_omega(self, level: int):
+        li = self.level_info(level)
+        return li["lmax"], li["omega"]
+
+    def constraints(self):
+        Cv = np.zeros(self.m)
+        b = np.zeros(self.m)
+        gd = np.zeros((self.E, 3))
+        gt = np.zeros((self.T, 4, 3))
+        _check(load().mgpbd_get_constraints(self.h, _ptr(Cv), _ptr(b), _ptr(gd), _ptr(gt),
+                                            MEM_HOST), "get_constraints")
+        return Cv, b, gd, gt
+
+    def lam(self):
+        lam = np.zeros(self.m)
+        dl = np.zeros(self.m)
+        _check(load().mgpbd_get_lambda(self.h, _ptr(lam), _ptr(dl), MEM_HOST), "get_lambda")
+        return lam, dl

@@ -1,0 +1,40 @@
+"""The C-ABI library builds, loads on a machine without a GPU, and exports
+every entry point include/mgpbd.h declares (no compute call is made here)."""
+import ctypes as C
+import os
+import re
+
+from paper_2505_13390_gb300 import build as B
+from paper_2505_13390_gb300 import mgpbd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    txt = open(os.path.join(ROOT, "include", "mgpbd.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return set(re.findall(r"\b(mgpbd_\w+)\s*\(", txt))
+
+
+def test_library_exports_every_declared_symbol():
+    path = B.build()
+    lib = C.CDLL(path)
+    names = declared()
+    assert len(names) >= 25
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert names == set(mgpbd.SIGNATURES), "binding and header disagree"
+
+
+def test_default_params_and_host_only_calls():
+    lib = mgpbd.load()
+    p = mgpbd.Params()
+    assert lib.mgpbd_default_params(C.byref(p)) == 0
+    assert (p.theta_s, p.smooth_sweeps, p.lambda_min_est, p.coarse_max) == (0.1, 2, 0.1, 400)
+    assert lib.mgpbd_default_params(None) == mgpbd.E_INVALID
+    # argument checks that return before any CUDA call
+    h = C.c_void_p()
+    assert lib.mgpbd_create(None, C.byref(p), None, C.byref(h)) == mgpbd.E_INVALID
+    assert not h.value
+    assert lib.mgpbd_step(None, 1) == mgpbd.E_INVALID
+    assert isinstance(lib.mgpbd_last_error(), bytes)

@@ -1,0 +1,208 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bit-exact: CSR pattern, assembly map, incidence, C / gradients / b, A values,
+near-kernel B, strength-driven aggregates and roots, P, coarse patterns and
+values from the canonical Galerkin product, colours.  Within tolerance:
+smoother weights (power method with a different summation order), the
+V-cycle, the PCG solution and the positions after whole iterations.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle.oracle import Oracle  # noqa: E402
+from paper_2505_13390_gb300.meshgen import cloth, default_params, hex_block, workload  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_13390_gb300 import mgpbd
+    mgpbd.load()
+    torch.cuda.set_device(0)
+
+
+def solver(mesh, params):
+    from paper_2505_13390_gb300.mgpbd import Solver
+    return Solver(mesh, params)
+
+
+CASES = {
+    "cloth8": lambda: (cloth(8, plane="xz", alpha=1e-6, pin="corners", noise=1e-3, seed=3),
+                       default_params(coarse_max=20, max_levels=4)),
+    "hex3": lambda: (hex_block(3, 2, 2, h=0.01, jitter=0.1, alpha=1e-7, pin="x0", seed=4),
+                     default_params(coarse_max=30, max_levels=4, omega_x=0.1)),
+    "cloth32": lambda: workload("cloth32"),
+    "beam40": lambda: workload("beam40"),
+    "block6": lambda: (hex_block(6, 5, 7, h=0.005, jitter=0.1, alpha=1e-10, pin="y0", seed=1),
+                       default_params(omega_x=0.1)),
+}
+
+
+def both(name, **over):
+    mesh, p = CASES[name]()
+    p = dict(p, **over)
+    return mesh, p, Oracle(mesh, p), solver(mesh, p)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_pattern_and_incidence_bit_exact(name):
+    mesh, p, o, g = both(name)
+    for a, b in zip(o.matrix(0)[:2], g.matrix(0)[:2]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(o.assembly_map(), g.assembly_map())
+    for a, b in zip(o.incidence(), g.incidence()):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_constraints_and_assembly_bit_exact(name):
+    mesh, p, o, g = both(name)
+    o.begin_frame()
+    g.begin_frame()
+    xo, vo = o.get_state()
+    xg, vg = g.get_state()
+    assert np.array_equal(xo, xg) and np.array_equal(vo, vg)
+    o.eval_assemble()
+    g.eval_assemble()
+    for a, b in zip(o.constraints(), g.constraints()):
+        assert np.array_equal(a, b)
+    assert np.array_equal(o.matrix(0)[2], g.matrix(0)[2])
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_setup_bit_exact(name):
+    mesh, p, o, g = both(name)
+    o.begin_frame()
+    g.begin_frame()
+    o.eval_assemble()
+    g.eval_assemble()
+    assert o.prepare_solve() == 0
+    g.prepare_solve()
+    assert o.levels == g.levels
+    for l in range(o.levels):
+        po, co, vo = o.matrix(l)
+        pg, cg, vg = g.matrix(l)
+        assert np.array_equal(po, pg) and np.array_equal(co, cg)
+        assert np.array_equal(vo, vg), f"level {l} values"
+        if l + 1 < o.levels:
+            nao, ago, ro, Po, Bo = o.level_agg(l)
+            nag, agg_, rg, Pg, Bg = g.level_agg(l)
+            assert nao == nag
+            assert np.array_equal(ro, rg)
+            assert np.array_equal(ago, agg_)
+            assert np.array_equal(Bo, Bg)
+            assert np.array_equal(Po, Pg)
+            nco, cco = o.level_color(l)
+            ncg, ccg = g.level_color(l)
+            assert nco == ncg and np.array_equal(cco, ccg)
+            lo, wo = o.level_omega(l)
+            lg, wg = g.level_omega(l)
+            assert lg == pytest.approx(lo, rel=1e-10) and wg == pytest.approx(wo, rel=1e-10)
+
+
+@pytest.mark.parametrize("name", ["cloth8", "hex3", "cloth32"])
+def test_vcycle_parity(name):
+    mesh, p, o, g = both(name)
+    o.begin_frame()
+    g.begin_frame()
+    o.eval_assemble()
+    g.eval_assemble()
+    o.prepare_solve()
+    g.prepare_solve()
+    r = np.random.default_rng(3).standard_normal(mesh.n_rows)
+    zo = o.vcycle(r)
+    zg = g.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
+    assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo)
+
+
+SOFT = {
+    "cloth8s": lambda: (cloth(8, plane="xz", alpha=1e-4, pin="corners", noise=1e-3, seed=3),
+                        default_params(coarse_max=20, max_levels=4)),
+    "hex3s": lambda: (hex_block(3, 2, 2, h=0.01, jitter=0.1, alpha=1e-4, pin="x0", seed=4),
+                      default_params(coarse_max=30, max_levels=4, omega_x=0.1)),
+}
+CASES.update(SOFT)
+
+
+@pytest.mark.parametrize("name", ["cloth8s", "hex3s"])
+def test_solve_parity(name):
+    """Moderate cond(A): same iteration count (+-1) and solutions within 1e-8."""
+    mesh, p, o, g = both(name, pcg_rtol=1e-10, pcg_maxiter=1000)
+    o.begin_frame()
+    g.begin_frame()
+    o.eval_assemble()
+    g.eval_assemble()
+    o.prepare_solve()
+    g.prepare_solve()
+    b = np.random.default_rng(4).standard_normal(mesh.n_rows)
+    xo, io = o.solve(b)
+    xg, ig = g.solve(torch.tensor(b, device="cuda"))
+    xg = xg.cpu().numpy()
+    assert ig["status"] == io["status"] == 0
+    assert abs(ig["pcg_iters"] - io["pcg_iters"]) <= 1
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+def test_solve_stiff_true_residual():
+    """cond(A) ~ 1e8: CG iterates drift apart by rounding order, so compare what
+    is unique -- both solutions reach the tolerance in the true FP64 residual
+    and agree to cond * rtol."""
+    mesh, p, o, g = both("hex3", pcg_rtol=1e-10, pcg_maxiter=2000)
+    for s in (o, g):
+        s.begin_frame()
+        s.eval_assemble()
+        s.prepare_solve()
+    b = np.random.default_rng(4).standard_normal(mesh.n_rows)
+    xo, io = o.solve(b)
+    xg, ig = g.solve(torch.tensor(b, device="cuda"))
+    xg = xg.cpu().numpy()
+    assert ig["status"] == io["status"] == 0
+    assert ig["true_rel_res"] <= 1e-8 and io["true_rel_res"] <= 1e-8
+    assert abs(ig["pcg_iters"] - io["pcg_iters"]) <= 0.1 * io["pcg_iters"]
+    assert np.linalg.norm(xg - xo) <= 1e-5 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("name,iters", [("cloth8", 6), ("hex3", 6), ("cloth32", 4), ("block6", 3)])
+def test_iterations_parity_fp64(name, iters):
+    mesh, p, o, g = both(name, pcg_maxiter=40)
+    o.begin_frame()
+    g.begin_frame()
+    scale = np.abs(mesh.rest_pos).max() + 1e-3
+    for it in range(iters):
+        do = o.iterate()
+        dg = g.iterate()
+        assert do["ret"] >= 0 and dg["ret"] >= 0
+        assert dg["bnorm"] == pytest.approx(do["bnorm"], rel=1e-9, abs=1e-300)
+        xo, _ = o.get_state()
+        xg, _ = g.get_state()
+        assert np.abs(xg - xo).max() <= 1e-9 * scale, f"iteration {it}"
+    o.end_frame()
+    g.end_frame()
+    _, vo = o.get_state()
+    _, vg = g.get_state()
+    assert np.abs(vg - vo).max() <= 1e-9 * scale / p["dt"]
+
+
+def test_empty_and_single_constraint():
+    from paper_2505_13390_gb300.meshgen import Mesh
+    rest = np.array([[0, 0, 0], [1, 0, 0]], float)
+    x0 = np.array([[0, 0, 0], [1.3, 0.1, -0.2]], float)
+    one = Mesh("one", rest, np.array([0.5, 2.0]), np.array([[0, 1]], np.int32),
+               np.zeros((0, 4), np.int32), np.array([1e-3]), x0, np.zeros((2, 3)))
+    p = default_params(gravity=(0.0, 0.0, 0.0), omega_x=1.0, max_iter=1)
+    o, g = Oracle(one, p), solver(one, p)
+    o.begin_frame()
+    g.begin_frame()
+    do, dg = o.iterate(), g.iterate()
+    assert dg["pcg_iters"] == do["pcg_iters"] == 1
+    assert np.allclose(g.lam()[1], o.lam()[1], rtol=1e-14, atol=0)
+    empty = Mesh("e", rest, np.ones(2), np.zeros((0, 2), np.int32), np.zeros((0, 4), np.int32),
+                 np.zeros(0), rest.copy(), np.zeros((2, 3)))
+    o, g = Oracle(empty, p), solver(empty, p)
+    assert o.step(2)[0] == 0 and g.step(2) >= 0
+    assert np.array_equal(o.get_state()[0], g.get_state()[0])
