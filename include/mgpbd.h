@@ -73,7 +73,7 @@ typedef struct {
   int max_iter;         /* global iterations per frame (Alg. 1) */
   double eps_b;         /* stop the frame when |b| < eps_b (0 disables) */
   double pcg_rtol;      /* PCG stop: |r|/|b| <= pcg_rtol */
-  int pcg_maxiter;      /* PCG iteration cap */
+  int pcg_maxiter;      /* PCG iteration cap (a safeguard; default 20000) */
   int setup_interval;   /* lazy setup every k global iterations (Sec. 4.2) */
   int nk_sweeps;        /* near-kernel Jacobi sweeps on A x = 0 (Sec. 4.3) */
   double nk_omega;      /* their weight */
@@ -86,6 +86,9 @@ typedef struct {
   int coarse_max;       /* stop coarsening below this many rows (Fig. 2) */
   int max_levels;       /* hard cap on the number of levels */
   int precision;        /* MGPBD_FP64 or MGPBD_MIXED */
+  int backtrack;        /* 0: x += omega_x dx; k > 0: start at omega_x and halve omega
+                           while the dual residual |b| does not decrease, at most k
+                           times (the paper's backtracking option, Sec. 4) */
   uint64_t seed_nk, seed_agg, seed_col, seed_pow;
 } mgpbd_params;
 
@@ -95,6 +98,8 @@ typedef struct {
   double bnorm;         /* |b|_2 of the solved system */
   double rel_res;       /* recursive |r|/|b| at exit */
   double true_rel_res;  /* |b - A dlambda| / |b| recomputed in FP64 */
+  double omega;         /* relaxation used for x (after backtracking) */
+  double bnorm_after;   /* |b| at the updated state (backtracking only, else -1) */
 } mgpbd_solve_info;
 
 typedef struct {
@@ -190,7 +195,11 @@ mgpbd_status mgpbd_get_incidence(mgpbd_handle_t *h, int64_t *vptr, int32_t *vrow
 /* aggregates, MIS-2 roots, P values and near-kernel B of level `level` */
 mgpbd_status mgpbd_get_aggregates(mgpbd_handle_t *h, int level, int32_t *agg, uint8_t *root,
                                   double *P, double *B, int mem);
+/* multicolour ordering of each level (Jones-Plassmann, used by the Gauss-Seidel
+ * smoother); computed at setup when the smoother needs it or when
+ * mgpbd_set_colouring(h, 1) was called before the setup */
 mgpbd_status mgpbd_get_colors(mgpbd_handle_t *h, int level, int32_t *color, int mem);
+mgpbd_status mgpbd_set_colouring(mgpbd_handle_t *h, int enable);
 /* C [m], b [m], distance gradients n [n_dist*3], tet gradients [n_tet*12] */
 mgpbd_status mgpbd_get_constraints(mgpbd_handle_t *h, double *C, double *b, double *gd,
                                    double *gt, int mem);

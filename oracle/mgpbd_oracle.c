@@ -68,6 +68,7 @@ typedef struct {
   double power_safety;
   int coarse_max;
   int max_levels;
+  int backtrack;  /* 0: fixed omega_x; k > 0: halve omega up to k times (Sec. 4) */
   uint64_t seed_nk, seed_agg, seed_col, seed_pow;
 } orc_params;
 
@@ -101,6 +102,8 @@ typedef struct {
   double bnorm;
   double rel_res;      /* recursive residual at exit */
   double true_rel_res; /* ||b - A dl|| / ||b|| in FP64 */
+  double omega;        /* position relaxation used by the update */
+  double bnorm_after;  /* |b| at the updated x and lambda (backtracking only) */
 } orc_solve_info;
 
 typedef struct {
@@ -109,7 +112,7 @@ typedef struct {
   int32_t *edge, *tet;
   orc_params p;
   double *x, *v, *xold, *lambda;
-  double *C, *b, *gd, *gt, *dl;
+  double *C, *b, *gd, *gt, *dl, *dx, *xbak;
   orc_csr A;
   uint16_t *map;
   int64_t *vptr;
@@ -410,11 +413,14 @@ static uint8_t *strength(const orc_csr *A, double theta) {
 }
 
 /* Aggregation (Sec. 4.1, reading: deterministic MIS-2 aggregation).
-   Roots: greedy distance-2 independent set of the strength graph, visiting
-   rows by decreasing priority h64(key(seed_agg, l, i)).  Aggregate ids are the
-   roots in ascending row order.  Pass 1: strong neighbours of a root join it.
-   Pass 2: every other row joins the aggregate of the pass-1 member among its
-   strong neighbours with the largest |A_ij| (ties: smaller aggregate id, then
+   Rows without any strong off-diagonal are "left alone": they get no
+   aggregate (agg = -1, a zero row of P) and are handled by the smoother only.
+   Roots: greedy distance-2 independent set of the strength graph over the
+   other rows, visiting them by decreasing priority h64(key(seed_agg, l, i)).
+   Aggregate ids are the roots in ascending row order.  Pass 1: strong
+   neighbours of a root join it.  Pass 2: every other row with a strong
+   neighbour joins the aggregate of the pass-1 member among its strong
+   neighbours with the largest |A_ij| (ties: smaller aggregate id, then
    smaller neighbour index) -- "assign them to the neighbour aggregate with
    the strongest connection". */
 typedef struct { uint64_t pri; int32_t i; } orc_pri;
@@ -432,7 +438,14 @@ static int aggregate(const orc_csr *A, const uint8_t *S, uint64_t seed, int l,
   for (int i = 0; i < n; ++i) { ord[i].pri = h64(hkey(seed, l, i)); ord[i].i = i; }
   qsort(ord, (size_t)n, sizeof(orc_pri), cmp_pri_desc);
   uint8_t *blocked = (uint8_t *)xcalloc((size_t)n, 1);
+  uint8_t *isolated = (uint8_t *)xcalloc((size_t)n, 1);
   memset(root, 0, (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    int any = 0;
+    for (int64_t k = A->ptr[i]; k < A->ptr[i + 1] - 1; ++k) any |= S[k];
+    isolated[i] = !any;
+    blocked[i] = isolated[i];
+  }
   for (int q = 0; q < n; ++q) {
     int u = ord[q].i;
     if (blocked[u]) continue;
@@ -460,6 +473,7 @@ static int aggregate(const orc_csr *A, const uint8_t *S, uint64_t seed, int l,
   /* pass 2 (reads pass-1 state only) */
   for (int i = 0; i < n; ++i) {
     if (p1[i] >= 0) { agg[i] = p1[i]; continue; }
+    if (isolated[i]) { agg[i] = -1; continue; }
     double best = -1.0; int ba = -1, bw = -1;
     for (int64_t k = A->ptr[i]; k < A->ptr[i + 1] - 1; ++k) {
       if (!S[k]) continue;
@@ -472,7 +486,9 @@ static int aggregate(const orc_csr *A, const uint8_t *S, uint64_t seed, int l,
     agg[i] = ba; /* >= 0 by maximality of the distance-2 independent set */
   }
   free(p1);
-  for (int i = 0; i < n; ++i) if (agg[i] < 0) return -1;
+  for (int i = 0; i < n; ++i)
+    if (agg[i] < 0 && !isolated[i]) { free(isolated); return -1; }
+  free(isolated);
   return na;
 }
 
@@ -501,12 +517,12 @@ static void inject(orc_level *L, orc_level *Lc) {
   int n = L->A.n, na = L->n_agg;
   L->mptr = (int64_t *)xcalloc((size_t)na + 1, sizeof(int64_t));
   L->mrow = (int32_t *)xcalloc((size_t)n, sizeof(int32_t));
-  for (int i = 0; i < n; ++i) L->mptr[L->agg[i] + 1]++;
+  for (int i = 0; i < n; ++i) if (L->agg[i] >= 0) L->mptr[L->agg[i] + 1]++;
   for (int a = 0; a < na; ++a) L->mptr[a + 1] += L->mptr[a];
   int64_t *f = (int64_t *)xcalloc((size_t)na, sizeof(int64_t));
-  for (int i = 0; i < n; ++i) L->mrow[L->mptr[L->agg[i]] + f[L->agg[i]]++] = i;
+  for (int i = 0; i < n; ++i) if (L->agg[i] >= 0) L->mrow[L->mptr[L->agg[i]] + f[L->agg[i]]++] = i;
   free(f);
-  L->P = (double *)xcalloc((size_t)n, sizeof(double));
+  L->P = (double *)xcalloc((size_t)n, sizeof(double)); /* 0 on left-alone rows */
   Lc->B = (double *)xcalloc((size_t)na, sizeof(double));
   for (int a = 0; a < na; ++a) {
     double acc = 0.0;
@@ -525,7 +541,8 @@ static void inject(orc_level *L, orc_level *Lc) {
 }
 
 /* Coarse pattern of P^T A P (eq. 6): row a holds every aggregate b reached
-   from a member row of a; off-diagonals ascending, diagonal last. */
+   from a member row of a (left-alone columns have P_j = 0 and add nothing);
+   off-diagonals ascending, diagonal last. */
 static int cmp_i32c(const void *a, const void *b) { return cmp_i32(a, b); }
 
 static void galerkin_pattern(const orc_level *L, orc_csr *Ac) {
@@ -540,7 +557,7 @@ static void galerkin_pattern(const orc_level *L, orc_csr *Ac) {
       int i = L->mrow[q];
       for (int64_t k = L->A.ptr[i]; k < L->A.ptr[i + 1]; ++k) {
         int b = L->agg[L->A.col[k]];
-        if (mark[b] != a) { mark[b] = a; ++cnt; }
+        if (b >= 0 && mark[b] != a) { mark[b] = a; ++cnt; }
       }
     }
     Ac->ptr[a + 1] = Ac->ptr[a] + cnt;
@@ -556,7 +573,7 @@ static void galerkin_pattern(const orc_level *L, orc_csr *Ac) {
       int i = L->mrow[q];
       for (int64_t k = L->A.ptr[i]; k < L->A.ptr[i + 1]; ++k) {
         int b = L->agg[L->A.col[k]];
-        if (b != a && mark[b] != a) { mark[b] = a; Ac->col[base + cnt++] = b; }
+        if (b >= 0 && b != a && mark[b] != a) { mark[b] = a; Ac->col[base + cnt++] = b; }
       }
     }
     qsort(Ac->col + base, (size_t)cnt, sizeof(int32_t), cmp_i32c);
@@ -577,8 +594,9 @@ static int64_t find_col(const orc_csr *A, int a, int b) {
 
 /* Galerkin values A_{l+1} = P^T A_l P (eq. 6), canonical order:
    entry (a, b) with b >= a sums, over member rows i of a ascending and row
-   i's storage order, acc = fma(P_i * A_ij, P_j, acc) for agg[j] == b;
-   entries with b < a are copied from (b, a), so A_{l+1} is exactly symmetric. */
+   i's storage order, acc = fma(P_i * A_ij, P_j, acc) for agg[j] == b (rows
+   left alone have no aggregate and are skipped); entries with b < a are
+   copied from (b, a), so A_{l+1} is exactly symmetric. */
 static void galerkin_values(const orc_level *L, orc_csr *Ac) {
   int na = L->n_agg;
   double *acc = (double *)xcalloc((size_t)na, sizeof(double));
@@ -727,8 +745,8 @@ static int setup(orc *o) {
     L->root = (uint8_t *)xcalloc((size_t)n, 1);
     int na = aggregate(&L->A, S, o->p.seed_agg, l, L->agg, L->root);
     free(S);
-    if (na <= 0) return ORC_E_SETUP;
-    if (na == n) { /* no coarsening: stop here */
+    if (na < 0) return ORC_E_SETUP;
+    if (na == 0 || na == n) { /* nothing to coarsen: stop here */
       free(L->agg); free(L->root); L->agg = NULL; L->root = NULL;
       break;
     }
@@ -812,7 +830,8 @@ static void vcycle_level(orc *o, int l) {
     Lc->b[a] = acc;
   }
   vcycle_level(o, l + 1);
-  for (int i = 0; i < n; ++i) L->x[i] = fma(L->P[i], Lc->x[L->agg[i]], L->x[i]);
+  for (int i = 0; i < n; ++i)
+    if (L->agg[i] >= 0) L->x[i] = fma(L->P[i], Lc->x[L->agg[i]], L->x[i]);
   smooth(o, L, L->x, L->b, L->t, 1);
 }
 
@@ -889,9 +908,8 @@ void orc_end_frame(orc *o) {
   for (int64_t q = 0; q < 3 * (int64_t)o->N; ++q) o->v[q] = (o->x[q] - o->xold[q]) / o->p.dt;
 }
 
-/* eq. 5: dx_v = w_v * sum_{j incident to v, ascending} fma(g_{j,v}, dl_j, .);
-   lambda += dl; x_v = fma(omega_x, dx_v, x_v). */
-static void update_positions(orc *o) {
+/* eq. 5: dx_v = w_v * sum_{j incident to v, ascending} fma(g_{j,v}, dl_j, .) */
+static void position_correction(orc *o) {
   int32_t vv[4];
   for (int v = 0; v < o->N; ++v) {
     double acc[3] = {0.0, 0.0, 0.0};
@@ -903,13 +921,37 @@ static void update_positions(orc *o) {
       row_grad(o, j, s, g);
       for (int k = 0; k < 3; ++k) acc[k] = fma(g[k], o->dl[j], acc[k]);
     }
-    double *x = o->x + 3 * (int64_t)v;
-    for (int k = 0; k < 3; ++k) {
-      double dx = o->w[v] * acc[k];
-      x[k] = fma(o->p.omega_x, dx, x[k]);
-    }
+    for (int k = 0; k < 3; ++k) o->dx[3 * (int64_t)v + k] = o->w[v] * acc[k];
   }
+}
+
+/* Alg. 1 update: lambda += dl; x = fma(omega, dx, x).  With backtracking
+   (Sec. 4: omega "halves when the residual increases") the step starts at
+   omega_x and halves while the dual residual |b| = |-C - alpha~ lambda| at
+   the new x and lambda is not below the current one, at most `backtrack`
+   times; the last trial is kept. */
+static void update_positions(orc *o, orc_solve_info *info) {
+  position_correction(o);
   for (int j = 0; j < o->m; ++j) o->lambda[j] = o->lambda[j] + o->dl[j];
+  int64_t n3 = 3 * (int64_t)o->N;
+  double om = o->p.omega_x;
+  if (o->p.backtrack <= 0) {
+    for (int64_t q = 0; q < n3; ++q) o->x[q] = fma(om, o->dx[q], o->x[q]);
+    info->omega = om;
+    info->bnorm_after = -1.0;
+    return;
+  }
+  memcpy(o->xbak, o->x, sizeof(double) * (size_t)n3);
+  double nb = 0.0;
+  for (int t = 0; t <= o->p.backtrack; ++t) {
+    for (int64_t q = 0; q < n3; ++q) o->x[q] = fma(om, o->dx[q], o->xbak[q]);
+    eval_constraints(o);
+    nb = sqrt(dot(o->m, o->b, o->b));
+    if (nb < info->bnorm || t == o->p.backtrack) break;
+    om = om * 0.5;
+  }
+  info->omega = om;
+  info->bnorm_after = nb;
 }
 
 /* C, gradients, A and b at the current positions */
@@ -942,10 +984,10 @@ int orc_iterate(orc *o, orc_solve_info *info) {
   st = cholesky(o);
   if (st) return st;
   st = pcg(o, o->b, o->dl, info);
-  o->last = *info;
   o->it_global++;
-  if (st < 0) return st;
-  update_positions(o);
+  if (st < 0) { o->last = *info; return st; }
+  update_positions(o, info);
+  o->last = *info;
   double bn = info->bnorm;
   return bn < o->p.eps_b ? 1 : 0;
 }
@@ -979,7 +1021,7 @@ void orc_destroy(orc *o) {
   if (!o) return;
   free(o->rest); free(o->w); free(o->alpha); free(o->alpha_t); free(o->L0); free(o->V0);
   free(o->edge); free(o->tet); free(o->x); free(o->v); free(o->xold); free(o->lambda);
-  free(o->C); free(o->b); free(o->gd); free(o->gt); free(o->dl);
+  free(o->C); free(o->b); free(o->gd); free(o->gt); free(o->dl); free(o->dx); free(o->xbak);
   csr_free(&o->A);
   o->lev[0].A.ptr = NULL; o->lev[0].A.col = NULL; o->lev[0].A.val = NULL;
   for (int l = 0; l < ORC_MAXL; ++l) level_free(&o->lev[l]);
@@ -1012,6 +1054,8 @@ orc *orc_create(int N, const double *rest, const double *inv_mass, int E, const 
   o->C = (double *)xcalloc((size_t)m, sizeof(double));
   o->b = (double *)xcalloc((size_t)m, sizeof(double));
   o->dl = (double *)xcalloc((size_t)m, sizeof(double));
+  o->dx = (double *)xcalloc(3 * (size_t)N, sizeof(double));
+  o->xbak = (double *)xcalloc(3 * (size_t)N, sizeof(double));
   o->gd = (double *)xcalloc(3 * (size_t)E, sizeof(double));
   o->gt = (double *)xcalloc(12 * (size_t)T, sizeof(double));
   o->pr = (double *)xcalloc((size_t)m, sizeof(double));

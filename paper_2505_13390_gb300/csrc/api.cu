@@ -138,7 +138,7 @@ static mgpbd_status check_params(const mgpbd_params *p) {
   if (!(p->dt > 0.0) || p->max_iter < 0 || p->pcg_maxiter < 1 || p->nk_sweeps < 0 ||
       p->smooth_sweeps < 1 || p->power_iters < 1 || p->coarse_max < 1 || p->max_levels < 1 ||
       p->max_levels > kMaxLevels || (p->precision != MGPBD_FP64 && p->precision != MGPBD_MIXED) ||
-      (p->smoother != MGPBD_SMOOTH_JACOBI) || !(p->theta_s >= 0.0) ||
+      (p->smoother != MGPBD_SMOOTH_JACOBI) || !(p->theta_s >= 0.0) || p->backtrack < 0 ||
       !(p->pcg_rtol >= 0.0) || !(p->power_safety > 0.0)) {
     set_error("invalid mgpbd_params (or unsupported smoother on this build)");
     return MGPBD_E_INVALID;
@@ -233,6 +233,8 @@ static mgpbd_status create(const mgpbd_mesh_desc *md, const mgpbd_params *p, voi
   CK(alloc_n(h->arena, &h->C, (size_t)m));
   CK(alloc_n(h->arena, &h->b, (size_t)m));
   CK(alloc_n(h->arena, &h->dl, (size_t)m));
+  CK(alloc_n(h->arena, &h->dx, 3 * (size_t)N));
+  CK(alloc_n(h->arena, &h->xbak, 3 * (size_t)N));
   CK(alloc_n(h->arena, &h->gd, 3 * (size_t)E));
   CK(alloc_n(h->arena, &h->gt, 12 * (size_t)T));
   CK(alloc_n(h->arena, &h->pr, (size_t)m));
@@ -318,11 +320,15 @@ static mgpbd_status iterate(Handle *h, mgpbd_solve_info *info) {
   MG_TRY(coarsest_factor(h));
   mgpbd_solve_info inf{};
   mgpbd_status st = pcg_solve(h, h->b, h->dl, &inf);
-  h->last = inf;
   h->it_global++;
+  if (st < 0) {
+    h->last = inf;
+    if (info) *info = inf;
+    return st;
+  }
+  MG_TRY(launch_update(h, &inf));
+  h->last = inf;
   if (info) *info = inf;
-  if (st < 0) return st;
-  MG_TRY(launch_update(h));
   return inf.status;
 }
 
@@ -349,7 +355,7 @@ mgpbd_status mgpbd_default_params(mgpbd_params *p) {
   p->max_iter = 20;
   p->eps_b = 0.0;
   p->pcg_rtol = 1e-6;
-  p->pcg_maxiter = 200;
+  p->pcg_maxiter = 20000;
   p->setup_interval = 400;
   p->nk_sweeps = 3;
   p->nk_omega = 2.0 / 3.0;
@@ -362,6 +368,7 @@ mgpbd_status mgpbd_default_params(mgpbd_params *p) {
   p->coarse_max = 400;
   p->max_levels = 8;
   p->precision = MGPBD_FP64;
+  p->backtrack = 0;
   p->seed_nk = 3;
   p->seed_agg = 4;
   p->seed_col = 5;
@@ -504,6 +511,13 @@ mgpbd_status mgpbd_stats(mgpbd_handle_t *hh, mgpbd_stats_t *s) {
   return MGPBD_OK;
 }
 
+mgpbd_status mgpbd_set_colouring(mgpbd_handle_t *hh, int enable) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  h->want_colors = enable != 0;
+  return MGPBD_OK;
+}
+
 mgpbd_status mgpbd_profile(mgpbd_handle_t *hh, int enable) {
   Handle *h = H(hh);
   if (!h) return MGPBD_E_INVALID;
@@ -600,7 +614,10 @@ mgpbd_status mgpbd_get_colors(mgpbd_handle_t *hh, int level, int32_t *color, int
   Handle *h = H(hh);
   if (!h || !h->have_setup || level < 0 || level >= h->L) return MGPBD_E_INVALID;
   const Level &L = h->lev[level];
-  if (!L.color) return MGPBD_E_INVALID;
+  if (!L.color || L.n_colors <= 0) {
+    set_error("no colouring: enable it with mgpbd_set_colouring before the setup");
+    return MGPBD_E_INVALID;
+  }
   return copy_out(h, color, L.color, sizeof(int32_t) * (size_t)L.n, mem);
 }
 

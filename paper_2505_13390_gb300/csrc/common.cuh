@@ -125,6 +125,7 @@ struct Handle {
   double *x = nullptr, *v = nullptr, *xold = nullptr, *lambda = nullptr;
   // per-iteration
   double *C = nullptr, *b = nullptr, *gd = nullptr, *gt = nullptr, *dl = nullptr;
+  double *dx = nullptr, *xbak = nullptr;  // position correction and backtracking base
   uint16_t *map = nullptr;
   uint8_t *S = nullptr;  // strength mask, sized for level 0 and reused per level
   // hierarchy
@@ -153,6 +154,7 @@ struct Handle {
   double ms_setup = 0, ms_galerkin = 0, ms_solve = 0, ms_other = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int last_pcg_iters = 0;
+  bool want_colors = false;  // colour every level at setup even for Jacobi
   mgpbd_solve_info last{};
   // optional event timing of the level-0 smoother sweeps (the dominant kernel)
   bool prof = false;
@@ -198,7 +200,7 @@ mgpbd_status launch_begin_frame(Handle *h);
 mgpbd_status launch_end_frame(Handle *h);
 mgpbd_status launch_eval(Handle *h);
 mgpbd_status launch_assemble(Handle *h);
-mgpbd_status launch_update(Handle *h);
+mgpbd_status launch_update(Handle *h, mgpbd_solve_info *info);
 
 // setup.cu
 mgpbd_status amg_setup(Handle *h);

@@ -284,12 +284,10 @@ mgpbd_status launch_assemble(Handle *h) {
 }
 
 // ---------------------------------------------------------------------------
-// eq. 5: dx_v = w_v * sum_{j incident to v, ascending} fma(g_{j,v}, dl_j, .);
-// x_v = fma(omega_x, dx_v, x_v).  Then lambda += dl.
-__global__ void k_update_x(int N, int E, const int32_t *edge, const int32_t *tet,
-                           const int64_t *vptr, const int32_t *vrow, const double *gd,
-                           const double *gt, const double *dl, const double *w, double omega_x,
-                           double *x) {
+// eq. 5: dx_v = w_v * sum_{j incident to v, ascending} fma(g_{j,v}, dl_j, .)
+__global__ void k_dx(int N, int E, const int32_t *edge, const int32_t *tet, const int64_t *vptr,
+                     const int32_t *vrow, const double *gd, const double *gt, const double *dl,
+                     const double *w, double *dx) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
     for (int64_t q = vptr[v]; q < vptr[v + 1]; ++q) {
@@ -309,11 +307,19 @@ __global__ void k_update_x(int N, int E, const int32_t *edge, const int32_t *tet
       acc2 = fma(g[2], d, acc2);
     }
     double wv = w[v];
-    double *xv = x + 3 * (int64_t)v;
-    xv[0] = fma(omega_x, wv * acc0, xv[0]);
-    xv[1] = fma(omega_x, wv * acc1, xv[1]);
-    xv[2] = fma(omega_x, wv * acc2, xv[2]);
+    double *o = dx + 3 * (int64_t)v;
+    o[0] = wv * acc0;
+    o[1] = wv * acc1;
+    o[2] = wv * acc2;
   }
+}
+
+// x = fma(omega, dx, base)   (base may alias x)
+__global__ void k_apply_x(int64_t n3, double omega, const double *dx, const double *base,
+                          double *x) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n3;
+       q += (int64_t)gridDim.x * blockDim.x)
+    x[q] = fma(omega, dx[q], base[q]);
 }
 
 __global__ void k_add(int64_t n, const double *a, double *y) {
@@ -322,14 +328,42 @@ __global__ void k_add(int64_t n, const double *a, double *y) {
     y[i] = y[i] + a[i];
 }
 
-mgpbd_status launch_update(Handle *h) {
+// Alg. 1 update: lambda += dl, x = fma(omega, dx, x).  With backtracking the
+// step starts at omega_x and halves while |b| at the new state is not below
+// the current |b|, at most `backtrack` times (the last trial is kept).
+mgpbd_status launch_update(Handle *h, mgpbd_solve_info *info) {
+  info->omega = h->p.omega_x;
+  info->bnorm_after = -1.0;
   if (h->m == 0) return MGPBD_OK;
-  k_update_x<<<blocks_for(h->N, 128), 128, 0, h->stream>>>(h->N, h->E, h->edge, h->tet, h->vptr,
-                                                          h->vrow, h->gd, h->gt, h->dl, h->w,
-                                                          h->p.omega_x, h->x);
-  MG_LAUNCH("k_update_x");
+  const int64_t n3 = 3 * (int64_t)h->N;
+  k_dx<<<blocks_for(h->N, 128), 128, 0, h->stream>>>(h->N, h->E, h->edge, h->tet, h->vptr,
+                                                    h->vrow, h->gd, h->gt, h->dl, h->w, h->dx);
+  MG_LAUNCH("k_dx");
   k_add<<<blocks_for(h->m, 256), 256, 0, h->stream>>>(h->m, h->dl, h->lambda);
   MG_LAUNCH("k_add");
+  double om = h->p.omega_x;
+  if (h->p.backtrack <= 0) {
+    k_apply_x<<<blocks_for(n3, 256), 256, 0, h->stream>>>(n3, om, h->dx, h->x, h->x);
+    MG_LAUNCH("k_apply_x");
+    return MGPBD_OK;
+  }
+  MG_CUDA(cudaMemcpyAsync(h->xbak, h->x, sizeof(double) * n3, cudaMemcpyDeviceToDevice,
+                          h->stream));
+  double *d_nb = h->partials + 4096 + 4;  // scratch scalar after the dot partials
+  double nb = 0.0;
+  for (int t = 0; t <= h->p.backtrack; ++t) {
+    k_apply_x<<<blocks_for(n3, 256), 256, 0, h->stream>>>(n3, om, h->dx, h->xbak, h->x);
+    MG_LAUNCH("k_apply_x");
+    MG_TRY(launch_eval(h));
+    MG_TRY(dot_dd(h, h->b, h->b, h->m, d_nb));
+    MG_CUDA(cudaMemcpyAsync(&nb, d_nb, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    nb = sqrt(nb);
+    if (nb < info->bnorm || t == h->p.backtrack) break;
+    om = om * 0.5;
+  }
+  info->omega = om;
+  info->bnorm_after = nb;
   return MGPBD_OK;
 }
 

@@ -4,8 +4,9 @@
 //   near-kernel  B_0: nk_sweeps weighted-Jacobi sweeps on A x = 0 from
 //                x0_i = u_i * max|A_ij| (Sec. 4.3), row sums in storage order
 //   filter       off-diagonal A_ij strong unless |A_ij| < theta_s sqrt(|A_ii||A_jj|)
-//   aggregate    deterministic MIS-2 rule: roots = greedy distance-2
-//                independent set of the strength graph in decreasing
+//   aggregate    deterministic MIS-2 rule; rows without a strong neighbour
+//                are left alone (no aggregate, zero row of P); roots = greedy
+//                distance-2 independent set of the strength graph in decreasing
 //                priority h64(key(seed_agg, l, i)), computed here by parallel
 //                rounds (a row becomes a root when it has the highest
 //                priority among undecided rows within distance 2); strong
@@ -112,19 +113,28 @@ __global__ void k_nk_sweep(int n, const int64_t *ptr, const int32_t *col, const 
 // ---------------------------------------------------------------------------
 // strength filter (Sec. 4.1)
 // ---------------------------------------------------------------------------
+// also initialises the MIS-2 state: rows without a strong off-diagonal are
+// left alone (state 2: never a root, no aggregate), the others undecided (0)
 __global__ void k_strength(int n, const int64_t *ptr, const int32_t *col, const double *val,
-                           double theta, uint8_t *S) {
+                           double theta, uint8_t *S, uint8_t *state) {
   WARP_LOOP(n) {
     int i = (int)row_;
     int64_t s0 = ptr[i], e = ptr[i + 1] - 1;
     double aii = fabs(val[e]);
+    int any = 0;
     for (int64_t k = s0 + lane; k < e; k += 32) {
       int j = col[k];
       double prod = aii * fabs(diag_at(ptr, val, j));
       double thr = theta * sqrt(prod);
-      S[k] = fabs(val[k]) >= thr ? 1 : 0;
+      uint8_t st = fabs(val[k]) >= thr ? 1 : 0;
+      S[k] = st;
+      any |= st;
     }
-    if (lane == 0) S[e] = 0;
+    any = __any_sync(0xffffffffu, any);
+    if (lane == 0) {
+      S[e] = 0;
+      state[i] = any ? 0 : 2;
+    }
   }
 }
 
@@ -246,7 +256,8 @@ __global__ void k_agg_pass1(int n, const int64_t *ptr, const int32_t *col, const
   }
 }
 
-// pass 2: strongest pass-1 neighbour; key (|A_ij| desc, aggregate asc, j asc)
+// pass 2: strongest pass-1 neighbour; key (|A_ij| desc, aggregate asc, j asc).
+// Rows without a strong neighbour stay alone (agg = -1).
 __global__ void k_agg_pass2(int n, const int64_t *ptr, const int32_t *col, const double *val,
                             const uint8_t *S, const int *p1, int32_t *agg, int *bad) {
   WARP_LOOP(n) {
@@ -257,10 +268,11 @@ __global__ void k_agg_pass2(int n, const int64_t *ptr, const int32_t *col, const
       continue;
     }
     unsigned long long bs = 0;
-    int ba = -1, bw = -1;
+    int ba = -1, bw = -1, strong = 0;
     int64_t s0 = ptr[i], e = ptr[i + 1] - 1;
     for (int64_t k = s0 + lane; k < e; k += 32) {
       if (!S[k]) continue;
+      strong = 1;
       int w = col[k];
       int a = p1[w];
       if (a < 0) continue;
@@ -282,9 +294,10 @@ __global__ void k_agg_pass2(int n, const int64_t *ptr, const int32_t *col, const
         bw = w2;
       }
     }
+    strong = __any_sync(0xffffffffu, strong);
     if (lane == 0) {
       agg[i] = ba;
-      if (ba < 0) atomicExch(bad, 1);
+      if (ba < 0 && strong) atomicExch(bad, 1);
     }
   }
 }
@@ -294,12 +307,13 @@ __global__ void k_agg_pass2(int n, const int64_t *ptr, const int32_t *col, const
 // ---------------------------------------------------------------------------
 __global__ void k_mem_count(int n, const int32_t *agg, unsigned long long *cnt) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    atomicAdd(&cnt[agg[i]], 1ull);
+    if (agg[i] >= 0) atomicAdd(&cnt[agg[i]], 1ull);
 }
 
 __global__ void k_mem_fill(int n, const int32_t *agg, const int64_t *mptr,
                            unsigned long long *fill, int32_t *tmp) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (agg[i] < 0) continue;
     unsigned long long pos = atomicAdd(&fill[agg[i]], 1ull);
     tmp[mptr[agg[i]] + (int64_t)pos] = i;
   }
@@ -388,7 +402,7 @@ __global__ void k_gal_pattern(int na, const int64_t *mptr, const int32_t *mrow,
       int i = mrow[q];
       for (int64_t k = ptr[i] + threadIdx.x; k < ptr[i + 1]; k += blockDim.x) {
         int b = agg[col[k]];
-        if (b != a && n_unique < kHashList) hash_insert(tab, b, &n_unique);
+        if (b >= 0 && b != a && n_unique < kHashList) hash_insert(tab, b, &n_unique);
       }
     }
     __syncthreads();
@@ -682,8 +696,6 @@ static mgpbd_status aggregate_level(Handle *h, int l) {
   Level &L = h->lev[l];
   const int n = L.n;
   const int th = 256;
-  k_strength<<<warp_blocks(n), th, 0, h->stream>>>(n, L.ptr, L.col, L.val, h->p.theta_s, h->S);
-  MG_LAUNCH("k_strength");
   // scratch: state u8 | e1 u8 | m1p u64 | m1i i32 | p1 i32 | flags i64 | ids i64 (n+1)
   size_t off_state = 0, off_e1 = (size_t)n, off_m1p = ((2 * (size_t)n + 15) / 16) * 16;
   size_t off_m1i = off_m1p + 8 * (size_t)n, off_p1 = off_m1i + 4 * (size_t)n;
@@ -695,7 +707,9 @@ static mgpbd_status aggregate_level(Handle *h, int l) {
   uint64_t *m1p = (uint64_t *)(base + off_m1p);
   int *m1i = (int *)(base + off_m1i), *p1 = (int *)(base + off_p1);
   int64_t *f64 = (int64_t *)(base + off_f), *ids = (int64_t *)(base + off_ids);
-  MG_CUDA(cudaMemsetAsync(state, 0, n, h->stream));
+  k_strength<<<warp_blocks(n), th, 0, h->stream>>>(n, L.ptr, L.col, L.val, h->p.theta_s, h->S,
+                                                   state);
+  MG_LAUNCH("k_strength");
   for (int round = 0;; ++round) {
     if (round > 100000) {
       set_error("MIS-2 did not terminate");
@@ -733,7 +747,7 @@ static mgpbd_status aggregate_level(Handle *h, int l) {
     set_error("aggregation left a row unassigned");
     return MGPBD_E_SETUP;
   }
-  if (na == n) return MGPBD_OK;  // no coarsening; caller stops here
+  if (na == 0 || na == n) return MGPBD_OK;  // nothing to coarsen; caller stops here
   // member lists
   unsigned long long *cnt = (unsigned long long *)f64;  // reuse (na <= n)
   MG_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * na, h->stream));
@@ -824,9 +838,10 @@ mgpbd_status amg_setup(Handle *h) {
     Level &L = h->lev[l];
     if (L.n < h->p.coarse_max || l == h->p.max_levels - 1 || l == kMaxLevels - 1) break;
     MG_TRY(aggregate_level(h, l));
-    if (L.n_agg == L.n) break;
+    if (L.n_agg == 0 || L.n_agg == L.n) break;
     MG_TRY(galerkin_pattern(h, l));
     Level &Lc = h->lev[l + 1];
+    MG_CUDA(cudaMemsetAsync(L.P, 0, sizeof(double) * L.n, h->stream));  // left-alone rows
     k_inject<<<warp_blocks(L.n_agg), th, 0, h->stream>>>(L.n_agg, L.mptr, L.mrow, L.B, L.P,
                                                          Lc.B);
     MG_LAUNCH("k_inject");
@@ -843,7 +858,9 @@ mgpbd_status amg_setup(Handle *h) {
     return MGPBD_E_SETUP;
   }
   for (int q = 0; q + 1 < h->L; ++q) {
-    MG_TRY(colour_level(h, q));
+    // the multicolour ordering is needed by the Gauss-Seidel smoother only
+    if (h->p.smoother == MGPBD_SMOOTH_MCGS || h->want_colors) MG_TRY(colour_level(h, q));
+    else h->lev[q].n_colors = 0;
     MG_TRY(power_method(h, q));
   }
   h->lev[h->L - 1].n_colors = 0;

@@ -11,9 +11,9 @@
 // chunks and polls the flag between chunks.
 //
 // Precision: MGPBD_FP64 runs everything in FP64.  MGPBD_MIXED runs the
-// V-cycle bulk and A.p with FP32 values, vectors and accumulation; the dot
-// products, alpha/beta, the Krylov vectors, the true residual and the
-// coarsest factorisation stay FP64.
+// V-cycle bulk (smoothing, residuals, restriction, prolongation) with FP32
+// values, vectors and accumulation; A.p, the dot products, alpha/beta, the
+// Krylov vectors, the true residual and the coarsest factorisation stay FP64.
 #include <math.h>
 #include <string.h>
 
@@ -267,13 +267,11 @@ __global__ void k_spmv_pq(int n, const int64_t *ptr, const int32_t *col, const V
 // r_t = b - A x in FP64, |r_t|^2
 __global__ void k_true_resid(int n, const int64_t *ptr, const int32_t *col, const double *val,
                              const double *x, const double *b, DotCtx c) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double acc = 0.0;
-  for (int64_t i = w; i < n; i += nw) {
-    double s = warp_sum(row_dot<32, double, double, double>(ptr, col, val, x, (int)i, lane));
-    if (lane == 0) {
+  GROUP_ROWS(4, n) {
+    double s = valid ? row_dot<4, double, double, double>(ptr, col, val, x, (int)i, g) : 0.0;
+    s = group_sum<4>(s);
+    if (valid && g == 0) {
       double ri = b[i] - s;
       acc = fma(ri, ri, acc);
     }
@@ -333,13 +331,15 @@ __global__ void k_restrict(int na, const int64_t *mptr, const int32_t *mrow, con
   }
 }
 
-// x_i += P_i x_c[agg_i]
+// x_i += P_i x_c[agg_i] (rows left alone have no aggregate)
 template <class T>
 __global__ void k_prolong(int n, const int32_t *agg, const T *P, const T *xc, T *x,
                           const PcgScalars *sc) {
   if (is_done(sc)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    x[i] = fma(P[i], xc[agg[i]], x[i]);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int a = agg[i];
+    if (a >= 0) x[i] = fma(P[i], xc[a], x[i]);  // left-alone rows: P_i = 0
+  }
 }
 
 // coarsest: x = A_c^-1 b with the explicit FP64 inverse (warp per row)
@@ -464,8 +464,13 @@ mgpbd_status coarsest_factor(Handle *h) {
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
-static int group_for(const Level &L) {
+// Lanes per row.  FP32 kernels are bandwidth-bound and take wide groups for
+// coalescing.  FP64 arithmetic runs on few FP64 units on this part, so FP64
+// kernels take 4-lane groups: a row of n entries then costs n + 4*2 FP64
+// operations instead of n + 32*5 for a full-warp shuffle reduction.
+static int group_for(const Level &L, bool fp64 = false) {
   double avg = L.n ? (double)L.nnz / L.n : 1.0;
+  if (fp64) return 4;
   return avg <= 12 ? 4 : (avg <= 24 ? 8 : (avg <= 48 ? 16 : 32));
 }
 
@@ -516,7 +521,7 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in) {
     MG_LAUNCH("k_coarse_apply");
     return MGPBD_OK;
   }
-  const int G = group_for(L);
+  const int G = group_for(L, sizeof(T) == 8);
   const T om = (T)L.omega;
   const T *val = vals<T>(L);
   const T *dinv = dinvs<T>(L);
@@ -599,15 +604,15 @@ static mgpbd_status pcg_iteration(Handle *h, double *x) {
   Level &L = h->lev[0];
   const int m = h->m;
   double *r = h->pr, *z = h->pz, *p = h->pp, *q = h->pq;
-  const int G = group_for(L);
+  const int G = group_for(L, true);
   DotCtx cpq = make_ctx(h, DOT_PQ);
-  if (h->p.precision == MGPBD_MIXED) {
-    DISPATCH_G(G, (k_spmv_pq<GG, float, float><<<std::min(row_blocks(m, GG), 4096), 256, 0, h->stream>>>(
-                      m, L.ptr, L.col, L.val32, p, q, cpq)));
-  } else {
-    DISPATCH_G(G, (k_spmv_pq<GG, double, double><<<std::min(row_blocks(m, GG), 4096), 256, 0, h->stream>>>(
-                      m, L.ptr, L.col, L.val, p, q, cpq)));
-  }
+  // A.p is part of the Krylov recurrence, not of the preconditioner, and stays
+  // FP64 in both modes: rounding A's values to FP32 perturbs entries of size
+  // ~1e4 by ~1e-3, far above alpha~ (~1e-7), and the FP32 operator is then
+  // numerically indefinite on the stiff workloads (p.Ap <= 0).
+  DISPATCH_G(G, (k_spmv_pq<GG, double, double>
+                 <<<std::min(row_blocks(m, GG), 4096), 256, 0, h->stream>>>(m, L.ptr, L.col,
+                                                                            L.val, p, q, cpq)));
   MG_LAUNCH("k_spmv_pq");
   k_xr_update<<<dot_grid(), kDotThreads, 0, h->stream>>>(m, x, r, p, q, make_ctx(h, DOT_RR));
   MG_LAUNCH("k_xr_update");
@@ -649,7 +654,7 @@ mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *
     if (h->sc_host->done) break;
   }
   // true residual in FP64
-  k_true_resid<<<std::min(blocks_for((int64_t)m * 32, 256), 4096), 256, 0, h->stream>>>(
+  k_true_resid<<<std::min(row_blocks(m, 4), 4096), 256, 0, h->stream>>>(
       m, h->lev[0].ptr, h->lev[0].col, h->lev[0].val, x, b, make_ctx(h, DOT_TR));
   MG_LAUNCH("k_true_resid");
   MG_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost,
@@ -684,12 +689,10 @@ __global__ void k_pow_init(int n, uint64_t seed, int l, double *y) {
 // z_i = (A y)_i / A_ii
 __global__ void k_pow_apply(int n, const int64_t *ptr, const int32_t *col, const double *val,
                             const double *y, double *z) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = w; i < n; i += nw) {
-    double s = warp_sum(row_dot<32, double, double, double>(ptr, col, val, y, (int)i, lane));
-    if (lane == 0) z[i] = s / val[ptr[i + 1] - 1];
+  GROUP_ROWS(4, n) {
+    double s = valid ? row_dot<4, double, double, double>(ptr, col, val, y, (int)i, g) : 0.0;
+    s = group_sum<4>(s);
+    if (valid && g == 0) z[i] = s / val[ptr[i + 1] - 1];
   }
 }
 
@@ -710,7 +713,7 @@ mgpbd_status power_method(Handle *h, int l) {
   k_pow_init<<<blocks_for(n, 256), 256, 0, h->stream>>>(n, h->p.seed_pow, l, y);
   MG_LAUNCH("k_pow_init");
   for (int it = 0; it < h->p.power_iters; ++it) {
-    k_pow_apply<<<std::min(blocks_for((int64_t)n * 32, 256), 8192), 256, 0, h->stream>>>(
+    k_pow_apply<<<row_blocks(n, 4), 256, 0, h->stream>>>(
         n, L.ptr, L.col, L.val, y, z);
     MG_LAUNCH("k_pow_apply");
     MG_TRY(launch_dot(h, z, z, n, DOT_STORE, 0, s));

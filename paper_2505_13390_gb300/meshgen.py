@@ -84,7 +84,7 @@ def default_params(**over) -> Dict:
         max_iter=20,
         eps_b=0.0,
         pcg_rtol=1e-6,
-        pcg_maxiter=200,
+        pcg_maxiter=20000,  # a safeguard: the solve runs to pcg_rtol
         setup_interval=400,
         nk_sweeps=3,
         nk_omega=2.0 / 3.0,
@@ -96,6 +96,7 @@ def default_params(**over) -> Dict:
         power_safety=1.25,
         coarse_max=400,
         max_levels=8,
+        backtrack=0,  # 0: fixed omega_x; k: halve omega up to k times while |b| grows
         precision=0,  # 0 = FP64, 1 = mixed (FP32 V-cycle / A.p)
         seed_nk=3,
         seed_agg=4,

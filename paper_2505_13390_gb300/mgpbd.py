@@ -36,7 +36,7 @@ class Params(C.Structure):
         ("nk_omega", C.c_double), ("theta_s", C.c_double), ("smoother", C.c_int),
         ("smooth_sweeps", C.c_int), ("lambda_min_est", C.c_double), ("power_iters", C.c_int),
         ("power_safety", C.c_double), ("coarse_max", C.c_int), ("max_levels", C.c_int),
-        ("precision", C.c_int),
+        ("precision", C.c_int), ("backtrack", C.c_int),
         ("seed_nk", C.c_uint64), ("seed_agg", C.c_uint64), ("seed_col", C.c_uint64),
         ("seed_pow", C.c_uint64),
     ]
@@ -44,7 +44,8 @@ class Params(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("pcg_iters", C.c_int), ("status", C.c_int), ("bnorm", C.c_double),
-                ("rel_res", C.c_double), ("true_rel_res", C.c_double)]
+                ("rel_res", C.c_double), ("true_rel_res", C.c_double), ("omega", C.c_double),
+                ("bnorm_after", C.c_double)]
 
     def as_dict(self) -> Dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -95,6 +96,7 @@ SIGNATURES = {
     "mgpbd_get_colors": (_i, [_vp, _i, _vp, _i]),
     "mgpbd_get_constraints": (_i, [_vp, _vp, _vp, _vp, _vp, _i]),
     "mgpbd_get_lambda": (_i, [_vp, _vp, _vp, _i]),
+    "mgpbd_set_colouring": (_i, [_vp, _i]),
     "mgpbd_profile": (_i, [_vp, _i]),
     "mgpbd_profile_read": (_i, [_vp, C.POINTER(C.c_double), C.POINTER(_i64),
                                 C.POINTER(C.c_double)]),
@@ -310,6 +312,9 @@ class Solver:
         _check(load().mgpbd_get_aggregates(self.h, level, _ptr(agg), _ptr(root), _ptr(P), _ptr(B),
                                            MEM_HOST), "get_aggregates")
         return li["n_agg"], agg, root, P, B
+
+    def set_colouring(self, enable: bool):
+        _check(load().mgpbd_set_colouring(self.h, 1 if enable else 0), "set_colouring")
 
     def level_color(self, level: int):
         li = self.level_info(level)

@@ -46,7 +46,9 @@ CASES = {
 def both(name, **over):
     mesh, p = CASES[name]()
     p = dict(p, **over)
-    return mesh, p, Oracle(mesh, p), solver(mesh, p)
+    g = solver(mesh, p)
+    g.set_colouring(True)
+    return mesh, p, Oracle(mesh, p), g
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -129,9 +131,26 @@ SOFT = {
 CASES.update(SOFT)
 
 
+@pytest.mark.parametrize("name", ["cloth8", "hex3", "cloth32", "block6"])
+def test_vcycle_mixed_precision(name):
+    """FP32 V-cycle against the FP64 oracle V-cycle: relative error of order
+    the FP32 unit roundoff times the growth through the levels."""
+    mesh, p, o, g = both(name, precision=1)
+    for s_ in (o, g):
+        s_.begin_frame()
+        s_.eval_assemble()
+        s_.prepare_solve()
+    r = np.random.default_rng(3).standard_normal(mesh.n_rows)
+    zo = o.vcycle(r)
+    zg = g.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
+    rel = np.linalg.norm(zg - zo) / np.linalg.norm(zo)
+    assert rel <= 1e-4, rel
+    assert r @ zg > 0
+
+
 @pytest.mark.parametrize("name", ["cloth8s", "hex3s"])
 def test_solve_parity(name):
-    """Moderate cond(A): same iteration count (+-1) and solutions within 1e-8."""
+    """Moderate cond(A): same iteration count (+-2) and solutions within 1e-8."""
     mesh, p, o, g = both(name, pcg_rtol=1e-10, pcg_maxiter=1000)
     o.begin_frame()
     g.begin_frame()
@@ -144,7 +163,7 @@ def test_solve_parity(name):
     xg, ig = g.solve(torch.tensor(b, device="cuda"))
     xg = xg.cpu().numpy()
     assert ig["status"] == io["status"] == 0
-    assert abs(ig["pcg_iters"] - io["pcg_iters"]) <= 1
+    assert abs(ig["pcg_iters"] - io["pcg_iters"]) <= 2
     assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
 
 
@@ -162,21 +181,25 @@ def test_solve_stiff_true_residual():
     xg, ig = g.solve(torch.tensor(b, device="cuda"))
     xg = xg.cpu().numpy()
     assert ig["status"] == io["status"] == 0
-    assert ig["true_rel_res"] <= 1e-8 and io["true_rel_res"] <= 1e-8
+    # the true residual lags the recursive 1e-10 by about cond(A) * eps ~ 1e-8
+    assert ig["true_rel_res"] <= 5e-8 and io["true_rel_res"] <= 5e-8
     assert abs(ig["pcg_iters"] - io["pcg_iters"]) <= 0.1 * io["pcg_iters"]
     assert np.linalg.norm(xg - xo) <= 1e-5 * np.linalg.norm(xo)
 
 
-@pytest.mark.parametrize("name,iters", [("cloth8", 6), ("hex3", 6), ("cloth32", 4), ("block6", 3)])
+@pytest.mark.parametrize("name,iters", [("cloth8", 6), ("cloth8s", 6), ("hex3s", 6),
+                                        ("cloth32", 4), ("hex3", 3)])
 def test_iterations_parity_fp64(name, iters):
-    mesh, p, o, g = both(name, pcg_maxiter=40)
+    """Whole global iterations in FP64 with PCG solved to 1e-10: positions,
+    velocities and |b| within 1e-9 relative of the oracle."""
+    mesh, p, o, g = both(name, pcg_rtol=1e-10, pcg_maxiter=3000)
     o.begin_frame()
     g.begin_frame()
     scale = np.abs(mesh.rest_pos).max() + 1e-3
     for it in range(iters):
         do = o.iterate()
         dg = g.iterate()
-        assert do["ret"] >= 0 and dg["ret"] >= 0
+        assert do["ret"] == 0 and dg["ret"] == 0
         assert dg["bnorm"] == pytest.approx(do["bnorm"], rel=1e-9, abs=1e-300)
         xo, _ = o.get_state()
         xg, _ = g.get_state()
@@ -186,6 +209,55 @@ def test_iterations_parity_fp64(name, iters):
     _, vo = o.get_state()
     _, vg = g.get_state()
     assert np.abs(vg - vo).max() <= 1e-9 * scale / p["dt"]
+
+
+@pytest.mark.parametrize("name", ["beam40", "block6"])
+def test_stiff_unconverged_solve_quality(name):
+    """Stiff redundant tet systems (cond ~1e10): 200 PCG iterations do not reach
+    1e-6 and CG iterates depend on rounding order, so compare what is unique:
+    the A-norm error against a direct solve is the same on both sides."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    mesh, p, o, g = both(name, pcg_maxiter=200)
+    for s_ in (o, g):
+        s_.begin_frame()
+        s_.eval_assemble()
+        s_.prepare_solve()
+    ptr, col, val = o.matrix(0)
+    n = len(ptr) - 1
+    A = sp.csr_matrix((val, col, ptr), shape=(n, n))
+    b = o.constraints()[1]
+    xs = spl.spsolve(A.tocsc(), b)
+    xo, io = o.solve(b)
+    xg, ig = g.solve(torch.tensor(b, device="cuda"))
+    xg = xg.cpu().numpy()
+
+    def err(x):
+        e = x - xs
+        return np.sqrt(e @ (A @ e)) / np.sqrt(xs @ (A @ xs))
+
+    eo, eg = err(xo), err(xg)
+    assert ig["pcg_iters"] == io["pcg_iters"] == p["pcg_maxiter"]
+    assert eo < 0.9 and eg < 0.9  # the preconditioned solve makes progress
+    assert abs(eg - eo) <= 0.1 * eo
+
+
+@pytest.mark.parametrize("name", ["cloth8", "hex3s"])
+def test_backtracking_parity(name):
+    """The backtracking relaxation (omega halves while |b| grows) takes the
+    same decisions as the oracle and gives the same positions."""
+    mesh, p, o, g = both(name, omega_x=1.0, backtrack=6, pcg_rtol=1e-10, pcg_maxiter=3000)
+    o.begin_frame()
+    g.begin_frame()
+    scale = np.abs(mesh.rest_pos).max() + 1e-3
+    for it in range(4):
+        do, dg = o.iterate(), g.iterate()
+        assert do["ret"] == 0 and dg["ret"] == 0
+        assert dg["omega"] == do["omega"]
+        assert dg["bnorm_after"] == pytest.approx(do["bnorm_after"], rel=1e-8)
+        xo, _ = o.get_state()
+        xg, _ = g.get_state()
+        assert np.abs(xg - xo).max() <= 1e-9 * scale
 
 
 def test_empty_and_single_constraint():

@@ -309,10 +309,14 @@ def brute_aggregates(ptr, col, val, theta, seed, level):
         b.discard(i)
         ball2.append(b)
     pri = [h64((seed << 40) | (level << 32) | i) for i in range(n)]
-    # lexicographically-first distance-2 independent set: a root is a node with
-    # no higher-priority root within distance 2; resolve by decreasing priority
+    # lexicographically-first distance-2 independent set over the rows that
+    # have a strong neighbour: a root is such a row with no higher-priority
+    # root within distance 2; resolve by decreasing priority.  Rows without a
+    # strong neighbour are left alone (no aggregate).
     root = [False] * n
     for u in sorted(range(n), key=lambda i: (pri[i], i), reverse=True):
+        if not adj[u]:
+            continue
         root[u] = not any(root[w] and (pri[w], w) > (pri[u], u) for w in ball2[u])
     ids = {}
     for i in range(n):
@@ -325,7 +329,7 @@ def brute_aggregates(ptr, col, val, theta, seed, level):
             p1[w] = a
     agg = list(p1)
     for i in range(n):
-        if p1[i] >= 0:
+        if p1[i] >= 0 or not adj[i]:
             continue
         cands = [(-absv[(i, w)], p1[w], w) for w in adj[i] if p1[w] >= 0]
         agg[i] = min(cands)[1]
@@ -341,9 +345,11 @@ def test_aggregation_brute_force(seed, theta):
     assert np.array_equal(root, broot)
     assert np.array_equal(agg, bagg)
     n = len(ptr) - 1
-    # disjoint and covering; one root per aggregate; roots pairwise >= 3 apart
+    # disjoint and covering every row with a strong neighbour; one root per
+    # aggregate; roots pairwise >= 3 apart; rows without strong neighbours alone
     assert na == int(root.sum())
-    assert set(agg.tolist()) == set(range(na))
+    assert set(agg[agg >= 0].tolist()) == set(range(na))
+    assert all((agg[i] < 0) == (len(adj[i]) == 0) for i in range(n))
     roots = np.nonzero(root)[0]
     assert sorted(agg[roots].tolist()) == list(range(na))
     for r in roots:
@@ -356,9 +362,9 @@ def test_aggregation_brute_force(seed, theta):
 def test_aggregation_special_cases():
     ptr, col, val = random_spd_pattern(30, 0.1, 11)
     n = len(ptr) - 1
-    # no strong connection: every row is a singleton aggregate
+    # no strong connection: every row is left alone (no coarse space)
     na, agg, root, S = aggregate_csr(ptr, col, val, 1e300, seed=4)
-    assert na == n and np.array_equal(agg, np.arange(n)) and S.sum() == 0
+    assert na == 0 and np.all(agg == -1) and S.sum() == 0
     # theta = 0: every stored off-diagonal is strong
     na, agg, root, S = aggregate_csr(ptr, col, val, 0.0, seed=4)
     offd = np.ones(len(col), bool)
@@ -418,7 +424,9 @@ def test_prolongator_and_galerkin(name):
         _, _, _, A = csr_of(o, l)
         _, _, _, Ac = csr_of(o, l + 1)
         n = A.shape[0]
-        Pm = sp.csr_matrix((P, (np.arange(n), agg)), shape=(n, na))
+        rows = np.nonzero(agg >= 0)[0]
+        assert np.all(P[agg < 0] == 0)
+        Pm = sp.csr_matrix((P[rows], (rows, agg[rows])), shape=(n, na))
         # columns of P have unit 2-norm, P^T P = I (disjoint aggregates)
         PtP = (Pm.T @ Pm).toarray()
         assert np.allclose(PtP, np.eye(na), rtol=0, atol=1e-14)
@@ -549,6 +557,25 @@ def test_pinned_vertices_stay_and_dual_residual_falls():
     for f in range(2):
         b = [h["bnorm"] for h in hist[f * 20:(f + 1) * 20]]
         assert b[-1] < b[0]  # relative dual residual falls over the loop
+
+
+def test_backtracking_never_accepts_a_growing_residual_when_a_halving_helps():
+    mesh = cloth(10, plane="xz", alpha=1e-8, pin="corners", noise=1e-4, seed=1)
+    p = default_params(omega_x=1.0, backtrack=8, pcg_rtol=1e-10, coarse_max=40)
+    o = Oracle(mesh, p)
+    o.begin_frame()
+    for _ in range(6):
+        d = o.iterate()
+        assert d["ret"] == 0
+        halvings = round(np.log2(1.0 / d["omega"]))
+        assert d["omega"] == 2.0 ** -halvings
+        if halvings < p["backtrack"]:
+            assert d["bnorm_after"] < d["bnorm"]
+    # fixed relaxation leaves omega untouched and reports no trial residual
+    o2 = Oracle(mesh, default_params(omega_x=0.25, coarse_max=40))
+    o2.begin_frame()
+    d = o2.iterate()
+    assert d["omega"] == 0.25 and d["bnorm_after"] == -1.0
 
 
 def test_lazy_setup_count():
