@@ -4,7 +4,8 @@ Workload (default): ``block100`` -- 100x33x100 hex cells of 0.005 m, 5 tets
 per cell (1.65M tets, 346,834 vertices), edge distance plus tet volume
 constraints (3,680,033 rows, 376,541,249 nonzeros in A), alpha = 1e-10,
 bottom face pinned, dt = 1/60, 20 global iterations per frame, lazy setup
-every 20 global iterations, PCG rtol 1e-6 capped at 200 iterations.
+every 20 global iterations, PCG to rtol 1e-6 (about 7,000 PCG iterations per
+global iteration on this workload).
 
 A step is one global iteration of Algorithm 1 (constraints, assembly, lazy
 setup when due, Galerkin re-form, coarsest factorisation, MGPCG with one
@@ -15,9 +16,9 @@ reported under "fp64".  Inputs are resident on the device; A alone is
 3-4.6 GB, far larger than L2, so no L2 flush is needed between steps.
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores on a
-bounded sample of the same workload (a 10x33x4-cell block of the same
+bounded sample of the same workload (a 4x33x4-cell block of the same
 recipe) and scales the time per iteration to the full workload by the
-nonzero count of A.
+nonzero count of A and by the ratio of PCG iterations.
 """
 from __future__ import annotations
 
@@ -34,14 +35,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FULL_NNZ = 376_541_249  # nonzeros of A for block100 (checked at run time)
-SAMPLE = (10, 33, 4)    # oracle sample: cells along x, y (vertical), z
+# PCG iterations per global iteration on block100 at frame 0, iterations 1-5,
+# as measured on GB300 (the reference arm cannot run the GPU to learn it)
+FULL_PCG_ITERS = 7300
+SAMPLE = (4, 33, 4)     # oracle sample: cells along x, y (vertical), z
+SAMPLE_PCG = 500        # PCG iterations per sampled global iteration (cost is linear in them)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-warmup", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="block100")
     ap.add_argument("--no-fp64", action="store_true")
@@ -237,13 +245,18 @@ def e2e(g, run, steps):
     return steps / dt, nbytes
 
 
-def cpu_sample_baseline(iters=3, warm=1):
-    """The FP64 oracle on the host cores (1 thread) on the bounded sample."""
+def cpu_sample_baseline(iters=2, warm=1, gpu_pcg=None):
+    """The FP64 oracle on the host cores (1 thread) on the bounded sample.
+
+    The time per global iteration is scaled to the full workload by the nnz
+    ratio and, when the GPU run's PCG iteration count is known, by the ratio
+    of PCG iterations (the cost of an iteration is the PCG iterations times
+    the A-passes per PCG iteration)."""
     from oracle.oracle import Oracle
     from paper_2505_13390_gb300.meshgen import default_params, hex_block
     mesh = hex_block(*SAMPLE, h=0.005, jitter=0.1, alpha=1e-10, pin="y0", seed=1,
                      name="block-sample")
-    p = default_params(omega_x=0.1, setup_interval=20)
+    p = default_params(omega_x=0.1, setup_interval=20, pcg_maxiter=SAMPLE_PCG)
     o = Oracle(mesh, p)
     nnz = int(o.matrix(0)[0][-1])
     o.begin_frame()
@@ -255,11 +268,14 @@ def cpu_sample_baseline(iters=3, warm=1):
         pcg.append(o.iterate()["pcg_iters"])
     dt = (time.perf_counter() - t0) / iters
     scale = FULL_NNZ / nnz
-    return {"value": 1.0 / (dt * scale), "unit": "global_iters/s", "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 C oracle, {iters} global iterations (after {warm} with setup) on a "
+    pscale = (sum(gpu_pcg) / len(gpu_pcg)) / (sum(pcg) / len(pcg)) if gpu_pcg else 1.0
+    return {"value": 1.0 / (dt * scale * pscale), "unit": "global_iters/s", "cores": 1,
+            "kind": "oracle",
+            "sample": (f"FP64 C oracle, {iters} global iteration(s) (after {warm} with setup) on a "
                        f"{SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]}-cell block of the same recipe "
-                       f"({mesh.n_rows} rows, {nnz} nnz), {dt:.2f} s/iteration, scaled by the "
-                       f"nnz ratio {scale:.1f} to 376.5M nnz; PCG iterations {pcg}")}, dt, scale
+                       f"({mesh.n_rows} rows, {nnz} nnz, PCG iterations {pcg}), {dt:.2f} s per "
+                       f"iteration, scaled by the nnz ratio {scale:.1f} and the PCG-iteration "
+                       f"ratio {pscale:.2f} to 376.5M nnz")}, dt, scale
 
 
 def run_ours(args, ws, rank):
@@ -270,10 +286,8 @@ def run_ours(args, ws, rank):
     if not os.path.exists(os.path.join(ROOT, "paper_2505_13390_gb300", "libmgpbd.so")):
         ge.build()
     cpu = None
-    if rank == 0 and not args.no_cpu:
-        cpu, _, _ = cpu_sample_baseline()
     mesh, params = workload(args.workload)
-    params = dict(params, precision=1)
+    params = dict(params, precision=1, autotune=1)
     res = measure(mesh, params, args.steps, args.warmup, ws)
     ms = max_over_ranks(ws, res["ms"])
     value = ws * args.steps / (ms / 1e3)
@@ -296,7 +310,7 @@ def run_ours(args, ws, rank):
     e2e_val = None
     e2e_bytes = 0
     if not args.no_e2e:
-        e2e_val, e2e_bytes = e2e(g, res["runner"], max(3, args.steps // 2))
+        e2e_val, e2e_bytes = e2e(g, res["runner"], args.e2e_steps)
         e2e_val = e2e_val * ws
     fp64 = None
     levels = [g.level_info(l) for l in range(g.levels)]
@@ -305,16 +319,20 @@ def run_ours(args, ws, rank):
     torch.cuda.empty_cache()
     if not args.no_fp64:
         p64 = dict(params, precision=0)
-        r64 = measure(mesh, p64, args.steps, args.warmup, ws)
+        r64 = measure(mesh, p64, args.fp64_steps, args.fp64_warmup, ws)
         ms64 = max_over_ranks(ws, r64["ms"])
         pr = r64["prof"]
         a64 = pr["bytes_per_launch"] / (pr["total_ms"] / max(pr["launches"], 1) / 1e3) / 1e9
-        fp64 = {"value": ws * args.steps / (ms64 / 1e3), "ms_per_step": ms64 / args.steps,
+        fp64 = {"value": ws * args.fp64_steps / (ms64 / 1e3),
+                "ms_per_step": ms64 / args.fp64_steps,
+                "steps": args.fp64_steps, "warmup": args.fp64_warmup,
                 "pcg_iters": r64["pcg"], "clocks": r64["clocks"],
                 "smoother_sweep_gbs": a64, "smoother_sweep_frac": a64 / hbm}
         r64["solver"].close()
     if rank != 0:
         return
+    if not args.no_cpu:
+        cpu, _, _ = cpu_sample_baseline(gpu_pcg=res["pcg"])
     line = {
         "metric": "global XPBD iters/s at 1.65M tets (mixed precision; FP64 under fp64)",
         "value": value,
@@ -353,22 +371,26 @@ def run_ours(args, ws, rank):
     print(json.dumps(line))
 
 
+_ORACLE_PCG = []
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
     from oracle.oracle import Oracle
     from paper_2505_13390_gb300.meshgen import default_params, hex_block
     mesh = hex_block(*SAMPLE, h=0.005, jitter=0.1, alpha=1e-10, pin="y0", seed=1)
-    p = default_params(omega_x=0.1, setup_interval=20)
+    p = default_params(omega_x=0.1, setup_interval=20, pcg_maxiter=SAMPLE_PCG)
     o = Oracle(mesh, p)
     nnz = int(o.matrix(0)[0][-1])
     scale = FULL_NNZ / nnz
     o.begin_frame()
     k = 0
+    _ORACLE_PCG.clear()
 
     def step():
         nonlocal k
-        o.iterate()
+        _ORACLE_PCG.append(o.iterate()["pcg_iters"])
         k += 1
         if k % p["max_iter"] == 0:
             o.end_frame()
@@ -376,14 +398,17 @@ def run_reference(args, ws, rank):
 
     for _ in range(args.warmup):
         step()
+    _ORACLE_PCG.clear()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         step()
     dt = time.perf_counter() - t0
-    value = args.steps / (dt * scale)
+    pscale = FULL_PCG_ITERS / max(1.0, sum(o_pcg) / len(o_pcg)) if (o_pcg := _ORACLE_PCG) else 1.0
+    value = args.steps / (dt * scale * pscale)
     sample = (f"FP64 C oracle (1 thread) on a {SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]}-cell block of "
-              f"the same recipe ({mesh.n_rows} rows, {nnz} nnz); time per global iteration "
-              f"scaled by the nnz ratio {scale:.1f} to 376.5M nnz")
+              f"the same recipe ({mesh.n_rows} rows, {nnz} nnz, PCG iterations {_ORACLE_PCG}); "
+              f"time per global iteration scaled by the nnz ratio {scale:.1f} and the "
+              f"PCG-iteration ratio {pscale:.2f} to 376.5M nnz and {FULL_PCG_ITERS} PCG iterations")
     line = {
         "impl": "reference",
         "metric": "global XPBD iters/s at 1.65M tets (mixed precision; FP64 under fp64)",

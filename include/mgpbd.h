@@ -89,6 +89,10 @@ typedef struct {
   int backtrack;        /* 0: x += omega_x dx; k > 0: start at omega_x and halve omega
                            while the dual residual |b| does not decrease, at most k
                            times (the paper's backtracking option, Sec. 4) */
+  int autotune;         /* 0: lanes per matrix row by a fixed rule (reproducible
+                           bit for bit); 1: time the row kernels of every level at
+                           each setup and keep the fastest shape (rounding of the
+                           row sums then depends on the choice) */
   uint64_t seed_nk, seed_agg, seed_col, seed_pow;
 } mgpbd_params;
 
@@ -117,6 +121,7 @@ typedef struct {
   int n_agg;            /* aggregates (0 on the coarsest level) */
   int n_colors;         /* colours of the multicolour ordering (0 if none) */
   double lmax, omega;   /* power-method lambda_max(D^-1 A) and Jacobi weight */
+  int lanes_fp32, lanes_fp64; /* lanes per row picked by the autotuner (0 = rule) */
 } mgpbd_level_info;
 
 /* Fills p with the defaults listed above.  Never fails for p != NULL. */

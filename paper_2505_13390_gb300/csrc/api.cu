@@ -139,6 +139,7 @@ static mgpbd_status check_params(const mgpbd_params *p) {
       p->smooth_sweeps < 1 || p->power_iters < 1 || p->coarse_max < 1 || p->max_levels < 1 ||
       p->max_levels > kMaxLevels || (p->precision != MGPBD_FP64 && p->precision != MGPBD_MIXED) ||
       (p->smoother != MGPBD_SMOOTH_JACOBI) || !(p->theta_s >= 0.0) || p->backtrack < 0 ||
+      (p->autotune != 0 && p->autotune != 1) ||
       !(p->pcg_rtol >= 0.0) || !(p->power_safety > 0.0)) {
     set_error("invalid mgpbd_params (or unsupported smoother on this build)");
     return MGPBD_E_INVALID;
@@ -369,6 +370,7 @@ mgpbd_status mgpbd_default_params(mgpbd_params *p) {
   p->max_levels = 8;
   p->precision = MGPBD_FP64;
   p->backtrack = 0;
+  p->autotune = 0;
   p->seed_nk = 3;
   p->seed_agg = 4;
   p->seed_col = 5;
@@ -567,6 +569,8 @@ mgpbd_status mgpbd_level_info_get(mgpbd_handle_t *hh, int level, mgpbd_level_inf
   info->n_colors = L.n_colors;
   info->lmax = L.lmax;
   info->omega = L.omega;
+  info->lanes_fp32 = L.G32;
+  info->lanes_fp64 = L.G64;
   return MGPBD_OK;
 }
 

@@ -103,6 +103,7 @@ struct Level {
   int32_t *mrow = nullptr;
   int max_members = 0;
   int max_coarse_row = 0;    // longest row of level+1 (Galerkin smem size)
+  int G32 = 0, G64 = 0;      // lanes per row of the FP32 / FP64 row kernels (0 = rule)
   int32_t *color = nullptr;
   int n_colors = 0;
   double lmax = 0.0, omega = 0.0;
@@ -208,6 +209,7 @@ mgpbd_status galerkin_reform(Handle *h);
 mgpbd_status level_precision_copies(Handle *h, int l);
 
 // solve.cu
+mgpbd_status autotune_levels(Handle *h);
 mgpbd_status coarsest_factor(Handle *h);
 mgpbd_status pcg_solve(Handle *h, const double *d_b, double *d_x, mgpbd_solve_info *info);
 mgpbd_status vcycle_apply(Handle *h, const double *d_r, double *d_z);

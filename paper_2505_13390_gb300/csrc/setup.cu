@@ -864,6 +864,7 @@ mgpbd_status amg_setup(Handle *h) {
     MG_TRY(power_method(h, q));
   }
   h->lev[h->L - 1].n_colors = 0;
+  if (h->p.autotune) MG_TRY(autotune_levels(h));
   h->have_setup = true;
   h->n_setups++;
   MG_CUDA(cudaStreamSynchronize(h->stream));

@@ -304,7 +304,7 @@ __global__ void k_jacobi(int n, const int64_t *ptr, const int32_t *col, const T 
 template <int G, class T>
 __global__ void k_resid(int n, const int64_t *ptr, const int32_t *col, const T *val, const T *b,
                         const T *x, T *r, const PcgScalars *sc) {
-  if (is_done(sc)) return;
+  if (sc && is_done(sc)) return;
   GROUP_ROWS(G, n) {
     T s = valid ? row_dot<G, T, T, T>(ptr, col, val, x, (int)i, g) : (T)0;
     s = group_sum<G>(s);
@@ -468,10 +468,15 @@ mgpbd_status coarsest_factor(Handle *h) {
 // coalescing.  FP64 arithmetic runs on few FP64 units on this part, so FP64
 // kernels take 4-lane groups: a row of n entries then costs n + 4*2 FP64
 // operations instead of n + 32*5 for a full-warp shuffle reduction.
-static int group_for(const Level &L, bool fp64 = false) {
+static int group_rule(const Level &L, bool fp64) {
   double avg = L.n ? (double)L.nnz / L.n : 1.0;
   if (fp64) return 4;
   return avg <= 12 ? 4 : (avg <= 24 ? 8 : (avg <= 48 ? 16 : 32));
+}
+
+static int group_for(const Level &L, bool fp64 = false) {
+  int g = fp64 ? L.G64 : L.G32;
+  return g ? g : group_rule(L, fp64);
 }
 
 static int row_blocks(int64_t rows, int G, int th = 256) {
@@ -676,6 +681,74 @@ mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *
   h->last_pcg_iters = s.iters;
   if (info->status == MGPBD_E_BREAKDOWN) set_error("PCG breakdown (p.Ap <= 0, r.z <= 0 or NaN)");
   return info->status;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: lanes per row of the row kernels, per level and precision
+// ---------------------------------------------------------------------------
+template <class T>
+static mgpbd_status time_resid(Handle *h, const Level &L, int G, const T *val, const T *b,
+                               const T *x, T *r, float *ms_out) {
+  const int n = L.n;
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    MG_CUDA(cudaEventRecord(h->ev0, h->stream));
+    DISPATCH_G(G, (k_resid<GG, T><<<row_blocks(n, GG), 256, 0, h->stream>>>(n, L.ptr, L.col, val,
+                                                                           b, x, r, nullptr)));
+    MG_LAUNCH("k_resid(tune)");
+    MG_CUDA(cudaEventRecord(h->ev1, h->stream));
+    MG_CUDA(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    MG_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    best = std::min(best, ms);
+  }
+  *ms_out = best;
+  return MGPBD_OK;
+}
+
+// Times the residual kernel (the access pattern of every row kernel) with
+// 4, 8, 16 and 32 lanes per row on each level, in the V-cycle precision, and
+// on level 0 in FP64 for A.p; keeps the fastest.  Runs after a setup when
+// params.autotune is set.
+mgpbd_status autotune_levels(Handle *h) {
+  const bool mixed = h->p.precision == MGPBD_MIXED;
+  for (int l = 0; l + 1 < h->L || (l == 0 && h->L >= 1); ++l) {
+    Level &L = h->lev[l];
+    if (L.n == 0) break;
+    const int cands[4] = {4, 8, 16, 32};
+    float best = 1e30f;
+    int bestG = group_rule(L, !mixed);
+    for (int c = 0; c < 4; ++c) {
+      float ms = 0.f;
+      if (mixed)
+        MG_TRY(time_resid<float>(h, L, cands[c], L.val32, (const float *)L.b, (const float *)L.x,
+                                 (float *)L.r, &ms));
+      else
+        MG_TRY(time_resid<double>(h, L, cands[c], L.val, (const double *)L.b,
+                                  (const double *)L.x, (double *)L.r, &ms));
+      if (ms < best) {
+        best = ms;
+        bestG = cands[c];
+      }
+    }
+    if (mixed) L.G32 = bestG;
+    else L.G64 = bestG;
+    if (l == 0 && mixed) {  // FP64 A.p on level 0
+      float b64 = 1e30f;
+      int g64 = 4;
+      for (int c = 0; c < 4; ++c) {
+        float ms = 0.f;
+        MG_TRY(time_resid<double>(h, L, cands[c], L.val, h->pr, h->pz, h->pq, &ms));
+        if (ms < b64) {
+          b64 = ms;
+          g64 = cands[c];
+        }
+      }
+      L.G64 = g64;
+    }
+    if (l + 1 >= h->L) break;
+  }
+  return MGPBD_OK;
 }
 
 // ---------------------------------------------------------------------------

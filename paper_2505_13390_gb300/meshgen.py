@@ -97,6 +97,7 @@ def default_params(**over) -> Dict:
         coarse_max=400,
         max_levels=8,
         backtrack=0,  # 0: fixed omega_x; k: halve omega up to k times while |b| grows
+        autotune=0,   # 1: time the row-kernel shapes at setup and keep the fastest
         precision=0,  # 0 = FP64, 1 = mixed (FP32 V-cycle / A.p)
         seed_nk=3,
         seed_agg=4,

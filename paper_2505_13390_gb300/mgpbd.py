@@ -36,7 +36,7 @@ class Params(C.Structure):
         ("nk_omega", C.c_double), ("theta_s", C.c_double), ("smoother", C.c_int),
         ("smooth_sweeps", C.c_int), ("lambda_min_est", C.c_double), ("power_iters", C.c_int),
         ("power_safety", C.c_double), ("coarse_max", C.c_int), ("max_levels", C.c_int),
-        ("precision", C.c_int), ("backtrack", C.c_int),
+        ("precision", C.c_int), ("backtrack", C.c_int), ("autotune", C.c_int),
         ("seed_nk", C.c_uint64), ("seed_agg", C.c_uint64), ("seed_col", C.c_uint64),
         ("seed_pow", C.c_uint64),
     ]
@@ -63,7 +63,8 @@ class Stats(C.Structure):
 
 class LevelInfo(C.Structure):
     _fields_ = [("n", C.c_int), ("nnz", C.c_int64), ("n_agg", C.c_int), ("n_colors", C.c_int),
-                ("lmax", C.c_double), ("omega", C.c_double)]
+                ("lmax", C.c_double), ("omega", C.c_double), ("lanes_fp32", C.c_int),
+                ("lanes_fp64", C.c_int)]
 
     def as_dict(self) -> Dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
