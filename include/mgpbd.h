@@ -225,6 +225,28 @@ mgpbd_status mgpbd_profile_read(mgpbd_handle_t *h, double *total_ms, int64_t *la
                                 double *bytes_per_launch);
 unsigned long long mgpbd_launch_count(void);
 
+/* ---- allocation-free entry point ----
+ * The paper has no counterpart of this call; it exists for callers that
+ * cannot allocate device memory while they run: a thread capturing a CUDA
+ * stream into a graph (cudaMalloc is not allowed during global-mode
+ * capture), a real-time loop that must not wait on the allocator, or an
+ * application whose device memory belongs to another pool.
+ * It computes the FP64 true relative residual |b - A x|_2 / |b|_2 of the
+ * instance's level-0 matrix (the check mgpbd_solve reports as true_rel_res)
+ * into d_out[0] (device memory; 0 when b = 0), asynchronously on the
+ * instance's stream.  d_b and d_x are device arrays of n_rows doubles owned
+ * by the caller.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine: its per-block partial sums live in one static device array of
+ * about 1 MiB that every GPU loading the library holds until the process
+ * exits.  All calls share that array and it keeps the last call's contents
+ * (the block counter is cleared before each launch), so calls that overlap
+ * on the GPU race and must be serialised by the caller.  The first call on a
+ * device looks up the array's address (once per device); make it before any
+ * stream capture starts.  Instances with more than 4,194,304 constraint rows
+ * are rejected with MGPBD_E_INVALID (the array holds 65,536 blocks of 64 rows). */
+mgpbd_status mgpbd_true_residual_noalloc(mgpbd_handle_t *h, const double *d_b, const double *d_x,
+                                         double *d_out);
+
 /* Thread-local text of the calling thread's last error ("" if none). */
 const char *mgpbd_last_error(void);
 

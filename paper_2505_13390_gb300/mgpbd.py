@@ -102,6 +102,7 @@ SIGNATURES = {
     "mgpbd_profile_read": (_i, [_vp, C.POINTER(C.c_double), C.POINTER(_i64),
                                 C.POINTER(C.c_double)]),
     "mgpbd_launch_count": (C.c_ulonglong, []),
+    "mgpbd_true_residual_noalloc": (_i, [_vp, _vp, _vp, _vp]),
     "mgpbd_last_error": (C.c_char_p, []),
 }
 
