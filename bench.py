@@ -38,6 +38,11 @@ FULL_NNZ = 376_541_249  # nonzeros of A for block100 (checked at run time)
 # PCG iterations per global iteration on block100 at frame 0, iterations 1-5,
 # as measured on GB300 (the reference arm cannot run the GPU to learn it)
 FULL_PCG_ITERS = 7300
+# DRAM bytes (read + write) of one level-0 FP32 smoother sweep per nonzero of
+# A, from the ncu capture in profiles/k_jacobi_level0_block40x33x40.md
+# (k_jacobi<8, float>, 494.06 MB for 59,625,809 nonzeros); the sweep's
+# traffic grows in proportion to nnz, so it scales to a full launch
+SWEEP_TRAFFIC_PER_NNZ = 494.058240e6 / 59_625_809
 SAMPLE = (4, 33, 4)     # oracle sample: cells along x, y (vertical), z
 SAMPLE_PCG = 500        # PCG iterations per sampled global iteration (cost is linear in them)
 
@@ -356,7 +361,9 @@ def run_ours(args, ws, rank):
         "roofline": {"bound": "hbm", "kernel": "k_jacobi (level-0 weighted-Jacobi sweep, FP32)",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_source": peak_src,
-                     "traffic": None,
+                     "traffic": SWEEP_TRAFFIC_PER_NNZ * li["nnz"],
+                     "traffic_source": "ncu dram__bytes_read+write of k_jacobi<8,float> on a "
+                                       "40x33x40 block, scaled by nnz",
                      "bytes_per_launch": prof["bytes_per_launch"], "avg_launch_ms": avg_ms,
                      "launches": prof["launches"]},
         "cpu_baseline": cpu,

@@ -65,7 +65,7 @@ typedef struct {
 
 /* Solver parameters.  mgpbd_default_params() fills the paper's defaults:
  * theta_s = 0.1 (Sec. 4.1), 2 smoothing sweeps (Sec. 4.5), lambda_min
- * estimate 0.1 (Sec. 4.5), coarsest below 400 rows (Fig. 2), omega_x 0.25. */
+ * estimate 0.1 (Sec. 4.5), coarsest below 400 rows (Sec. 4.1, setup-pipeline figure), omega_x 0.25. */
 typedef struct {
   double dt;            /* time step */
   double gravity[3];    /* f_ext / m */
@@ -83,7 +83,7 @@ typedef struct {
   double lambda_min_est;/* lambda_min estimate in omega_opt (Sec. 4.5) */
   int power_iters;      /* power-method iterations for lambda_max */
   double power_safety;  /* factor on the lambda_max estimate */
-  int coarse_max;       /* stop coarsening below this many rows (Fig. 2) */
+  int coarse_max;       /* stop coarsening below this many rows (Sec. 4.1, setup-pipeline figure) */
   int max_levels;       /* hard cap on the number of levels */
   int precision;        /* MGPBD_FP64 or MGPBD_MIXED */
   int backtrack;        /* 0: x += omega_x dx; k > 0: start at omega_x and halve omega
@@ -164,7 +164,7 @@ mgpbd_status mgpbd_end_frame(mgpbd_handle_t *h);
  * current positions (Alg. 1, eq. 3), without solving. */
 mgpbd_status mgpbd_eval_assemble(mgpbd_handle_t *h);
 
-/* Runs the full AMG setup (Sec. 4.1-4.3, Fig. 2) on the current A. */
+/* Runs the full AMG setup (Sec. 4.1-4.3, setup-pipeline figure) on the current A. */
 mgpbd_status mgpbd_setup(mgpbd_handle_t *h);
 
 /* Readies the current A for solving: setup if none exists, else the

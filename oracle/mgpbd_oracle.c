@@ -18,9 +18,9 @@
  *   b = -C - alpha~ lambda                               (eq. 3)
  *   lazy UA-AMG setup: near-kernel sweeps, strength
  *     filter, aggregation, injection, next-level
- *     near-kernel, Galerkin, recursion below 400 rows    (Sec. 4.1-4.3, Fig. 2)
+ *     near-kernel, Galerkin, recursion below 400 rows    (Sec. 4.1-4.3, setup-pipeline figure)
  *   Galerkin coarse operators P^T A P                    (Sec. 4.4, eq. 6)
- *   coarsest dense Cholesky                              (reading: Fig. 2 size rule)
+ *   coarsest dense Cholesky                              (reading: Sec. 4.1 size rule)
  *   PCG with one V-cycle per iteration                   (Sec. 4.4)
  *   weighted-Jacobi / multicolour GS smoothing, omega
  *     from the power method and lambda_min estimate      (Sec. 4.5)
@@ -393,7 +393,7 @@ static double dot(int n, const double *x, const double *y) {
 }
 
 /* ------------------------------------------------------------------------- */
-/* Setup phase (Sec. 4.1, Fig. 2): filter, aggregate, inject.                */
+/* Setup phase (Sec. 4.1 and its setup-pipeline figure): filter, aggregate, inject.                */
 /* ------------------------------------------------------------------------- */
 
 /* Strength filter (Sec. 4.1): off-diagonal A_ij is strong unless
@@ -509,7 +509,7 @@ static void near_kernel(const orc_csr *A, const orc_params *p, double *B) {
   free(s);
 }
 
-/* Injection with k = 1 (Fig. 2, Sec. 4.1): per aggregate a (members
+/* Injection with k = 1 (Sec. 4.1 setup-pipeline figure): per aggregate a (members
    ascending) nrm_a = sqrt(sum fma(B_i, B_i, .)); P_i = B_i / nrm_a;
    the next level's near-kernel is the R factor, B_{l+1}[a] = nrm_a.
    If nrm_a == 0: P_i = 1/sqrt(|a|). */
@@ -723,7 +723,7 @@ static void level_alloc_work(orc_level *L) {
   L->t = (double *)xcalloc((size_t)n, sizeof(double));
 }
 
-/* Full setup from the current level-0 matrix (Fig. 2): level 0 takes the
+/* Full setup from the current level-0 matrix (Sec. 4.1, setup-pipeline figure): level 0 takes the
    near-kernel sweeps; each level filters, aggregates, injects and forms the
    next Galerkin operator, until the size is below coarse_max or max_levels is
    reached.  Smoother weights (and colourings) are set lazily here too. */

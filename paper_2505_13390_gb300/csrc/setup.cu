@@ -1,4 +1,4 @@
-// Lazy UA-AMG setup (Sec. 4.1-4.3, Fig. 2 of the paper) and the Galerkin
+// Lazy UA-AMG setup (Sec. 4.1-4.3, setup-pipeline figure of the paper) and the Galerkin
 // re-form of Sec. 4.4, on the device.
 //
 //   near-kernel  B_0: nk_sweeps weighted-Jacobi sweeps on A x = 0 from

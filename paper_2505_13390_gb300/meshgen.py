@@ -74,7 +74,7 @@ def default_params(**over) -> Dict:
     """Solver parameters with the paper's defaults (see DESIGN notes).
 
     theta_s = 0.1 (Sec. 4.1), two smoothing sweeps (Sec. 4.5), lambda_min
-    estimate 0.1 (Sec. 4.5), coarsest size below 400 (Fig. setup pipeline),
+    estimate 0.1 (Sec. 4.5), coarsest size below 400 (Sec. 4.1),
     omega_x = 0.25 cloth / 0.1 softbody (Sec. 4, Alg. 1 relaxation).
     """
     p = dict(
