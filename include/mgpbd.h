@@ -93,6 +93,11 @@ typedef struct {
                            bit for bit); 1: time the row kernels of every level at
                            each setup and keep the fastest shape (rounding of the
                            row sums then depends on the choice) */
+  int level0_op;        /* 0: level-0 products (A.p, V-cycle sweeps and residual) with
+                           the assembled CSR matrix; 1: matrix-free, y = J (W (J^T x))
+                           + alpha~ x through the constraint gradients (the paper's
+                           future-work direction, Sec. 6).  Setup and Galerkin
+                           products always use the assembled matrix. */
   uint64_t seed_nk, seed_agg, seed_col, seed_pow;
 } mgpbd_params;
 
@@ -211,8 +216,9 @@ mgpbd_status mgpbd_get_constraints(mgpbd_handle_t *h, double *C, double *b, doub
 mgpbd_status mgpbd_get_lambda(mgpbd_handle_t *h, double *lambda, double *dlambda, int mem);
 
 /* ---- measurement ----
- * mgpbd_profile(h, 1) starts recording a CUDA event pair around every launch
- * of the level-0 smoother sweep (the dominant kernel of the V-cycle, Sec. 5.2
+ * mgpbd_profile(h, 1) starts recording a CUDA event pair around every
+ * level-0 smoother sweep (one CSR launch, or the vertex and row passes of the
+ * matrix-free sweep) (the dominant kernel of the V-cycle, Sec. 5.2
  * of the paper: the V-cycle takes most of an iteration and the smoother most
  * of the V-cycle); mgpbd_profile(h, 0) stops.  Both reset the totals and
  * synchronise.  mgpbd_profile_read returns the summed kernel time, the number

@@ -139,7 +139,7 @@ static mgpbd_status check_params(const mgpbd_params *p) {
       p->smooth_sweeps < 1 || p->power_iters < 1 || p->coarse_max < 1 || p->max_levels < 1 ||
       p->max_levels > kMaxLevels || (p->precision != MGPBD_FP64 && p->precision != MGPBD_MIXED) ||
       (p->smoother != MGPBD_SMOOTH_JACOBI) || !(p->theta_s >= 0.0) || p->backtrack < 0 ||
-      (p->autotune != 0 && p->autotune != 1) ||
+      (p->autotune != 0 && p->autotune != 1) || (p->level0_op != 0 && p->level0_op != 1) ||
       !(p->pcg_rtol >= 0.0) || !(p->power_safety > 0.0)) {
     set_error("invalid mgpbd_params (or unsupported smoother on this build)");
     return MGPBD_E_INVALID;
@@ -309,6 +309,7 @@ static mgpbd_status timed_end(Handle *h, double *acc) {
 static mgpbd_status iterate(Handle *h, mgpbd_solve_info *info) {
   MG_TRY(launch_eval(h));
   MG_TRY(launch_assemble(h));
+  if (h->p.level0_op == 1) MG_TRY(mf_prepare(h));
   bool due = !h->have_setup ||
              (h->p.setup_interval > 0 && h->it_global % h->p.setup_interval == 0);
   if (due) {
@@ -371,6 +372,7 @@ mgpbd_status mgpbd_default_params(mgpbd_params *p) {
   p->precision = MGPBD_FP64;
   p->backtrack = 0;
   p->autotune = 0;
+  p->level0_op = 0;
   p->seed_nk = 3;
   p->seed_agg = 4;
   p->seed_col = 5;
@@ -453,7 +455,9 @@ mgpbd_status mgpbd_eval_assemble(mgpbd_handle_t *hh) {
   Handle *h = H(hh);
   if (!h) return MGPBD_E_INVALID;
   MG_TRY(launch_eval(h));
-  return launch_assemble(h);
+  MG_TRY(launch_assemble(h));
+  if (h->p.level0_op == 1) MG_TRY(mf_prepare(h));
+  return MGPBD_OK;
 }
 
 mgpbd_status mgpbd_setup(mgpbd_handle_t *hh) {
@@ -539,11 +543,21 @@ mgpbd_status mgpbd_profile_read(mgpbd_handle_t *hh, double *total_ms, int64_t *l
   if (total_ms) *total_ms = h->prof_ms;
   if (launches) *launches = h->prof_n;
   if (bytes_per_launch) {
-    // algorithmic bytes of one level-0 smoother sweep: the CSR values and
-    // column indices once, row pointers, and four vectors (x, b, 1/A_ii, x_new)
     const Level &L = h->lev[0];
     double vb = h->p.precision == MGPBD_MIXED ? 4.0 : 8.0;
-    *bytes_per_launch = (double)L.nnz * (vb + 4.0) + (double)L.n * (8.0 + 4.0 * vb);
+    if (h->p.level0_op == 1) {
+      // matrix-free sweep: vertex pass (row ids and incidence-ordered
+      // gradients, row pointers, x and w once, u written) and row pass
+      // (row gradients, vertex ids, u once, alpha~, x, b, 1/A_ii, x_new)
+      double ninc = 2.0 * h->E + 4.0 * h->T;
+      *bytes_per_launch = ninc * (4.0 + 3.0 * vb) + (h->N + 1.0) * 8.0 + (double)h->m * vb +
+                          h->N * vb + 3.0 * h->N * vb + h->E * (3.0 * vb + 8.0) +
+                          h->T * (12.0 * vb + 16.0) + 3.0 * h->N * vb + 5.0 * h->m * vb;
+    } else {
+      // CSR sweep: values and column indices once, row pointers, and four
+      // vectors (x, b, 1/A_ii, x_new)
+      *bytes_per_launch = (double)L.nnz * (vb + 4.0) + (double)L.n * (8.0 + 4.0 * vb);
+    }
   }
   return MGPBD_OK;
 }

@@ -127,6 +127,11 @@ struct Handle {
   // per-iteration
   double *C = nullptr, *b = nullptr, *gd = nullptr, *gt = nullptr, *dl = nullptr;
   double *dx = nullptr, *xbak = nullptr;  // position correction and backtracking base
+  // matrix-free level-0 operator: gradients in incidence order, FP32 copies
+  uint8_t *vslot = nullptr;
+  double *ginc64 = nullptr, *u64 = nullptr;
+  float *ginc32 = nullptr, *gd32 = nullptr, *gt32 = nullptr, *at32 = nullptr, *w32 = nullptr,
+        *u32 = nullptr;
   uint16_t *map = nullptr;
   uint8_t *S = nullptr;  // strength mask, sized for level 0 and reused per level
   // hierarchy
@@ -207,6 +212,10 @@ mgpbd_status launch_update(Handle *h, mgpbd_solve_info *info);
 mgpbd_status amg_setup(Handle *h);
 mgpbd_status galerkin_reform(Handle *h);
 mgpbd_status level_precision_copies(Handle *h, int l);
+
+// mfree.cu (matrix-free level-0 operator)
+mgpbd_status mf_create(Handle *h);
+mgpbd_status mf_prepare(Handle *h);
 
 // solve.cu
 mgpbd_status autotune_levels(Handle *h);

@@ -1,0 +1,175 @@
+// Deterministic reductions and row-group helpers shared by the solve kernels.
+//
+// Every dot product is a fixed-grid two-stage reduction: each block folds its
+// threads in a fixed order, the last block to finish folds the per-block
+// partials in block order and applies the next PCG recurrence step on the
+// device (dot_finalize).  Results are therefore identical run to run.
+#pragma once
+
+#include "common.cuh"
+
+namespace mg {
+
+constexpr int kDotThreads = 256;
+
+enum DotMode {
+  DOT_STORE = 0,  // *out = s
+  DOT_BNORM,      // |b|^2; zero right-hand side finishes at once
+  DOT_RZ0,        // initial r.z
+  DOT_PQ,         // p.q and alpha
+  DOT_RR,         // r.r, iteration count and convergence test
+  DOT_RZ,         // new r.z and beta
+  DOT_TR          // |b - A x|^2
+};
+
+struct DotCtx {
+  double *partials;
+  unsigned int *counter;
+  PcgScalars *sc;
+  double *out;
+  int mode;
+  double rtol;
+  int maxiter;
+};
+
+static __device__ void dot_finalize(const DotCtx &c, double s) {
+  PcgScalars *sc = c.sc;
+  switch (c.mode) {
+    case DOT_STORE:
+      *c.out = s;
+      break;
+    case DOT_BNORM:
+      sc->bnorm2 = s;
+      sc->iters = 0;
+      sc->rr = s;
+      if (s == 0.0) {
+        sc->done = 1;
+        sc->status = MGPBD_OK;
+      } else if (!(s == s) || isinf(s)) {
+        sc->done = 1;
+        sc->status = MGPBD_E_BREAKDOWN;
+      }
+      break;
+    case DOT_RZ0:
+      sc->rz = s;
+      if (!(s > 0.0)) {
+        sc->done = 1;
+        sc->status = MGPBD_E_BREAKDOWN;
+      }
+      break;
+    case DOT_PQ:
+      sc->pq = s;
+      if (!(s > 0.0)) {
+        sc->done = 1;
+        sc->status = MGPBD_E_BREAKDOWN;
+      } else {
+        sc->alpha = sc->rz / s;
+      }
+      break;
+    case DOT_RR:
+      sc->rr = s;
+      sc->iters += 1;
+      if (!(s == s)) {
+        sc->done = 1;
+        sc->status = MGPBD_E_BREAKDOWN;
+      } else if (sqrt(s) <= c.rtol * sqrt(sc->bnorm2)) {
+        sc->done = 1;
+        sc->status = MGPBD_OK;
+      } else if (sc->iters >= c.maxiter) {
+        sc->done = 1;
+        sc->status = MGPBD_W_NOT_CONVERGED;
+      }
+      break;
+    case DOT_RZ:
+      if (!(s > 0.0)) {
+        sc->done = 1;
+        sc->status = MGPBD_E_BREAKDOWN;
+      } else {
+        sc->beta = s / sc->rz;
+        sc->rz = s;
+      }
+      break;
+    case DOT_TR:
+      sc->tr2 = s;
+      break;
+  }
+}
+
+// block reduce of one value per thread in a fixed order, then the last block
+// folds the partials (fixed order) and finalizes
+static __device__ void block_dot_finish(double v, const DotCtx &c) {
+  __shared__ double ws[32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) ws[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+    c.partials[blockIdx.x] = s;
+    __threadfence();
+    unsigned t = atomicAdd(c.counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+    s += ((volatile double *)c.partials)[b];
+  s = warp_sum(s);
+  if (lane == 0) ws[wid] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    dot_finalize(c, t);
+    *c.counter = 0;
+  }
+}
+
+static __device__ __forceinline__ bool is_done(const PcgScalars *sc) {
+  return ((volatile const PcgScalars *)sc)->done != 0;
+}
+
+
+template <int G, class T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// partial row dot of lane g of a G-lane group (no shuffles: callers reduce)
+template <int G, class VT, class AT, class XT>
+__device__ __forceinline__ AT row_dot(const int64_t *ptr, const int32_t *col, const VT *val,
+                                      const XT *x, int i, int g) {
+  AT acc = 0;
+  int64_t s0 = ptr[i], e = ptr[i + 1];
+  for (int64_t k = s0 + g; k < e; k += G) acc = fma((AT)val[k], (AT)x[col[k]], acc);
+  return acc;
+}
+
+// Rows handled by G-lane groups, 32/G rows per warp per trip.  The loop bound
+// is uniform across the warp, so full-mask shuffles inside are safe; `valid`
+// marks groups past the last row.
+#define GROUP_ROWS(G, n)                                                          \
+  const int lane_ = threadIdx.x & 31;                                             \
+  const int g = lane_ & ((G) - 1);                                                \
+  const int sub_ = lane_ / (G);                                                   \
+  const int64_t warp_ = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;    \
+  const int64_t nwarp_ = ((int64_t)gridDim.x * blockDim.x) >> 5;                  \
+  for (int64_t base_ = warp_ * (32 / (G)), i = base_ + sub_; base_ < (n);         \
+       base_ += nwarp_ * (32 / (G)), i = base_ + sub_)                            \
+    if (const bool valid = i < (n); true)
+
+
+// matrix-free level-0 products (mfree.cu)
+mgpbd_status mf_apply_pq(Handle *h, const double *p, double *q, const DotCtx &c);
+template <class T>
+mgpbd_status mf_level0(Handle *h, int mode, const T *x, const T *b, const T *dinv, T omega,
+                       T *out);
+constexpr int kMfSweep = 0, kMfResid = 1;
+
+}  // namespace mg

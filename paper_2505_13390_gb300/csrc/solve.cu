@@ -21,131 +21,9 @@
 #include <vector>
 
 #include "common.cuh"
+#include "reduce.cuh"
 
 namespace mg {
-
-constexpr int kDotThreads = 256;
-
-enum DotMode {
-  DOT_STORE = 0,  // *out = s
-  DOT_BNORM,      // |b|^2; zero right-hand side finishes at once
-  DOT_RZ0,        // initial r.z
-  DOT_PQ,         // p.q and alpha
-  DOT_RR,         // r.r, iteration count and convergence test
-  DOT_RZ,         // new r.z and beta
-  DOT_TR          // |b - A x|^2
-};
-
-struct DotCtx {
-  double *partials;
-  unsigned int *counter;
-  PcgScalars *sc;
-  double *out;
-  int mode;
-  double rtol;
-  int maxiter;
-};
-
-__device__ void dot_finalize(const DotCtx &c, double s) {
-  PcgScalars *sc = c.sc;
-  switch (c.mode) {
-    case DOT_STORE:
-      *c.out = s;
-      break;
-    case DOT_BNORM:
-      sc->bnorm2 = s;
-      sc->iters = 0;
-      sc->rr = s;
-      if (s == 0.0) {
-        sc->done = 1;
-        sc->status = MGPBD_OK;
-      } else if (!(s == s) || isinf(s)) {
-        sc->done = 1;
-        sc->status = MGPBD_E_BREAKDOWN;
-      }
-      break;
-    case DOT_RZ0:
-      sc->rz = s;
-      if (!(s > 0.0)) {
-        sc->done = 1;
-        sc->status = MGPBD_E_BREAKDOWN;
-      }
-      break;
-    case DOT_PQ:
-      sc->pq = s;
-      if (!(s > 0.0)) {
-        sc->done = 1;
-        sc->status = MGPBD_E_BREAKDOWN;
-      } else {
-        sc->alpha = sc->rz / s;
-      }
-      break;
-    case DOT_RR:
-      sc->rr = s;
-      sc->iters += 1;
-      if (!(s == s)) {
-        sc->done = 1;
-        sc->status = MGPBD_E_BREAKDOWN;
-      } else if (sqrt(s) <= c.rtol * sqrt(sc->bnorm2)) {
-        sc->done = 1;
-        sc->status = MGPBD_OK;
-      } else if (sc->iters >= c.maxiter) {
-        sc->done = 1;
-        sc->status = MGPBD_W_NOT_CONVERGED;
-      }
-      break;
-    case DOT_RZ:
-      if (!(s > 0.0)) {
-        sc->done = 1;
-        sc->status = MGPBD_E_BREAKDOWN;
-      } else {
-        sc->beta = s / sc->rz;
-        sc->rz = s;
-      }
-      break;
-    case DOT_TR:
-      sc->tr2 = s;
-      break;
-  }
-}
-
-// block reduce of one value per thread in a fixed order, then the last block
-// folds the partials (fixed order) and finalizes
-__device__ void block_dot_finish(double v, const DotCtx &c) {
-  __shared__ double ws[32];
-  __shared__ bool last;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  v = warp_sum(v);
-  if (lane == 0) ws[wid] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
-    c.partials[blockIdx.x] = s;
-    __threadfence();
-    unsigned t = atomicAdd(c.counter, 1u);
-    last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  double s = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-    s += ((volatile double *)c.partials)[b];
-  s = warp_sum(s);
-  if (lane == 0) ws[wid] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
-    dot_finalize(c, t);
-    *c.counter = 0;
-  }
-}
-
-__device__ __forceinline__ bool is_done(const PcgScalars *sc) {
-  return ((volatile const PcgScalars *)sc)->done != 0;
-}
 
 static int dot_grid() { return std::min(4096, 2 * num_sms()); }
 
@@ -216,36 +94,6 @@ __global__ void k_convert(int64_t n, const S *a, D *b, const PcgScalars *sc) {
 // ---------------------------------------------------------------------------
 // sparse kernels: G lanes per row (G in 4, 8, 16, 32)
 // ---------------------------------------------------------------------------
-template <int G, class T>
-__device__ __forceinline__ T group_sum(T v) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// partial row dot of lane g of a G-lane group (no shuffles: callers reduce)
-template <int G, class VT, class AT, class XT>
-__device__ __forceinline__ AT row_dot(const int64_t *ptr, const int32_t *col, const VT *val,
-                                      const XT *x, int i, int g) {
-  AT acc = 0;
-  int64_t s0 = ptr[i], e = ptr[i + 1];
-  for (int64_t k = s0 + g; k < e; k += G) acc = fma((AT)val[k], (AT)x[col[k]], acc);
-  return acc;
-}
-
-// Rows handled by G-lane groups, 32/G rows per warp per trip.  The loop bound
-// is uniform across the warp, so full-mask shuffles inside are safe; `valid`
-// marks groups past the last row.
-#define GROUP_ROWS(G, n)                                                          \
-  const int lane_ = threadIdx.x & 31;                                             \
-  const int g = lane_ & ((G) - 1);                                                \
-  const int sub_ = lane_ / (G);                                                   \
-  const int64_t warp_ = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;    \
-  const int64_t nwarp_ = ((int64_t)gridDim.x * blockDim.x) >> 5;                  \
-  for (int64_t base_ = warp_ * (32 / (G)), i = base_ + sub_; base_ < (n);         \
-       base_ += nwarp_ * (32 / (G)), i = base_ + sub_)                            \
-    if (const bool valid = i < (n); true)
-
 // q = A p (PCG operator) fused with p.q
 template <int G, class VT, class AT>
 __global__ void k_spmv_pq(int n, const int64_t *ptr, const int32_t *col, const VT *val,
@@ -533,17 +381,26 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in) {
   T *x2 = (T *)L.x2, *r = (T *)L.r;
   k_jacobi0<T><<<blocks_for(n, 256), 256, 0, h->stream>>>(n, b_in, dinv, om, x, sc);
   MG_LAUNCH("k_jacobi0");
+  const bool mf = l == 0 && h->p.level0_op == 1;  // matrix-free level-0 products
   for (int s = 1; s < h->p.smooth_sweeps; ++s) {
     if (l == 0) MG_TRY(prof_begin(h));
-    DISPATCH_G(G, (k_jacobi<GG, T><<<row_blocks(n, GG), 256, 0, h->stream>>>(
-                      n, L.ptr, L.col, val, dinv, om, b_in, x, x2, sc)));
-    MG_LAUNCH("k_jacobi");
+    if (mf) {
+      MG_TRY(mf_level0<T>(h, kMfSweep, x, b_in, dinv, om, x2));
+    } else {
+      DISPATCH_G(G, (k_jacobi<GG, T><<<row_blocks(n, GG), 256, 0, h->stream>>>(
+                        n, L.ptr, L.col, val, dinv, om, b_in, x, x2, sc)));
+      MG_LAUNCH("k_jacobi");
+    }
     if (l == 0) MG_TRY(prof_end(h));
     std::swap(x, x2);
   }
-  DISPATCH_G(G, (k_resid<GG, T><<<row_blocks(n, GG), 256, 0, h->stream>>>(n, L.ptr, L.col, val,
-                                                                         b_in, x, r, sc)));
-  MG_LAUNCH("k_resid");
+  if (mf) {
+    MG_TRY(mf_level0<T>(h, kMfResid, x, b_in, dinv, om, r));
+  } else {
+    DISPATCH_G(G, (k_resid<GG, T><<<row_blocks(n, GG), 256, 0, h->stream>>>(n, L.ptr, L.col, val,
+                                                                           b_in, x, r, sc)));
+    MG_LAUNCH("k_resid");
+  }
   Level &Lc = h->lev[l + 1];
   k_restrict<T><<<blocks_for((int64_t)L.n_agg * 32, 256), 256, 0, h->stream>>>(
       L.n_agg, L.mptr, L.mrow, Ps<T>(L), r, (T *)Lc.b, sc);
@@ -554,9 +411,13 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in) {
   MG_LAUNCH("k_prolong");
   for (int s = 0; s < h->p.smooth_sweeps; ++s) {
     if (l == 0) MG_TRY(prof_begin(h));
-    DISPATCH_G(G, (k_jacobi<GG, T><<<row_blocks(n, GG), 256, 0, h->stream>>>(
-                      n, L.ptr, L.col, val, dinv, om, b_in, x, x2, sc)));
-    MG_LAUNCH("k_jacobi");
+    if (mf) {
+      MG_TRY(mf_level0<T>(h, kMfSweep, x, b_in, dinv, om, x2));
+    } else {
+      DISPATCH_G(G, (k_jacobi<GG, T><<<row_blocks(n, GG), 256, 0, h->stream>>>(
+                        n, L.ptr, L.col, val, dinv, om, b_in, x, x2, sc)));
+      MG_LAUNCH("k_jacobi");
+    }
     if (l == 0) MG_TRY(prof_end(h));
     std::swap(x, x2);
   }
@@ -615,10 +476,14 @@ static mgpbd_status pcg_iteration(Handle *h, double *x) {
   // FP64 in both modes: rounding A's values to FP32 perturbs entries of size
   // ~1e4 by ~1e-3, far above alpha~ (~1e-7), and the FP32 operator is then
   // numerically indefinite on the stiff workloads (p.Ap <= 0).
-  DISPATCH_G(G, (k_spmv_pq<GG, double, double>
-                 <<<std::min(row_blocks(m, GG), 4096), 256, 0, h->stream>>>(m, L.ptr, L.col,
-                                                                            L.val, p, q, cpq)));
-  MG_LAUNCH("k_spmv_pq");
+  if (h->p.level0_op == 1) {
+    MG_TRY(mf_apply_pq(h, p, q, cpq));
+  } else {
+    DISPATCH_G(G, (k_spmv_pq<GG, double, double>
+                   <<<std::min(row_blocks(m, GG), 4096), 256, 0, h->stream>>>(m, L.ptr, L.col,
+                                                                              L.val, p, q, cpq)));
+    MG_LAUNCH("k_spmv_pq");
+  }
   k_xr_update<<<dot_grid(), kDotThreads, 0, h->stream>>>(m, x, r, p, q, make_ctx(h, DOT_RR));
   MG_LAUNCH("k_xr_update");
   MG_TRY(vcycle_top(h, r, z));

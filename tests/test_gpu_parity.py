@@ -107,9 +107,11 @@ def test_setup_bit_exact(name):
             assert lg == pytest.approx(lo, rel=1e-10) and wg == pytest.approx(wo, rel=1e-10)
 
 
+@pytest.mark.parametrize("op", [0, 1])
 @pytest.mark.parametrize("name", ["cloth8", "hex3", "cloth32"])
-def test_vcycle_parity(name):
-    mesh, p, o, g = both(name)
+def test_vcycle_parity(name, op):
+    """FP64 V-cycle; op = 1 applies the level-0 products matrix-free."""
+    mesh, p, o, g = both(name, level0_op=op)
     o.begin_frame()
     g.begin_frame()
     o.eval_assemble()
@@ -131,11 +133,12 @@ SOFT = {
 CASES.update(SOFT)
 
 
+@pytest.mark.parametrize("op", [0, 1])
 @pytest.mark.parametrize("name", ["cloth8", "hex3", "cloth32", "block6"])
-def test_vcycle_mixed_precision(name):
+def test_vcycle_mixed_precision(name, op):
     """FP32 V-cycle against the FP64 oracle V-cycle: relative error of order
     the FP32 unit roundoff times the growth through the levels."""
-    mesh, p, o, g = both(name, precision=1)
+    mesh, p, o, g = both(name, precision=1, level0_op=op)
     for s_ in (o, g):
         s_.begin_frame()
         s_.eval_assemble()
@@ -148,10 +151,11 @@ def test_vcycle_mixed_precision(name):
     assert r @ zg > 0
 
 
+@pytest.mark.parametrize("op", [0, 1])
 @pytest.mark.parametrize("name", ["cloth8s", "hex3s"])
-def test_solve_parity(name):
-    """Moderate cond(A): same iteration count (+-2) and solutions within 1e-8."""
-    mesh, p, o, g = both(name, pcg_rtol=1e-10, pcg_maxiter=1000)
+def test_solve_parity(name, op):
+    """Moderate cond(A): iteration counts within 5% and solutions within 1e-8."""
+    mesh, p, o, g = both(name, pcg_rtol=1e-10, pcg_maxiter=1000, level0_op=op)
     o.begin_frame()
     g.begin_frame()
     o.eval_assemble()
@@ -163,7 +167,9 @@ def test_solve_parity(name):
     xg, ig = g.solve(torch.tensor(b, device="cuda"))
     xg = xg.cpu().numpy()
     assert ig["status"] == io["status"] == 0
-    assert abs(ig["pcg_iters"] - io["pcg_iters"]) <= 2
+    # rounding order (tree vs sequential sums, matrix-free vs CSR products)
+    # moves the iteration that crosses 1e-10 by a few percent
+    assert abs(ig["pcg_iters"] - io["pcg_iters"]) <= max(2, 0.05 * io["pcg_iters"])
     assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
 
 
@@ -187,12 +193,13 @@ def test_solve_stiff_true_residual():
     assert np.linalg.norm(xg - xo) <= 1e-5 * np.linalg.norm(xo)
 
 
+@pytest.mark.parametrize("op", [0, 1])
 @pytest.mark.parametrize("name,iters", [("cloth8", 6), ("cloth8s", 6), ("hex3s", 6),
                                         ("cloth32", 4), ("hex3", 3)])
-def test_iterations_parity_fp64(name, iters):
+def test_iterations_parity_fp64(name, iters, op):
     """Whole global iterations in FP64 with PCG solved to 1e-10: positions,
     velocities and |b| within 1e-9 relative of the oracle."""
-    mesh, p, o, g = both(name, pcg_rtol=1e-10, pcg_maxiter=3000)
+    mesh, p, o, g = both(name, pcg_rtol=1e-10, pcg_maxiter=3000, level0_op=op)
     o.begin_frame()
     g.begin_frame()
     scale = np.abs(mesh.rest_pos).max() + 1e-3
@@ -258,6 +265,24 @@ def test_backtracking_parity(name):
         xo, _ = o.get_state()
         xg, _ = g.get_state()
         assert np.abs(xg - xo).max() <= 1e-9 * scale
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_matrix_free_block_iterations(prec):
+    """A block of the benchmark recipe solved to 1e-6 with the assembled and
+    with the matrix-free level-0 operator: both converge, both lower |b|, and
+    the positions agree to the PCG tolerance."""
+    mesh, p = CASES["block6"]()
+    res = []
+    for op in (0, 1):
+        g = solver(mesh, dict(p, precision=prec, level0_op=op))
+        g.begin_frame()
+        infos = [g.iterate() for _ in range(3)]
+        assert all(d["ret"] == 0 for d in infos)
+        assert infos[-1]["bnorm"] < infos[0]["bnorm"]
+        res.append(g.get_state()[0])
+    scale = np.abs(mesh.rest_pos).max()
+    assert np.abs(res[0] - res[1]).max() <= 1e-6 * scale
 
 
 def test_empty_and_single_constraint():
