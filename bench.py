@@ -43,6 +43,11 @@ FULL_PCG_ITERS = 7300
 # (k_jacobi<8, float>, 494.06 MB for 59,625,809 nonzeros); the sweep's
 # traffic grows in proportion to nnz, so it scales to a full launch
 SWEEP_TRAFFIC_PER_NNZ = 494.058240e6 / 59_625_809
+# DRAM bytes of one matrix-free level-0 FP32 sweep (k_mf_vertex<float> 30.51 MB
+# + k_mf_row<float,0> 33.68 MB) per constraint row, from the ncu captures in
+# profiles/k_mf_sweep_level0_block40x33x40.md (593,633 rows); the passes
+# stream per-row and per-incidence arrays, so traffic scales with the rows
+MF_SWEEP_TRAFFIC_PER_ROW = (30.514176e6 + 33.680384e6) / 593_633
 SAMPLE = (4, 33, 4)     # oracle sample: cells along x, y (vertical), z
 SAMPLE_PCG = 500        # PCG iterations per sampled global iteration (cost is linear in them)
 
@@ -60,6 +65,12 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--level0-op", type=int, default=1,
+                    help="1: matrix-free level-0 products (headline); 0: assembled CSR")
+    ap.add_argument("--no-assembled", action="store_true",
+                    help="skip the assembled-CSR comparison line")
+    ap.add_argument("--assembled-steps", type=int, default=1)
+    ap.add_argument("--assembled-warmup", type=int, default=1)
     return ap.parse_args()
 
 
@@ -174,6 +185,18 @@ class Runner:
             self.g.end_frame()
             self.g.begin_frame()
         return d
+
+
+def _measured_hbm():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs")
+    except Exception:
+        return None
+
+
+def hbm_peak() -> float:
+    """Measured copy bandwidth (GB/s) of the GB300s, else 6,800 GB/s."""
+    return _measured_hbm() or 6800.0
 
 
 def measure(mesh, params, steps, warmup, ws, profile=True):
@@ -292,7 +315,7 @@ def run_ours(args, ws, rank):
         ge.build()
     cpu = None
     mesh, params = workload(args.workload)
-    params = dict(params, precision=1, autotune=1)
+    params = dict(params, precision=1, autotune=1, level0_op=args.level0_op)
     res = measure(mesh, params, args.steps, args.warmup, ws)
     ms = max_over_ranks(ws, res["ms"])
     value = ws * args.steps / (ms / 1e3)
@@ -302,14 +325,8 @@ def run_ours(args, ws, rank):
     li = g.level_info(0)
     if li["nnz"] != FULL_NNZ and args.workload == "block100":
         raise RuntimeError(f"unexpected nnz {li['nnz']}")
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm = peaks.get("hbm_gbs")
-    peak_src = "measured" if hbm else "fallback"
-    hbm = hbm or 6800.0
+    hbm = hbm_peak()
+    peak_src = "measured" if _measured_hbm() else "fallback"
     avg_ms = prof["total_ms"] / max(prof["launches"], 1)
     achieved = prof["bytes_per_launch"] / (avg_ms / 1e3) / 1e9
     e2e_val = None
@@ -318,10 +335,31 @@ def run_ours(args, ws, rank):
         e2e_val, e2e_bytes = e2e(g, res["runner"], args.e2e_steps)
         e2e_val = e2e_val * ws
     fp64 = None
+    assembled = None
     levels = [g.level_info(l) for l in range(g.levels)]
     g.close()
     del res["solver"], res["runner"]
     torch.cuda.empty_cache()
+    if args.level0_op == 1 and not args.no_assembled:
+        pa = dict(params, level0_op=0)
+        ra = measure(mesh, pa, args.assembled_steps, args.assembled_warmup, ws)
+        msa = max_over_ranks(ws, ra["ms"])
+        pr = ra["prof"]
+        aa = pr["bytes_per_launch"] / (pr["total_ms"] / max(pr["launches"], 1) / 1e3) / 1e9
+        assembled = {"value": ws * args.assembled_steps / (msa / 1e3),
+                     "ms_per_step": msa / args.assembled_steps,
+                     "steps": args.assembled_steps, "warmup": args.assembled_warmup,
+                     "pcg_iters": ra["pcg"], "clocks": ra["clocks"],
+                     "roofline": {"bound": "hbm",
+                                  "kernel": "k_jacobi (level-0 CSR weighted-Jacobi sweep, FP32)",
+                                  "achieved": aa, "peak": hbm_peak(), "unit": "GB/s",
+                                  "frac": aa / hbm_peak(),
+                                  "bytes_per_launch": pr["bytes_per_launch"],
+                                  "avg_launch_ms": pr["total_ms"] / max(pr["launches"], 1),
+                                  "traffic": SWEEP_TRAFFIC_PER_NNZ * li["nnz"]}}
+        ra["solver"].close()
+        del ra
+        torch.cuda.empty_cache()
     if not args.no_fp64:
         p64 = dict(params, precision=0)
         r64 = measure(mesh, p64, args.fp64_steps, args.fp64_warmup, ws)
@@ -352,18 +390,24 @@ def run_ours(args, ws, rank):
         "dtype": "f32+f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "rows": li["n"], "nnz": li["nnz"],
+                   "level0_operator": "matrix-free" if args.level0_op == 1 else "assembled CSR",
                    "tets": mesh.n_tet, "verts": mesh.n_verts, "iters_per_frame": 20,
                    "setup_interval": params["setup_interval"], "pcg_rtol": 1e-6,
                    "pcg_maxiter": params["pcg_maxiter"], "parallelism": f"replicas{ws}",
                    "l2": "inputs larger than L2 (A is 3.1 GB in FP32, 4.6 GB in FP64)",
                    "levels": [(l["n"], l["nnz"]) for l in levels]},
         "pcg_iters": res["pcg"],
-        "roofline": {"bound": "hbm", "kernel": "k_jacobi (level-0 weighted-Jacobi sweep, FP32)",
+        "roofline": {"bound": "hbm",
+                     "kernel": ("level-0 matrix-free weighted-Jacobi sweep, FP32 "
+                                "(k_mf_vertex + k_mf_row)") if args.level0_op == 1 else
+                               "k_jacobi (level-0 CSR weighted-Jacobi sweep, FP32)",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_source": peak_src,
-                     "traffic": SWEEP_TRAFFIC_PER_NNZ * li["nnz"],
-                     "traffic_source": "ncu dram__bytes_read+write of k_jacobi<8,float> on a "
-                                       "40x33x40 block, scaled by nnz",
+                     "traffic": ((MF_SWEEP_TRAFFIC_PER_ROW * li["n"])
+                                 if MF_SWEEP_TRAFFIC_PER_ROW else None) if args.level0_op == 1
+                                else SWEEP_TRAFFIC_PER_NNZ * li["nnz"],
+                     "traffic_source": "ncu dram__bytes_read+write on a 40x33x40 block of the "
+                                       "same recipe, scaled by the units processed",
                      "bytes_per_launch": prof["bytes_per_launch"], "avg_launch_ms": avg_ms,
                      "launches": prof["launches"]},
         "cpu_baseline": cpu,
@@ -372,6 +416,7 @@ def run_ours(args, ws, rank):
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
         "fp64": fp64,
+        "assembled": assembled,
         "create_s": res["create_s"],
         "stats": {k: res["stats"][k] for k in ("levels", "op_complexity", "device_bytes")},
     }
