@@ -84,11 +84,19 @@ def dist_init(args):
     if ws > 1:
         import torch
         import torch.distributed as dist
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
-        if torch.cuda.is_available():
+        backend = os.environ.get("MGPBD_DIST_BACKEND") or (
+            "nccl" if torch.cuda.is_available() else "gloo")
+        if backend == "nccl":
             torch.cuda.set_device(local)
         dist.init_process_group(backend=backend)
     return ws, rank, local
+
+
+def job_rate(ws: int, steps: int, ms_local: float):
+    """Whole-job global iterations/s of N replicas: every rank ran `steps`
+    steps; the job takes as long as its slowest rank (max over ranks)."""
+    ms = max_over_ranks(ws, ms_local)
+    return ws * steps / (ms / 1e3), ms
 
 
 def barrier(ws):
@@ -102,7 +110,7 @@ def max_over_ranks(ws, v: float) -> float:
         return v
     import torch
     import torch.distributed as dist
-    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
     t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
@@ -317,8 +325,7 @@ def run_ours(args, ws, rank):
     mesh, params = workload(args.workload)
     params = dict(params, precision=1, autotune=1, level0_op=args.level0_op)
     res = measure(mesh, params, args.steps, args.warmup, ws)
-    ms = max_over_ranks(ws, res["ms"])
-    value = ws * args.steps / (ms / 1e3)
+    value, ms = job_rate(ws, args.steps, res["ms"])
     prof = res["prof"]
     g = res["solver"]
     nnz = res["stats"]
