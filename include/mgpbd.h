@@ -98,6 +98,11 @@ typedef struct {
                            + alpha~ x through the constraint gradients (the paper's
                            future-work direction, Sec. 6).  Setup and Galerkin
                            products always use the assembled matrix. */
+  int use_graphs;       /* 1: capture chunks of 8 PCG iterations into a CUDA graph and
+                           replay it (one launch instead of ~40 per iteration; the
+                           graph is re-captured after each setup); 0: plain launches.
+                           Needs a stream of the caller's own: on the legacy default
+                           stream (NULL) launches stay plain. */
   uint64_t seed_nk, seed_agg, seed_col, seed_pow;
 } mgpbd_params;
 
@@ -230,6 +235,50 @@ mgpbd_status mgpbd_profile(mgpbd_handle_t *h, int enable);
 mgpbd_status mgpbd_profile_read(mgpbd_handle_t *h, double *total_ms, int64_t *launches,
                                 double *bytes_per_launch);
 unsigned long long mgpbd_launch_count(void);
+
+/* ---- serving: continuous batching of many instances ----
+ * Not in the paper, which steps one instance at a time.  A batch holds many
+ * instances (meshes with their parameters and state) and serves step
+ * requests: one request = `frames` frames of Alg. 1 on one instance.
+ * mgpbd_batch_run admits a request once its arrival time has passed, its
+ * instance is idle, a worker is free and the instance fits the device-memory
+ * budget (idle resident instances are evicted least recently used first;
+ * their state moves to host memory and back on their next admission).  Up to
+ * max_active instances run at the same time on their own streams and host
+ * worker threads.  Requests of one instance run in arrival order.  The call
+ * returns when every request has finished; results carry arrival, start and
+ * finish times (seconds from the start of the call) for latency statistics.
+ * A request whose instance can never fit the budget fails with
+ * MGPBD_E_BUDGET.  Instances must not be added while a run is in progress. */
+typedef struct mgpbd_batch mgpbd_batch_t;
+typedef struct {
+  size_t hbm_budget;  /* bytes of device memory the resident instances may hold */
+  int max_active;     /* instances stepping at the same time (worker threads) */
+} mgpbd_batch_config;
+typedef struct {
+  int id;             /* caller's request id, copied to the result */
+  int instance;       /* instance index returned by mgpbd_batch_add_instance */
+  int frames;         /* frames of Alg. 1 to run (each max_iter global iterations) */
+  double arrival_s;   /* arrival time, seconds after mgpbd_batch_run starts */
+} mgpbd_step_request;
+typedef struct {
+  int id, instance, status;
+  double arrival_s, start_s, finish_s;  /* latency = finish_s - arrival_s */
+  int64_t global_iters, pcg_iters;
+} mgpbd_step_result;
+mgpbd_status mgpbd_batch_create(const mgpbd_batch_config *cfg, mgpbd_batch_t **out);
+/* copies the mesh (host pointers) and the initial state (x0/v0 may be NULL:
+ * rest positions, zero velocity); the instance is not resident until needed */
+mgpbd_status mgpbd_batch_add_instance(mgpbd_batch_t *b, const mgpbd_mesh_desc *mesh,
+                                      const mgpbd_params *p, const double *x0, const double *v0,
+                                      int *instance);
+mgpbd_status mgpbd_batch_run(mgpbd_batch_t *b, const mgpbd_step_request *req, int n_req,
+                             mgpbd_step_result *res);
+/* host copy of an instance's positions/velocities (synchronises if resident) */
+mgpbd_status mgpbd_batch_get_state(mgpbd_batch_t *b, int instance, double *x, double *v);
+/* resident instances and bytes held now */
+mgpbd_status mgpbd_batch_resident(mgpbd_batch_t *b, int *n_resident, size_t *bytes);
+void mgpbd_batch_destroy(mgpbd_batch_t *b);
 
 /* ---- allocation-free entry point ----
  * The paper has no counterpart of this call; it exists for callers that

@@ -54,6 +54,7 @@ mgpbd_status prof_harvest(Handle *h, int iters) {
 void set_error(const std::string &msg) { g_err = msg; }
 
 mgpbd_status cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+  cudaGetLastError();  // a failed call must not resurface at the next launch check
   char buf[512];
   snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
   set_error(buf);
@@ -63,31 +64,38 @@ mgpbd_status cuda_fail(cudaError_t e, const char *what, const char *file, int li
 mgpbd_status Arena::alloc(void **p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 16;
-  cudaError_t e = cudaMalloc(p, n);
+  n = (n + 255) & ~(size_t)255;  // keep every buffer 256-byte aligned
+  cudaError_t e = cudaMallocAsync(p, n, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
     char buf[128];
-    snprintf(buf, sizeof(buf), "cudaMalloc of %zu bytes failed: %s", n, cudaGetErrorString(e));
+    snprintf(buf, sizeof(buf), "device allocation of %zu bytes failed: %s", n,
+             cudaGetErrorString(e));
     set_error(buf);
     return MGPBD_E_OOM;
   }
   bytes += n;
-  live.push_back(*p);
+  live.emplace_back(*p, n);
   return MGPBD_OK;
 }
 
 void Arena::release(void *p) {
   if (!p) return;
-  auto it = std::find(live.begin(), live.end(), p);
-  if (it != live.end()) live.erase(it);
-  cudaFree(p);
+  for (auto it = live.begin(); it != live.end(); ++it)
+    if (it->first == p) {
+      bytes -= it->second;
+      live.erase(it);
+      break;
+    }
+  cudaFreeAsync(p, stream);
 }
 
 void Arena::release_all() {
-  for (void *p : live) cudaFree(p);
+  for (auto &q : live) cudaFreeAsync(q.first, stream);
   live.clear();
   bytes = 0;
+  cudaStreamSynchronize(stream);
 }
 
 int num_sms() {
@@ -140,6 +148,7 @@ static mgpbd_status check_params(const mgpbd_params *p) {
       p->max_levels > kMaxLevels || (p->precision != MGPBD_FP64 && p->precision != MGPBD_MIXED) ||
       (p->smoother != MGPBD_SMOOTH_JACOBI) || !(p->theta_s >= 0.0) || p->backtrack < 0 ||
       (p->autotune != 0 && p->autotune != 1) || (p->level0_op != 0 && p->level0_op != 1) ||
+      (p->use_graphs != 0 && p->use_graphs != 1) ||
       !(p->pcg_rtol >= 0.0) || !(p->power_safety > 0.0)) {
     set_error("invalid mgpbd_params (or unsupported smoother on this build)");
     return MGPBD_E_INVALID;
@@ -155,6 +164,7 @@ static void destroy(Handle *h) {
   if (h->sc_host) cudaFreeHost(h->sc_host);
   if (h->flag_host) cudaFreeHost(h->flag_host);
   for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
+  if (h->pcg_graph) cudaGraphExecDestroy(h->pcg_graph);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   delete h;
@@ -204,6 +214,7 @@ static mgpbd_status create(const mgpbd_mesh_desc *md, const mgpbd_params *p, voi
 
   Handle *h = new Handle();
   h->stream = (cudaStream_t)stream;
+  h->arena.stream = h->stream;
   h->p = *p;
   h->N = md->n_verts;
   h->E = md->n_dist;
@@ -373,6 +384,7 @@ mgpbd_status mgpbd_default_params(mgpbd_params *p) {
   p->backtrack = 0;
   p->autotune = 0;
   p->level0_op = 0;
+  p->use_graphs = 0;
   p->seed_nk = 3;
   p->seed_agg = 4;
   p->seed_col = 5;

@@ -31,10 +31,10 @@ mgpbd_status cuda_fail(cudaError_t e, const char *what, const char *file, int li
     if (e_ != cudaSuccess) return mg::cuda_fail(e_, #call, __FILE__, __LINE__); \
   } while (0)
 // every kernel launch is followed by MG_LAUNCH, which also counts it
-extern unsigned long long g_launches;
+extern unsigned long long g_launches;  // updated atomically
 #define MG_LAUNCH(what)                                                   \
   do {                                                                    \
-    ++mg::g_launches;                                                     \
+    __atomic_fetch_add(&mg::g_launches, 1ull, __ATOMIC_RELAXED);          \
     cudaError_t e_ = cudaGetLastError();                                  \
     if (e_ != cudaSuccess) return mg::cuda_fail(e_, what, __FILE__, __LINE__); \
   } while (0)
@@ -47,9 +47,13 @@ extern unsigned long long g_launches;
 // ---------------------------------------------------------------------------
 // device memory owned by a handle
 // ---------------------------------------------------------------------------
+// Stream-ordered allocations on the owning handle's stream (cudaMallocAsync /
+// cudaFreeAsync): freeing never synchronises the whole device, so instances
+// that run side by side on their own streams do not stall each other.
 struct Arena {
   size_t bytes = 0;
-  std::vector<void *> live;
+  cudaStream_t stream = nullptr;
+  std::vector<std::pair<void *, size_t>> live;
   mgpbd_status alloc(void **p, size_t n);
   void release(void *p);
   void release_all();
@@ -170,6 +174,13 @@ struct Handle {
   int pcg_k = -1;                // PCG iteration being launched
   double prof_ms = 0.0;
   long long prof_n = 0;
+  // CUDA graph of a chunk of PCG iterations, valid while `graph_gen` matches
+  unsigned long long gen = 1;      // bumped whenever device pointers or setup change
+  unsigned long long graph_gen = 0;
+  const double *graph_x = nullptr;
+  int graph_chunk = 0;
+  unsigned long long graph_kernels = 0;  // kernels in one replay of the graph
+  cudaGraphExec_t pcg_graph = nullptr;
 };
 
 // event pair around one launch of the profiled kernel (no-op when disabled)

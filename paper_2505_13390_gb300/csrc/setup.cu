@@ -867,6 +867,7 @@ mgpbd_status amg_setup(Handle *h) {
   if (h->p.autotune) MG_TRY(autotune_levels(h));
   h->have_setup = true;
   h->n_setups++;
+  h->gen++;  // new hierarchy: captured PCG graphs are stale
   MG_CUDA(cudaStreamSynchronize(h->stream));
   return MGPBD_OK;
 }

@@ -285,6 +285,7 @@ mgpbd_status coarsest_factor(Handle *h) {
     MG_TRY(alloc_n(h->arena, &h->cdense, (size_t)n * n));
     MG_TRY(alloc_n(h->arena, &h->cinv, 2 * (size_t)n * n));
     h->cap_nc = n;
+    h->gen++;  // captured PCG graphs refer to the old buffers
   }
   h->nc = n;
   MG_CUDA(cudaMemsetAsync(h->cdense, 0, sizeof(double) * (size_t)n * n, h->stream));
@@ -511,11 +512,48 @@ mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *
   MG_TRY(launch_dot(h, r, z, m, DOT_RZ0, 1));
   const int chunk = 8;
   int launched = 0;
+  // Chunks of PCG iterations replay a captured CUDA graph (one launch instead
+  // of ~40 per iteration); the graph is re-captured when the hierarchy or the
+  // output array changes.  Event timing of the smoother needs plain launches.
+  // (the legacy default stream cannot be captured: graphs need the caller's own stream)
+  const bool graphs = h->p.use_graphs && !h->prof && h->stream != nullptr &&
+                      h->stream != cudaStreamLegacy && h->stream != cudaStreamPerThread;
   while (launched < h->p.pcg_maxiter) {
     int c = std::min(chunk, h->p.pcg_maxiter - launched);
-    for (int k = 0; k < c; ++k) {
-      h->pcg_k = launched + k;
-      MG_TRY(pcg_iteration(h, x));
+    if (graphs && c == chunk) {
+      if (!h->pcg_graph || h->graph_gen != h->gen || h->graph_x != x || h->graph_chunk != c) {
+        if (h->pcg_graph) {
+          cudaGraphExecDestroy(h->pcg_graph);
+          h->pcg_graph = nullptr;
+        }
+        cudaGraph_t gr = nullptr;
+        unsigned long long n0 = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+        MG_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        mgpbd_status cs = MGPBD_OK;
+        for (int k = 0; k < c && cs >= 0; ++k) cs = pcg_iteration(h, x);
+        cudaError_t ce = cudaStreamEndCapture(h->stream, &gr);
+        // captured launches run at each replay, not now: count them there
+        h->graph_kernels = __atomic_load_n(&g_launches, __ATOMIC_RELAXED) - n0;
+        __atomic_fetch_sub(&g_launches, h->graph_kernels, __ATOMIC_RELAXED);
+        if (cs < 0) {
+          if (gr) cudaGraphDestroy(gr);
+          return cs;
+        }
+        MG_CUDA(ce);
+        ce = cudaGraphInstantiate(&h->pcg_graph, gr, 0);
+        cudaGraphDestroy(gr);
+        MG_CUDA(ce);
+        h->graph_gen = h->gen;
+        h->graph_x = x;
+        h->graph_chunk = c;
+      }
+      MG_CUDA(cudaGraphLaunch(h->pcg_graph, h->stream));
+      __atomic_fetch_add(&g_launches, h->graph_kernels, __ATOMIC_RELAXED);
+    } else {
+      for (int k = 0; k < c; ++k) {
+        h->pcg_k = launched + k;
+        MG_TRY(pcg_iteration(h, x));
+      }
     }
     launched += c;
     MG_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost,

@@ -99,6 +99,7 @@ def default_params(**over) -> Dict:
         backtrack=0,  # 0: fixed omega_x; k: halve omega up to k times while |b| grows
         autotune=0,   # 1: time the row-kernel shapes at setup and keep the fastest
         level0_op=0,  # 1: matrix-free level-0 products through the constraint gradients
+        use_graphs=0,  # 1: replay PCG iteration chunks from a captured CUDA graph
         precision=0,  # 0 = FP64, 1 = mixed (FP32 V-cycle / A.p)
         seed_nk=3,
         seed_agg=4,

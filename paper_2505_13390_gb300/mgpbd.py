@@ -37,7 +37,7 @@ class Params(C.Structure):
         ("smooth_sweeps", C.c_int), ("lambda_min_est", C.c_double), ("power_iters", C.c_int),
         ("power_safety", C.c_double), ("coarse_max", C.c_int), ("max_levels", C.c_int),
         ("precision", C.c_int), ("backtrack", C.c_int), ("autotune", C.c_int),
-        ("level0_op", C.c_int),
+        ("level0_op", C.c_int), ("use_graphs", C.c_int),
         ("seed_nk", C.c_uint64), ("seed_agg", C.c_uint64), ("seed_col", C.c_uint64),
         ("seed_pow", C.c_uint64),
     ]
@@ -66,6 +66,24 @@ class LevelInfo(C.Structure):
     _fields_ = [("n", C.c_int), ("nnz", C.c_int64), ("n_agg", C.c_int), ("n_colors", C.c_int),
                 ("lmax", C.c_double), ("omega", C.c_double), ("lanes_fp32", C.c_int),
                 ("lanes_fp64", C.c_int)]
+
+    def as_dict(self) -> Dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BatchConfig(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int)]
+
+
+class StepRequest(C.Structure):
+    _fields_ = [("id", C.c_int), ("instance", C.c_int), ("frames", C.c_int),
+                ("arrival_s", C.c_double)]
+
+
+class StepResult(C.Structure):
+    _fields_ = [("id", C.c_int), ("instance", C.c_int), ("status", C.c_int),
+                ("arrival_s", C.c_double), ("start_s", C.c_double), ("finish_s", C.c_double),
+                ("global_iters", C.c_int64), ("pcg_iters", C.c_int64)]
 
     def as_dict(self) -> Dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -104,6 +122,13 @@ SIGNATURES = {
                                 C.POINTER(C.c_double)]),
     "mgpbd_launch_count": (C.c_ulonglong, []),
     "mgpbd_true_residual_noalloc": (_i, [_vp, _vp, _vp, _vp]),
+    "mgpbd_batch_create": (_i, [C.POINTER(BatchConfig), C.POINTER(_vp)]),
+    "mgpbd_batch_add_instance": (_i, [_vp, C.POINTER(MeshDesc), C.POINTER(Params), _vp, _vp,
+                                      C.POINTER(_i)]),
+    "mgpbd_batch_run": (_i, [_vp, _vp, _i, _vp]),
+    "mgpbd_batch_get_state": (_i, [_vp, _i, _vp, _vp]),
+    "mgpbd_batch_resident": (_i, [_vp, C.POINTER(_i), C.POINTER(C.c_size_t)]),
+    "mgpbd_batch_destroy": (None, [_vp]),
     "mgpbd_last_error": (C.c_char_p, []),
 }
 
@@ -343,3 +368,63 @@ class Solver:
         dl = np.zeros(self.m)
         _check(load().mgpbd_get_lambda(self.h, _ptr(lam), _ptr(dl), MEM_HOST), "get_lambda")
         return lam, dl
+
+
+class Batch:
+    """Continuous-batching service of many instances (mgpbd_batch_*)."""
+
+    def __init__(self, hbm_budget: int, max_active: int):
+        self.cfg = BatchConfig(int(hbm_budget), int(max_active))
+        h = C.c_void_p()
+        _check(load().mgpbd_batch_create(C.byref(self.cfg), C.byref(h)), "batch_create")
+        self.h = h
+        self.sizes = []
+
+    def add(self, mesh, params: Dict) -> int:
+        keep = [np.ascontiguousarray(mesh.rest_pos, np.float64),
+                np.ascontiguousarray(mesh.inv_mass, np.float64),
+                np.ascontiguousarray(mesh.dist, np.int32).reshape(-1, 2),
+                np.ascontiguousarray(mesh.tet, np.int32).reshape(-1, 4),
+                np.ascontiguousarray(mesh.alpha, np.float64),
+                np.ascontiguousarray(mesh.x0, np.float64),
+                np.ascontiguousarray(mesh.v0, np.float64)]
+        md = MeshDesc(mesh.n_verts, _ptr(keep[0]), _ptr(keep[1]), mesh.n_dist, _ptr(keep[2]),
+                      mesh.n_tet, _ptr(keep[3]), _ptr(keep[4]))
+        p = make_params(params)
+        i = C.c_int()
+        _check(load().mgpbd_batch_add_instance(self.h, C.byref(md), C.byref(p), _ptr(keep[5]),
+                                               _ptr(keep[6]), C.byref(i)), "batch_add_instance")
+        self.sizes.append(mesh.n_verts)
+        return i.value
+
+    def run(self, requests):
+        """requests: iterable of (id, instance, frames, arrival_s)."""
+        reqs = list(requests)
+        n = len(reqs)
+        rq = (StepRequest * max(n, 1))(*[StepRequest(*r) for r in reqs])
+        rs = (StepResult * max(n, 1))()
+        st = load().mgpbd_batch_run(self.h, C.cast(rq, C.c_void_p), n, C.cast(rs, C.c_void_p))
+        return st, [rs[i].as_dict() for i in range(n)]
+
+    def state(self, instance: int):
+        n = self.sizes[instance]
+        x = np.zeros((n, 3))
+        v = np.zeros((n, 3))
+        _check(load().mgpbd_batch_get_state(self.h, instance, _ptr(x), _ptr(v)), "batch_get_state")
+        return x, v
+
+    def resident(self):
+        n, b = C.c_int(), C.c_size_t()
+        _check(load().mgpbd_batch_resident(self.h, C.byref(n), C.byref(b)), "batch_resident")
+        return n.value, b.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().mgpbd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

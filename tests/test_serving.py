@@ -1,0 +1,117 @@
+"""Continuous-batching service (mgpbd_batch_*) on one GPU.
+
+Each instance runs on its own stream with deterministic kernels, so its
+results do not depend on what else is on the GPU: a step served in the mix
+equals the same step served alone, bit for bit.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2505_13390_gb300.meshgen import cloth, default_params, hex_block  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def meshes():
+    out = []
+    for k, n in enumerate((12, 20)):
+        out.append((cloth(n, plane="xz", alpha=1e-6, pin="corners", seed=10 + k),
+                    default_params(omega_x=0.25)))
+    for k, L in enumerate((3, 5)):
+        out.append((hex_block(L, 3, 3, h=0.01, alpha=1e-7, pin="x0", seed=20 + k),
+                    default_params(omega_x=0.1)))
+    return out
+
+
+def common(p, prec):
+    # setup at the start of every frame: a re-admitted instance (fresh handle)
+    # then repeats exactly what a resident one does
+    return dict(p, precision=prec, max_iter=4, setup_interval=4, pcg_maxiter=5000, autotune=0,
+                use_graphs=1, level0_op=prec)
+
+
+def serve(ms, prec, max_active, budget, requests):
+    from paper_2505_13390_gb300.mgpbd import Batch
+    b = Batch(budget, max_active)
+    ids = [b.add(m, common(p, prec)) for m, p in ms]
+    st, res = b.run(requests)
+    states = [b.state(i) for i in ids]
+    b.close()
+    return st, res, states
+
+
+def trace(n_inst, per_inst, spacing):
+    reqs = []
+    rid = 0
+    for r in range(per_inst):
+        for i in range(n_inst):
+            reqs.append((rid, i, 1, rid * spacing))
+            rid += 1
+    return reqs
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mix_equals_alone_bitwise(prec):
+    ms = meshes()
+    reqs = trace(len(ms), 2, 0.0)
+    st1, res1, alone = serve(ms, prec, 1, 64 << 30, reqs)
+    st4, res4, mixed = serve(ms, prec, 4, 64 << 30, reqs)
+    assert st1 >= 0 and st4 >= 0
+    for (x1, v1), (x4, v4) in zip(alone, mixed):
+        assert np.array_equal(x1, x4) and np.array_equal(v1, v4)
+    assert [r["pcg_iters"] for r in res1] == [r["pcg_iters"] for r in res4]
+    # the served state equals a plain one-instance run of the same frames
+    from paper_2505_13390_gb300.mgpbd import Solver
+    m, p = ms[0]
+    g = Solver(m, common(p, prec))
+    for _ in range(2):
+        g.begin_frame()
+        for _ in range(4):
+            g.iterate()
+        g.end_frame()
+    x, v = g.get_state()
+    assert np.array_equal(x, alone[0][0]) and np.array_equal(v, alone[0][1])
+
+
+def test_budget_evicts_and_restores_state():
+    ms = meshes()
+    reqs = trace(len(ms), 2, 0.0)
+    _, _, roomy = serve(ms, 0, 2, 64 << 30, reqs)
+    # about two instances fit: the others wait, and idle ones are evicted
+    from paper_2505_13390_gb300.mgpbd import Batch
+    probe = Batch(64 << 30, 1)
+    i = probe.add(*[ms[-1][0], common(ms[-1][1], 0)])
+    probe.run([(0, i, 1, 0.0)])
+    n, one = probe.resident()
+    probe.close()
+    st, res, tight = serve(ms, 0, 2, int(2.5 * one), reqs)
+    assert st >= 0 and all(r["status"] >= 0 for r in res)
+    for (x1, v1), (x2, v2) in zip(roomy, tight):
+        assert np.array_equal(x1, x2) and np.array_equal(v1, v2)
+
+
+def test_instance_larger_than_budget_is_rejected():
+    from paper_2505_13390_gb300 import mgpbd
+    m, p = meshes()[-1]
+    st, res, _ = serve([(m, p)], 0, 1, 1 << 20, [(0, 0, 1, 0.0)])
+    assert st == mgpbd.E_BUDGET and res[0]["status"] == mgpbd.E_BUDGET
+
+
+def test_late_arrivals_join_while_others_run():
+    ms = meshes()
+    # a long request on the largest instance, then short ones arriving later
+    reqs = [(0, 3, 3, 0.0)] + [(1 + k, k, 1, 0.05 * (k + 1)) for k in range(3)]
+    st, res, _ = serve(ms, 1, 4, 64 << 30, reqs)
+    assert st >= 0
+    r0 = res[0]
+    assert any(r["start_s"] < r0["finish_s"] for r in res[1:])  # overlapped on the GPU
+    assert all(r["start_s"] >= r["arrival_s"] for r in res)
