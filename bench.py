@@ -69,6 +69,12 @@ def parse():
                     help="1: matrix-free level-0 products (headline); 0: assembled CSR")
     ap.add_argument("--no-assembled", action="store_true",
                     help="skip the assembled-CSR comparison line")
+    ap.add_argument("--serve-requests", type=int, default=8,
+                    help="step requests of the serving trace (the full trace has 512)")
+    ap.add_argument("--serve-instances", type=int, default=4)
+    ap.add_argument("--serve-rate", type=float, default=0.5, help="arrivals per second")
+    ap.add_argument("--serve-active", type=int, default=8)
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--assembled-steps", type=int, default=1)
     ap.add_argument("--assembled-warmup", type=int, default=1)
     return ap.parse_args()
@@ -281,6 +287,48 @@ def e2e(g, run, steps):
     return steps / dt, nbytes
 
 
+def serving(args):
+    """Serving load: step requests of uneven instances with Poisson arrivals.
+
+    Batched: mixed precision, matrix-free level 0, CUDA graphs, up to
+    --serve-active instances at once, admission by a device-memory budget.
+    Plain: FP64, assembled CSR, plain launches, one instance at a time.  Both
+    serve the same seeded trace; latency = finish - arrival of each request."""
+    import numpy as np
+    import torch
+
+    from paper_2505_13390_gb300.meshgen import instance_mesh, serving_trace
+    from paper_2505_13390_gb300.mgpbd import Batch
+    inst, reqs = serving_trace(args.serve_requests, args.serve_instances, args.serve_rate)
+    meshes = [instance_mesh(d) for d in inst]
+    free, total = torch.cuda.mem_get_info()
+    out = {}
+    for name, prec, op, graphs, active in (("batched_mixed", 1, 1, 1, args.serve_active),
+                                            ("plain_fp64", 0, 0, 0, 1)):
+        b = Batch(int(0.5 * free), active)
+        for m, p in meshes:
+            b.add(m, dict(p, precision=prec, level0_op=op, use_graphs=graphs, autotune=0,
+                          setup_interval=20))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, res = b.run([(r["id"], r["instance"], r["frames"], r["t"]) for r in reqs])
+        wall = time.perf_counter() - t0
+        b.close()
+        lat = np.array([r["finish_s"] - r["arrival_s"] for r in res])
+        iters = sum(r["global_iters"] for r in res)
+        out[name] = {"status": st, "p50_latency_s": float(np.percentile(lat, 50)),
+                     "p99_latency_s": float(np.percentile(lat, 99)),
+                     "global_iters_per_s": iters / wall, "makespan_s": wall,
+                     "pcg_iters_per_request": [int(r["pcg_iters"]) for r in res],
+                     "max_active": active}
+    out["trace"] = {"requests": len(reqs), "instances": len(inst),
+                    "rate_hz": args.serve_rate, "meshes": [f"{d['kind']}{d['size']}" for d in inst],
+                    "budget": "half of free device memory", "frames_per_request": 1}
+    out["speedup_iters_per_s"] = (out["batched_mixed"]["global_iters_per_s"] /
+                                  out["plain_fp64"]["global_iters_per_s"])
+    return out
+
+
 def cpu_sample_baseline(iters=2, warm=1, gpu_pcg=None):
     """The FP64 oracle on the host cores (1 thread) on the bounded sample.
 
@@ -379,12 +427,16 @@ def run_ours(args, ws, rank):
                 "pcg_iters": r64["pcg"], "clocks": r64["clocks"],
                 "smoother_sweep_gbs": a64, "smoother_sweep_frac": a64 / hbm}
         r64["solver"].close()
+    serve = None
+    if not args.no_serve:
+        serve = serving(args)
     if rank != 0:
         return
     if not args.no_cpu:
         cpu, _, _ = cpu_sample_baseline(gpu_pcg=res["pcg"])
     line = {
-        "metric": "global XPBD iters/s at 1.65M tets (mixed precision; FP64 under fp64)",
+        "metric": "global XPBD iters/s at 1.65M tets (mixed precision; FP64 under fp64; "
+                  "p50/p99 step latency under serving)",
         "value": value,
         "unit": "global_iters/s",
         "n_gpus": ws,
@@ -424,6 +476,7 @@ def run_ours(args, ws, rank):
         "clocks": res["clocks"],
         "fp64": fp64,
         "assembled": assembled,
+        "serving": serve,
         "create_s": res["create_s"],
         "stats": {k: res["stats"][k] for k in ("levels", "op_complexity", "device_bytes")},
     }
@@ -470,7 +523,8 @@ def run_reference(args, ws, rank):
               f"PCG-iteration ratio {pscale:.2f} to 376.5M nnz and {FULL_PCG_ITERS} PCG iterations")
     line = {
         "impl": "reference",
-        "metric": "global XPBD iters/s at 1.65M tets (mixed precision; FP64 under fp64)",
+        "metric": "global XPBD iters/s at 1.65M tets (mixed precision; FP64 under fp64; "
+                  "p50/p99 step latency under serving)",
         "value": value, "unit": "global_iters/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * scale * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

@@ -303,26 +303,35 @@ def workload(name: str) -> Tuple[Mesh, Dict]:
     return mesh, params
 
 
-def serving_requests(n_req: int = 512, rate_hz: float = 10.0, seed: int = 6) -> List[Dict]:
-    """Seeded request trace: Poisson arrivals, half cloth N x N, half beam L x 10 x 10."""
+def serving_trace(n_requests: int = 512, n_instances: int = 64, rate_hz: float = 2.0,
+                  seed: int = 6) -> Tuple[List[Dict], List[Dict]]:
+    """Seeded serving trace: instances and step requests.
+
+    Instances: with probability 1/2 a cloth of N x N (N ~ U{16..256}), else a
+    tet beam of L x 10 x 10 cells (L ~ U{10..80}); alpha = 10^U(-9, -6).
+    Requests: Poisson arrivals at `rate_hz`; each is one step (one frame of
+    20 global iterations) of an instance drawn uniformly; an instance's state
+    persists between its requests.
+    """
     rng = np.random.default_rng(seed)
-    t = 0.0
-    out = []
-    for r in range(n_req):
-        t += rng.exponential(1.0 / rate_hz)
+    inst = []
+    for k in range(n_instances):
         log_a = rng.uniform(-9.0, -6.0)
         if rng.uniform() < 0.5:
-            n = int(rng.integers(16, 257))
-            out.append(dict(id=r, t=t, kind="cloth", size=n, alpha=10.0 ** log_a,
-                            seed=1000 + r))
+            inst.append(dict(kind="cloth", size=int(rng.integers(16, 257)),
+                             alpha=10.0 ** log_a, seed=1000 + k))
         else:
-            L = int(rng.integers(10, 81))
-            out.append(dict(id=r, t=t, kind="beam", size=L, alpha=10.0 ** log_a,
-                            seed=1000 + r))
-    return out
+            inst.append(dict(kind="beam", size=int(rng.integers(10, 81)),
+                             alpha=10.0 ** log_a, seed=1000 + k))
+    t = 0.0
+    reqs = []
+    for r in range(n_requests):
+        t += rng.exponential(1.0 / rate_hz)
+        reqs.append(dict(id=r, t=t, instance=int(rng.integers(0, n_instances)), frames=1))
+    return inst, reqs
 
 
-def request_mesh(req: Dict) -> Tuple[Mesh, Dict]:
+def instance_mesh(req: Dict) -> Tuple[Mesh, Dict]:
     if req["kind"] == "cloth":
         mesh = cloth(req["size"], plane="xz", alpha=req["alpha"], pin="corners",
                      seed=req["seed"], name=f"cloth{req['size']}")
