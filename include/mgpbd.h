@@ -78,7 +78,9 @@ typedef struct {
   int nk_sweeps;        /* near-kernel Jacobi sweeps on A x = 0 (Sec. 4.3) */
   double nk_omega;      /* their weight */
   double theta_s;       /* strength threshold (Sec. 4.1) */
-  int smoother;         /* MGPBD_SMOOTH_JACOBI (MCGS: see mgpbd_create) */
+  int smoother;         /* MGPBD_SMOOTH_JACOBI (weighted Jacobi, default) or
+                           MGPBD_SMOOTH_MCGS (multicolour Gauss-Seidel: forward colours
+                           before, reverse colours after the coarse correction) */
   int smooth_sweeps;    /* pre- and post-smoothing sweeps (Sec. 4.5) */
   double lambda_min_est;/* lambda_min estimate in omega_opt (Sec. 4.5) */
   int power_iters;      /* power-method iterations for lambda_max */

@@ -110,6 +110,8 @@ struct Level {
   int G32 = 0, G64 = 0;      // lanes per row of the FP32 / FP64 row kernels (0 = rule)
   int32_t *color = nullptr;
   int n_colors = 0;
+  int32_t *crow = nullptr;          // rows grouped by colour (multicolour GS)
+  std::vector<int64_t> hcptr;       // host offsets of each colour in crow
   double lmax = 0.0, omega = 0.0;
   // V-cycle vectors in the working precision (double or float)
   void *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr;

@@ -604,9 +604,11 @@ static mgpbd_status ensure_level(Handle *h, int l, int n, int64_t nnz) {
       MG_TRY(alloc_n(h->arena, &L.dinv, (size_t)cap));
       if (mixed) MG_TRY(alloc_n(h->arena, &L.dinv32, (size_t)cap));
     }
-    void *olds[] = {L.agg, L.root, L.P, L.P32, L.B, L.mptr, L.mrow, L.color, L.x, L.x2, L.b, L.r};
+    void *olds[] = {L.agg, L.root, L.P, L.P32, L.B, L.mptr, L.mrow, L.color, L.crow,
+                    L.x, L.x2, L.b, L.r};
     for (void *o : olds) h->arena.release(o);
     L.P32 = nullptr;
+    L.crow = nullptr;
     MG_TRY(alloc_n(h->arena, &L.agg, (size_t)cap));
     MG_TRY(alloc_n(h->arena, &L.root, (size_t)cap));
     MG_TRY(alloc_n(h->arena, &L.P, (size_t)cap));
@@ -688,6 +690,44 @@ static mgpbd_status colour_level(Handle *h, int l) {
   int mx = -1;
   MG_TRY(read_int(h, h->flag, &mx));
   L.n_colors = mx + 1;
+  return MGPBD_OK;
+}
+
+// rows grouped by colour for the multicolour Gauss-Seidel sweeps
+__global__ void k_col_count(int n, const int32_t *color, unsigned long long *cnt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    atomicAdd(&cnt[color[i]], 1ull);
+}
+
+__global__ void k_col_fill(int n, const int32_t *color, const int64_t *cptr,
+                           unsigned long long *fill, int32_t *crow) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    unsigned long long pos = atomicAdd(&fill[color[i]], 1ull);
+    crow[cptr[color[i]] + (int64_t)pos] = i;
+  }
+}
+
+static mgpbd_status colour_groups(Handle *h, int l) {
+  Level &L = h->lev[l];
+  const int nc = L.n_colors;
+  if (!L.crow) MG_TRY(alloc_n(h->arena, &L.crow, (size_t)L.cap_n));
+  MG_TRY(ensure_tmp(h, sizeof(int64_t) * (2 * (size_t)nc + 2)));
+  unsigned long long *cnt = (unsigned long long *)h->tmp;
+  int64_t *dptr = (int64_t *)h->tmp + nc + 1;
+  MG_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * nc, h->stream));
+  k_col_count<<<blocks_for(L.n, 256), 256, 0, h->stream>>>(L.n, L.color, cnt);
+  MG_LAUNCH("k_col_count");
+  std::vector<int64_t> c((size_t)nc);
+  MG_CUDA(cudaMemcpyAsync(c.data(), cnt, sizeof(int64_t) * nc, cudaMemcpyDeviceToHost, h->stream));
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  L.hcptr.assign((size_t)nc + 1, 0);
+  for (int k = 0; k < nc; ++k) L.hcptr[k + 1] = L.hcptr[k] + c[k];
+  MG_CUDA(cudaMemcpyAsync(dptr, L.hcptr.data(), sizeof(int64_t) * (nc + 1), cudaMemcpyHostToDevice,
+                          h->stream));
+  MG_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * nc, h->stream));
+  k_col_fill<<<blocks_for(L.n, 256), 256, 0, h->stream>>>(L.n, L.color, dptr, cnt, L.crow);
+  MG_LAUNCH("k_col_fill");
+  MG_CUDA(cudaStreamSynchronize(h->stream));
   return MGPBD_OK;
 }
 
@@ -861,6 +901,7 @@ mgpbd_status amg_setup(Handle *h) {
     // the multicolour ordering is needed by the Gauss-Seidel smoother only
     if (h->p.smoother == MGPBD_SMOOTH_MCGS || h->want_colors) MG_TRY(colour_level(h, q));
     else h->lev[q].n_colors = 0;
+    if (h->p.smoother == MGPBD_SMOOTH_MCGS) MG_TRY(colour_groups(h, q));
     MG_TRY(power_method(h, q));
   }
   h->lev[h->L - 1].n_colors = 0;

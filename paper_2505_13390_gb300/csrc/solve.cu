@@ -135,6 +135,21 @@ __global__ void k_jacobi0(int n, const T *b, const T *dinv, T omega, T *x, const
     x[i] = omega * (b[i] * dinv[i]);
 }
 
+// Gauss-Seidel over the rows of one colour, in place (rows of one colour are
+// not coupled): x_i += (b_i - sum_j A_ij x_j) / A_ii
+template <int G, class T>
+__global__ void k_gs_colour(int nrows, const int32_t *crow, const int64_t *ptr,
+                            const int32_t *col, const T *val, const T *dinv, const T *b, T *x,
+                            const PcgScalars *sc) {
+  if (is_done(sc)) return;
+  GROUP_ROWS(G, nrows) {
+    int row = valid ? crow[i] : 0;
+    T s = valid ? row_dot<G, T, T, T>(ptr, col, val, x, row, g) : (T)0;
+    s = group_sum<G>(s);
+    if (valid && g == 0) x[row] = fma(b[row] - s, dinv[row], x[row]);
+  }
+}
+
 // weighted Jacobi sweep: xn = x + omega D^-1 (b - A x)
 template <int G, class T>
 __global__ void k_jacobi(int n, const int64_t *ptr, const int32_t *col, const T *val,
@@ -380,10 +395,31 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in) {
   const T *val = vals<T>(L);
   const T *dinv = dinvs<T>(L);
   T *x2 = (T *)L.x2, *r = (T *)L.r;
-  k_jacobi0<T><<<blocks_for(n, 256), 256, 0, h->stream>>>(n, b_in, dinv, om, x, sc);
-  MG_LAUNCH("k_jacobi0");
   const bool mf = l == 0 && h->p.level0_op == 1;  // matrix-free level-0 products
-  for (int s = 1; s < h->p.smooth_sweeps; ++s) {
+  const bool gs = h->p.smoother == MGPBD_SMOOTH_MCGS;
+  // multicolour Gauss-Seidel: forward colours before the coarse correction,
+  // reverse colours after (symmetric smoothing, Sec. 4.5)
+  auto gs_sweeps = [&](bool reverse) -> mgpbd_status {
+    const int nc = L.n_colors;
+    for (int s = 0; s < h->p.smooth_sweeps; ++s)
+      for (int k = 0; k < nc; ++k) {
+        int c = reverse ? nc - 1 - k : k;
+        int64_t off = L.hcptr[c], cnt = L.hcptr[c + 1] - off;
+        if (cnt == 0) continue;
+        DISPATCH_G(G, (k_gs_colour<GG, T><<<row_blocks(cnt, GG), 256, 0, h->stream>>>(
+                          (int)cnt, L.crow + off, L.ptr, L.col, val, dinv, b_in, x, sc)));
+        MG_LAUNCH("k_gs_colour");
+      }
+    return MGPBD_OK;
+  };
+  if (gs) {
+    MG_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * n, h->stream));
+    MG_TRY(gs_sweeps(false));
+  } else {
+    k_jacobi0<T><<<blocks_for(n, 256), 256, 0, h->stream>>>(n, b_in, dinv, om, x, sc);
+    MG_LAUNCH("k_jacobi0");
+  }
+  for (int s = 1; s < h->p.smooth_sweeps && !gs; ++s) {
     if (l == 0) MG_TRY(prof_begin(h));
     if (mf) {
       MG_TRY(mf_level0<T>(h, kMfSweep, x, b_in, dinv, om, x2));
@@ -410,7 +446,8 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in) {
   k_prolong<T><<<blocks_for(n, 256), 256, 0, h->stream>>>(n, L.agg, Ps<T>(L), (const T *)Lc.x, x,
                                                           sc);
   MG_LAUNCH("k_prolong");
-  for (int s = 0; s < h->p.smooth_sweeps; ++s) {
+  if (gs) MG_TRY(gs_sweeps(true));
+  for (int s = 0; s < h->p.smooth_sweeps && !gs; ++s) {
     if (l == 0) MG_TRY(prof_begin(h));
     if (mf) {
       MG_TRY(mf_level0<T>(h, kMfSweep, x, b_in, dinv, om, x2));

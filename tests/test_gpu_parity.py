@@ -107,11 +107,13 @@ def test_setup_bit_exact(name):
             assert lg == pytest.approx(lo, rel=1e-10) and wg == pytest.approx(wo, rel=1e-10)
 
 
+@pytest.mark.parametrize("smoother", [0, 1])
 @pytest.mark.parametrize("op", [0, 1])
 @pytest.mark.parametrize("name", ["cloth8", "hex3", "cloth32"])
-def test_vcycle_parity(name, op):
-    """FP64 V-cycle; op = 1 applies the level-0 products matrix-free."""
-    mesh, p, o, g = both(name, level0_op=op)
+def test_vcycle_parity(name, op, smoother):
+    """FP64 V-cycle; op = 1 applies the level-0 products matrix-free;
+    smoother = 1 is the multicolour Gauss-Seidel smoother."""
+    mesh, p, o, g = both(name, level0_op=op, smoother=smoother)
     o.begin_frame()
     g.begin_frame()
     o.eval_assemble()
@@ -193,13 +195,16 @@ def test_solve_stiff_true_residual():
     assert np.linalg.norm(xg - xo) <= 1e-5 * np.linalg.norm(xo)
 
 
+@pytest.mark.parametrize("smoother", [0, 1])
 @pytest.mark.parametrize("op", [0, 1])
 @pytest.mark.parametrize("name,iters", [("cloth8", 6), ("cloth8s", 6), ("hex3s", 6),
                                         ("cloth32", 4), ("hex3", 3)])
-def test_iterations_parity_fp64(name, iters, op):
+def test_iterations_parity_fp64(name, iters, op, smoother):
     """Whole global iterations in FP64 with PCG solved to 1e-10: positions,
-    velocities and |b| within 1e-9 relative of the oracle."""
-    mesh, p, o, g = both(name, pcg_rtol=1e-10, pcg_maxiter=3000, level0_op=op)
+    velocities and |b| within 1e-9 relative of the oracle (Jacobi or
+    multicolour Gauss-Seidel smoothing)."""
+    mesh, p, o, g = both(name, pcg_rtol=1e-10, pcg_maxiter=3000, level0_op=op,
+                         smoother=smoother)
     o.begin_frame()
     g.begin_frame()
     scale = np.abs(mesh.rest_pos).max() + 1e-3
