@@ -105,6 +105,8 @@ typedef struct {
                            graph is re-captured after each setup); 0: plain launches.
                            Needs a stream of the caller's own: on the legacy default
                            stream (NULL) launches stay plain. */
+  int linear_solver;    /* 0: MGPCG (Sec. 4.4); 1: XPBD's local step dl_j = b_j / A_jj
+                           (eq. 4, the Jacobi form the paper compares against) */
   uint64_t seed_nk, seed_agg, seed_col, seed_pow;
 } mgpbd_params;
 

@@ -69,6 +69,7 @@ typedef struct {
   int coarse_max;
   int max_levels;
   int backtrack;  /* 0: fixed omega_x; k > 0: halve omega up to k times (Sec. 4) */
+  int linear_solver; /* 0: MGPCG (Sec. 4.4); 1: XPBD diagonal step dl_j = b_j / A_jj (eq. 4) */
   uint64_t seed_nk, seed_agg, seed_col, seed_pow;
 } orc_params;
 
@@ -971,10 +972,28 @@ int orc_prepare_solve(orc *o) {
 
 /* One global iteration (Alg. 1 loop body).  Returns 1 if the loop should
    stop (|b| < eps_b), 0 to go on, < 0 on error. */
+/* XPBD's local solve (eq. 4): every constraint takes dl_j = b_j / A_jj from
+   the same state (the Jacobi form the paper compares against). */
+static int xpbd_step(orc *o, orc_solve_info *info) {
+  memset(info, 0, sizeof(*info));
+  info->bnorm = sqrt(dot(o->m, o->b, o->b));
+  for (int j = 0; j < o->m; ++j) o->dl[j] = o->b[j] / diag_of(&o->A, j);
+  info->pcg_iters = 1;
+  info->status = ORC_OK;
+  return ORC_OK;
+}
+
 int orc_iterate(orc *o, orc_solve_info *info) {
   eval_constraints(o);
   assemble(o);
   int st;
+  if (o->p.linear_solver == 1) {
+    xpbd_step(o, info);
+    o->it_global++;
+    update_positions(o, info);
+    o->last = *info;
+    return info->bnorm < o->p.eps_b ? 1 : 0;
+  }
   if (!o->have_setup || (o->p.setup_interval > 0 && o->it_global % o->p.setup_interval == 0)) {
     st = setup(o);
     if (st) return st;

@@ -36,7 +36,7 @@ class Params(C.Structure):
         ("nk_omega", C.c_double), ("theta_s", C.c_double), ("smoother", C.c_int),
         ("smooth_sweeps", C.c_int), ("lambda_min_est", C.c_double), ("power_iters", C.c_int),
         ("power_safety", C.c_double), ("coarse_max", C.c_int), ("max_levels", C.c_int),
-        ("backtrack", C.c_int), ("seed_nk", C.c_uint64), ("seed_agg", C.c_uint64), ("seed_col", C.c_uint64),
+        ("backtrack", C.c_int), ("linear_solver", C.c_int), ("seed_nk", C.c_uint64), ("seed_agg", C.c_uint64), ("seed_col", C.c_uint64),
         ("seed_pow", C.c_uint64),
     ]
 
@@ -118,7 +118,8 @@ def make_params(d: Dict) -> Params:
               "power_safety"):
         setattr(p, k, float(d[k]))
     for k in ("max_iter", "pcg_maxiter", "setup_interval", "nk_sweeps", "smoother",
-              "smooth_sweeps", "power_iters", "coarse_max", "max_levels", "backtrack"):
+              "smooth_sweeps", "power_iters", "coarse_max", "max_levels", "backtrack",
+              "linear_solver"):
         setattr(p, k, int(d[k]))
     for k in ("seed_nk", "seed_agg", "seed_col", "seed_pow"):
         setattr(p, k, int(d[k]))

@@ -150,6 +150,7 @@ static mgpbd_status check_params(const mgpbd_params *p) {
       !(p->theta_s >= 0.0) || p->backtrack < 0 ||
       (p->autotune != 0 && p->autotune != 1) || (p->level0_op != 0 && p->level0_op != 1) ||
       (p->use_graphs != 0 && p->use_graphs != 1) ||
+      (p->linear_solver != 0 && p->linear_solver != 1) ||
       !(p->pcg_rtol >= 0.0) || !(p->power_safety > 0.0)) {
     set_error("invalid mgpbd_params");
     return MGPBD_E_INVALID;
@@ -321,6 +322,15 @@ static mgpbd_status timed_end(Handle *h, double *acc) {
 static mgpbd_status iterate(Handle *h, mgpbd_solve_info *info) {
   MG_TRY(launch_eval(h));
   MG_TRY(launch_assemble(h));
+  if (h->p.linear_solver == 1) {  // XPBD's local step (eq. 4)
+    mgpbd_solve_info inf{};
+    MG_TRY(xpbd_step(h, &inf));
+    h->it_global++;
+    MG_TRY(launch_update(h, &inf));
+    h->last = inf;
+    if (info) *info = inf;
+    return MGPBD_OK;
+  }
   if (h->p.level0_op == 1) MG_TRY(mf_prepare(h));
   bool due = !h->have_setup ||
              (h->p.setup_interval > 0 && h->it_global % h->p.setup_interval == 0);
@@ -386,6 +396,7 @@ mgpbd_status mgpbd_default_params(mgpbd_params *p) {
   p->autotune = 0;
   p->level0_op = 0;
   p->use_graphs = 0;
+  p->linear_solver = 0;
   p->seed_nk = 3;
   p->seed_agg = 4;
   p->seed_col = 5;

@@ -236,6 +236,7 @@ mgpbd_status coarsest_factor(Handle *h);
 mgpbd_status pcg_solve(Handle *h, const double *d_b, double *d_x, mgpbd_solve_info *info);
 mgpbd_status vcycle_apply(Handle *h, const double *d_r, double *d_z);
 mgpbd_status dot_dd(Handle *h, const double *x, const double *y, int64_t n, double *d_out);
+mgpbd_status xpbd_step(Handle *h, mgpbd_solve_info *info);
 mgpbd_status power_method(Handle *h, int l);
 
 // ---------------------------------------------------------------------------

@@ -692,6 +692,32 @@ mgpbd_status autotune_levels(Handle *h) {
 }
 
 // ---------------------------------------------------------------------------
+// XPBD's local step (eq. 4): dl_j = b_j / A_jj for every constraint at once
+// ---------------------------------------------------------------------------
+__global__ void k_xpbd_step(int m, const int64_t *ptr, const double *val, const double *b,
+                            double *dl) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x)
+    dl[j] = b[j] / val[ptr[j + 1] - 1];
+}
+
+mgpbd_status xpbd_step(Handle *h, mgpbd_solve_info *info) {
+  memset(info, 0, sizeof(*info));
+  if (h->m == 0) return MGPBD_OK;
+  const Level &L = h->lev[0];
+  double *d_bn = h->partials + 4096 + 6;
+  MG_TRY(dot_dd(h, h->b, h->b, h->m, d_bn));
+  k_xpbd_step<<<blocks_for(h->m, 256), 256, 0, h->stream>>>(h->m, L.ptr, L.val, h->b, h->dl);
+  MG_LAUNCH("k_xpbd_step");
+  double bn2 = 0.0;
+  MG_CUDA(cudaMemcpyAsync(&bn2, d_bn, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  info->bnorm = sqrt(bn2);
+  info->pcg_iters = 1;
+  info->status = MGPBD_OK;
+  return MGPBD_OK;
+}
+
+// ---------------------------------------------------------------------------
 // power method for lambda_max(D^-1 A) (Sec. 4.5)
 // ---------------------------------------------------------------------------
 __global__ void k_pow_init(int n, uint64_t seed, int l, double *y) {

@@ -100,6 +100,7 @@ def default_params(**over) -> Dict:
         autotune=0,   # 1: time the row-kernel shapes at setup and keep the fastest
         level0_op=0,  # 1: matrix-free level-0 products through the constraint gradients
         use_graphs=0,  # 1: replay PCG iteration chunks from a captured CUDA graph
+        linear_solver=0,  # 0: MGPCG; 1: XPBD's diagonal step (eq. 4), the baseline
         precision=0,  # 0 = FP64, 1 = mixed (FP32 V-cycle / A.p)
         seed_nk=3,
         seed_agg=4,

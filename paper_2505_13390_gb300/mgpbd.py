@@ -37,7 +37,7 @@ class Params(C.Structure):
         ("smooth_sweeps", C.c_int), ("lambda_min_est", C.c_double), ("power_iters", C.c_int),
         ("power_safety", C.c_double), ("coarse_max", C.c_int), ("max_levels", C.c_int),
         ("precision", C.c_int), ("backtrack", C.c_int), ("autotune", C.c_int),
-        ("level0_op", C.c_int), ("use_graphs", C.c_int),
+        ("level0_op", C.c_int), ("use_graphs", C.c_int), ("linear_solver", C.c_int),
         ("seed_nk", C.c_uint64), ("seed_agg", C.c_uint64), ("seed_col", C.c_uint64),
         ("seed_pow", C.c_uint64),
     ]

@@ -311,6 +311,22 @@ def test_graph_replay_is_bitwise_identical(prec):
     assert np.array_equal(x0, x1) and np.array_equal(v0, v1) and np.array_equal(l0, l1)
 
 
+@pytest.mark.parametrize("name", ["cloth32", "block6"])
+def test_xpbd_baseline_parity(name):
+    """XPBD's local step (eq. 4) through the same iteration: positions track
+    the oracle's to rounding (division vs multiplication by 1/A_jj)."""
+    mesh, p, o, g = both(name, linear_solver=1)
+    o.begin_frame()
+    g.begin_frame()
+    scale = np.abs(mesh.rest_pos).max() + 1e-3
+    for it in range(8):
+        do, dg = o.iterate(), g.iterate()
+        assert dg["bnorm"] == pytest.approx(do["bnorm"], rel=1e-10)
+        xo, _ = o.get_state()
+        xg, _ = g.get_state()
+        assert np.abs(xg - xo).max() <= 1e-12 * scale
+
+
 def test_empty_and_single_constraint():
     from paper_2505_13390_gb300.meshgen import Mesh
     rest = np.array([[0, 0, 0], [1, 0, 0]], float)

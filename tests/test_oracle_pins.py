@@ -578,6 +578,32 @@ def test_backtracking_never_accepts_a_growing_residual_when_a_halving_helps():
     assert d["omega"] == 0.25 and d["bnorm_after"] == -1.0
 
 
+def test_xpbd_step_is_the_diagonal_solve_and_stalls_where_mgpcg_does_not():
+    # eq. 4 on a single constraint is exact, like the global solve
+    rest = np.array([[0, 0, 0], [1, 0, 0]], float)
+    x0 = np.array([[0, 0, 0], [1.3, 0.1, -0.2]], float)
+    one = Mesh("one", rest, np.array([0.5, 2.0]), np.array([[0, 1]], np.int32),
+               np.zeros((0, 4), np.int32), np.array([1e-3]), x0, np.zeros((2, 3)))
+    outs = []
+    for solver in (0, 1):
+        o = Oracle(one, default_params(gravity=(0.0, 0.0, 0.0), omega_x=1.0, max_iter=1,
+                                       linear_solver=solver))
+        o.step(1)
+        outs.append(o.get_state()[0])
+    assert np.allclose(outs[0], outs[1], rtol=0, atol=1e-15)
+    # on a stiff cloth the local solve leaves a larger dual residual than the
+    # global one after the same number of iterations (Sec. 5.4, cloth and bunny)
+    mesh = cloth(16, plane="xz", alpha=1e-8, pin="corners", noise=1e-4, seed=1)
+    res = []
+    for solver in (0, 1):
+        o = Oracle(mesh, default_params(omega_x=0.25, max_iter=20, coarse_max=60,
+                                        linear_solver=solver))
+        o.begin_frame()
+        hist = [o.iterate()["bnorm"] for _ in range(20)]
+        res.append(hist[-1] / hist[0])
+    assert res[0] < 0.5 * res[1]
+
+
 def test_lazy_setup_count():
     mesh = cloth(8, plane="xz", alpha=1e-8, pin="corners", noise=1e-4, seed=1)
     p = default_params(max_iter=5, setup_interval=7, coarse_max=20, pcg_maxiter=50)
