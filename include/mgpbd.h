@@ -41,7 +41,7 @@ enum {
 };
 
 enum { MGPBD_MEM_HOST = 0, MGPBD_MEM_DEVICE = 1 };
-enum { MGPBD_SMOOTH_JACOBI = 0, MGPBD_SMOOTH_MCGS = 1 };
+enum { MGPBD_SMOOTH_JACOBI = 0, MGPBD_SMOOTH_MCGS = 1, MGPBD_SMOOTH_CHEBYSHEV = 2 };
 enum { MGPBD_FP64 = 0, MGPBD_MIXED = 1 };
 
 /* Problem definition (eq. 1-3 of the paper).  Host pointers, copied at
@@ -78,9 +78,11 @@ typedef struct {
   int nk_sweeps;        /* near-kernel Jacobi sweeps on A x = 0 (Sec. 4.3) */
   double nk_omega;      /* their weight */
   double theta_s;       /* strength threshold (Sec. 4.1) */
-  int smoother;         /* MGPBD_SMOOTH_JACOBI (weighted Jacobi, default) or
+  int smoother;         /* MGPBD_SMOOTH_JACOBI (weighted Jacobi, default),
                            MGPBD_SMOOTH_MCGS (multicolour Gauss-Seidel: forward colours
-                           before, reverse colours after the coarse correction) */
+                           before, reverse colours after the coarse correction) or
+                           MGPBD_SMOOTH_CHEBYSHEV (Chebyshev polynomial of degree
+                           smooth_sweeps on [lambda_min_est, safety*lambda_max]) */
   int smooth_sweeps;    /* pre- and post-smoothing sweeps (Sec. 4.5) */
   double lambda_min_est;/* lambda_min estimate in omega_opt (Sec. 4.5) */
   int power_iters;      /* power-method iterations for lambda_max */

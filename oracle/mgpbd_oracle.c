@@ -61,7 +61,7 @@ typedef struct {
   int nk_sweeps;
   double nk_omega;
   double theta_s;
-  int smoother; /* 0 weighted Jacobi, 1 multicolour Gauss-Seidel */
+  int smoother; /* 0 weighted Jacobi, 1 multicolour Gauss-Seidel, 2 Chebyshev */
   int smooth_sweeps;
   double lambda_min_est;
   int power_iters;
@@ -799,7 +799,47 @@ static void gs_colour(const orc_level *L, double *x, const double *b, int c) {
   }
 }
 
+/* Chebyshev smoother (Sec. 4.5): the Chebyshev iteration on D^-1 A x = D^-1 b
+   over the eigenvalue interval [lo, hi] = [lambda_min_est, safety * lambda_max]
+   (the interval of the omega-Jacobi formula, whose weight 2/(lo+hi) is the
+   degree-1 case), with smooth_sweeps products:
+     theta = (hi+lo)/2, delta = (hi-lo)/2, sigma = theta/delta, rho = 1/sigma
+     r = D^-1 (b - A x), d = r/theta
+     repeat: x += d; r -= D^-1 A d; rho' = 1/(2 sigma - rho);
+             d = rho' rho d + (2 rho'/delta) r; rho = rho'
+   A polynomial in D^-1 A, so identical pre and post smoothing keeps the
+   V-cycle symmetric. */
+static void chebyshev(const orc *o, const orc_level *L, double *x, const double *b, double *t) {
+  int n = L->A.n;
+  double lo = o->p.lambda_min_est, hi = o->p.power_safety * L->lmax;
+  double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+  double sigma = theta / delta, rho = 1.0 / sigma;
+  double *r = (double *)xcalloc((size_t)n, sizeof(double));
+  double *d = (double *)xcalloc((size_t)n, sizeof(double));
+  spmv(&L->A, x, t);
+  for (int i = 0; i < n; ++i) {
+    r[i] = (b[i] - t[i]) / diag_of(&L->A, i);
+    d[i] = r[i] / theta;
+  }
+  for (int k = 0; k < o->p.smooth_sweeps; ++k) {
+    for (int i = 0; i < n; ++i) x[i] = x[i] + d[i];
+    if (k + 1 == o->p.smooth_sweeps) break;
+    spmv(&L->A, d, t);
+    for (int i = 0; i < n; ++i) r[i] = r[i] - t[i] / diag_of(&L->A, i);
+    double rho2 = 1.0 / (2.0 * sigma - rho);
+    double c1 = rho2 * rho, c2 = 2.0 * rho2 / delta;
+    for (int i = 0; i < n; ++i) d[i] = fma(c1, d[i], c2 * r[i]);
+    rho = rho2;
+  }
+  free(r);
+  free(d);
+}
+
 static void smooth(const orc *o, const orc_level *L, double *x, const double *b, double *t, int post) {
+  if (o->p.smoother == 2) {
+    chebyshev(o, L, x, b, t);
+    return;
+  }
   for (int s = 0; s < o->p.smooth_sweeps; ++s) {
     if (o->p.smoother == 1) {
       if (!post) for (int c = 0; c < L->n_colors; ++c) gs_colour(L, x, b, c);
@@ -1187,4 +1227,11 @@ int orc_colour_csr(int n, const int64_t *ptr, const int32_t *col, uint64_t seed,
   if (n <= 0) return 0;
   orc_csr A = {n, ptr[n], (int64_t *)ptr, (int32_t *)col, NULL};
   return colour(&A, seed, l, color);
+}
+
+/* test-only: one pre-smoothing of level l from x = 0 */
+void orc_smooth_test(orc *o, int l, const double *b, double *x) {
+  orc_level *L = &o->lev[l];
+  memset(x, 0, sizeof(double) * (size_t)L->A.n);
+  smooth(o, L, x, b, L->t, 0);
 }

@@ -98,6 +98,7 @@ def lib():
         L.orc_aggregate_csr.restype = C.c_int
         L.orc_colour_csr.argtypes = [C.c_int, vp, vp, C.c_uint64, C.c_int, vp]
         L.orc_colour_csr.restype = C.c_int
+        L.orc_smooth_test.argtypes = [vp, C.c_int, vp, vp]
         L.orc_h64.argtypes = [C.c_uint64]
         L.orc_h64.restype = C.c_uint64
         assert L.orc_sizeof_params() == C.sizeof(Params)
@@ -228,6 +229,13 @@ class Oracle:
         inf = SolveInfo()
         lib().orc_solve(self.h, _p(b), _p(x), C.byref(inf))
         return x, inf.as_dict()
+
+    def smooth(self, level: int, b):
+        """Test-only: one pre-smoothing of `level` from x = 0."""
+        b = np.ascontiguousarray(b, np.float64)
+        x = np.zeros_like(b)
+        lib().orc_smooth_test(self.h, level, _p(b), _p(x))
+        return x
 
     def vcycle(self, r):
         r = np.ascontiguousarray(r, np.float64)

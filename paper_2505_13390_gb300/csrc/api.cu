@@ -146,7 +146,8 @@ static mgpbd_status check_params(const mgpbd_params *p) {
   if (!(p->dt > 0.0) || p->max_iter < 0 || p->pcg_maxiter < 1 || p->nk_sweeps < 0 ||
       p->smooth_sweeps < 1 || p->power_iters < 1 || p->coarse_max < 1 || p->max_levels < 1 ||
       p->max_levels > kMaxLevels || (p->precision != MGPBD_FP64 && p->precision != MGPBD_MIXED) ||
-      (p->smoother != MGPBD_SMOOTH_JACOBI && p->smoother != MGPBD_SMOOTH_MCGS) ||
+      (p->smoother != MGPBD_SMOOTH_JACOBI && p->smoother != MGPBD_SMOOTH_MCGS &&
+       p->smoother != MGPBD_SMOOTH_CHEBYSHEV) ||
       !(p->theta_s >= 0.0) || p->backtrack < 0 ||
       (p->autotune != 0 && p->autotune != 1) || (p->level0_op != 0 && p->level0_op != 1) ||
       (p->use_graphs != 0 && p->use_graphs != 1) ||

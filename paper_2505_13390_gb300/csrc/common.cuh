@@ -114,7 +114,7 @@ struct Level {
   std::vector<int64_t> hcptr;       // host offsets of each colour in crow
   double lmax = 0.0, omega = 0.0;
   // V-cycle vectors in the working precision (double or float)
-  void *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr;
+  void *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
 };
 
 struct Handle {

@@ -111,7 +111,7 @@ __global__ void k_mf_vertex(int N, const int64_t *vptr, const int32_t *vrow, con
   }
 }
 
-enum { MF_SWEEP = kMfSweep, MF_RESID = kMfResid, MF_APPLY_DOT = 2 };
+enum { MF_SWEEP = kMfSweep, MF_RESID = kMfResid, MF_APPLY_DOT = 2, MF_APPLY = kMfApply };
 
 // row pass: y_i = sum_s g_{i,s}.u_{v_s} + alpha~_i x_i, then
 //   MF_SWEEP     out = x + omega D^-1 (b - y)
@@ -149,6 +149,7 @@ __global__ void k_mf_row(int E, int m, const int32_t *edge, const int32_t *tet, 
     y = fma(at[i], xi, y);
     if (MODE == MF_SWEEP) out[i] = fma(omega, (b[i] - y) * dinv[i], xi);
     else if (MODE == MF_RESID) out[i] = b[i] - y;
+    else if (MODE == MF_APPLY) out[i] = y;
     else {
       out[i] = y;
       acc = fma((double)xi, (double)y, acc);
@@ -242,6 +243,9 @@ mgpbd_status mf_level0<float>(Handle *h, int mode, const float *x, const float *
   if (mode == MF_SWEEP)
     k_mf_row<float, MF_SWEEP><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
         h->E, h->m, h->edge, h->tet, h->gd32, h->gt32, h->u32, h->at32, x, b, dinv, omega, out, c);
+  else if (mode == MF_APPLY)
+    k_mf_row<float, MF_APPLY><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
+        h->E, h->m, h->edge, h->tet, h->gd32, h->gt32, h->u32, h->at32, x, b, dinv, omega, out, c);
   else
     k_mf_row<float, MF_RESID><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
         h->E, h->m, h->edge, h->tet, h->gd32, h->gt32, h->u32, h->at32, x, b, dinv, omega, out, c);
@@ -257,6 +261,9 @@ mgpbd_status mf_level0<double>(Handle *h, int mode, const double *x, const doubl
   c.sc = h->sc;
   if (mode == MF_SWEEP)
     k_mf_row<double, MF_SWEEP><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
+        h->E, h->m, h->edge, h->tet, h->gd, h->gt, h->u64, h->alpha_t, x, b, dinv, omega, out, c);
+  else if (mode == MF_APPLY)
+    k_mf_row<double, MF_APPLY><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
         h->E, h->m, h->edge, h->tet, h->gd, h->gt, h->u64, h->alpha_t, x, b, dinv, omega, out, c);
   else
     k_mf_row<double, MF_RESID><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(

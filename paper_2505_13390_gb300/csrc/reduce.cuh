@@ -170,6 +170,6 @@ mgpbd_status mf_apply_pq(Handle *h, const double *p, double *q, const DotCtx &c)
 template <class T>
 mgpbd_status mf_level0(Handle *h, int mode, const T *x, const T *b, const T *dinv, T omega,
                        T *out);
-constexpr int kMfSweep = 0, kMfResid = 1;
+constexpr int kMfSweep = 0, kMfResid = 1, kMfApply = 3;
 
 }  // namespace mg

@@ -605,7 +605,7 @@ static mgpbd_status ensure_level(Handle *h, int l, int n, int64_t nnz) {
       if (mixed) MG_TRY(alloc_n(h->arena, &L.dinv32, (size_t)cap));
     }
     void *olds[] = {L.agg, L.root, L.P, L.P32, L.B, L.mptr, L.mrow, L.color, L.crow,
-                    L.x, L.x2, L.b, L.r};
+                    L.x, L.x2, L.b, L.r, L.t};
     for (void *o : olds) h->arena.release(o);
     L.P32 = nullptr;
     L.crow = nullptr;
@@ -621,6 +621,7 @@ static mgpbd_status ensure_level(Handle *h, int l, int n, int64_t nnz) {
     MG_TRY(h->arena.alloc(&L.x2, tsize(h) * cap));
     MG_TRY(h->arena.alloc(&L.b, tsize(h) * cap));
     MG_TRY(h->arena.alloc(&L.r, tsize(h) * cap));
+    MG_TRY(h->arena.alloc(&L.t, tsize(h) * cap));
     L.cap_n = cap;
   }
   if (l > 0 && nnz > L.cap_nnz) {

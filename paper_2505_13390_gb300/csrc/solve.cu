@@ -150,6 +150,46 @@ __global__ void k_gs_colour(int nrows, const int32_t *crow, const int64_t *ptr,
   }
 }
 
+// y = A v (Chebyshev products on CSR levels)
+template <int G, class T>
+__global__ void k_spmv_plain(int n, const int64_t *ptr, const int32_t *col, const T *val,
+                             const T *v, T *y, const PcgScalars *sc) {
+  if (is_done(sc)) return;
+  GROUP_ROWS(G, n) {
+    T s = valid ? row_dot<G, T, T, T>(ptr, col, val, v, (int)i, g) : (T)0;
+    s = group_sum<G>(s);
+    if (valid && g == 0) y[i] = s;
+  }
+}
+
+// Chebyshev recurrence: start r = D^-1 (b - A x), d = r / theta, x += d;
+// step r -= D^-1 (A d), d = c1 d + c2 r, x += d
+template <class T>
+__global__ void k_cheb_start(int n, const T *b, const T *Ax, const T *dinv, T inv_theta, T *r,
+                             T *d, T *x, const PcgScalars *sc) {
+  if (is_done(sc)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    T ri = (b[i] - Ax[i]) * dinv[i];
+    T di = ri * inv_theta;
+    r[i] = ri;
+    d[i] = di;
+    x[i] = x[i] + di;
+  }
+}
+
+template <class T>
+__global__ void k_cheb_step(int n, const T *Ad, const T *dinv, T c1, T c2, T *r, T *d, T *x,
+                            const PcgScalars *sc) {
+  if (is_done(sc)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    T ri = r[i] - Ad[i] * dinv[i];
+    T di = fma(c1, d[i], c2 * ri);
+    r[i] = ri;
+    d[i] = di;
+    x[i] = x[i] + di;
+  }
+}
+
 // weighted Jacobi sweep: xn = x + omega D^-1 (b - A x)
 template <int G, class T>
 __global__ void k_jacobi(int n, const int64_t *ptr, const int32_t *col, const T *val,
@@ -412,14 +452,47 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in) {
       }
     return MGPBD_OK;
   };
-  if (gs) {
+  // Chebyshev smoother on [lambda_min_est, safety * lambda_max] with
+  // smooth_sweeps products; coefficients follow from the lazily estimated
+  // lambda_max of the setup (Sec. 4.5)
+  const bool cheb = h->p.smoother == MGPBD_SMOOTH_CHEBYSHEV;
+  auto apply = [&](const T *v, T *y) -> mgpbd_status {
+    if (mf) return mf_level0<T>(h, kMfApply, v, b_in, dinv, om, y);
+    DISPATCH_G(G, (k_spmv_plain<GG, T><<<row_blocks(n, GG), 256, 0, h->stream>>>(
+                      n, L.ptr, L.col, val, v, y, sc)));
+    MG_LAUNCH("k_spmv_plain");
+    return MGPBD_OK;
+  };
+  auto cheb_smooth = [&]() -> mgpbd_status {
+    const double lo = h->p.lambda_min_est, hi = h->p.power_safety * L.lmax;
+    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    T *t = (T *)L.t, *d = x2;
+    MG_TRY(apply(x, t));
+    k_cheb_start<T><<<blocks_for(n, 256), 256, 0, h->stream>>>(n, b_in, t, dinv, (T)(1.0 / theta),
+                                                              r, d, x, sc);
+    MG_LAUNCH("k_cheb_start");
+    for (int k = 1; k < h->p.smooth_sweeps; ++k) {
+      MG_TRY(apply(d, t));
+      double rho2 = 1.0 / (2.0 * sigma - rho);
+      k_cheb_step<T><<<blocks_for(n, 256), 256, 0, h->stream>>>(
+          n, t, dinv, (T)(rho2 * rho), (T)(2.0 * rho2 / delta), r, d, x, sc);
+      MG_LAUNCH("k_cheb_step");
+      rho = rho2;
+    }
+    return MGPBD_OK;
+  };
+  if (cheb) {
+    MG_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * n, h->stream));
+    MG_TRY(cheb_smooth());
+  } else if (gs) {
     MG_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * n, h->stream));
     MG_TRY(gs_sweeps(false));
   } else {
     k_jacobi0<T><<<blocks_for(n, 256), 256, 0, h->stream>>>(n, b_in, dinv, om, x, sc);
     MG_LAUNCH("k_jacobi0");
   }
-  for (int s = 1; s < h->p.smooth_sweeps && !gs; ++s) {
+  for (int s = 1; s < h->p.smooth_sweeps && !gs && !cheb; ++s) {
     if (l == 0) MG_TRY(prof_begin(h));
     if (mf) {
       MG_TRY(mf_level0<T>(h, kMfSweep, x, b_in, dinv, om, x2));
@@ -447,7 +520,8 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in) {
                                                           sc);
   MG_LAUNCH("k_prolong");
   if (gs) MG_TRY(gs_sweeps(true));
-  for (int s = 0; s < h->p.smooth_sweeps && !gs; ++s) {
+  if (cheb) MG_TRY(cheb_smooth());
+  for (int s = 0; s < h->p.smooth_sweeps && !gs && !cheb; ++s) {
     if (l == 0) MG_TRY(prof_begin(h));
     if (mf) {
       MG_TRY(mf_level0<T>(h, kMfSweep, x, b_in, dinv, om, x2));

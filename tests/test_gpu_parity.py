@@ -107,12 +107,12 @@ def test_setup_bit_exact(name):
             assert lg == pytest.approx(lo, rel=1e-10) and wg == pytest.approx(wo, rel=1e-10)
 
 
-@pytest.mark.parametrize("smoother", [0, 1])
+@pytest.mark.parametrize("smoother", [0, 1, 2])
 @pytest.mark.parametrize("op", [0, 1])
 @pytest.mark.parametrize("name", ["cloth8", "hex3", "cloth32"])
 def test_vcycle_parity(name, op, smoother):
     """FP64 V-cycle; op = 1 applies the level-0 products matrix-free;
-    smoother = 1 is the multicolour Gauss-Seidel smoother."""
+    smoother = 1 is multicolour Gauss-Seidel, 2 Chebyshev."""
     mesh, p, o, g = both(name, level0_op=op, smoother=smoother)
     o.begin_frame()
     g.begin_frame()
@@ -195,7 +195,7 @@ def test_solve_stiff_true_residual():
     assert np.linalg.norm(xg - xo) <= 1e-5 * np.linalg.norm(xo)
 
 
-@pytest.mark.parametrize("smoother", [0, 1])
+@pytest.mark.parametrize("smoother", [0, 1, 2])
 @pytest.mark.parametrize("op", [0, 1])
 @pytest.mark.parametrize("name,iters", [("cloth8", 6), ("cloth8s", 6), ("hex3s", 6),
                                         ("cloth32", 4), ("hex3", 3)])

@@ -476,12 +476,12 @@ def test_power_method_omega(name):
 # solve phase: V-cycle and MGPCG (Sec. 4.4-4.5)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("smoother", [0, 1])
+@pytest.mark.parametrize("smoother", [0, 1, 2])
 @pytest.mark.parametrize("name", ["c8", "h3"])
 def test_vcycle_is_symmetric(name, smoother):
     mesh, p, o = hierarchy_case(name)
     if smoother:
-        o2 = Oracle(mesh, dict(p, smoother=1))
+        o2 = Oracle(mesh, dict(p, smoother=smoother))
         o2.begin_frame()
         o2.eval_assemble()
         o2.prepare_solve()
@@ -492,12 +492,12 @@ def test_vcycle_is_symmetric(name, smoother):
     assert abs(a - b) <= 1e-12 * max(abs(a), abs(b))
 
 
-@pytest.mark.parametrize("smoother", [0, 1])
+@pytest.mark.parametrize("smoother", [0, 1, 2])
 @pytest.mark.parametrize("name", ["c8", "h3"])
 def test_pcg_matches_dense_cholesky(name, smoother):
     mesh, p, o = hierarchy_case(name, soft=True)
     if smoother:
-        o = Oracle(mesh, dict(p, smoother=1))
+        o = Oracle(mesh, dict(p, smoother=smoother))
         o.begin_frame()
         o.eval_assemble()
         o.prepare_solve()
@@ -510,6 +510,46 @@ def test_pcg_matches_dense_cholesky(name, smoother):
     assert info["status"] == 0
     assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
     assert info["true_rel_res"] <= 1e-10
+
+
+def test_chebyshev_degree_one_is_optimal_weighted_jacobi():
+    """Degree-1 Chebyshev on [lo, hi] is weighted Jacobi with omega = 2/(lo+hi),
+    the paper's omega_opt: both smoothers give the same V-cycle."""
+    mesh, p, o = hierarchy_case("c8")
+    r = np.random.default_rng(8).standard_normal(mesh.n_rows)
+    outs = []
+    for sm in (0, 2):
+        q = Oracle(mesh, dict(p, smoother=sm, smooth_sweeps=1))
+        q.begin_frame()
+        q.eval_assemble()
+        q.prepare_solve()
+        outs.append(q.vcycle(r))
+    assert np.allclose(outs[0], outs[1], rtol=1e-12, atol=1e-14 * np.abs(outs[0]).max())
+
+
+def test_chebyshev_matches_the_chebyshev_polynomial():
+    """Two Chebyshev steps from x = 0 equal x = (I - R2(M)) M^-1 D^-1 b, where
+    M = D^-1 A and R2(t) = T2((theta - t)/delta) / T2(theta/delta) is the
+    residual polynomial of degree 2 on [lo, hi] (dense check)."""
+    mesh, p, o = hierarchy_case("c8")
+    q = Oracle(mesh, dict(p, smoother=2, smooth_sweeps=2))
+    q.begin_frame()
+    q.eval_assemble()
+    q.prepare_solve()
+    _, _, _, A = csr_of(q, 0)
+    Ad = A.toarray()
+    d = np.diag(Ad)
+    lmax, _ = q.level_omega(0)
+    lo, hi = p["lambda_min_est"], p["power_safety"] * lmax
+    th, de = (hi + lo) / 2, (hi - lo) / 2
+    M = Ad / d[:, None]
+    I = np.eye(len(d))
+    Z = (th * I - M) / de
+    R2 = (2 * Z @ Z - I) / (2 * (th / de) ** 2 - 1)
+    b = np.random.default_rng(9).standard_normal(mesh.n_rows)
+    x_ref = np.linalg.solve(M, (I - R2) @ (b / d))
+    x = q.smooth(0, b)
+    assert np.allclose(x, x_ref, rtol=1e-9, atol=1e-12 * np.abs(x_ref).max())
 
 
 def test_one_level_hierarchy_converges_in_one_iteration():
