@@ -138,6 +138,7 @@ struct Handle {
   double *ginc64 = nullptr, *u64 = nullptr;
   float *ginc32 = nullptr, *gd32 = nullptr, *gt32 = nullptr, *at32 = nullptr, *w32 = nullptr,
         *u32 = nullptr;
+  int mf_g32 = 8, mf_g64 = 4;  // lanes per vertex of the vertex pass (autotuned)
   uint16_t *map = nullptr;
   uint8_t *S = nullptr;  // strength mask, sized for level 0 and reused per level
   // hierarchy

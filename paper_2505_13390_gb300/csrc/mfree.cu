@@ -84,43 +84,47 @@ __global__ void k_to_f32_mf(int64_t n, const double *a, float *b) {
     b[k] = (float)a[k];
 }
 
-// vertex pass: u_v = w_v * sum_q ginc_q * x_{row(q)}
-template <class T>
+// vertex pass: u_v = w_v * sum_q ginc_q * x_{row(q)}, G lanes per vertex
+template <int G, class T>
 __global__ void k_mf_vertex(int N, const int64_t *vptr, const int32_t *vrow, const T *ginc,
                             const T *w, const T *x, T *u, const PcgScalars *sc) {
   if (sc && is_done(sc)) return;
-  GROUP_ROWS(kMfVertexLanes, N) {
+  GROUP_ROWS(G, N) {
     T a0 = 0, a1 = 0, a2 = 0;
     if (valid) {
-      for (int64_t q = vptr[i] + g; q < vptr[i + 1]; q += kMfVertexLanes) {
+      for (int64_t q = vptr[i] + g; q < vptr[i + 1]; q += G) {
         T xj = x[vrow[q]];
         a0 = fma(ginc[3 * q], xj, a0);
         a1 = fma(ginc[3 * q + 1], xj, a1);
         a2 = fma(ginc[3 * q + 2], xj, a2);
       }
     }
-    a0 = group_sum<kMfVertexLanes>(a0);
-    a1 = group_sum<kMfVertexLanes>(a1);
-    a2 = group_sum<kMfVertexLanes>(a2);
-    if (valid && g == 0) {
-      T wv = w[i];
-      u[3 * i] = wv * a0;
-      u[3 * i + 1] = wv * a1;
-      u[3 * i + 2] = wv * a2;
-    }
+    T s = group_sum3<G>(a0, a1, a2, g);
+    const int comp = group_sum3_component<G>(g);
+    if (valid && comp < 3 && (g & (G / 4 - 1)) == 0) u[3 * i + comp] = w[i] * s;
   }
 }
 
-enum { MF_SWEEP = kMfSweep, MF_RESID = kMfResid, MF_APPLY_DOT = 2, MF_APPLY = kMfApply };
+enum {
+  MF_SWEEP = kMfSweep,
+  MF_RESID = kMfResid,
+  MF_APPLY_DOT = 2,
+  MF_APPLY = kMfApply,
+  MF_SWEEP_Z = 4,
+  MF_SWEEP_ZDOT = 5
+};
 
 // row pass: y_i = sum_s g_{i,s}.u_{v_s} + alpha~_i x_i, then
-//   MF_SWEEP     out = x + omega D^-1 (b - y)
-//   MF_RESID     out = b - y
-//   MF_APPLY_DOT out = y, with x.y folded into the PCG scalars (DOT_PQ)
+//   MF_SWEEP      out = x + omega D^-1 (b - y)
+//   MF_RESID      out = b - y
+//   MF_APPLY_DOT  out = y, with x.y folded into the PCG scalars (DOT_PQ)
+//   MF_SWEEP_Z    z = x + omega D^-1 (b - y) widened to FP64
+//   MF_SWEEP_ZDOT the same, with r.z folded into the PCG scalars
 template <class T, int MODE>
 __global__ void k_mf_row(int E, int m, const int32_t *edge, const int32_t *tet, const T *gd,
                          const T *gt, const T *u, const T *at, const T *x, const T *b,
-                         const T *dinv, T omega, T *out, DotCtx c) {
+                         const T *dinv, T omega, T *out, DotCtx c, double *z = nullptr,
+                         const double *rr = nullptr) {
   if (is_done(c.sc)) return;
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
@@ -150,12 +154,16 @@ __global__ void k_mf_row(int E, int m, const int32_t *edge, const int32_t *tet, 
     if (MODE == MF_SWEEP) out[i] = fma(omega, (b[i] - y) * dinv[i], xi);
     else if (MODE == MF_RESID) out[i] = b[i] - y;
     else if (MODE == MF_APPLY) out[i] = y;
-    else {
+    else if (MODE == MF_APPLY_DOT) {
       out[i] = y;
       acc = fma((double)xi, (double)y, acc);
+    } else {
+      double zi = (double)fma(omega, (b[i] - y) * dinv[i], xi);
+      z[i] = zi;
+      if (MODE == MF_SWEEP_ZDOT) acc = fma(rr[i], zi, acc);
     }
   }
-  if (MODE == MF_APPLY_DOT) block_dot_finish(acc, c);
+  if (MODE == MF_APPLY_DOT || MODE == MF_SWEEP_ZDOT) block_dot_finish(acc, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -210,12 +218,56 @@ mgpbd_status mf_prepare(Handle *h) {
 }
 
 template <class T>
-static mgpbd_status mf_vertex(Handle *h, const T *ginc, const T *w, const T *x, T *u) {
+static mgpbd_status mf_vertex(Handle *h, const T *ginc, const T *w, const T *x, T *u, int G = 0,
+                              bool check_done = true) {
+  if (G == 0) G = sizeof(T) == 8 ? h->mf_g64 : h->mf_g32;
+  const PcgScalars *sc = check_done ? h->sc : nullptr;
   int64_t groups = (int64_t)h->N;
-  int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(
-                   (groups * kMfVertexLanes + 255) / 256, 64 * (int64_t)num_sms()));
-  k_mf_vertex<T><<<blocks, 256, 0, h->stream>>>(h->N, h->vptr, h->vrow, ginc, w, x, u, h->sc);
+  int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((groups * G + 255) / 256,
+                                                            64 * (int64_t)num_sms()));
+  switch (G) {
+    case 4:
+      k_mf_vertex<4, T><<<blocks, 256, 0, h->stream>>>(h->N, h->vptr, h->vrow, ginc, w, x, u, sc);
+      break;
+    case 16:
+      k_mf_vertex<16, T><<<blocks, 256, 0, h->stream>>>(h->N, h->vptr, h->vrow, ginc, w, x, u, sc);
+      break;
+    default:
+      k_mf_vertex<8, T><<<blocks, 256, 0, h->stream>>>(h->N, h->vptr, h->vrow, ginc, w, x, u, sc);
+      break;
+  }
   MG_LAUNCH("k_mf_vertex");
+  return MGPBD_OK;
+}
+
+// Times the vertex pass with 4, 8 and 16 lanes per vertex in each precision
+// the solve uses and keeps the fastest (params.autotune).
+mgpbd_status mf_autotune(Handle *h) {
+  if (h->m == 0 || !h->vslot) return MGPBD_OK;
+  auto pick = [&](auto *ginc, auto *w, auto *x, auto *u, int *out) -> mgpbd_status {
+    const int cands[3] = {4, 8, 16};
+    float best = 1e30f;
+    for (int c = 0; c < 3; ++c) {
+      for (int rep = 0; rep < 3; ++rep) {
+        MG_CUDA(cudaEventRecord(h->ev0, h->stream));
+        MG_TRY(mf_vertex(h, ginc, w, x, u, cands[c], false));
+        MG_CUDA(cudaEventRecord(h->ev1, h->stream));
+        MG_CUDA(cudaEventSynchronize(h->ev1));
+        float ms = 0.f;
+        MG_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        if (ms < best) {
+          best = ms;
+          *out = cands[c];
+        }
+      }
+    }
+    return MGPBD_OK;
+  };
+  MG_TRY(pick((const double *)h->ginc64, (const double *)h->w, (const double *)h->pr, h->u64,
+              &h->mf_g64));
+  if (h->p.precision == MGPBD_MIXED)
+    MG_TRY(pick((const float *)h->ginc32, (const float *)h->w32, (const float *)h->lev[0].b,
+                h->u32, &h->mf_g32));
   return MGPBD_OK;
 }
 
@@ -271,5 +323,32 @@ mgpbd_status mf_level0<double>(Handle *h, int mode, const double *x, const doubl
   MG_LAUNCH("k_mf_row(f64)");
   return MGPBD_OK;
 }
+
+template <class T>
+mgpbd_status mf_level0_final(Handle *h, const T *x, const T *b, const T *dinv, T omega,
+                             const TopOut &o) {
+  const bool dbl = sizeof(T) == 8;
+  MG_TRY(mf_vertex<T>(h, dbl ? (const T *)h->ginc64 : (const T *)h->ginc32,
+                      dbl ? (const T *)h->w : (const T *)h->w32, x, dbl ? (T *)h->u64 : (T *)h->u32));
+  const T *gd = dbl ? (const T *)h->gd : (const T *)h->gd32;
+  const T *gt = dbl ? (const T *)h->gt : (const T *)h->gt32;
+  const T *u = dbl ? (const T *)h->u64 : (const T *)h->u32;
+  const T *at = dbl ? (const T *)h->alpha_t : (const T *)h->at32;
+  DotCtx c = o.c;
+  c.sc = h->sc;
+  if (o.dot)
+    k_mf_row<T, MF_SWEEP_ZDOT><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
+        h->E, h->m, h->edge, h->tet, gd, gt, u, at, x, b, dinv, omega, nullptr, c, o.z, o.r);
+  else
+    k_mf_row<T, MF_SWEEP_Z><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
+        h->E, h->m, h->edge, h->tet, gd, gt, u, at, x, b, dinv, omega, nullptr, c, o.z, o.r);
+  MG_LAUNCH("k_mf_row(final sweep)");
+  return MGPBD_OK;
+}
+
+template mgpbd_status mf_level0_final<float>(Handle *, const float *, const float *, const float *,
+                                             float, const TopOut &);
+template mgpbd_status mf_level0_final<double>(Handle *, const double *, const double *,
+                                              const double *, double, const TopOut &);
 
 }  // namespace mg

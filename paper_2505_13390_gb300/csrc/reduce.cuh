@@ -141,6 +141,32 @@ __device__ __forceinline__ T group_sum(T v) {
   return v;
 }
 
+// Sum of three values over the G lanes of a group (G >= 4) by
+// reduce-scatter with a zero fourth slot: two exchange steps leave each lane
+// one component summed over four lanes, butterflies finish it.  Lane g ends
+// with component 2 * [g & G/2] + [g & G/4]; log2(G) + 1 adds per lane instead
+// of 3 log2(G) for three butterflies (the FP64 vertex pass is bound by them).
+template <int G, class T>
+__device__ __forceinline__ T group_sum3(T a0, T a1, T a2, int g) {
+  static_assert(G >= 4 && G <= 32, "group of 4..32 lanes");
+  constexpr int o1 = G / 2, o2 = G / 4;
+  const bool h1 = (g & o1) != 0, h2 = (g & o2) != 0;
+  T k0 = h1 ? a2 : a0, k1 = h1 ? (T)0 : a1;  // kept: components (0,1) or (2,3)
+  T s0 = h1 ? a0 : a2, s1 = h1 ? a1 : (T)0;  // sent to the partner
+  k0 += __shfl_xor_sync(0xffffffffu, s0, o1);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, o1);
+  T k = h2 ? k1 : k0, s = h2 ? k0 : k1;
+  k += __shfl_xor_sync(0xffffffffu, s, o2);
+#pragma unroll
+  for (int o = o2 / 2; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+  return k;
+}
+
+template <int G>
+__device__ __forceinline__ int group_sum3_component(int g) {
+  return 2 * ((g & (G / 2)) != 0) + ((g & (G / 4)) != 0);
+}
+
 // partial row dot of lane g of a G-lane group (no shuffles: callers reduce)
 template <int G, class VT, class AT, class XT>
 __device__ __forceinline__ AT row_dot(const int64_t *ptr, const int32_t *col, const VT *val,
@@ -171,5 +197,18 @@ template <class T>
 mgpbd_status mf_level0(Handle *h, int mode, const T *x, const T *b, const T *dinv, T omega,
                        T *out);
 constexpr int kMfSweep = 0, kMfResid = 1, kMfApply = 3;
+mgpbd_status mf_autotune(Handle *h);
+
+// The last level-0 sweep of a top V-cycle can write the preconditioned
+// residual z = x_new straight in FP64 and fold r.z into the PCG scalars.
+struct TopOut {
+  const double *r;  // FP64 residual the V-cycle was applied to
+  double *z;        // FP64 output
+  DotCtx c;         // r.z reduction (when dot is set)
+  bool dot;
+};
+template <class T>
+mgpbd_status mf_level0_final(Handle *h, const T *x, const T *b, const T *dinv, T omega,
+                             const TopOut &o);
 
 }  // namespace mg

@@ -51,9 +51,12 @@ __global__ void k_dot(int64_t n, const double *x, const double *y, DotCtx c, int
   block_dot_finish(acc, c);
 }
 
-// x += alpha p; r -= alpha q; then r.r (convergence test)
+// x += alpha p; r -= alpha q; then r.r (convergence test).  The start of the
+// next V-cycle is folded in: bl = r in the V-cycle's precision (MGPBD_MIXED)
+// and, with the Jacobi smoother, its first sweep from zero x0 = omega D^-1 r.
+template <class T>
 __global__ void k_xr_update(int64_t n, double *x, double *r, const double *p, const double *q,
-                            DotCtx c) {
+                            DotCtx c, T *bl, const T *dinv, T om, T *x0) {
   if (is_done(c.sc)) return;
   const double al = c.sc->alpha;
   double acc = 0.0;
@@ -63,8 +66,25 @@ __global__ void k_xr_update(int64_t n, double *x, double *r, const double *p, co
     double ri = fma(-al, q[i], r[i]);
     r[i] = ri;
     acc = fma(ri, ri, acc);
+    T bi = (T)ri;
+    if (bl) bl[i] = bi;
+    if (x0) x0[i] = om * (bi * dinv[i]);
   }
   block_dot_finish(acc, c);
+}
+
+// the same start of a V-cycle on its own: bl = r in the V-cycle's precision,
+// x0 = omega D^-1 bl (Jacobi)
+template <class T>
+__global__ void k_top_prep(int64_t n, const double *r, T *bl, const T *dinv, T om, T *x0,
+                           const PcgScalars *sc) {
+  if (sc && is_done(sc)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T bi = (T)r[i];
+    if (bl) bl[i] = bi;
+    if (x0) x0[i] = om * (bi * dinv[i]);
+  }
 }
 
 // p = z + beta p
@@ -169,11 +189,11 @@ __global__ void k_cheb_start(int n, const T *b, const T *Ax, const T *dinv, T in
                              T *d, T *x, const PcgScalars *sc) {
   if (is_done(sc)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    T ri = (b[i] - Ax[i]) * dinv[i];
+    T ri = (Ax ? b[i] - Ax[i] : b[i]) * dinv[i];  // no Ax: x = 0 on entry
     T di = ri * inv_theta;
     r[i] = ri;
     d[i] = di;
-    x[i] = x[i] + di;
+    x[i] = Ax ? x[i] + di : di;
   }
 }
 
@@ -417,9 +437,13 @@ const double *Ps<double>(const Level &L) { return L.P; }
 template <>
 const float *Ps<float>(const Level &L) { return L.P32; }
 
-// V-cycle on level l in precision T: L.b -> L.x (zero start)
+// V-cycle on level l in precision T: L.b -> L.x (zero start).  On level 0 of
+// a top V-cycle, `x0_ready` says the first Jacobi sweep is already in L.x,
+// and `top` lets the last matrix-free sweep write z in FP64 (and r.z)
+// instead of L.x; `*z_written` then reports that it did.
 template <class T>
-static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in) {
+static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in, bool x0_ready = false,
+                                 const TopOut *top = nullptr, bool *z_written = nullptr) {
   Level &L = h->lev[l];
   const PcgScalars *sc = h->sc;
   const int n = L.n;
@@ -463,14 +487,15 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in) {
     MG_LAUNCH("k_spmv_plain");
     return MGPBD_OK;
   };
-  auto cheb_smooth = [&]() -> mgpbd_status {
+  // (from_zero: x = 0 on entry, so A x = 0 needs no product)
+  auto cheb_smooth = [&](bool from_zero) -> mgpbd_status {
     const double lo = h->p.lambda_min_est, hi = h->p.power_safety * L.lmax;
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
     double rho = 1.0 / sigma;
     T *t = (T *)L.t, *d = x2;
-    MG_TRY(apply(x, t));
-    k_cheb_start<T><<<blocks_for(n, 256), 256, 0, h->stream>>>(n, b_in, t, dinv, (T)(1.0 / theta),
-                                                              r, d, x, sc);
+    if (!from_zero) MG_TRY(apply(x, t));
+    k_cheb_start<T><<<blocks_for(n, 256), 256, 0, h->stream>>>(
+        n, b_in, from_zero ? nullptr : t, dinv, (T)(1.0 / theta), r, d, x, sc);
     MG_LAUNCH("k_cheb_start");
     for (int k = 1; k < h->p.smooth_sweeps; ++k) {
       MG_TRY(apply(d, t));
@@ -483,12 +508,11 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in) {
     return MGPBD_OK;
   };
   if (cheb) {
-    MG_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * n, h->stream));
-    MG_TRY(cheb_smooth());
+    MG_TRY(cheb_smooth(true));
   } else if (gs) {
     MG_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * n, h->stream));
     MG_TRY(gs_sweeps(false));
-  } else {
+  } else if (!x0_ready) {
     k_jacobi0<T><<<blocks_for(n, 256), 256, 0, h->stream>>>(n, b_in, dinv, om, x, sc);
     MG_LAUNCH("k_jacobi0");
   }
@@ -520,8 +544,14 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in) {
                                                           sc);
   MG_LAUNCH("k_prolong");
   if (gs) MG_TRY(gs_sweeps(true));
-  if (cheb) MG_TRY(cheb_smooth());
+  if (cheb) MG_TRY(cheb_smooth(false));
+  bool zw = false;
   for (int s = 0; s < h->p.smooth_sweeps && !gs && !cheb; ++s) {
+    if (mf && top && s + 1 == h->p.smooth_sweeps) {
+      MG_TRY(mf_level0_final<T>(h, x, b_in, dinv, om, *top));
+      zw = true;
+      break;
+    }
     if (l == 0) MG_TRY(prof_begin(h));
     if (mf) {
       MG_TRY(mf_level0<T>(h, kMfSweep, x, b_in, dinv, om, x2));
@@ -533,36 +563,11 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in) {
     if (l == 0) MG_TRY(prof_end(h));
     std::swap(x, x2);
   }
-  if (x != (T *)L.x) {  // keep the result in L.x
+  if (z_written) *z_written = zw;
+  if (x != (T *)L.x && !zw) {  // keep the result in L.x
     MG_CUDA(cudaMemcpyAsync(L.x, x, sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream));
   }
   return MGPBD_OK;
-}
-
-// z = V(r) on level 0, FP64 in and out
-static mgpbd_status vcycle_top(Handle *h, const double *r, double *z) {
-  Level &L = h->lev[0];
-  const int m = h->m;
-  if (h->p.precision == MGPBD_MIXED) {
-    k_convert<double, float><<<blocks_for(m, 256), 256, 0, h->stream>>>(m, r, (float *)L.b, h->sc);
-    MG_LAUNCH("k_convert");
-    MG_TRY(vcycle_level<float>(h, 0, (const float *)L.b));
-    k_convert<float, double><<<blocks_for(m, 256), 256, 0, h->stream>>>(m, (const float *)L.x, z,
-                                                                        h->sc);
-    MG_LAUNCH("k_convert");
-  } else {
-    MG_TRY(vcycle_level<double>(h, 0, r));
-    k_convert<double, double><<<blocks_for(m, 256), 256, 0, h->stream>>>(m, (const double *)L.x,
-                                                                         z, h->sc);
-    MG_LAUNCH("k_convert");
-  }
-  return MGPBD_OK;
-}
-
-mgpbd_status vcycle_apply(Handle *h, const double *d_r, double *d_z) {
-  k_pcg_init<<<1, 1, 0, h->stream>>>(h->sc);
-  MG_LAUNCH("k_pcg_init");
-  return vcycle_top(h, d_r, d_z);
 }
 
 static mgpbd_status launch_dot(Handle *h, const double *x, const double *y, int64_t n, int mode,
@@ -571,6 +576,61 @@ static mgpbd_status launch_dot(Handle *h, const double *x, const double *y, int6
   k_dot<<<dot_grid(), kDotThreads, 0, h->stream>>>(n, x, y, c, check_done);
   MG_LAUNCH("k_dot");
   return MGPBD_OK;
+}
+
+// level 0 starts its V-cycle with a Jacobi sweep from zero (not the coarsest)
+static bool top_jacobi(const Handle *h) {
+  return h->p.smoother == MGPBD_SMOOTH_JACOBI && h->L > 1 && h->p.smooth_sweeps >= 1;
+}
+
+// z = V(r) on level 0, FP64 in and out.  `prepared`: the PCG update already
+// wrote the V-cycle's right-hand side in its precision and, with the Jacobi
+// smoother, the first sweep (k_xr_update).  dot_mode >= 0 folds r.z into the
+// PCG scalars, inside the last matrix-free sweep when there is one.
+static mgpbd_status vcycle_top(Handle *h, const double *r, double *z, bool prepared,
+                               int dot_mode) {
+  Level &L = h->lev[0];
+  const int m = h->m;
+  const bool jac = top_jacobi(h);
+  TopOut o;
+  o.r = r;
+  o.z = z;
+  o.dot = dot_mode >= 0;
+  o.c = make_ctx(h, o.dot ? dot_mode : DOT_STORE);
+  bool zw = false;
+  if (h->p.precision == MGPBD_MIXED) {
+    if (!prepared) {
+      k_top_prep<float><<<blocks_for(m, 256), 256, 0, h->stream>>>(
+          m, r, (float *)L.b, L.dinv32, (float)L.omega, jac ? (float *)L.x : nullptr, h->sc);
+      MG_LAUNCH("k_top_prep");
+    }
+    MG_TRY(vcycle_level<float>(h, 0, (const float *)L.b, jac, &o, &zw));
+    if (!zw) {
+      k_convert<float, double><<<blocks_for(m, 256), 256, 0, h->stream>>>(m, (const float *)L.x,
+                                                                          z, h->sc);
+      MG_LAUNCH("k_convert");
+    }
+  } else {
+    if (!prepared && jac) {
+      k_top_prep<double><<<blocks_for(m, 256), 256, 0, h->stream>>>(m, r, nullptr, L.dinv, L.omega,
+                                                                    (double *)L.x, h->sc);
+      MG_LAUNCH("k_top_prep");
+    }
+    MG_TRY(vcycle_level<double>(h, 0, r, jac, &o, &zw));
+    if (!zw) {
+      k_convert<double, double><<<blocks_for(m, 256), 256, 0, h->stream>>>(
+          m, (const double *)L.x, z, h->sc);
+      MG_LAUNCH("k_convert");
+    }
+  }
+  if (o.dot && !zw) MG_TRY(launch_dot(h, r, z, m, dot_mode, 1));
+  return MGPBD_OK;
+}
+
+mgpbd_status vcycle_apply(Handle *h, const double *d_r, double *d_z) {
+  k_pcg_init<<<1, 1, 0, h->stream>>>(h->sc);
+  MG_LAUNCH("k_pcg_init");
+  return vcycle_top(h, d_r, d_z, false, -1);
 }
 
 mgpbd_status dot_dd(Handle *h, const double *x, const double *y, int64_t n, double *d_out) {
@@ -596,10 +656,18 @@ static mgpbd_status pcg_iteration(Handle *h, double *x) {
                                                                               L.val, p, q, cpq)));
     MG_LAUNCH("k_spmv_pq");
   }
-  k_xr_update<<<dot_grid(), kDotThreads, 0, h->stream>>>(m, x, r, p, q, make_ctx(h, DOT_RR));
+  // the update also starts the V-cycle (right-hand side, first Jacobi sweep)
+  const bool jac = top_jacobi(h);
+  if (h->p.precision == MGPBD_MIXED)
+    k_xr_update<float><<<dot_grid(), kDotThreads, 0, h->stream>>>(
+        m, x, r, p, q, make_ctx(h, DOT_RR), (float *)L.b, L.dinv32, (float)L.omega,
+        jac ? (float *)L.x : nullptr);
+  else
+    k_xr_update<double><<<dot_grid(), kDotThreads, 0, h->stream>>>(
+        m, x, r, p, q, make_ctx(h, DOT_RR), nullptr, L.dinv, L.omega,
+        jac ? (double *)L.x : nullptr);
   MG_LAUNCH("k_xr_update");
-  MG_TRY(vcycle_top(h, r, z));
-  MG_TRY(launch_dot(h, r, z, m, DOT_RZ, 1));
+  MG_TRY(vcycle_top(h, r, z, true, DOT_RZ));
   k_p_update<<<blocks_for(m, 256), 256, 0, h->stream>>>(m, p, z, h->sc);
   MG_LAUNCH("k_p_update");
   return MGPBD_OK;
@@ -618,9 +686,8 @@ mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *
   MG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * m, h->stream));
   MG_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->stream));
   MG_TRY(launch_dot(h, b, b, m, DOT_BNORM, 0));
-  MG_TRY(vcycle_top(h, r, z));
+  MG_TRY(vcycle_top(h, r, z, false, DOT_RZ0));
   MG_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->stream));
-  MG_TRY(launch_dot(h, r, z, m, DOT_RZ0, 1));
   const int chunk = 8;
   int launched = 0;
   // Chunks of PCG iterations replay a captured CUDA graph (one launch instead
@@ -762,6 +829,7 @@ mgpbd_status autotune_levels(Handle *h) {
     }
     if (l + 1 >= h->L) break;
   }
+  if (h->p.level0_op == 1) MG_TRY(mf_autotune(h));
   return MGPBD_OK;
 }
 
