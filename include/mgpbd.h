@@ -286,6 +286,19 @@ mgpbd_status mgpbd_batch_get_state(mgpbd_batch_t *b, int instance, double *x, do
 mgpbd_status mgpbd_batch_resident(mgpbd_batch_t *b, int *n_resident, size_t *bytes);
 void mgpbd_batch_destroy(mgpbd_batch_t *b);
 
+/* ---- precision conversions of the mixed-precision path ----
+ * The paper has no counterpart of this call: it exposes the conversions the
+ * MGPBD_MIXED solve uses between its FP64 Krylov vectors and its FP32
+ * V-cycle, integer implementations of IEEE 754-2008 binary64 -> binary32
+ * with roundTiesToEven (section 4.3.1) and of the exact binary32 ->
+ * binary64 widening.  d_in64 (n doubles) is narrowed into d_out32 (n floats)
+ * and d_in32 (n floats) is widened into d_out64 (n doubles); either pair may
+ * be NULL/NULL to skip it.  All four are device pointers owned by the caller.
+ * Asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * MGPBD_E_INVALID for n < 0 or a pair given by half. */
+mgpbd_status mgpbd_convert(const double *d_in64, float *d_out32, const float *d_in32,
+                           double *d_out64, int64_t n, void *stream);
+
 /* ---- allocation-free entry point ----
  * The paper has no counterpart of this call; it exists for callers that
  * cannot allocate device memory while they run: a thread capturing a CUDA

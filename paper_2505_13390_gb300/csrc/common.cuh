@@ -136,8 +136,8 @@ struct Handle {
   // matrix-free level-0 operator: gradients in incidence order, FP32 copies
   uint8_t *vslot = nullptr;
   double *ginc64 = nullptr, *u64 = nullptr;
-  float *ginc32 = nullptr, *gd32 = nullptr, *gt32 = nullptr, *at32 = nullptr, *w32 = nullptr,
-        *u32 = nullptr;
+  float4 *ginc4 = nullptr;  // FP32 gradient and row id (bits in .w) per incidence
+  float *gd32 = nullptr, *gt32 = nullptr, *at32 = nullptr, *w32 = nullptr, *u32 = nullptr;
   int mf_g32 = 8, mf_g64 = 4;  // lanes per vertex of the vertex pass (autotuned)
   uint16_t *map = nullptr;
   uint8_t *S = nullptr;  // strength mask, sized for level 0 and reused per level
@@ -256,6 +256,71 @@ __host__ __device__ __forceinline__ uint64_t hkey(uint64_t seed, int l, int i) {
 __host__ __device__ __forceinline__ double u01(uint64_t hv) {
   return ((double)(hv >> 11) + 0.5) * 0x1p-53;
 }
+
+// Conversions between IEEE 754 binary64 and binary32 written with integer
+// operations.  The hardware conversion instructions between the two formats
+// issue on the FP64 pipe, which is narrow on this GPU (a level-0 vector of
+// 3.7M entries took ~28 us to convert), while the integer pipes are wide.
+//
+// binary32 -> binary64 is exact: rebias the exponent (127 -> 1023), widen the
+// fraction, normalise subnormals; infinities and NaNs keep sign and payload.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t s = u & 0x80000000u, e = (u >> 23) & 0xffu;
+  uint32_t m = u & 0x7fffffu, hi, lo;
+  if (e == 0xffu) {
+    hi = s | 0x7ff00000u | (m >> 3);
+    lo = m << 29;
+  } else if (e != 0u) {
+    hi = s | ((e + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  } else if (m == 0u) {
+    hi = s;
+    lo = 0u;
+  } else {  // subnormal m * 2^-149: shift the leading one to bit 23
+    const int n = __clz(m) - 8;
+    m = (m << n) & 0x7fffffu;
+    hi = s | ((uint32_t)(897 - n) << 20) | (m >> 3);
+    lo = m << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// binary64 -> binary32 with roundTiesToEven (IEEE 754-2008, 4.3.1): keep the
+// leading 24 significant bits, round on the dropped bits (above half: up;
+// exactly half: to the even neighbour), overflow to infinity, results below
+// the binary32 normal range rounded in units of 2^-149.
+__device__ __forceinline__ float f64_to_f32(double d) {
+  const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+  const uint32_t s = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const uint64_t m = ((uint64_t)(hi & 0xfffffu) << 32) | lo;
+  if (e == 0x7ff) return __uint_as_float(s | 0x7f800000u | (m ? 0x400000u | (uint32_t)(m >> 29) : 0u));
+  const int ef = e - 896;  // binary32 biased exponent
+  if (ef >= 0xff) return __uint_as_float(s | 0x7f800000u);
+  if (ef >= 1) {
+    const uint32_t r = (uint32_t)(m >> 29), rem = (uint32_t)m & 0x1fffffffu;
+    uint32_t bits = ((uint32_t)ef << 23) | r;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) bits += 1u;  // carries into exponent
+    return __uint_as_float(s | bits);
+  }
+  // value = (2^52 + m) * 2^(e - 1075) = sig * 2^(ef - 30) units of 2^-149
+  const int sh = 30 - ef;
+  if (e == 0 || sh >= 54) return __uint_as_float(s);  // below half the smallest subnormal
+  const uint64_t sig = m | (1ull << 52);
+  const uint32_t q = (uint32_t)(sig >> sh);
+  const uint64_t rem = sig & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+  return __uint_as_float(s | (q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u)));
+}
+
+template <class T>
+__device__ __forceinline__ T narrow(double v);
+template <>
+__device__ __forceinline__ float narrow<float>(double v) { return f64_to_f32(v); }
+template <>
+__device__ __forceinline__ double narrow<double>(double v) { return v; }
+__device__ __forceinline__ double widen(float v) { return f32_to_f64(v); }
+__device__ __forceinline__ double widen(double v) { return v; }
 
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {

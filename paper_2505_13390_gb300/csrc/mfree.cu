@@ -11,9 +11,11 @@
 // which is A x term for term (A_ij = sum over shared v of w_v g_{i,v}.g_{j,v}).
 // The vertex pass reads the gradients in incidence order from `ginc`, a copy
 // laid out per (vertex, incident row) that is rebuilt once per global
-// iteration, so both passes stream their inputs.  Per product at block100
-// this moves about 0.5 GB (FP32) / 0.8 GB (FP64) instead of 3.1 / 4.7 GB for
-// the CSR pass, and about 4x fewer FP64 multiply-adds.
+// iteration, so both passes stream their inputs; in FP32 each incidence is
+// one 16-byte record (gradient and row id).  Per product on the 1.65M-tet
+// block this moves about 0.4 GB (FP32) / 0.8 GB (FP64) instead of 3.1 /
+// 4.7 GB for the CSR pass, and about 4x fewer FP64 multiply-adds.
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -41,11 +43,11 @@ __global__ void k_vslot(int N, int E, const int32_t *edge, const int32_t *tet, c
   }
 }
 
-// gradients in incidence order (FP64 and optionally FP32), and FP32 copies
-// of the row gradients
+// gradients in incidence order: FP64 (row ids apart) and optionally FP32
+// packed with the row id, one 16-byte load per incidence
 __global__ void k_mf_prep(int N, int E, const int64_t *vptr, const int32_t *vrow,
                           const uint8_t *vslot, const double *gd, const double *gt, double *g64,
-                          float *g32) {
+                          float4 *g4) {
   GROUP_ROWS(kMfVertexLanes, N) {
     if (!valid) continue;
     for (int64_t q = vptr[i] + g; q < vptr[i + 1]; q += kMfVertexLanes) {
@@ -69,11 +71,8 @@ __global__ void k_mf_prep(int N, int E, const int64_t *vptr, const int32_t *vrow
         g64[3 * q + 1] = a1;
         g64[3 * q + 2] = a2;
       }
-      if (g32) {
-        g32[3 * q] = (float)a0;
-        g32[3 * q + 1] = (float)a1;
-        g32[3 * q + 2] = (float)a2;
-      }
+      if (g4)
+        g4[q] = make_float4(f64_to_f32(a0), f64_to_f32(a1), f64_to_f32(a2), __int_as_float(j));
     }
   }
 }
@@ -81,25 +80,79 @@ __global__ void k_mf_prep(int N, int E, const int64_t *vptr, const int32_t *vrow
 __global__ void k_to_f32_mf(int64_t n, const double *a, float *b) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
-    b[k] = (float)a[k];
+    b[k] = f64_to_f32(a[k]);
 }
 
-// vertex pass: u_v = w_v * sum_q ginc_q * x_{row(q)}, G lanes per vertex
-template <int G, class T>
-__global__ void k_mf_vertex(int N, const int64_t *vptr, const int32_t *vrow, const T *ginc,
-                            const T *w, const T *x, T *u, const PcgScalars *sc) {
+// vertex pass: u_v = w_v * sum_q ginc_q * x_{row(q)}, G lanes per vertex.
+// Each lane loads four incidences before it uses them (four gathers in
+// flight); the sum order is the plain lane-strided order.
+template <int G>
+__global__ void k_mf_vertex64(int N, const int64_t *vptr, const int32_t *vrow, const double *ginc,
+                              const double *w, const double *x, double *u, const PcgScalars *sc) {
   if (sc && is_done(sc)) return;
   GROUP_ROWS(G, N) {
-    T a0 = 0, a1 = 0, a2 = 0;
+    double a0 = 0, a1 = 0, a2 = 0;
     if (valid) {
-      for (int64_t q = vptr[i] + g; q < vptr[i + 1]; q += G) {
-        T xj = x[vrow[q]];
-        a0 = fma(ginc[3 * q], xj, a0);
-        a1 = fma(ginc[3 * q + 1], xj, a1);
-        a2 = fma(ginc[3 * q + 2], xj, a2);
+      int64_t q = vptr[i] + g;
+      const int64_t e = vptr[i + 1];
+      for (; q + 3 * G < e; q += 4 * G) {
+        double xv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) xv[k] = x[vrow[q + k * G]];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const double *gq = ginc + 3 * (q + k * G);
+          a0 = fma(gq[0], xv[k], a0);
+          a1 = fma(gq[1], xv[k], a1);
+          a2 = fma(gq[2], xv[k], a2);
+        }
+      }
+      for (; q < e; q += G) {
+        const double xa = x[vrow[q]];
+        a0 = fma(ginc[3 * q], xa, a0);
+        a1 = fma(ginc[3 * q + 1], xa, a1);
+        a2 = fma(ginc[3 * q + 2], xa, a2);
       }
     }
-    T s = group_sum3<G>(a0, a1, a2, g);
+    double s = group_sum3<G>(a0, a1, a2, g);
+    const int comp = group_sum3_component<G>(g);
+    if (valid && comp < 3 && (g & (G / 4 - 1)) == 0) u[3 * i + comp] = w[i] * s;
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(256, 8)
+    k_mf_vertex32(int N, const int64_t *vptr, const float4 *ginc, const float *w, const float *x,
+                  float *u, const PcgScalars *sc) {
+  if (sc && is_done(sc)) return;
+  GROUP_ROWS(G, N) {
+    float a0 = 0, a1 = 0, a2 = 0;
+    if (valid) {
+      int64_t q = vptr[i] + g;
+      const int64_t e = vptr[i + 1];
+      for (; q + 3 * G < e; q += 4 * G) {
+        float4 ev[4];
+        float xv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ev[k] = ginc[q + k * G];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) xv[k] = x[__float_as_int(ev[k].w)];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          a0 = fmaf(ev[k].x, xv[k], a0);
+          a1 = fmaf(ev[k].y, xv[k], a1);
+          a2 = fmaf(ev[k].z, xv[k], a2);
+        }
+      }
+      for (; q < e; q += G) {
+        const float4 ea = ginc[q];
+        const float xa = x[__float_as_int(ea.w)];
+        a0 = fmaf(ea.x, xa, a0);
+        a1 = fmaf(ea.y, xa, a1);
+        a2 = fmaf(ea.z, xa, a2);
+      }
+    }
+    float s = group_sum3<G>(a0, a1, a2, g);
     const int comp = group_sum3_component<G>(g);
     if (valid && comp < 3 && (g & (G / 4 - 1)) == 0) u[3 * i + comp] = w[i] * s;
   }
@@ -156,9 +209,9 @@ __global__ void k_mf_row(int E, int m, const int32_t *edge, const int32_t *tet, 
     else if (MODE == MF_APPLY) out[i] = y;
     else if (MODE == MF_APPLY_DOT) {
       out[i] = y;
-      acc = fma((double)xi, (double)y, acc);
+      acc = fma(widen(xi), widen(y), acc);
     } else {
-      double zi = (double)fma(omega, (b[i] - y) * dinv[i], xi);
+      double zi = widen(fma(omega, (b[i] - y) * dinv[i], xi));
       z[i] = zi;
       if (MODE == MF_SWEEP_ZDOT) acc = fma(rr[i], zi, acc);
     }
@@ -175,7 +228,7 @@ mgpbd_status mf_create(Handle *h) {
   MG_TRY(alloc_n(h->arena, &h->ginc64, 3 * (size_t)ninc));
   MG_TRY(alloc_n(h->arena, &h->u64, 3 * (size_t)h->N));
   if (mixed) {
-    MG_TRY(alloc_n(h->arena, &h->ginc32, 3 * (size_t)ninc));
+    MG_TRY(alloc_n(h->arena, &h->ginc4, (size_t)ninc));
     MG_TRY(alloc_n(h->arena, &h->gd32, 3 * (size_t)h->E));
     MG_TRY(alloc_n(h->arena, &h->gt32, 12 * (size_t)h->T));
     MG_TRY(alloc_n(h->arena, &h->at32, (size_t)h->m));
@@ -204,7 +257,7 @@ mgpbd_status mf_prepare(Handle *h) {
   int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(
                    (groups * kMfVertexLanes + 255) / 256, 64 * (int64_t)num_sms()));
   k_mf_prep<<<blocks, 256, 0, h->stream>>>(h->N, h->E, h->vptr, h->vrow, h->vslot, h->gd, h->gt,
-                                          h->ginc64, mixed ? h->ginc32 : nullptr);
+                                          h->ginc64, mixed ? h->ginc4 : nullptr);
   MG_LAUNCH("k_mf_prep");
   if (mixed) {
     k_to_f32_mf<<<blocks_for(3 * (int64_t)h->E, 256), 256, 0, h->stream>>>(3 * (int64_t)h->E,
@@ -217,26 +270,43 @@ mgpbd_status mf_prepare(Handle *h) {
   return MGPBD_OK;
 }
 
-template <class T>
-static mgpbd_status mf_vertex(Handle *h, const T *ginc, const T *w, const T *x, T *u, int G = 0,
-                              bool check_done = true) {
-  if (G == 0) G = sizeof(T) == 8 ? h->mf_g64 : h->mf_g32;
-  const PcgScalars *sc = check_done ? h->sc : nullptr;
-  int64_t groups = (int64_t)h->N;
-  int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((groups * G + 255) / 256,
-                                                            64 * (int64_t)num_sms()));
-  switch (G) {
-    case 4:
-      k_mf_vertex<4, T><<<blocks, 256, 0, h->stream>>>(h->N, h->vptr, h->vrow, ginc, w, x, u, sc);
-      break;
-    case 16:
-      k_mf_vertex<16, T><<<blocks, 256, 0, h->stream>>>(h->N, h->vptr, h->vrow, ginc, w, x, u, sc);
-      break;
-    default:
-      k_mf_vertex<8, T><<<blocks, 256, 0, h->stream>>>(h->N, h->vptr, h->vrow, ginc, w, x, u, sc);
-      break;
+static int mf_vertex_blocks(const Handle *h, int G) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)h->N * G + 255) / 256,
+                                                      64 * (int64_t)num_sms()));
+}
+
+#define MF_G_DISPATCH(G, launch) \
+  switch (G) {                   \
+    case 4: {                    \
+      constexpr int GG = 4;      \
+      launch;                    \
+    } break;                     \
+    case 16: {                   \
+      constexpr int GG = 16;     \
+      launch;                    \
+    } break;                     \
+    default: {                   \
+      constexpr int GG = 8;      \
+      launch;                    \
+    } break;                     \
   }
-  MG_LAUNCH("k_mf_vertex");
+
+// u = W J^T x (FP64: u64; FP32: u32); G = 0 takes the tuned lanes per vertex
+static mgpbd_status mf_vertex(Handle *h, const double *x, int G = 0, bool check_done = true) {
+  if (G == 0) G = h->mf_g64;
+  const PcgScalars *sc = check_done ? h->sc : nullptr;
+  MF_G_DISPATCH(G, (k_mf_vertex64<GG><<<mf_vertex_blocks(h, GG), 256, 0, h->stream>>>(
+                       h->N, h->vptr, h->vrow, h->ginc64, h->w, x, h->u64, sc)));
+  MG_LAUNCH("k_mf_vertex64");
+  return MGPBD_OK;
+}
+
+static mgpbd_status mf_vertex(Handle *h, const float *x, int G = 0, bool check_done = true) {
+  if (G == 0) G = h->mf_g32;
+  const PcgScalars *sc = check_done ? h->sc : nullptr;
+  MF_G_DISPATCH(G, (k_mf_vertex32<GG><<<mf_vertex_blocks(h, GG), 256, 0, h->stream>>>(
+                       h->N, h->vptr, h->ginc4, h->w32, x, h->u32, sc)));
+  MG_LAUNCH("k_mf_vertex32");
   return MGPBD_OK;
 }
 
@@ -244,13 +314,13 @@ static mgpbd_status mf_vertex(Handle *h, const T *ginc, const T *w, const T *x, 
 // the solve uses and keeps the fastest (params.autotune).
 mgpbd_status mf_autotune(Handle *h) {
   if (h->m == 0 || !h->vslot) return MGPBD_OK;
-  auto pick = [&](auto *ginc, auto *w, auto *x, auto *u, int *out) -> mgpbd_status {
+  auto pick = [&](auto *x, int *out) -> mgpbd_status {
     const int cands[3] = {4, 8, 16};
     float best = 1e30f;
     for (int c = 0; c < 3; ++c) {
       for (int rep = 0; rep < 3; ++rep) {
         MG_CUDA(cudaEventRecord(h->ev0, h->stream));
-        MG_TRY(mf_vertex(h, ginc, w, x, u, cands[c], false));
+        MG_TRY(mf_vertex(h, x, cands[c], false));
         MG_CUDA(cudaEventRecord(h->ev1, h->stream));
         MG_CUDA(cudaEventSynchronize(h->ev1));
         float ms = 0.f;
@@ -263,17 +333,14 @@ mgpbd_status mf_autotune(Handle *h) {
     }
     return MGPBD_OK;
   };
-  MG_TRY(pick((const double *)h->ginc64, (const double *)h->w, (const double *)h->pr, h->u64,
-              &h->mf_g64));
-  if (h->p.precision == MGPBD_MIXED)
-    MG_TRY(pick((const float *)h->ginc32, (const float *)h->w32, (const float *)h->lev[0].b,
-                h->u32, &h->mf_g32));
+  MG_TRY(pick((const double *)h->pr, &h->mf_g64));
+  if (h->p.precision == MGPBD_MIXED) MG_TRY(pick((const float *)h->lev[0].b, &h->mf_g32));
   return MGPBD_OK;
 }
 
 // A.p in FP64 with p.Ap folded into the PCG scalars
 mgpbd_status mf_apply_pq(Handle *h, const double *p, double *q, const DotCtx &c) {
-  MG_TRY(mf_vertex<double>(h, h->ginc64, h->w, p, h->u64));
+  MG_TRY(mf_vertex(h, p));
   k_mf_row<double, MF_APPLY_DOT><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
       h->E, h->m, h->edge, h->tet, h->gd, h->gt, h->u64, h->alpha_t, p, nullptr, nullptr, 0.0, q,
       c);
@@ -289,7 +356,7 @@ mgpbd_status mf_level0(Handle *h, int mode, const T *x, const T *b, const T *din
 template <>
 mgpbd_status mf_level0<float>(Handle *h, int mode, const float *x, const float *b,
                               const float *dinv, float omega, float *out) {
-  MG_TRY(mf_vertex<float>(h, h->ginc32, h->w32, x, h->u32));
+  MG_TRY(mf_vertex(h, x));
   DotCtx c{};
   c.sc = h->sc;
   if (mode == MF_SWEEP)
@@ -308,7 +375,7 @@ mgpbd_status mf_level0<float>(Handle *h, int mode, const float *x, const float *
 template <>
 mgpbd_status mf_level0<double>(Handle *h, int mode, const double *x, const double *b,
                                const double *dinv, double omega, double *out) {
-  MG_TRY(mf_vertex<double>(h, h->ginc64, h->w, x, h->u64));
+  MG_TRY(mf_vertex(h, x));
   DotCtx c{};
   c.sc = h->sc;
   if (mode == MF_SWEEP)
@@ -328,8 +395,7 @@ template <class T>
 mgpbd_status mf_level0_final(Handle *h, const T *x, const T *b, const T *dinv, T omega,
                              const TopOut &o) {
   const bool dbl = sizeof(T) == 8;
-  MG_TRY(mf_vertex<T>(h, dbl ? (const T *)h->ginc64 : (const T *)h->ginc32,
-                      dbl ? (const T *)h->w : (const T *)h->w32, x, dbl ? (T *)h->u64 : (T *)h->u32));
+  MG_TRY(mf_vertex(h, x));
   const T *gd = dbl ? (const T *)h->gd : (const T *)h->gd32;
   const T *gt = dbl ? (const T *)h->gt : (const T *)h->gt32;
   const T *u = dbl ? (const T *)h->u64 : (const T *)h->u32;

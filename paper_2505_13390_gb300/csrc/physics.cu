@@ -254,7 +254,7 @@ __global__ void k_assemble(int m, int E, const int32_t *edge, const int32_t *tet
         acc = fma(wi[si], gdot(gi[si], gj), acc);
       }
       val[k] = acc;
-      if (val32) val32[k] = (float)acc;
+      if (val32) val32[k] = f64_to_f32(acc);
     }
     if (lane == 0) {
       double acc = 0.0;
@@ -263,8 +263,8 @@ __global__ void k_assemble(int m, int E, const int32_t *edge, const int32_t *tet
       val[e] = d;
       dinv[i] = 1.0 / d;
       if (val32) {
-        val32[e] = (float)d;
-        dinv32[i] = (float)(1.0 / d);
+        val32[e] = f64_to_f32(d);
+        dinv32[i] = f64_to_f32(1.0 / d);
       }
     }
   }

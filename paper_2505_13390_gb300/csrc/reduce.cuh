@@ -167,13 +167,25 @@ __device__ __forceinline__ int group_sum3_component(int g) {
   return 2 * ((g & (G / 2)) != 0) + ((g & (G / 4)) != 0);
 }
 
-// partial row dot of lane g of a G-lane group (no shuffles: callers reduce)
+// partial row dot of lane g of a G-lane group (no shuffles: callers reduce).
+// Four entries per trip are loaded before any is used, so a lane has four
+// gathers in flight; the sum order is the plain lane-strided order.
 template <int G, class VT, class AT, class XT>
 __device__ __forceinline__ AT row_dot(const int64_t *ptr, const int32_t *col, const VT *val,
                                       const XT *x, int i, int g) {
   AT acc = 0;
-  int64_t s0 = ptr[i], e = ptr[i + 1];
-  for (int64_t k = s0 + g; k < e; k += G) acc = fma((AT)val[k], (AT)x[col[k]], acc);
+  int64_t k = ptr[i] + g;
+  const int64_t e = ptr[i + 1];
+  for (; k + 3 * G < e; k += 4 * G) {
+    const int32_t c0 = col[k], c1 = col[k + G], c2 = col[k + 2 * G], c3 = col[k + 3 * G];
+    const VT v0 = val[k], v1 = val[k + G], v2 = val[k + 2 * G], v3 = val[k + 3 * G];
+    const XT x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+    acc = fma((AT)v0, (AT)x0, acc);
+    acc = fma((AT)v1, (AT)x1, acc);
+    acc = fma((AT)v2, (AT)x2, acc);
+    acc = fma((AT)v3, (AT)x3, acc);
+  }
+  for (; k < e; k += G) acc = fma((AT)val[k], (AT)x[col[k]], acc);
   return acc;
 }
 

@@ -57,7 +57,7 @@ static size_t estimate_bytes(const Instance &in) {
   for (int64_t j = 0; j < 2 * (int64_t)E; ++j) nnz += (double)deg[in.dist[j]];
   for (int64_t j = 0; j < 4 * (int64_t)T; ++j) nnz += (double)deg[in.tet[j]];
   double m = (double)E + T, ninc = 2.0 * E + 4.0 * T;
-  double b = nnz * (4 + 8 + 4 + 2 + 1) + m * 400.0 + N * 200.0 + ninc * 40.0 + (2 << 20);
+  double b = nnz * (4 + 8 + 4 + 2 + 1) + m * 400.0 + N * 200.0 + ninc * 48.0 + (2 << 20);
   return (size_t)b;
 }
 

@@ -521,14 +521,14 @@ __global__ void k_level_aux(int n, const int64_t *ptr, const double *val, double
     double d = val[ptr[i + 1] - 1];
     double r = 1.0 / d;
     dinv[i] = r;
-    if (dinv32) dinv32[i] = (float)r;
+    if (dinv32) dinv32[i] = f64_to_f32(r);
   }
 }
 
 __global__ void k_to_f32(int64_t n, const double *a, float *b) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
-    b[k] = (float)a[k];
+    b[k] = f64_to_f32(a[k]);
 }
 
 // ---------------------------------------------------------------------------

@@ -25,7 +25,11 @@
 
 namespace mg {
 
-static int dot_grid() { return std::min(4096, 2 * num_sms()); }
+// blocks of a dot-product kernel over n entries: about 4 entries per thread,
+// at least two blocks per SM, at most the 4096 partials the handle holds
+static int dot_grid(int64_t n) {
+  return (int)std::min<int64_t>(4096, std::max<int64_t>(2 * num_sms(), (n + 1023) / 1024));
+}
 
 static DotCtx make_ctx(Handle *h, int mode, double *out = nullptr) {
   DotCtx c;
@@ -54,23 +58,70 @@ __global__ void k_dot(int64_t n, const double *x, const double *y, DotCtx c, int
 // x += alpha p; r -= alpha q; then r.r (convergence test).  The start of the
 // next V-cycle is folded in: bl = r in the V-cycle's precision (MGPBD_MIXED)
 // and, with the Jacobi smoother, its first sweep from zero x0 = omega D^-1 r.
+// In mixed precision each thread sums the squares of its FP32 copies of r in
+// FP32 (the stopping test needs a few digits, and every FP64 operation is
+// scarce); the sum over threads stays FP64.  Each thread takes two adjacent
+// entries per trip with 16-byte loads (the vectors are 256-byte aligned).
+template <class T>
+struct Pair;
+template <>
+struct Pair<float> {
+  using V = float2;
+};
+template <>
+struct Pair<double> {
+  using V = double2;
+};
+
+template <class T>
+__device__ __forceinline__ T xr_entry(double al, double &xi, double &ri, double pi, double qi,
+                                      T di, T om, T *bi_out, T *x0i) {
+  xi = fma(al, pi, xi);
+  ri = fma(-al, qi, ri);
+  const T bi = narrow<T>(ri);
+  *bi_out = bi;
+  *x0i = om * (bi * di);
+  return bi;
+}
+
 template <class T>
 __global__ void k_xr_update(int64_t n, double *x, double *r, const double *p, const double *q,
                             DotCtx c, T *bl, const T *dinv, T om, T *x0) {
+  using V = typename Pair<T>::V;
   if (is_done(c.sc)) return;
   const double al = c.sc->alpha;
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = fma(al, p[i], x[i]);
-    double ri = fma(-al, q[i], r[i]);
-    r[i] = ri;
-    acc = fma(ri, ri, acc);
-    T bi = (T)ri;
-    if (bl) bl[i] = bi;
-    if (x0) x0[i] = om * (bi * dinv[i]);
+  T acc = 0;
+  const int64_t n2 = n / 2;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n2;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double2 xv = reinterpret_cast<const double2 *>(x)[k];
+    double2 rv = reinterpret_cast<const double2 *>(r)[k];
+    const double2 pv = reinterpret_cast<const double2 *>(p)[k];
+    const double2 qv = reinterpret_cast<const double2 *>(q)[k];
+    V dv = {};
+    if (x0) dv = reinterpret_cast<const V *>(dinv)[k];
+    V bv, xv0;
+    const T b0 = xr_entry<T>(al, xv.x, rv.x, pv.x, qv.x, dv.x, om, &bv.x, &xv0.x);
+    const T b1 = xr_entry<T>(al, xv.y, rv.y, pv.y, qv.y, dv.y, om, &bv.y, &xv0.y);
+    acc = fma(b0, b0, acc);
+    acc = fma(b1, b1, acc);
+    reinterpret_cast<double2 *>(x)[k] = xv;
+    reinterpret_cast<double2 *>(r)[k] = rv;
+    if (bl) reinterpret_cast<V *>(bl)[k] = bv;
+    if (x0) reinterpret_cast<V *>(x0)[k] = xv0;
   }
-  block_dot_finish(acc, c);
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t i = n - 1;
+    double xi = x[i], ri = r[i];
+    T bi, x0i;
+    const T b0 = xr_entry<T>(al, xi, ri, p[i], q[i], x0 ? dinv[i] : (T)0, om, &bi, &x0i);
+    acc = fma(b0, b0, acc);
+    x[i] = xi;
+    r[i] = ri;
+    if (bl) bl[i] = bi;
+    if (x0) x0[i] = x0i;
+  }
+  block_dot_finish(widen(acc), c);
 }
 
 // the same start of a V-cycle on its own: bl = r in the V-cycle's precision,
@@ -81,19 +132,28 @@ __global__ void k_top_prep(int64_t n, const double *r, T *bl, const T *dinv, T o
   if (sc && is_done(sc)) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    T bi = (T)r[i];
+    T bi = narrow<T>(r[i]);
     if (bl) bl[i] = bi;
     if (x0) x0[i] = om * (bi * dinv[i]);
   }
 }
 
-// p = z + beta p
+// p = z + beta p, two entries per thread (16-byte loads; p and z are
+// 256-byte aligned)
 __global__ void k_p_update(int64_t n, double *p, const double *z, const PcgScalars *sc) {
   if (is_done(sc)) return;
   const double be = sc->beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = fma(be, p[i], z[i]);
+  const int64_t n2 = n / 2;
+  double2 *p2 = reinterpret_cast<double2 *>(p);
+  const double2 *z2 = reinterpret_cast<const double2 *>(z);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n2;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double2 pv = p2[k], zv = z2[k];
+    pv.x = fma(be, pv.x, zv.x);
+    pv.y = fma(be, pv.y, zv.y);
+    p2[k] = pv;
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) p[n - 1] = fma(be, p[n - 1], z[n - 1]);
 }
 
 __global__ void k_pcg_init(PcgScalars *sc) {
@@ -103,12 +163,21 @@ __global__ void k_pcg_init(PcgScalars *sc) {
   sc->rz = sc->pq = sc->rr = sc->alpha = sc->beta = sc->tr2 = 0.0;
 }
 
+template <class D>
+__device__ __forceinline__ D convert_to(float v);
+template <>
+__device__ __forceinline__ float convert_to<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ double convert_to<double>(float v) { return f32_to_f64(v); }
+template <class D>
+__device__ __forceinline__ D convert_to(double v) { return narrow<D>(v); }
+
 template <class S, class D>
 __global__ void k_convert(int64_t n, const S *a, D *b, const PcgScalars *sc) {
   if (sc && is_done(sc)) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (D)a[i];
+    b[i] = convert_to<D>(a[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -254,14 +323,35 @@ __global__ void k_restrict(int na, const int64_t *mptr, const int32_t *mrow, con
   }
 }
 
-// x_i += P_i x_c[agg_i] (rows left alone have no aggregate)
+// x_i += P_i x_c[agg_i] (rows left alone have no aggregate); each thread
+// takes four rows a block-width apart so that its loads are in flight together
+constexpr int kProlongRows = 4;
 template <class T>
 __global__ void k_prolong(int n, const int32_t *agg, const T *P, const T *xc, T *x,
                           const PcgScalars *sc) {
   if (is_done(sc)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int a = agg[i];
-    if (a >= 0) x[i] = fma(P[i], xc[a], x[i]);  // left-alone rows: P_i = 0
+  const int64_t tile = (int64_t)blockDim.x * kProlongRows;
+  for (int64_t base = blockIdx.x * tile + threadIdx.x; base < n; base += gridDim.x * tile) {
+    int a[kProlongRows];
+    T p[kProlongRows], xv[kProlongRows];
+#pragma unroll
+    for (int k = 0; k < kProlongRows; ++k) {
+      const int64_t i = base + k * (int64_t)blockDim.x;
+      a[k] = i < n ? agg[i] : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kProlongRows; ++k) {
+      const int64_t i = base + k * (int64_t)blockDim.x;
+      if (a[k] >= 0) {  // left-alone rows: P_i = 0
+        p[k] = P[i];
+        xv[k] = x[i];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kProlongRows; ++k) {
+      const int64_t i = base + k * (int64_t)blockDim.x;
+      if (a[k] >= 0) x[i] = fma(p[k], xc[a[k]], xv[k]);
+    }
   }
 }
 
@@ -274,9 +364,9 @@ __global__ void k_coarse_apply(int n, const double *inv, const T *b, T *x, const
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = w; i < n; i += nw) {
     double acc = 0.0;
-    for (int j = lane; j < n; j += 32) acc = fma(inv[i * (int64_t)n + j], (double)b[j], acc);
+    for (int j = lane; j < n; j += 32) acc = fma(inv[i * (int64_t)n + j], widen(b[j]), acc);
     acc = warp_sum(acc);
-    if (lane == 0) x[i] = (T)acc;
+    if (lane == 0) x[i] = narrow<T>(acc);
   }
 }
 
@@ -540,8 +630,8 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in, bool x0_ready 
       L.n_agg, L.mptr, L.mrow, Ps<T>(L), r, (T *)Lc.b, sc);
   MG_LAUNCH("k_restrict");
   MG_TRY(vcycle_level<T>(h, l + 1, (const T *)Lc.b));
-  k_prolong<T><<<blocks_for(n, 256), 256, 0, h->stream>>>(n, L.agg, Ps<T>(L), (const T *)Lc.x, x,
-                                                          sc);
+  k_prolong<T><<<blocks_for((n + kProlongRows - 1) / kProlongRows, 256), 256, 0, h->stream>>>(
+      n, L.agg, Ps<T>(L), (const T *)Lc.x, x, sc);
   MG_LAUNCH("k_prolong");
   if (gs) MG_TRY(gs_sweeps(true));
   if (cheb) MG_TRY(cheb_smooth(false));
@@ -573,7 +663,7 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in, bool x0_ready 
 static mgpbd_status launch_dot(Handle *h, const double *x, const double *y, int64_t n, int mode,
                                int check_done, double *out = nullptr) {
   DotCtx c = make_ctx(h, mode, out);
-  k_dot<<<dot_grid(), kDotThreads, 0, h->stream>>>(n, x, y, c, check_done);
+  k_dot<<<dot_grid(n), kDotThreads, 0, h->stream>>>(n, x, y, c, check_done);
   MG_LAUNCH("k_dot");
   return MGPBD_OK;
 }
@@ -659,16 +749,16 @@ static mgpbd_status pcg_iteration(Handle *h, double *x) {
   // the update also starts the V-cycle (right-hand side, first Jacobi sweep)
   const bool jac = top_jacobi(h);
   if (h->p.precision == MGPBD_MIXED)
-    k_xr_update<float><<<dot_grid(), kDotThreads, 0, h->stream>>>(
+    k_xr_update<float><<<dot_grid(m), kDotThreads, 0, h->stream>>>(
         m, x, r, p, q, make_ctx(h, DOT_RR), (float *)L.b, L.dinv32, (float)L.omega,
         jac ? (float *)L.x : nullptr);
   else
-    k_xr_update<double><<<dot_grid(), kDotThreads, 0, h->stream>>>(
+    k_xr_update<double><<<dot_grid(m), kDotThreads, 0, h->stream>>>(
         m, x, r, p, q, make_ctx(h, DOT_RR), nullptr, L.dinv, L.omega,
         jac ? (double *)L.x : nullptr);
   MG_LAUNCH("k_xr_update");
   MG_TRY(vcycle_top(h, r, z, true, DOT_RZ));
-  k_p_update<<<blocks_for(m, 256), 256, 0, h->stream>>>(m, p, z, h->sc);
+  k_p_update<<<blocks_for(std::max(1, m / 2), 256), 256, 0, h->stream>>>(m, p, z, h->sc);
   MG_LAUNCH("k_p_update");
   return MGPBD_OK;
 }
@@ -832,6 +922,36 @@ mgpbd_status autotune_levels(Handle *h) {
   if (h->p.level0_op == 1) MG_TRY(mf_autotune(h));
   return MGPBD_OK;
 }
+
+// ---------------------------------------------------------------------------
+// the conversions of the mixed-precision path on caller vectors
+// ---------------------------------------------------------------------------
+__global__ void k_convert_pair(int64_t n, const double *a64, float *b32, const float *a32,
+                              double *b64) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (a64) b32[i] = f64_to_f32(a64[i]);
+    if (a32) b64[i] = f32_to_f64(a32[i]);
+  }
+}
+
+}  // namespace mg
+
+extern "C" mgpbd_status mgpbd_convert(const double *d_in64, float *d_out32, const float *d_in32,
+                                      double *d_out64, int64_t n, void *stream) {
+  using namespace mg;
+  if (n < 0 || (!d_in64) != (!d_out32) || (!d_in32) != (!d_out64)) {
+    set_error("mgpbd_convert: n < 0 or an input without its output");
+    return MGPBD_E_INVALID;
+  }
+  if (n == 0 || (!d_in64 && !d_in32)) return MGPBD_OK;
+  k_convert_pair<<<(int)std::min<int64_t>((n + 255) / 256, 65535), 256, 0,
+                   (cudaStream_t)stream>>>(n, d_in64, d_out32, d_in32, d_out64);
+  MG_LAUNCH("k_convert_pair");
+  return MGPBD_OK;
+}
+
+namespace mg {
 
 // ---------------------------------------------------------------------------
 // XPBD's local step (eq. 4): dl_j = b_j / A_jj for every constraint at once

@@ -122,6 +122,7 @@ SIGNATURES = {
                                 C.POINTER(C.c_double)]),
     "mgpbd_launch_count": (C.c_ulonglong, []),
     "mgpbd_true_residual_noalloc": (_i, [_vp, _vp, _vp, _vp]),
+    "mgpbd_convert": (_i, [_vp, _vp, _vp, _vp, _i64, _vp]),
     "mgpbd_batch_create": (_i, [C.POINTER(BatchConfig), C.POINTER(_vp)]),
     "mgpbd_batch_add_instance": (_i, [_vp, C.POINTER(MeshDesc), C.POINTER(Params), _vp, _vp,
                                       C.POINTER(_i)]),
@@ -152,6 +153,18 @@ def load(path: str = LIB_PATH):
 
 def launch_count() -> int:
     return int(load().mgpbd_launch_count())
+
+
+def convert(in64=None, out32=None, in32=None, out64=None, stream=None) -> None:
+    """The mixed-precision path's FP64 -> FP32 (round to nearest even) and
+    exact FP32 -> FP64 conversions on device tensors (mgpbd_convert)."""
+    n = (in64 if in64 is not None else in32).numel()
+    for a in (in64, out32, in32, out64):
+        if a is not None and a.numel() != n:
+            raise ValueError("all vectors must have the same length")
+    _check(load().mgpbd_convert(_ptr(in64), _ptr(out32), _ptr(in32), _ptr(out64), n,
+                                 stream.cuda_stream if stream is not None else None),
+           "mgpbd_convert")
 
 
 class MgpbdError(RuntimeError):
