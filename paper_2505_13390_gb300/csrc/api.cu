@@ -6,7 +6,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 
 #include "common.cuh"
 
@@ -106,6 +108,23 @@ int num_sms() {
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     if (n <= 0) n = 1;
   }
+  return n;
+}
+
+int wave_blocks(const void *kernel, int threads) {
+  static std::mutex mu;
+  static std::unordered_map<const void *, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(kernel);
+  if (it != cache.end()) return it->second;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+      per_sm <= 0) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const int n = per_sm * num_sms();
+  cache.emplace(kernel, n);
   return n;
 }
 

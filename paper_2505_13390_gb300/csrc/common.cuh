@@ -194,6 +194,10 @@ mgpbd_status prof_harvest(Handle *h, int iters);
 
 // grid sizing
 int num_sms();
+// blocks of `kernel` (with `threads` per block) that fit on the GPU at once:
+// kernels that end in a last-block reduction run as one such wave, so that
+// each block's serialised tail (fence, counter atomic) is paid once
+int wave_blocks(const void *kernel, int threads);
 inline int blocks_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   return (int)(b < 1 ? 1 : (b > 1048576 ? 1048576 : b));
@@ -239,6 +243,7 @@ mgpbd_status vcycle_apply(Handle *h, const double *d_r, double *d_z);
 mgpbd_status dot_dd(Handle *h, const double *x, const double *y, int64_t n, double *d_out);
 mgpbd_status xpbd_step(Handle *h, mgpbd_solve_info *info);
 mgpbd_status power_method(Handle *h, int l);
+mgpbd_status evict_l2(Handle *h);  // autotuner: start timings from an evicted L2
 
 // ---------------------------------------------------------------------------
 // device helpers

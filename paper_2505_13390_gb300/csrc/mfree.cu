@@ -318,7 +318,8 @@ mgpbd_status mf_autotune(Handle *h) {
     const int cands[3] = {4, 8, 16};
     float best = 1e30f;
     for (int c = 0; c < 3; ++c) {
-      for (int rep = 0; rep < 3; ++rep) {
+      for (int rep = 0; rep < 5; ++rep) {
+        MG_TRY(evict_l2(h));
         MG_CUDA(cudaEventRecord(h->ev0, h->stream));
         MG_TRY(mf_vertex(h, x, cands[c], false));
         MG_CUDA(cudaEventRecord(h->ev1, h->stream));
@@ -341,7 +342,9 @@ mgpbd_status mf_autotune(Handle *h) {
 // A.p in FP64 with p.Ap folded into the PCG scalars
 mgpbd_status mf_apply_pq(Handle *h, const double *p, double *q, const DotCtx &c) {
   MG_TRY(mf_vertex(h, p));
-  k_mf_row<double, MF_APPLY_DOT><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
+  const int grid = std::min(mf_grid(h->m, 256),
+                            wave_blocks((const void *)k_mf_row<double, MF_APPLY_DOT>, 256));
+  k_mf_row<double, MF_APPLY_DOT><<<grid, 256, 0, h->stream>>>(
       h->E, h->m, h->edge, h->tet, h->gd, h->gt, h->u64, h->alpha_t, p, nullptr, nullptr, 0.0, q,
       c);
   MG_LAUNCH("k_mf_row(A.p)");
@@ -403,7 +406,10 @@ mgpbd_status mf_level0_final(Handle *h, const T *x, const T *b, const T *dinv, T
   DotCtx c = o.c;
   c.sc = h->sc;
   if (o.dot)
-    k_mf_row<T, MF_SWEEP_ZDOT><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
+    k_mf_row<T, MF_SWEEP_ZDOT><<<std::min(mf_grid(h->m, 256),
+                                          wave_blocks((const void *)k_mf_row<T, MF_SWEEP_ZDOT>,
+                                                      256)),
+                                 256, 0, h->stream>>>(
         h->E, h->m, h->edge, h->tet, gd, gt, u, at, x, b, dinv, omega, nullptr, c, o.z, o.r);
   else
     k_mf_row<T, MF_SWEEP_Z><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
