@@ -40,14 +40,14 @@ FULL_NNZ = 376_541_249  # nonzeros of A for block100 (checked at run time)
 FULL_PCG_ITERS = 7300
 # DRAM bytes (read + write) of one level-0 FP32 smoother sweep per nonzero of
 # A, from the ncu capture in profiles/k_jacobi_level0_block40x33x40.md
-# (k_jacobi<8, float>, 494.06 MB for 59,625,809 nonzeros); the sweep's
+# (k_jacobi<16, float>, 494.52 MB for 59,625,809 nonzeros); the sweep's
 # traffic grows in proportion to nnz, so it scales to a full launch
-SWEEP_TRAFFIC_PER_NNZ = 494.058240e6 / 59_625_809
-# DRAM bytes of one matrix-free level-0 FP32 sweep (k_mf_vertex<float> 30.51 MB
+SWEEP_TRAFFIC_PER_NNZ = (489.342720e6 + 5.179904e6) / 59_625_809
+# DRAM bytes of one matrix-free level-0 FP32 sweep (k_mf_vertex32<8> 30.51 MB
 # + k_mf_row<float,0> 33.68 MB) per constraint row, from the ncu captures in
 # profiles/k_mf_sweep_level0_block40x33x40.md (593,633 rows); the passes
 # stream per-row and per-incidence arrays, so traffic scales with the rows
-MF_SWEEP_TRAFFIC_PER_ROW = (30.514176e6 + 33.680384e6) / 593_633
+MF_SWEEP_TRAFFIC_PER_ROW = (30.513152e6 + 33.678592e6) / 593_633
 SAMPLE = (4, 33, 4)     # oracle sample: cells along x, y (vertical), z
 SAMPLE_PCG = 500        # PCG iterations per sampled global iteration (cost is linear in them)
 
@@ -190,10 +190,12 @@ class Runner:
         self.k = 0
         self.g.begin_frame()
         self.pcg = []
+        self.true_res = []
 
     def step(self):
         d = self.g.iterate()
         self.pcg.append(d["pcg_iters"])
+        self.true_res.append(d["true_rel_res"])
         self.k += 1
         if self.k % self.max_iter == 0:
             self.g.end_frame()
@@ -257,7 +259,7 @@ def measure(mesh, params, steps, warmup, ws, profile=True):
         g.profile(False)
     st = g.stats()
     out = dict(ms=ms, launches=launches, clocks=ck, prof=prof, stats=st, create_s=create_s,
-               pcg=run.pcg[pcg0:], solver=g, runner=run)
+               pcg=run.pcg[pcg0:], true_res=run.true_res[pcg0:], solver=g, runner=run)
     return out
 
 
@@ -404,7 +406,8 @@ def run_ours(args, ws, rank):
         assembled = {"value": ws * args.assembled_steps / (msa / 1e3),
                      "ms_per_step": msa / args.assembled_steps,
                      "steps": args.assembled_steps, "warmup": args.assembled_warmup,
-                     "pcg_iters": ra["pcg"], "clocks": ra["clocks"],
+                     "pcg_iters": ra["pcg"], "true_rel_res": ra["true_res"],
+                     "clocks": ra["clocks"],
                      "roofline": {"bound": "hbm",
                                   "kernel": "k_jacobi (level-0 CSR weighted-Jacobi sweep, FP32)",
                                   "achieved": aa, "peak": hbm_peak(), "unit": "GB/s",
@@ -424,7 +427,8 @@ def run_ours(args, ws, rank):
         fp64 = {"value": ws * args.fp64_steps / (ms64 / 1e3),
                 "ms_per_step": ms64 / args.fp64_steps,
                 "steps": args.fp64_steps, "warmup": args.fp64_warmup,
-                "pcg_iters": r64["pcg"], "clocks": r64["clocks"],
+                "pcg_iters": r64["pcg"], "true_rel_res": r64["true_res"],
+                "clocks": r64["clocks"],
                 "smoother_sweep_gbs": a64, "smoother_sweep_frac": a64 / hbm}
         r64["solver"].close()
     serve = None
@@ -456,6 +460,9 @@ def run_ours(args, ws, rank):
                    "l2": "inputs larger than L2 (A is 3.1 GB in FP32, 4.6 GB in FP64)",
                    "levels": [(l["n"], l["nnz"]) for l in levels]},
         "pcg_iters": res["pcg"],
+        # FP64 |b - A dlambda| / |b| of each timed solve: the error statement
+        # of the mixed-precision result (the oracle cannot run this size)
+        "true_rel_res": res["true_res"],
         "roofline": {"bound": "hbm",
                      "kernel": ("level-0 matrix-free weighted-Jacobi sweep, FP32 "
                                 "(k_mf_vertex + k_mf_row)") if args.level0_op == 1 else

@@ -272,6 +272,44 @@ def test_backtracking_parity(name):
         assert np.abs(xg - xo).max() <= 1e-9 * scale
 
 
+@pytest.mark.parametrize("op", [0, 1])
+@pytest.mark.parametrize("name,rtol", [("cloth32", 1e-10), ("hex3s", 1e-10), ("block6", 1e-6)])
+def test_mixed_precision_error_vs_oracle(name, rtol, op):
+    """The error of the mixed-precision path (FP32 V-cycle, FP64 recurrences
+    and A.p) against the FP64 oracle over three global iterations, next to the
+    FP64 GPU path's own: the preconditioner's precision changes how fast PCG
+    converges, not what it converges to, so both differ from the oracle by
+    about the PCG tolerance's share.  The figures are printed (pytest -s)."""
+    mesh, p = CASES[name]()
+    p = dict(p, pcg_rtol=rtol, pcg_maxiter=5000, level0_op=op)
+    o = Oracle(mesh, p)
+    runs = {"oracle": o, "fp64": solver(mesh, dict(p, precision=0)),
+            "mixed": solver(mesh, dict(p, precision=1))}
+    scale = np.abs(mesh.rest_pos).max() + 1e-3
+    for r in runs.values():
+        r.begin_frame()
+    err = {"fp64": 0.0, "mixed": 0.0}
+    tres = {"fp64": [], "mixed": []}
+    for it in range(3):
+        do = o.iterate()
+        assert do["ret"] == 0
+        xo, _ = o.get_state()
+        for k in ("fp64", "mixed"):
+            d = runs[k].iterate()
+            assert d["ret"] == 0
+            tres[k].append(d["true_rel_res"])
+            xg, _ = runs[k].get_state()
+            err[k] = max(err[k], float(np.abs(xg - xo).max() / scale))
+    print(f"\n{name} op={op} rtol={rtol:g}: max |x - x_oracle| / |x|_max  fp64 {err['fp64']:.2e}"
+          f"  mixed {err['mixed']:.2e}; true relative residuals fp64 "
+          + " ".join(f"{t:.1e}" for t in tres["fp64"]) + "  mixed "
+          + " ".join(f"{t:.1e}" for t in tres["mixed"]))
+    assert err["mixed"] <= max(10 * err["fp64"], 1e-9)
+    # on stiff systems the FP64 true residual sits above rtol (cond * eps);
+    # the mixed path's stays within a small factor of the FP64 path's
+    assert max(tres["mixed"]) <= 4 * max(max(tres["fp64"]), rtol)
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_matrix_free_block_iterations(prec):
     """A block of the benchmark recipe solved to 1e-6 with the assembled and
