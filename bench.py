@@ -75,6 +75,10 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=0.5, help="arrivals per second")
     ap.add_argument("--serve-active", type=int, default=8)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-arap", action="store_true",
+                    help="skip the ARAP-constraint leg (block100arap)")
+    ap.add_argument("--arap-steps", type=int, default=3)
+    ap.add_argument("--arap-warmup", type=int, default=3)
     ap.add_argument("--assembled-steps", type=int, default=1)
     ap.add_argument("--assembled-warmup", type=int, default=1)
     return ap.parse_args()
@@ -219,7 +223,8 @@ def measure(mesh, params, steps, warmup, ws, profile=True):
     import torch
 
     from paper_2505_13390_gb300.mgpbd import Solver, launch_count
-    stream = torch.cuda.current_stream()
+    # a stream of our own: CUDA graphs cannot capture the legacy default stream
+    stream = torch.cuda.Stream()
     t0 = time.perf_counter()
     g = Solver(mesh, params, stream=stream)
     create_s = time.perf_counter() - t0
@@ -373,7 +378,7 @@ def run_ours(args, ws, rank):
         ge.build()
     cpu = None
     mesh, params = workload(args.workload)
-    params = dict(params, precision=1, autotune=1, level0_op=args.level0_op)
+    params = dict(params, precision=1, autotune=1, level0_op=args.level0_op, use_graphs=1)
     res = measure(mesh, params, args.steps, args.warmup, ws)
     value, ms = job_rate(ws, args.steps, res["ms"])
     prof = res["prof"]
@@ -431,6 +436,25 @@ def run_ours(args, ws, rank):
                 "clocks": r64["clocks"],
                 "smoother_sweep_gbs": a64, "smoother_sweep_frac": a64 / hbm}
         r64["solver"].close()
+    arap = None
+    if not args.no_arap:
+        # the same lattice with one ARAP row per tet (Sec. 5.3) instead of
+        # distance + volume rows, same solver settings
+        amesh, ap_ = workload("block100arap")
+        ap_ = dict(ap_, autotune=1, use_graphs=1, level0_op=args.level0_op,
+                   pcg_maxiter=params["pcg_maxiter"])
+        rar = measure(amesh, ap_, args.arap_steps, args.arap_warmup, ws)
+        msr = max_over_ranks(ws, rar["ms"])
+        arap = {"workload": "block100arap: the 100x33x100 block with one ARAP row per tet "
+                            "(1,650,000 rows), mu = 1e7 Pa, alpha = 1/(mu V_tet)",
+                "value": ws * args.arap_steps / (msr / 1e3), "unit": "global_iters/s",
+                "ms_per_step": msr / args.arap_steps, "steps": args.arap_steps,
+                "warmup": args.arap_warmup, "pcg_iters": rar["pcg"],
+                "true_rel_res": rar["true_res"], "clocks": rar["clocks"],
+                "n_setups": rar["solver"].stats()["n_setups"]}
+        rar["solver"].close()
+        del rar
+        torch.cuda.empty_cache()
     serve = None
     if not args.no_serve:
         serve = serving(args)
@@ -483,6 +507,7 @@ def run_ours(args, ws, rank):
         "clocks": res["clocks"],
         "fp64": fp64,
         "assembled": assembled,
+        "arap": arap,
         "serving": serve,
         "create_s": res["create_s"],
         "stats": {k: res["stats"][k] for k in ("levels", "op_complexity", "device_bytes")},

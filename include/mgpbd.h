@@ -46,12 +46,17 @@ enum { MGPBD_FP64 = 0, MGPBD_MIXED = 1 };
 
 /* Problem definition (eq. 1-3 of the paper).  Host pointers, copied at
  * create.  Rows of the constraint system are all distance rows (in the order
- * of `dist`) followed by all volume rows (in the order of `tet`).
- *   rest_pos  [n_verts*3]  rest shape (AoS xyz), defines L0 and V0
+ * of `dist`) followed by one row per tetrahedron (in the order of `tet`).
+ *   rest_pos  [n_verts*3]  rest shape (AoS xyz), defines L0, V0 and Dm
  *   inv_mass  [n_verts]    M^-1 per vertex; 0 pins the vertex
  *   dist      [n_dist*2]   distance pairs, C = |x_a - x_b| - L0
- *   tet       [n_tet*4]    tetrahedra, C = V(x) - V0 with V = det[x1-x0,x2-x0,x3-x0]/6
- *   alpha     [n_dist+n_tet] compliance per row; alpha~ = alpha/dt^2 (eq. 2) */
+ *   tet       [n_tet*4]    tetrahedra; their rows are, by tet_kind,
+ *                          0: volume, C = V(x) - V0 with V = det[x1-x0,x2-x0,x3-x0]/6
+ *                          1: ARAP (Sec. 5.3), C = |F - R|_F^2 with F = Ds Dm^-1 the
+ *                             deformation gradient and R its polar rotation
+ *   alpha     [n_dist+n_tet] compliance per row; alpha~ = alpha/dt^2 (eq. 2)
+ *                          (Sec. 5.3 uses alpha = 1/(mu V_tet) for ARAP rows)
+ * A zero-initialised descriptor has tet_kind 0. */
 typedef struct {
   int n_verts;
   const double *rest_pos;
@@ -61,6 +66,7 @@ typedef struct {
   int n_tet;
   const int32_t *tet;
   const double *alpha;
+  int tet_kind;
 } mgpbd_mesh_desc;
 
 /* Solver parameters.  mgpbd_default_params() fills the paper's defaults:

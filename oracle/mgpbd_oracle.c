@@ -110,6 +110,8 @@ typedef struct {
 typedef struct {
   int N, E, T, m;
   double *rest, *w, *alpha, *alpha_t, *L0, *V0;
+  int tet_kind;  /* 0: volume rows; 1: ARAP rows (Sec. 5.3) */
+  double *Dminv; /* ARAP: inverse rest edge matrix per tet, row-major [T][9] */
   int32_t *edge, *tet;
   orc_params p;
   double *x, *v, *xold, *lambda;
@@ -224,6 +226,72 @@ static double tet_eval(const double *x0, const double *x1, const double *x2,
   return V - V0;
 }
 
+/* ARAP constraint (Sec. 5.3): C = |F - R|_F^2 with F = Ds Dm^-1 the
+   deformation gradient (Ds, Dm: edge matrices [x1-x0, x2-x0, x3-x0] now and
+   at rest) and R the rotation of F's polar decomposition F = R S.
+   R: Newton's iteration for the orthogonal polar factor, R <- (R + R^-T)/2
+   from R = F, a fixed ARAP_POLAR_ITERS times (quadratic convergence; the
+   singular values map to (s + 1/s)/2).  R^-T = [c1 x c2, c2 x c0, c0 x c1] /
+   det R for the columns c_k of R.  A singular F (det F = 0) has no unique
+   polar factor: the row gets C = 0 and zero gradient.
+   Gradient: dC = 2 (F - R) : dF (the term (F - R) : dR vanishes because
+   R^T (F - R) = S - I is symmetric and R^T dR is skew), so with B = Dm^-1
+   dC/dx_k = 2 (F - R) B^T e_k for k = 1..3 and dC/dx_0 = -((g1 + g2) + g3).
+   Inverse rest edge matrix: the rows of Dm^-1 are (e2 x e3, e3 x e1,
+   e1 x e2) / det Dm. */
+#define ARAP_POLAR_ITERS 20
+
+static void arap_rest(const double *x0, const double *x1, const double *x2, const double *x3,
+                      double B[9]) {
+  double e1[3], e2[3], e3[3], c[3][3];
+  for (int k = 0; k < 3; ++k) { e1[k] = x1[k] - x0[k]; e2[k] = x2[k] - x0[k]; e3[k] = x3[k] - x0[k]; }
+  cross(e2, e3, c[0]); cross(e3, e1, c[1]); cross(e1, e2, c[2]);
+  double det = fma(e1[2], c[0][2], fma(e1[1], c[0][1], e1[0] * c[0][0]));
+  for (int r = 0; r < 3; ++r)
+    for (int k = 0; k < 3; ++k) B[3 * r + k] = det != 0.0 ? c[r][k] / det : 0.0;
+}
+
+static double arap_eval(const double *x0, const double *x1, const double *x2, const double *x3,
+                        const double B[9], double g[12]) {
+  double d[3][3]; /* d[k] = x_{k+1} - x_0 (column k of Ds) */
+  for (int a = 0; a < 3; ++a) { d[0][a] = x1[a] - x0[a]; d[1][a] = x2[a] - x0[a]; d[2][a] = x3[a] - x0[a]; }
+  double F[3][3], R[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c)
+      F[a][c] = fma(d[2][a], B[6 + c], fma(d[1][a], B[3 + c], d[0][a] * B[c]));
+  /* det F = c0 . (c1 x c2) over the columns of F */
+  double col[3][3], x12[3];
+  for (int k = 0; k < 3; ++k) for (int a = 0; a < 3; ++a) col[k][a] = F[a][k];
+  cross(col[1], col[2], x12);
+  double detF = fma(col[0][2], x12[2], fma(col[0][1], x12[1], col[0][0] * x12[0]));
+  if (detF == 0.0) {
+    for (int k = 0; k < 12; ++k) g[k] = 0.0;
+    return 0.0;
+  }
+  memcpy(R, F, sizeof(R));
+  for (int it = 0; it < ARAP_POLAR_ITERS; ++it) {
+    double cc[3][3], dual[3][3];
+    for (int k = 0; k < 3; ++k) for (int a = 0; a < 3; ++a) cc[k][a] = R[a][k];
+    cross(cc[1], cc[2], dual[0]); cross(cc[2], cc[0], dual[1]); cross(cc[0], cc[1], dual[2]);
+    double det = fma(cc[0][2], dual[0][2], fma(cc[0][1], dual[0][1], cc[0][0] * dual[0][0]));
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < 3; ++k) R[a][k] = 0.5 * (R[a][k] + dual[k][a] / det);
+  }
+  double C = 0.0, D[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) {
+      D[a][c] = F[a][c] - R[a][c];
+      C = fma(D[a][c], D[a][c], C);
+    }
+  for (int k = 0; k < 3; ++k)
+    for (int a = 0; a < 3; ++a) {
+      double t = fma(D[a][2], B[3 * k + 2], fma(D[a][1], B[3 * k + 1], D[a][0] * B[3 * k]));
+      g[3 * (k + 1) + a] = 2.0 * t;
+    }
+  for (int a = 0; a < 3; ++a) g[a] = -((g[3 + a] + g[6 + a]) + g[9 + a]);
+  return C;
+}
+
 /* Alg. 1 (calculate C and grad C), eq. 3 (b = -C - alpha~ lambda) */
 static void eval_constraints(orc *o) {
   for (int j = 0; j < o->E; ++j) {
@@ -233,9 +301,11 @@ static void eval_constraints(orc *o) {
   }
   for (int t = 0; t < o->T; ++t) {
     const int32_t *tv = o->tet + 4 * (int64_t)t;
-    o->C[o->E + t] = tet_eval(o->x + 3 * (int64_t)tv[0], o->x + 3 * (int64_t)tv[1],
-                              o->x + 3 * (int64_t)tv[2], o->x + 3 * (int64_t)tv[3],
-                              o->V0[t], o->gt + 12 * (int64_t)t);
+    const double *p0 = o->x + 3 * (int64_t)tv[0], *p1 = o->x + 3 * (int64_t)tv[1];
+    const double *p2 = o->x + 3 * (int64_t)tv[2], *p3 = o->x + 3 * (int64_t)tv[3];
+    o->C[o->E + t] = o->tet_kind == 1
+                         ? arap_eval(p0, p1, p2, p3, o->Dminv + 9 * (int64_t)t, o->gt + 12 * (int64_t)t)
+                         : tet_eval(p0, p1, p2, p3, o->V0[t], o->gt + 12 * (int64_t)t);
   }
   for (int j = 0; j < o->m; ++j) {
     double t = o->alpha_t[j] * o->lambda[j];
@@ -1034,15 +1104,28 @@ int orc_iterate(orc *o, orc_solve_info *info) {
     o->last = *info;
     return info->bnorm < o->p.eps_b ? 1 : 0;
   }
+  int fresh = 0;
   if (!o->have_setup || (o->p.setup_interval > 0 && o->it_global % o->p.setup_interval == 0)) {
     st = setup(o);
     if (st) return st;
+    fresh = 1;
   } else {
     reform(o);
   }
   st = cholesky(o);
   if (st) return st;
   st = pcg(o, o->b, o->dl, info);
+  /* Reading of the lazy setup (Sec. 4.2, 4.5): P and omega are reused while
+     they still fit A.  A breakdown on a reused hierarchy (omega or P built for
+     an A that has since changed, e.g. ARAP rows leaving the rest state) sets
+     up afresh for the current A and solves once more. */
+  if (st == ORC_E_BREAKDOWN && !fresh) {
+    st = setup(o);
+    if (st) return st;
+    st = cholesky(o);
+    if (st) return st;
+    st = pcg(o, o->b, o->dl, info);
+  }
   o->it_global++;
   if (st < 0) { o->last = *info; return st; }
   update_positions(o, info);
@@ -1078,7 +1161,7 @@ void orc_vcycle(orc *o, const double *r, double *z) { vcycle(o, r, z); }
 /* ------------------------------------------------------------------------- */
 void orc_destroy(orc *o) {
   if (!o) return;
-  free(o->rest); free(o->w); free(o->alpha); free(o->alpha_t); free(o->L0); free(o->V0);
+  free(o->rest); free(o->w); free(o->alpha); free(o->alpha_t); free(o->L0); free(o->V0); free(o->Dminv);
   free(o->edge); free(o->tet); free(o->x); free(o->v); free(o->xold); free(o->lambda);
   free(o->C); free(o->b); free(o->gd); free(o->gt); free(o->dl); free(o->dx); free(o->xbak);
   csr_free(&o->A);
@@ -1090,13 +1173,14 @@ void orc_destroy(orc *o) {
 }
 
 orc *orc_create(int N, const double *rest, const double *inv_mass, int E, const int32_t *edge,
-                int T, const int32_t *tet, const double *alpha, const orc_params *p, int *status) {
+                int T, const int32_t *tet, int tet_kind, const double *alpha, const orc_params *p,
+                int *status) {
   *status = ORC_E_INVALID;
-  if (N <= 0 || E < 0 || T < 0 || !p || p->dt <= 0.0) return NULL;
+  if (N <= 0 || E < 0 || T < 0 || !p || p->dt <= 0.0 || tet_kind < 0 || tet_kind > 1) return NULL;
   for (int j = 0; j < 2 * E; ++j) if (edge[j] < 0 || edge[j] >= N) return NULL;
   for (int64_t j = 0; j < 4 * (int64_t)T; ++j) if (tet[j] < 0 || tet[j] >= N) return NULL;
   orc *o = (orc *)xcalloc(1, sizeof(orc));
-  o->N = N; o->E = E; o->T = T; o->m = E + T; o->p = *p;
+  o->N = N; o->E = E; o->T = T; o->m = E + T; o->p = *p; o->tet_kind = tet_kind;
   int m = o->m;
   o->rest = (double *)xcalloc(3 * (size_t)N, sizeof(double));
   o->w = (double *)xcalloc((size_t)N, sizeof(double));
@@ -1106,6 +1190,7 @@ orc *orc_create(int N, const double *rest, const double *inv_mass, int E, const 
   o->alpha_t = (double *)xcalloc((size_t)m, sizeof(double));
   o->L0 = (double *)xcalloc((size_t)E, sizeof(double));
   o->V0 = (double *)xcalloc((size_t)T, sizeof(double));
+  o->Dminv = (double *)xcalloc(9 * (size_t)T + 1, sizeof(double));
   o->x = (double *)xcalloc(3 * (size_t)N, sizeof(double));
   o->v = (double *)xcalloc(3 * (size_t)N, sizeof(double));
   o->xold = (double *)xcalloc(3 * (size_t)N, sizeof(double));
@@ -1138,6 +1223,8 @@ orc *orc_create(int N, const double *rest, const double *inv_mass, int E, const 
     const int32_t *tv = tet + 4 * (int64_t)t;
     o->V0[t] = tet_eval(rest + 3 * (int64_t)tv[0], rest + 3 * (int64_t)tv[1], rest + 3 * (int64_t)tv[2],
                         rest + 3 * (int64_t)tv[3], 0.0, g12);
+    arap_rest(rest + 3 * (int64_t)tv[0], rest + 3 * (int64_t)tv[1], rest + 3 * (int64_t)tv[2],
+              rest + 3 * (int64_t)tv[3], o->Dminv + 9 * (int64_t)t);
   }
   int st = build_pattern(o);
   if (st) { orc_destroy(o); *status = st; return NULL; }

@@ -60,7 +60,7 @@ def lib():
         L = C.CDLL(LIB)
         vp = C.c_void_p
         L.orc_create.restype = vp
-        L.orc_create.argtypes = [C.c_int, vp, vp, C.c_int, vp, C.c_int, vp, vp,
+        L.orc_create.argtypes = [C.c_int, vp, vp, C.c_int, vp, C.c_int, vp, C.c_int, vp,
                                  C.POINTER(Params), C.POINTER(C.c_int)]
         L.orc_destroy.argtypes = [vp]
         for name in ("orc_begin_frame", "orc_end_frame", "orc_eval_assemble"):
@@ -172,7 +172,8 @@ class Oracle:
         self._p = make_params(params)
         self.h = L.orc_create(self.N, _p(self._keep[0]), _p(self._keep[1]), self.E,
                               _p(self._keep[2]), self.T, _p(self._keep[3]),
-                              _p(self._keep[4]), C.byref(self._p), C.byref(st))
+                              int(getattr(mesh, "tet_kind", 0)), _p(self._keep[4]),
+                              C.byref(self._p), C.byref(st))
         if not self.h:
             raise RuntimeError(f"oracle create failed: {st.value}")
         self.set_state(mesh.x0, mesh.v0)

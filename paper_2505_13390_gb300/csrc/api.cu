@@ -17,24 +17,64 @@ namespace mg {
 static thread_local std::string g_err;
 unsigned long long g_launches = 0;
 
+static mgpbd_status grow_events(std::vector<cudaEvent_t> &ev, std::vector<int> &it, int pairs) {
+  if ((int)ev.size() >= 2 * pairs) return MGPBD_OK;
+  size_t old = ev.size();
+  size_t want = std::max<size_t>({(size_t)2048, 2 * old, 2 * (size_t)pairs});
+  ev.resize(want);
+  it.resize(want / 2);
+  for (size_t k = old; k < want; ++k) MG_CUDA(cudaEventCreate(&ev[k]));
+  return MGPBD_OK;
+}
+
+// events for a chunk's graph are created before capture begins
+mgpbd_status prof_reserve_graph(Handle *h, int pairs) {
+  return grow_events(h->gev, h->gev_iter, pairs);
+}
+
 mgpbd_status prof_begin(Handle *h) {
   if (!h->prof) return MGPBD_OK;
-  if (h->pev_used + 1 > (int)h->pev.size() / 2) {
-    size_t old = h->pev.size();
-    size_t want = std::max<size_t>(2048, 2 * old);
-    h->pev.resize(want);
-    h->pev_iter.resize(want / 2);
-    for (size_t k = old; k < want; ++k) MG_CUDA(cudaEventCreate(&h->pev[k]));
+  if (h->capturing) {
+    if (h->gev_used + 1 > (int)h->gev.size() / 2) {
+      set_error("profiling: event pool of the captured chunk is too small");
+      return MGPBD_E_INVALID;
+    }
+    MG_CUDA(cudaEventRecordWithFlags(h->gev[2 * h->gev_used], h->stream, cudaEventRecordExternal));
+    return MGPBD_OK;
   }
+  MG_TRY(grow_events(h->pev, h->pev_iter, h->pev_used + 1));
   MG_CUDA(cudaEventRecord(h->pev[2 * h->pev_used], h->stream));
   return MGPBD_OK;
 }
 
 mgpbd_status prof_end(Handle *h) {
   if (!h->prof) return MGPBD_OK;
+  if (h->capturing) {
+    MG_CUDA(cudaEventRecordWithFlags(h->gev[2 * h->gev_used + 1], h->stream,
+                                     cudaEventRecordExternal));
+    h->gev_iter[h->gev_used] = h->pcg_k;
+    h->gev_used++;
+    return MGPBD_OK;
+  }
   MG_CUDA(cudaEventRecord(h->pev[2 * h->pev_used + 1], h->stream));
   h->pev_iter[h->pev_used] = h->pcg_k;
   h->pev_used++;
+  return MGPBD_OK;
+}
+
+// after a replay of the chunk that starts at PCG iteration first_iter (the
+// host has synchronised and copied the scalars): the V-cycle of iteration k
+// ran unless the solve had finished before it
+mgpbd_status prof_harvest_graph(Handle *h, int first_iter) {
+  const PcgScalars &s = *h->sc_host;
+  for (int k = 0; k < h->gev_used; ++k) {
+    const int it = first_iter + h->gev_iter[k];
+    if (s.done && it > s.iters - 2) continue;
+    float ms = 0.f;
+    MG_CUDA(cudaEventElapsedTime(&ms, h->gev[2 * k], h->gev[2 * k + 1]));
+    h->prof_ms += ms;
+    h->prof_n++;
+  }
   return MGPBD_OK;
 }
 
@@ -186,6 +226,7 @@ static void destroy(Handle *h) {
   if (h->sc_host) cudaFreeHost(h->sc_host);
   if (h->flag_host) cudaFreeHost(h->flag_host);
   for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->gev) cudaEventDestroy(e);
   if (h->pcg_graph) cudaGraphExecDestroy(h->pcg_graph);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
@@ -197,7 +238,7 @@ static mgpbd_status create(const mgpbd_mesh_desc *md, const mgpbd_params *p, voi
   *out = nullptr;
   if (!md || !p || md->n_verts <= 0 || md->n_dist < 0 || md->n_tet < 0 || !md->rest_pos ||
       !md->inv_mass || (md->n_dist > 0 && !md->dist) || (md->n_tet > 0 && !md->tet) ||
-      (md->n_dist + md->n_tet > 0 && !md->alpha)) {
+      (md->n_dist + md->n_tet > 0 && !md->alpha) || md->tet_kind < 0 || md->tet_kind > 1) {
     set_error("invalid mesh descriptor");
     return MGPBD_E_INVALID;
   }
@@ -242,6 +283,7 @@ static mgpbd_status create(const mgpbd_mesh_desc *md, const mgpbd_params *p, voi
   h->E = md->n_dist;
   h->T = md->n_tet;
   h->m = h->E + h->T;
+  h->tet_kind = md->tet_kind;
   auto fail = [&](mgpbd_status s) {
     destroy(h);
     return s;
@@ -258,6 +300,7 @@ static mgpbd_status create(const mgpbd_mesh_desc *md, const mgpbd_params *p, voi
   CK(alloc_n(h->arena, &h->alpha_t, (size_t)m));
   CK(alloc_n(h->arena, &h->L0, (size_t)E));
   CK(alloc_n(h->arena, &h->V0, (size_t)T));
+  if (h->tet_kind == 1) CK(alloc_n(h->arena, &h->Dminv, 9 * (size_t)T));
   CK(alloc_n(h->arena, &h->edge, 2 * (size_t)E));
   CK(alloc_n(h->arena, &h->tet, 4 * (size_t)T));
   CK(alloc_n(h->arena, &h->x, 3 * (size_t)N));
@@ -364,6 +407,16 @@ static mgpbd_status iterate(Handle *h, mgpbd_solve_info *info) {
   MG_TRY(coarsest_factor(h));
   mgpbd_solve_info inf{};
   mgpbd_status st = pcg_solve(h, h->b, h->dl, &inf);
+  // a breakdown on a reused hierarchy (omega or P built for an A that has
+  // since changed): set up afresh for the current A and solve once more
+  if (st == MGPBD_E_BREAKDOWN && !due) {
+    MG_TRY(timed_begin(h));
+    MG_TRY(amg_setup(h));
+    MG_TRY(timed_end(h, &h->ms_setup));
+    MG_TRY(coarsest_factor(h));
+    inf = mgpbd_solve_info{};
+    st = pcg_solve(h, h->b, h->dl, &inf);
+  }
   h->it_global++;
   if (st < 0) {
     h->last = inf;

@@ -125,6 +125,8 @@ struct Handle {
   // mesh (device)
   double *rest = nullptr, *w = nullptr, *alpha_t = nullptr, *L0 = nullptr, *V0 = nullptr;
   int32_t *edge = nullptr, *tet = nullptr;
+  int tet_kind = 0;          // tet rows: 0 volume, 1 ARAP (Sec. 5.3)
+  double *Dminv = nullptr;   // ARAP: inverse rest edge matrix per tet, row-major [T][9]
   // incidence
   int64_t *vptr = nullptr;
   int32_t *vrow = nullptr;
@@ -177,6 +179,13 @@ struct Handle {
   int pcg_k = -1;                // PCG iteration being launched
   double prof_ms = 0.0;
   long long prof_n = 0;
+  // the same timing inside a captured PCG chunk: event-record nodes of the
+  // graph, read back after every replay
+  bool capturing = false;
+  std::vector<cudaEvent_t> gev;  // pairs
+  std::vector<int> gev_iter;     // iteration within the chunk of each pair
+  int gev_used = 0;
+  bool graph_prof = false;       // the captured graph records gev
   // CUDA graph of a chunk of PCG iterations, valid while `graph_gen` matches
   unsigned long long gen = 1;      // bumped whenever device pointers or setup change
   unsigned long long graph_gen = 0;
@@ -187,6 +196,8 @@ struct Handle {
 };
 
 // event pair around one launch of the profiled kernel (no-op when disabled)
+mgpbd_status prof_reserve_graph(Handle *h, int pairs);
+mgpbd_status prof_harvest_graph(Handle *h, int first_iter);
 mgpbd_status prof_begin(Handle *h);
 mgpbd_status prof_end(Handle *h);
 // sums the pairs recorded during the last solve that belong to iterations that ran

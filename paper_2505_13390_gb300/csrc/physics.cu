@@ -10,6 +10,13 @@
 //   volume    e_k = x_k - x_0, V = fma(e1z,c23z, fma(e1y,c23y, e1x*c23x))/6,
 //             g1 = (e2 x e3)/6, g2 = (e3 x e1)/6, g3 = (e1 x e2)/6,
 //             g0 = -((g1 + g2) + g3)
+//   ARAP      (Sec. 5.3) C = |F - R|_F^2, F = Ds B with B = Dm^-1 (rows of B:
+//             (e2 x e3, e3 x e1, e1 x e2) / det Dm at rest),
+//             F_ac = fma(d3_a,B_2c, fma(d2_a,B_1c, d1_a*B_0c)); R by 20 Newton steps
+//             R <- 0.5 * (R + R^-T) from R = F, R^-T = [c1 x c2, c2 x c0, c0 x c1] / det
+//             (columns c_k of R); det F = 0 gives C = 0 and zero gradient;
+//             C = sum over (a, c) row-major of fma(D_ac, D_ac, .), D = F - R;
+//             g_k = 2 D B^T e_k (k = 1..3), g0 = -((g1 + g2) + g3)
 //   A_ij      sum over shared vertices (ascending id) acc = fma(w_v, g_i.g_j, acc),
 //             g_i.g_j = fma(gz_i,gz_j, fma(gy_i,gy_j, gx_i*gx_j)); A_ii + alpha~ last
 #include "common.cuh"
@@ -58,6 +65,73 @@ __device__ __forceinline__ double tet_eval(const double *x0, const double *x1, c
   return V - V0;
 }
 
+constexpr int kArapPolarIters = 20;
+
+__device__ void arap_rest(const double *x0, const double *x1, const double *x2,
+                          const double *x3, double *B) {
+  double e1[3], e2[3], e3[3], c[3][3];
+  for (int k = 0; k < 3; ++k) {
+    e1[k] = x1[k] - x0[k];
+    e2[k] = x2[k] - x0[k];
+    e3[k] = x3[k] - x0[k];
+  }
+  cross3(e2, e3, c[0]);
+  cross3(e3, e1, c[1]);
+  cross3(e1, e2, c[2]);
+  const double det = fma(e1[2], c[0][2], fma(e1[1], c[0][1], e1[0] * c[0][0]));
+  for (int r = 0; r < 3; ++r)
+    for (int k = 0; k < 3; ++k) B[3 * r + k] = det != 0.0 ? c[r][k] / det : 0.0;
+}
+
+__device__ double arap_eval(const double *x0, const double *x1, const double *x2,
+                            const double *x3, const double *B, double g[12]) {
+  double d[3][3];  // d[k] = x_{k+1} - x_0, column k of Ds
+  for (int a = 0; a < 3; ++a) {
+    d[0][a] = x1[a] - x0[a];
+    d[1][a] = x2[a] - x0[a];
+    d[2][a] = x3[a] - x0[a];
+  }
+  double F[3][3], R[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c)
+      F[a][c] = fma(d[2][a], B[6 + c], fma(d[1][a], B[3 + c], d[0][a] * B[c]));
+  double col[3][3], x12[3];
+  for (int k = 0; k < 3; ++k)
+    for (int a = 0; a < 3; ++a) col[k][a] = F[a][k];
+  cross3(col[1], col[2], x12);
+  const double detF = fma(col[0][2], x12[2], fma(col[0][1], x12[1], col[0][0] * x12[0]));
+  if (detF == 0.0) {
+    for (int k = 0; k < 12; ++k) g[k] = 0.0;
+    return 0.0;
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) R[a][c] = F[a][c];
+  for (int it = 0; it < kArapPolarIters; ++it) {
+    double cc[3][3], dual[3][3];
+    for (int k = 0; k < 3; ++k)
+      for (int a = 0; a < 3; ++a) cc[k][a] = R[a][k];
+    cross3(cc[1], cc[2], dual[0]);
+    cross3(cc[2], cc[0], dual[1]);
+    cross3(cc[0], cc[1], dual[2]);
+    const double det = fma(cc[0][2], dual[0][2], fma(cc[0][1], dual[0][1], cc[0][0] * dual[0][0]));
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < 3; ++k) R[a][k] = 0.5 * (R[a][k] + dual[k][a] / det);
+  }
+  double C = 0.0, D[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) {
+      D[a][c] = F[a][c] - R[a][c];
+      C = fma(D[a][c], D[a][c], C);
+    }
+  for (int k = 0; k < 3; ++k)
+    for (int a = 0; a < 3; ++a) {
+      const double t = fma(D[a][2], B[3 * k + 2], fma(D[a][1], B[3 * k + 1], D[a][0] * B[3 * k]));
+      g[3 * (k + 1) + a] = 2.0 * t;
+    }
+  for (int a = 0; a < 3; ++a) g[a] = -((g[3 + a] + g[6 + a]) + g[9 + a]);
+  return C;
+}
+
 __device__ __forceinline__ void load3(const double *p, double *o) {
   o[0] = p[0];
   o[1] = p[1];
@@ -66,7 +140,7 @@ __device__ __forceinline__ void load3(const double *p, double *o) {
 
 // ---------------------------------------------------------------------------
 __global__ void k_rest(int E, int T, const int32_t *edge, const int32_t *tet, const double *X,
-                       double *L0, double *V0) {
+                       double *L0, double *V0, double *Dminv) {
   int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = tid; j < (int64_t)E + T; j += stride) {
@@ -84,6 +158,7 @@ __global__ void k_rest(int E, int T, const int32_t *edge, const int32_t *tet, co
       load3(X + 3 * (int64_t)q[2], p2);
       load3(X + 3 * (int64_t)q[3], p3);
       V0[t] = tet_eval(p0, p1, p2, p3, 0.0, g);
+      if (Dminv) arap_rest(p0, p1, p2, p3, Dminv + 9 * t);
     }
   }
 }
@@ -91,7 +166,7 @@ __global__ void k_rest(int E, int T, const int32_t *edge, const int32_t *tet, co
 mgpbd_status rest_shape(Handle *h) {
   if (h->m == 0) return MGPBD_OK;
   k_rest<<<blocks_for(h->m, 256), 256, 0, h->stream>>>(h->E, h->T, h->edge, h->tet, h->rest,
-                                                       h->L0, h->V0);
+                                                       h->L0, h->V0, h->Dminv);
   MG_LAUNCH("k_rest");
   return MGPBD_OK;
 }
@@ -145,8 +220,9 @@ mgpbd_status launch_end_frame(Handle *h) {
 // ---------------------------------------------------------------------------
 // Alg. 1: C and grad C; eq. 3: b = -C - alpha~ lambda
 __global__ void k_eval(int E, int T, const int32_t *edge, const int32_t *tet, const double *x,
-                       const double *L0, const double *V0, const double *alpha_t,
-                       const double *lambda, double *C, double *b, double *gd, double *gt) {
+                       const double *L0, const double *V0, const double *Dminv,
+                       const double *alpha_t, const double *lambda, double *C, double *b,
+                       double *gd, double *gt) {
   int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = tid; j < (int64_t)E + T; j += stride) {
@@ -167,7 +243,7 @@ __global__ void k_eval(int E, int T, const int32_t *edge, const int32_t *tet, co
       load3(x + 3 * (int64_t)q[1], p1);
       load3(x + 3 * (int64_t)q[2], p2);
       load3(x + 3 * (int64_t)q[3], p3);
-      c = tet_eval(p0, p1, p2, p3, V0[t], g);
+      c = Dminv ? arap_eval(p0, p1, p2, p3, Dminv + 9 * t, g) : tet_eval(p0, p1, p2, p3, V0[t], g);
       double *o = gt + 12 * t;
       for (int k = 0; k < 12; ++k) o[k] = g[k];
     }
@@ -180,8 +256,8 @@ __global__ void k_eval(int E, int T, const int32_t *edge, const int32_t *tet, co
 mgpbd_status launch_eval(Handle *h) {
   if (h->m == 0) return MGPBD_OK;
   k_eval<<<blocks_for(h->m, 256), 256, 0, h->stream>>>(h->E, h->T, h->edge, h->tet, h->x, h->L0,
-                                                       h->V0, h->alpha_t, h->lambda, h->C, h->b,
-                                                       h->gd, h->gt);
+                                                       h->V0, h->Dminv, h->alpha_t, h->lambda,
+                                                       h->C, h->b, h->gd, h->gt);
   MG_LAUNCH("k_eval");
   return MGPBD_OK;
 }

@@ -159,6 +159,7 @@ mgpbd_status mgpbd_batch_add_instance(mgpbd_batch_t *bb, const mgpbd_mesh_desc *
   r.desc.n_tet = T;
   r.desc.tet = T ? r.tet.data() : nullptr;
   r.desc.alpha = (E + T) ? r.alpha.data() : nullptr;
+  r.desc.tet_kind = md->tet_kind;
   r.est_bytes = estimate_bytes(r);
   *id = (int)b->inst.size() - 1;
   // descriptors of earlier instances stay valid: vectors own their storage and

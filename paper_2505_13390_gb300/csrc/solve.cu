@@ -795,24 +795,35 @@ mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *
   const int chunk = 8;
   int launched = 0;
   // Chunks of PCG iterations replay a captured CUDA graph (one launch instead
-  // of ~40 per iteration); the graph is re-captured when the hierarchy or the
-  // output array changes.  Event timing of the smoother needs plain launches.
+  // of ~33 per iteration); the graph is re-captured when the hierarchy, the
+  // output array or the profiling switch changes.  With profiling on, the
+  // graph carries event-record nodes around the level-0 sweeps, read back
+  // after every replay.
   // (the legacy default stream cannot be captured: graphs need the caller's own stream)
-  const bool graphs = h->p.use_graphs && !h->prof && h->stream != nullptr &&
+  const bool graphs = h->p.use_graphs && h->stream != nullptr &&
                       h->stream != cudaStreamLegacy && h->stream != cudaStreamPerThread;
   while (launched < h->p.pcg_maxiter) {
     int c = std::min(chunk, h->p.pcg_maxiter - launched);
-    if (graphs && c == chunk) {
-      if (!h->pcg_graph || h->graph_gen != h->gen || h->graph_x != x || h->graph_chunk != c) {
+    const bool replay = graphs && c == chunk;
+    if (replay) {
+      if (!h->pcg_graph || h->graph_gen != h->gen || h->graph_x != x || h->graph_chunk != c ||
+          h->graph_prof != h->prof) {
         if (h->pcg_graph) {
           cudaGraphExecDestroy(h->pcg_graph);
           h->pcg_graph = nullptr;
         }
+        if (h->prof) MG_TRY(prof_reserve_graph(h, c * 2 * std::max(1, h->p.smooth_sweeps) + 8));
         cudaGraph_t gr = nullptr;
         unsigned long long n0 = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+        h->gev_used = 0;
         MG_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        h->capturing = true;
         mgpbd_status cs = MGPBD_OK;
-        for (int k = 0; k < c && cs >= 0; ++k) cs = pcg_iteration(h, x);
+        for (int k = 0; k < c && cs >= 0; ++k) {
+          h->pcg_k = k;
+          cs = pcg_iteration(h, x);
+        }
+        h->capturing = false;
         cudaError_t ce = cudaStreamEndCapture(h->stream, &gr);
         // captured launches run at each replay, not now: count them there
         h->graph_kernels = __atomic_load_n(&g_launches, __ATOMIC_RELAXED) - n0;
@@ -828,6 +839,7 @@ mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *
         h->graph_gen = h->gen;
         h->graph_x = x;
         h->graph_chunk = c;
+        h->graph_prof = h->prof;
       }
       MG_CUDA(cudaGraphLaunch(h->pcg_graph, h->stream));
       __atomic_fetch_add(&g_launches, h->graph_kernels, __ATOMIC_RELAXED);
@@ -841,6 +853,7 @@ mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *
     MG_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost,
                             h->stream));
     MG_CUDA(cudaStreamSynchronize(h->stream));
+    if (replay && h->graph_prof) MG_TRY(prof_harvest_graph(h, launched - c));
     if (h->sc_host->done) break;
   }
   // true residual in FP64

@@ -32,7 +32,7 @@ tets of volume h^3/6, and each tet gives a quarter of rho*V to each vertex.
 from __future__ import annotations
 
 import dataclasses
-from typing import Dict, List, Tuple
+from typing import Dict, List, Optional, Tuple
 
 import numpy as np
 
@@ -52,6 +52,7 @@ class Mesh:
     alpha: np.ndarray  # (E + T,) float64 compliance per row
     x0: np.ndarray  # (N, 3) float64 initial positions
     v0: np.ndarray  # (N, 3) float64 initial velocities
+    tet_kind: int = 0  # tet rows: 0 volume C = V - V0, 1 ARAP C = |F - R|_F^2 (Sec. 5.3)
 
     @property
     def n_verts(self) -> int:
@@ -207,12 +208,15 @@ def _tet_templates() -> Tuple[List[List[Tuple[int, int, int]]], List[List[Tuple[
 
 def hex_block(nx: int, ny: int, nz: int, *, h: float, rho: float = 1000.0,
               jitter: float = 0.0, alpha=1e-9, alpha_log_range=None,
-              pin: str = "x0", seed: int = 1, name: str = "block") -> Mesh:
+              pin: str = "x0", seed: int = 1, name: str = "block",
+              arap_mu: Optional[float] = None) -> Mesh:
     """Hex lattice of nx*ny*nz cells split into 5 tets per cell.
 
     Vertex (i,j,k) -> (i*(ny+1) + j)*(nz+1) + k.  Rows: unique tet edges
     sorted by (min, max) vertex, then tets in cell order (i, j, k), each cell
-    giving its central tet first.
+    giving its central tet first.  With arap_mu set, the rows are one ARAP
+    constraint per tet and nothing else, with compliance 1/(mu V_tet) from
+    the rest volume (Sec. 5.3).
     """
     vx, vy, vz = nx + 1, ny + 1, nz + 1
     n = vx * vy * vz
@@ -253,6 +257,12 @@ def hex_block(nx: int, ny: int, nz: int, *, h: float, rho: float = 1000.0,
     elif pin == "y0":
         inv_mass[J.ravel() == 0] = 0.0
 
+    if arap_mu is not None:
+        p = pos[tets]
+        e = p[:, 1:, :] - p[:, :1, :]
+        v_rest = np.abs(np.linalg.det(e)) / 6.0
+        return Mesh(name, pos, inv_mass, np.zeros((0, 2), np.int32), tets.astype(np.int32),
+                    1.0 / (float(arap_mu) * v_rest), pos.copy(), np.zeros_like(pos), tet_kind=1)
     m = dist.shape[0] + tets.shape[0]
     if alpha_log_range is not None:
         arng = np.random.default_rng(seed + 1)
@@ -285,6 +295,14 @@ def workload(name: str) -> Tuple[Mesh, Dict]:
                          seed=1, name=name)
         params = default_params(omega_x=0.1, setup_interval=20, frames=1,
                                 precision=1)
+    elif name == "block100arap":
+        # the block100 lattice with one ARAP row per tet (Sec. 5.3), mu = 1e7 Pa
+        mesh = hex_block(100, 33, 100, h=0.005, jitter=0.1, arap_mu=1e7, pin="y0", seed=1,
+                         name=name)
+        params = default_params(omega_x=0.1, setup_interval=20, frames=1, precision=1)
+    elif name == "beam40arap":
+        mesh = hex_block(40, 10, 10, h=0.01, arap_mu=1e7, pin="x0", seed=1, name=name)
+        params = default_params(omega_x=0.1, setup_interval=10, frames=30)
     elif name.startswith("cloth") and name[5:].isdigit():
         n = int(name[5:])
         mesh = cloth(n, plane="xz", alpha=1e-8, pin="corners", seed=1, name=name)

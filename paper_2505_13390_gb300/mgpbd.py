@@ -25,7 +25,7 @@ FP64, MIXED = 0, 1
 class MeshDesc(C.Structure):
     _fields_ = [("n_verts", C.c_int), ("rest_pos", C.c_void_p), ("inv_mass", C.c_void_p),
                 ("n_dist", C.c_int), ("dist", C.c_void_p), ("n_tet", C.c_int),
-                ("tet", C.c_void_p), ("alpha", C.c_void_p)]
+                ("tet", C.c_void_p), ("alpha", C.c_void_p), ("tet_kind", C.c_int)]
 
 
 class Params(C.Structure):
@@ -217,7 +217,7 @@ class Solver:
                 np.ascontiguousarray(mesh.tet, np.int32).reshape(-1, 4),
                 np.ascontiguousarray(mesh.alpha, np.float64)]
         md = MeshDesc(self.N, _ptr(keep[0]), _ptr(keep[1]), self.E, _ptr(keep[2]), self.T,
-                      _ptr(keep[3]), _ptr(keep[4]))
+                      _ptr(keep[3]), _ptr(keep[4]), int(getattr(mesh, "tet_kind", 0)))
         self.params = dict(params)
         self._p = make_params(params)
         h = C.c_void_p()
@@ -402,7 +402,7 @@ class Batch:
                 np.ascontiguousarray(mesh.x0, np.float64),
                 np.ascontiguousarray(mesh.v0, np.float64)]
         md = MeshDesc(mesh.n_verts, _ptr(keep[0]), _ptr(keep[1]), mesh.n_dist, _ptr(keep[2]),
-                      mesh.n_tet, _ptr(keep[3]), _ptr(keep[4]))
+                      mesh.n_tet, _ptr(keep[3]), _ptr(keep[4]), int(getattr(mesh, "tet_kind", 0)))
         p = make_params(params)
         i = C.c_int()
         _check(load().mgpbd_batch_add_instance(self.h, C.byref(md), C.byref(p), _ptr(keep[5]),

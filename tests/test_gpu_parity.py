@@ -40,6 +40,9 @@ CASES = {
     "beam40": lambda: workload("beam40"),
     "block6": lambda: (hex_block(6, 5, 7, h=0.005, jitter=0.1, alpha=1e-10, pin="y0", seed=1),
                        default_params(omega_x=0.1)),
+    # ARAP rows only (Sec. 5.3), compliance 1/(mu V_tet)
+    "arap": lambda: (hex_block(6, 3, 3, h=0.01, jitter=0.1, arap_mu=1e6, pin="x0", seed=4),
+                     default_params(omega_x=0.1, setup_interval=10)),
 }
 
 
@@ -198,7 +201,7 @@ def test_solve_stiff_true_residual():
 @pytest.mark.parametrize("smoother", [0, 1, 2])
 @pytest.mark.parametrize("op", [0, 1])
 @pytest.mark.parametrize("name,iters", [("cloth8", 6), ("cloth8s", 6), ("hex3s", 6),
-                                        ("cloth32", 4), ("hex3", 3)])
+                                        ("cloth32", 4), ("hex3", 3), ("arap", 4)])
 def test_iterations_parity_fp64(name, iters, op, smoother):
     """Whole global iterations in FP64 with PCG solved to 1e-10: positions,
     velocities and |b| within 1e-9 relative of the oracle (Jacobi or
@@ -273,7 +276,8 @@ def test_backtracking_parity(name):
 
 
 @pytest.mark.parametrize("op", [0, 1])
-@pytest.mark.parametrize("name,rtol", [("cloth32", 1e-10), ("hex3s", 1e-10), ("block6", 1e-6)])
+@pytest.mark.parametrize("name,rtol", [("cloth32", 1e-10), ("hex3s", 1e-10), ("block6", 1e-6),
+                                       ("arap", 1e-10)])
 def test_mixed_precision_error_vs_oracle(name, rtol, op):
     """The error of the mixed-precision path (FP32 V-cycle, FP64 recurrences
     and A.p) against the FP64 oracle over three global iterations, next to the
@@ -308,6 +312,25 @@ def test_mixed_precision_error_vs_oracle(name, rtol, op):
     # on stiff systems the FP64 true residual sits above rtol (cond * eps);
     # the mixed path's stays within a small factor of the FP64 path's
     assert max(tres["mixed"]) <= 4 * max(max(tres["fp64"]), rtol)
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_breakdown_resetup_parity(op):
+    """ARAP rows leaving the rest state break PCG down on the reused
+    hierarchy; both sides set up afresh at the same iteration and retry, and
+    the positions agree with the oracle to 1e-9 (FP64, PCG to 1e-10)."""
+    mesh = hex_block(4, 12, 4, h=0.005, jitter=0.1, arap_mu=1e7, pin="y0", seed=1)
+    p = default_params(omega_x=0.1, setup_interval=4, pcg_rtol=1e-10, pcg_maxiter=5000,
+                       level0_op=op)
+    o, g = Oracle(mesh, p), solver(mesh, p)
+    o.begin_frame()
+    g.begin_frame()
+    scale = np.abs(mesh.rest_pos).max()
+    for it in range(4):
+        assert o.iterate()["ret"] == 0
+        assert g.iterate()["ret"] == 0
+        assert np.abs(g.get_state()[0] - o.get_state()[0]).max() <= 1e-9 * scale, it
+    assert o.n_setups == 2 and g.stats()["n_setups"] == 2
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -347,6 +370,33 @@ def test_graph_replay_is_bitwise_identical(prec):
     (x1, v1), it1, l1 = states[1]
     assert it0 == it1
     assert np.array_equal(x0, x1) and np.array_equal(v0, v1) and np.array_equal(l0, l1)
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_sweep_timing_inside_graphs(op):
+    """The level-0 sweep timing (profile on) also works when PCG chunks replay
+    a captured graph: the graph's event-record nodes are read back after each
+    replay.  Same launch count as plain launches, a positive finite time of
+    the same order, and identical results."""
+    from paper_2505_13390_gb300.mgpbd import Solver
+    mesh, p = CASES["block6"]()
+    out = {}
+    stream = torch.cuda.Stream()  # graphs need a stream of the caller's own
+    for graphs in (0, 1):
+        g = Solver(mesh, dict(p, precision=1, level0_op=op, use_graphs=graphs, pcg_maxiter=400),
+                   stream=stream)
+        g.begin_frame()
+        g.iterate()
+        g.profile(True)
+        d = g.iterate()
+        pr = g.profile_read()
+        out[graphs] = (d["pcg_iters"], pr, g.get_state()[0])
+    (i0, p0, x0), (i1, p1, x1) = out[0], out[1]
+    assert i0 == i1 and np.array_equal(x0, x1)
+    assert p1["launches"] == p0["launches"] > 0
+    assert np.isfinite(p1["total_ms"]) and p1["total_ms"] > 0
+    r = (p1["total_ms"] / p1["launches"]) / (p0["total_ms"] / p0["launches"])
+    assert 0.2 < r < 5.0
 
 
 @pytest.mark.parametrize("name", ["cloth32", "block6"])
