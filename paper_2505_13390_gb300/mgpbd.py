@@ -321,13 +321,25 @@ class Solver:
     def levels(self) -> int:
         return self.stats()["levels"]
 
-    def matrix(self, level: int = 0):
+    def matrix(self, level: int = 0, device: bool = False):
+        """CSR (ptr, col, val) of a level: numpy arrays, or CUDA tensors with
+        device=True (no host copy of a multi-GB level 0)."""
         li = self.level_info(level)
-        ptr = np.zeros(li["n"] + 1, np.int64)
-        col = np.zeros(li["nnz"], np.int32)
-        val = np.zeros(li["nnz"], np.float64)
-        _check(load().mgpbd_get_matrix(self.h, level, _ptr(ptr), _ptr(col), _ptr(val), MEM_HOST),
+        if device:
+            torch = self.torch
+            ptr = torch.empty(li["n"] + 1, dtype=torch.int64, device="cuda")
+            col = torch.empty(li["nnz"], dtype=torch.int32, device="cuda")
+            val = torch.empty(li["nnz"], dtype=torch.float64, device="cuda")
+            mem = MEM_DEVICE
+        else:
+            ptr = np.zeros(li["n"] + 1, np.int64)
+            col = np.zeros(li["nnz"], np.int32)
+            val = np.zeros(li["nnz"], np.float64)
+            mem = MEM_HOST
+        _check(load().mgpbd_get_matrix(self.h, level, _ptr(ptr), _ptr(col), _ptr(val), mem),
                "get_matrix")
+        if device:
+            self.torch.cuda.synchronize()
         return ptr, col, val
 
     def assembly_map(self):
