@@ -70,6 +70,7 @@ typedef struct {
   int max_levels;
   int backtrack;  /* 0: fixed omega_x; k > 0: halve omega up to k times (Sec. 4) */
   int linear_solver; /* 0: MGPCG (Sec. 4.4); 1: XPBD diagonal step dl_j = b_j / A_jj (eq. 4) */
+  int nk_vectors;    /* k near-kernel vectors, k columns of P per aggregate (Sec. 4.3) */
   uint64_t seed_nk, seed_agg, seed_col, seed_pow;
 } orc_params;
 
@@ -87,8 +88,9 @@ typedef struct {
   int n_agg;
   int32_t *agg;     /* aggregate of each row */
   uint8_t *root;    /* 1 for the MIS-2 roots */
-  double *B;        /* near-kernel at this level */
-  double *P;        /* the one nonzero of row i of P */
+  double *B;        /* near-kernel at this level, n x k row-major */
+  double *P;        /* row i of P: k values in columns agg_i*k .. agg_i*k+k-1 */
+  uint8_t *pdead;   /* n_agg*k: 1 where a column of P is zero (rank-deficient B_a) */
   int64_t *mptr;    /* members of each aggregate, ascending */
   int32_t *mrow;
   double lmax, omega;
@@ -161,7 +163,7 @@ static void csr_free(orc_csr *a) {
 
 static void level_free(orc_level *L) {
   csr_free(&L->A);
-  free(L->agg); free(L->root); free(L->B); free(L->P); free(L->mptr); free(L->mrow);
+  free(L->agg); free(L->root); free(L->B); free(L->P); free(L->pdead); free(L->mptr); free(L->mrow);
   free(L->color); free(L->x); free(L->b); free(L->r); free(L->t);
   memset(L, 0, sizeof(*L));
 }
@@ -567,11 +569,11 @@ static int aggregate(const orc_csr *A, const uint8_t *S, uint64_t seed, int l,
    x0_i = u_i * max|A_ij| (u_i in (0,1) from the counter generator).
    Sweep: s_i = sum over storage order fma(A_ij, x_j, s);
           x_i <- fma(-omega_nk, s_i / A_ii, x_i). */
-static void near_kernel(const orc_csr *A, const orc_params *p, double *B) {
+static void near_kernel_one(const orc_csr *A, const orc_params *p, uint64_t seed, double *B) {
   int n = A->n;
   double amax = 0.0;
   for (int64_t k = 0; k < A->nnz; ++k) if (fabs(A->val[k]) > amax) amax = fabs(A->val[k]);
-  for (int i = 0; i < n; ++i) B[i] = u01(h64(hkey(p->seed_nk, 0, i))) * amax;
+  for (int i = 0; i < n; ++i) B[i] = u01(h64(hkey(seed, 0, i))) * amax;
   double *s = (double *)xcalloc((size_t)n, sizeof(double));
   for (int sw = 0; sw < p->nk_sweeps; ++sw) {
     spmv(A, B, s);
@@ -580,11 +582,29 @@ static void near_kernel(const orc_csr *A, const orc_params *p, double *B) {
   free(s);
 }
 
+/* k vectors (Sec. 4.3 repeats the sweeps for each B): vector c starts from
+   the generator stream seed_nk + c; B is n x k row-major. */
+static void near_kernel(const orc_csr *A, const orc_params *p, double *B) {
+  int n = A->n, k = p->nk_vectors;
+  if (k == 1) { near_kernel_one(A, p, p->seed_nk, B); return; }
+  double *v = (double *)xcalloc((size_t)n, sizeof(double));
+  for (int c = 0; c < k; ++c) {
+    near_kernel_one(A, p, p->seed_nk + (uint64_t)c, v);
+    for (int i = 0; i < n; ++i) B[(size_t)i * k + c] = v[i];
+  }
+  free(v);
+}
+
 /* Injection with k = 1 (Sec. 4.1 setup-pipeline figure): per aggregate a (members
    ascending) nrm_a = sqrt(sum fma(B_i, B_i, .)); P_i = B_i / nrm_a;
    the next level's near-kernel is the R factor, B_{l+1}[a] = nrm_a.
    If nrm_a == 0: P_i = 1/sqrt(|a|). */
-static void inject(orc_level *L, orc_level *Lc) {
+#define ORC_QR_DROP 1e-6
+
+static void inject_k(orc_level *L, orc_level *Lc, int k);
+
+static void inject(orc_level *L, orc_level *Lc, int k) {
+  if (k > 1) { inject_k(L, Lc, k); return; }
   int n = L->A.n, na = L->n_agg;
   L->mptr = (int64_t *)xcalloc((size_t)na + 1, sizeof(int64_t));
   L->mrow = (int32_t *)xcalloc((size_t)n, sizeof(int32_t));
@@ -609,6 +629,66 @@ static void inject(orc_level *L, orc_level *Lc) {
     }
     Lc->B[a] = nrm;
   }
+}
+
+static void member_lists(orc_level *L) {
+  int n = L->A.n, na = L->n_agg;
+  L->mptr = (int64_t *)xcalloc((size_t)na + 1, sizeof(int64_t));
+  L->mrow = (int32_t *)xcalloc((size_t)n, sizeof(int32_t));
+  for (int i = 0; i < n; ++i) if (L->agg[i] >= 0) L->mptr[L->agg[i] + 1]++;
+  for (int a = 0; a < na; ++a) L->mptr[a + 1] += L->mptr[a];
+  int64_t *f = (int64_t *)xcalloc((size_t)na, sizeof(int64_t));
+  for (int i = 0; i < n; ++i) if (L->agg[i] >= 0) L->mrow[L->mptr[L->agg[i]] + f[L->agg[i]]++] = i;
+  free(f);
+}
+
+/* Injection with k > 1 (Sec. 4.3, six B; the tentative prolongator of
+   smoothed-aggregation AMG): per aggregate a the member rows of B (|a| x k)
+   are factored B_a = Q R by modified Gram-Schmidt with one re-orthogonal-
+   isation pass (the smoothed near-kernel columns are close to dependent on
+   small aggregates), column by column, each sum over the members in
+   ascending order with fma:
+     v = B_a[:,c]; twice: for d < c: r = q_d . v, R[d][c] += r,
+                                     v = v - r q_d  (fma(-r, q_d, v))
+     r_cc = |v|; q_c = v / r_cc, or q_c = 0 (a dead column) when
+     r_cc <= ORC_QR_DROP * |B_a[:,c]| (B_a numerically rank-deficient).
+   P rows of a take Q; the next level's near-kernel rows (a, d) take R[d][:].
+   Rows left alone keep zero rows of P. */
+static void inject_k(orc_level *L, orc_level *Lc, int k) {
+  int n = L->A.n, na = L->n_agg;
+  member_lists(L);
+  L->P = (double *)xcalloc((size_t)n * k, sizeof(double));
+  L->pdead = (uint8_t *)xcalloc((size_t)na * k, 1);
+  Lc->B = (double *)xcalloc((size_t)na * k * k, sizeof(double));
+  double *v = (double *)xcalloc((size_t)n, sizeof(double)); /* by member position */
+  for (int a = 0; a < na; ++a) {
+    int64_t q0 = L->mptr[a], q1 = L->mptr[a + 1];
+    double *R = Lc->B + (size_t)a * k * k; /* rows (a, d), column c: R[d * k + c] */
+    for (int c = 0; c < k; ++c) {
+      for (int64_t q = q0; q < q1; ++q) v[q - q0] = L->B[(size_t)L->mrow[q] * k + c];
+      for (int pass = 0; pass < 2; ++pass)
+        for (int d = 0; d < c; ++d) {
+          double r = 0.0;
+          for (int64_t q = q0; q < q1; ++q) r = fma(L->P[(size_t)L->mrow[q] * k + d], v[q - q0], r);
+          R[d * k + c] = pass ? R[d * k + c] + r : r;
+          for (int64_t q = q0; q < q1; ++q)
+            v[q - q0] = fma(-r, L->P[(size_t)L->mrow[q] * k + d], v[q - q0]);
+        }
+      double nb = 0.0, nv = 0.0;
+      for (int64_t q = q0; q < q1; ++q) {
+        double bq = L->B[(size_t)L->mrow[q] * k + c];
+        nb = fma(bq, bq, nb);
+        nv = fma(v[q - q0], v[q - q0], nv);
+      }
+      double nrm = sqrt(nv);
+      int live = nv > 0.0 && nrm > ORC_QR_DROP * sqrt(nb);
+      for (int64_t q = q0; q < q1; ++q)
+        L->P[(size_t)L->mrow[q] * k + c] = live ? v[q - q0] / nrm : 0.0;
+      R[c * k + c] = live ? nrm : 0.0;
+      L->pdead[(size_t)a * k + c] = (uint8_t)!live;
+    }
+  }
+  free(v);
 }
 
 /* Coarse pattern of P^T A P (eq. 6): row a holds every aggregate b reached
@@ -693,6 +773,120 @@ static void galerkin_values(const orc_level *L, orc_csr *Ac) {
       if (b < a) Ac->val[k] = Ac->val[find_col(Ac, b, a)];
     }
   free(acc);
+}
+
+/* Coarse pattern with k unknowns per aggregate (Sec. 4.3): aggregate a's
+   block list is every aggregate reached from a member row of a, a included,
+   ascending; coarse row (a, p) = a*k+p holds the columns b*k+q of those
+   blocks in ascending order with its own diagonal moved last. */
+static void galerkin_pattern_k(const orc_level *L, orc_csr *Ac, int k) {
+  int na = L->n_agg, nc = na * k;
+  int32_t *mark = (int32_t *)xcalloc((size_t)na, sizeof(int32_t));
+  int32_t *blk = (int32_t *)xcalloc((size_t)na + 1, sizeof(int32_t));
+  for (int a = 0; a < na; ++a) mark[a] = -1;
+  Ac->n = nc;
+  Ac->ptr = (int64_t *)xcalloc((size_t)nc + 1, sizeof(int64_t));
+  for (int a = 0; a < na; ++a) {
+    int cnt = 0;
+    for (int64_t q = L->mptr[a]; q < L->mptr[a + 1]; ++q) {
+      int i = L->mrow[q];
+      for (int64_t e = L->A.ptr[i]; e < L->A.ptr[i + 1]; ++e) {
+        int b = L->agg[L->A.col[e]];
+        if (b >= 0 && mark[b] != a) { mark[b] = a; ++cnt; }
+      }
+    }
+    for (int p = 0; p < k; ++p) Ac->ptr[(int64_t)a * k + p + 1] = (int64_t)cnt * k;
+  }
+  for (int r = 0; r < nc; ++r) Ac->ptr[r + 1] += Ac->ptr[r];
+  Ac->nnz = Ac->ptr[nc];
+  Ac->col = (int32_t *)xcalloc((size_t)Ac->nnz, sizeof(int32_t));
+  Ac->val = (double *)xcalloc((size_t)Ac->nnz, sizeof(double));
+  for (int a = 0; a < na; ++a) mark[a] = -1;
+  for (int a = 0; a < na; ++a) {
+    int cnt = 0;
+    for (int64_t q = L->mptr[a]; q < L->mptr[a + 1]; ++q) {
+      int i = L->mrow[q];
+      for (int64_t e = L->A.ptr[i]; e < L->A.ptr[i + 1]; ++e) {
+        int b = L->agg[L->A.col[e]];
+        if (b >= 0 && mark[b] != a) { mark[b] = a; blk[cnt++] = b; }
+      }
+    }
+    qsort(blk, (size_t)cnt, sizeof(int32_t), cmp_i32c);
+    for (int p = 0; p < k; ++p) {
+      int r = a * k + p;
+      int64_t w = Ac->ptr[r];
+      for (int t = 0; t < cnt; ++t)
+        for (int q = 0; q < k; ++q) {
+          int c = blk[t] * k + q;
+          if (c != r) Ac->col[w++] = c;
+        }
+      Ac->col[w] = r;
+    }
+  }
+  free(mark); free(blk);
+}
+
+/* Galerkin values with k unknowns per aggregate (eq. 6), the canonical
+   order of the k = 1 case per entry: entry (r, c) = ((a,p), (b,q)) with
+   c >= r sums, over member rows i of a ascending and row i's storage order,
+   acc = fma(P_ip * A_ij, P_jq, acc) for agg[j] == b; entries with c < r are
+   copied from (c, r).  A dead column (a, p) of P leaves a zero row and
+   column; its diagonal is set to 1 so that the coarse matrix stays SPD. */
+static void galerkin_values_k(const orc_level *L, orc_csr *Ac, int k) {
+  int na = L->n_agg, nc = na * k;
+  int32_t *slot = (int32_t *)xcalloc((size_t)na, sizeof(int32_t));
+  for (int a = 0; a < na; ++a) slot[a] = -1;
+  int maxblk = 0;
+  for (int a = 0; a < na; ++a) {
+    int len = (int)(Ac->ptr[a * k + 1] - Ac->ptr[a * k]) / k;
+    if (len > maxblk) maxblk = len;
+  }
+  double *acc = (double *)xcalloc((size_t)k * maxblk * k, sizeof(double));
+  int32_t *blk = (int32_t *)xcalloc((size_t)maxblk, sizeof(int32_t));
+  for (int a = 0; a < na; ++a) {
+    /* block list of a from row (a, 0): its columns in blocks of k, with
+       (a, 0) moved last */
+    int r0 = a * k, nb = 0;
+    for (int64_t e = Ac->ptr[r0]; e < Ac->ptr[r0 + 1]; ++e) {
+      int b = Ac->col[e] / k;
+      if (slot[b] != -2 - a) { slot[b] = -2 - a; blk[nb++] = b; }
+    }
+    qsort(blk, (size_t)nb, sizeof(int32_t), cmp_i32c);
+    for (int t = 0; t < nb; ++t) slot[blk[t]] = t;
+    memset(acc, 0, sizeof(double) * (size_t)k * nb * k);
+    for (int64_t q = L->mptr[a]; q < L->mptr[a + 1]; ++q) {
+      int i = L->mrow[q];
+      for (int64_t e = L->A.ptr[i]; e < L->A.ptr[i + 1]; ++e) {
+        int j = L->A.col[e];
+        int b = L->agg[j];
+        if (b < a) continue;
+        int sb = slot[b];
+        for (int p = 0; p < k; ++p) {
+          double t = L->P[(size_t)i * k + p] * L->A.val[e];
+          for (int qq = (b == a ? p : 0); qq < k; ++qq) {
+            double *cell = acc + (size_t)p * nb * k + (size_t)sb * k + qq;
+            *cell = fma(t, L->P[(size_t)j * k + qq], *cell);
+          }
+        }
+      }
+    }
+    for (int p = 0; p < k; ++p) {
+      int r = a * k + p;
+      for (int64_t e = Ac->ptr[r]; e < Ac->ptr[r + 1]; ++e) {
+        int c = Ac->col[e];
+        if (c >= r) Ac->val[e] = acc[(size_t)p * nb * k + (size_t)slot[c / k] * k + c % k];
+      }
+    }
+    for (int t = 0; t < nb; ++t) slot[blk[t]] = -1;
+  }
+  for (int r = 0; r < nc; ++r)
+    for (int64_t e = Ac->ptr[r]; e < Ac->ptr[r + 1] - 1; ++e) {
+      int c = Ac->col[e];
+      if (c < r) Ac->val[e] = Ac->val[find_col(Ac, c, r)];
+    }
+  for (int r = 0; r < nc; ++r)
+    if (L->pdead[r]) Ac->val[Ac->ptr[r + 1] - 1] = 1.0;
+  free(acc); free(blk); free(slot);
 }
 
 /* Multicolour ordering (Sec. 4.5, "parallel GS"): greedy colouring in
@@ -801,9 +995,11 @@ static void level_alloc_work(orc_level *L) {
 static int setup(orc *o) {
   for (int l = 1; l < ORC_MAXL; ++l) level_free(&o->lev[l]);
   orc_level *L0 = &o->lev[0];
-  free(L0->agg); free(L0->root); free(L0->B); free(L0->P); free(L0->mptr); free(L0->mrow); free(L0->color);
-  L0->agg = NULL; L0->root = NULL; L0->B = NULL; L0->P = NULL; L0->mptr = NULL; L0->mrow = NULL; L0->color = NULL;
-  L0->B = (double *)xcalloc((size_t)o->m, sizeof(double));
+  free(L0->agg); free(L0->root); free(L0->B); free(L0->P); free(L0->pdead); free(L0->mptr); free(L0->mrow);
+  free(L0->color);
+  L0->agg = NULL; L0->root = NULL; L0->B = NULL; L0->P = NULL; L0->pdead = NULL; L0->mptr = NULL;
+  L0->mrow = NULL; L0->color = NULL;
+  L0->B = (double *)xcalloc((size_t)o->m * o->p.nk_vectors, sizeof(double));
   near_kernel(&L0->A, &o->p, L0->B);
   int l = 0;
   for (;;) {
@@ -823,9 +1019,14 @@ static int setup(orc *o) {
     }
     L->n_agg = na;
     orc_level *Lc = &o->lev[l + 1];
-    inject(L, Lc);
-    galerkin_pattern(L, &Lc->A);
-    galerkin_values(L, &Lc->A);
+    inject(L, Lc, o->p.nk_vectors);
+    if (o->p.nk_vectors > 1) {
+      galerkin_pattern_k(L, &Lc->A, o->p.nk_vectors);
+      galerkin_values_k(L, &Lc->A, o->p.nk_vectors);
+    } else {
+      galerkin_pattern(L, &Lc->A);
+      galerkin_values(L, &Lc->A);
+    }
     ++l;
   }
   o->L = l + 1;
@@ -845,7 +1046,10 @@ static int setup(orc *o) {
 
 /* Galerkin re-form on reuse (Sec. 4.4): P kept, values recomputed. */
 static void reform(orc *o) {
-  for (int l = 0; l + 1 < o->L; ++l) galerkin_values(&o->lev[l], &o->lev[l + 1].A);
+  for (int l = 0; l + 1 < o->L; ++l) {
+    if (o->p.nk_vectors > 1) galerkin_values_k(&o->lev[l], &o->lev[l + 1].A, o->p.nk_vectors);
+    else galerkin_values(&o->lev[l], &o->lev[l + 1].A);
+  }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -932,17 +1136,21 @@ static void vcycle_level(orc *o, int l) {
   spmv(&L->A, L->x, L->t);
   for (int i = 0; i < n; ++i) L->r[i] = L->b[i] - L->t[i];
   orc_level *Lc = &o->lev[l + 1];
-  for (int a = 0; a < L->n_agg; ++a) {
-    double acc = 0.0;
-    for (int64_t q = L->mptr[a]; q < L->mptr[a + 1]; ++q) {
-      int i = L->mrow[q];
-      acc = fma(L->P[i], L->r[i], acc);
+  const int k = o->p.nk_vectors;
+  for (int a = 0; a < L->n_agg; ++a)
+    for (int c = 0; c < k; ++c) {
+      double acc = 0.0;
+      for (int64_t q = L->mptr[a]; q < L->mptr[a + 1]; ++q) {
+        int i = L->mrow[q];
+        acc = fma(L->P[(size_t)i * k + c], L->r[i], acc);
+      }
+      Lc->b[a * k + c] = acc;
     }
-    Lc->b[a] = acc;
-  }
   vcycle_level(o, l + 1);
   for (int i = 0; i < n; ++i)
-    if (L->agg[i] >= 0) L->x[i] = fma(L->P[i], Lc->x[L->agg[i]], L->x[i]);
+    if (L->agg[i] >= 0)
+      for (int c = 0; c < k; ++c)
+        L->x[i] = fma(L->P[(size_t)i * k + c], Lc->x[L->agg[i] * k + c], L->x[i]);
   smooth(o, L, L->x, L->b, L->t, 1);
 }
 
@@ -1176,7 +1384,8 @@ orc *orc_create(int N, const double *rest, const double *inv_mass, int E, const 
                 int T, const int32_t *tet, int tet_kind, const double *alpha, const orc_params *p,
                 int *status) {
   *status = ORC_E_INVALID;
-  if (N <= 0 || E < 0 || T < 0 || !p || p->dt <= 0.0 || tet_kind < 0 || tet_kind > 1) return NULL;
+  if (N <= 0 || E < 0 || T < 0 || !p || p->dt <= 0.0 || tet_kind < 0 || tet_kind > 1 ||
+      p->nk_vectors < 1 || p->nk_vectors > 8) return NULL;
   for (int j = 0; j < 2 * E; ++j) if (edge[j] < 0 || edge[j] >= N) return NULL;
   for (int64_t j = 0; j < 4 * (int64_t)T; ++j) if (tet[j] < 0 || tet[j] >= N) return NULL;
   orc *o = (orc *)xcalloc(1, sizeof(orc));
@@ -1260,11 +1469,12 @@ void orc_incidence(const orc *o, int64_t *vptr, int32_t *vrow) {
 /* aggregates, roots, P and B of level l (l < levels-1) */
 int orc_level_agg(const orc *o, int l, int32_t *agg, uint8_t *root, double *P, double *B) {
   const orc_level *L = &o->lev[l];
-  if (l + 1 >= o->L) { if (B && L->B) memcpy(B, L->B, sizeof(double) * (size_t)L->A.n); return 0; }
+  const size_t nk = (size_t)L->A.n * o->p.nk_vectors;
+  if (l + 1 >= o->L) { if (B && L->B) memcpy(B, L->B, sizeof(double) * nk); return 0; }
   if (agg) memcpy(agg, L->agg, sizeof(int32_t) * (size_t)L->A.n);
   if (root) memcpy(root, L->root, (size_t)L->A.n);
-  if (P) memcpy(P, L->P, sizeof(double) * (size_t)L->A.n);
-  if (B) memcpy(B, L->B, sizeof(double) * (size_t)L->A.n);
+  if (P) memcpy(P, L->P, sizeof(double) * nk);
+  if (B) memcpy(B, L->B, sizeof(double) * nk);
   return L->n_agg;
 }
 int orc_level_color(const orc *o, int l, int32_t *color) {

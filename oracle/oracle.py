@@ -36,7 +36,8 @@ class Params(C.Structure):
         ("nk_omega", C.c_double), ("theta_s", C.c_double), ("smoother", C.c_int),
         ("smooth_sweeps", C.c_int), ("lambda_min_est", C.c_double), ("power_iters", C.c_int),
         ("power_safety", C.c_double), ("coarse_max", C.c_int), ("max_levels", C.c_int),
-        ("backtrack", C.c_int), ("linear_solver", C.c_int), ("seed_nk", C.c_uint64), ("seed_agg", C.c_uint64), ("seed_col", C.c_uint64),
+        ("backtrack", C.c_int), ("linear_solver", C.c_int), ("nk_vectors", C.c_int),
+        ("seed_nk", C.c_uint64), ("seed_agg", C.c_uint64), ("seed_col", C.c_uint64),
         ("seed_pow", C.c_uint64),
     ]
 
@@ -120,7 +121,7 @@ def make_params(d: Dict) -> Params:
         setattr(p, k, float(d[k]))
     for k in ("max_iter", "pcg_maxiter", "setup_interval", "nk_sweeps", "smoother",
               "smooth_sweeps", "power_iters", "coarse_max", "max_levels", "backtrack",
-              "linear_solver"):
+              "linear_solver", "nk_vectors"):
         setattr(p, k, int(d[k]))
     for k in ("seed_nk", "seed_agg", "seed_col", "seed_pow"):
         setattr(p, k, int(d[k]))
@@ -278,12 +279,17 @@ class Oracle:
         return vptr, vrow
 
     def level_agg(self, level: int):
+        """(n_agg, agg, root, P, B); P and B are (n,) for one near-kernel
+        vector and (n, k) for k > 1."""
         n = lib().orc_rows(self.h, level)
+        k = int(self.params.get("nk_vectors", 1))
         agg = np.zeros(n, np.int32)
         root = np.zeros(n, np.uint8)
-        P = np.zeros(n)
-        B = np.zeros(n)
+        P = np.zeros(n * k)
+        B = np.zeros(n * k)
         na = lib().orc_level_agg(self.h, level, _p(agg), _p(root), _p(P), _p(B))
+        if k > 1:
+            P, B = P.reshape(n, k), B.reshape(n, k)
         return na, agg, root, P, B
 
     def level_color(self, level: int):

@@ -88,6 +88,7 @@ def default_params(**over) -> Dict:
         pcg_maxiter=20000,  # a safeguard: the solve runs to pcg_rtol
         setup_interval=400,
         nk_sweeps=3,
+        nk_vectors=1,  # near-kernel vectors k = columns of P per aggregate (Sec. 4.3)
         nk_omega=2.0 / 3.0,
         theta_s=0.1,
         smoother=0,  # 0 = weighted Jacobi, 1 = multicolour Gauss-Seidel
