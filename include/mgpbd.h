@@ -115,6 +115,9 @@ typedef struct {
                            stream (NULL) launches stay plain. */
   int linear_solver;    /* 0: MGPCG (Sec. 4.4); 1: XPBD's local step dl_j = b_j / A_jj
                            (eq. 4, the Jacobi form the paper compares against) */
+  int nk_vectors;       /* k near-kernel vectors (Sec. 4.3; the paper uses six), 1..8: P
+                           has k columns per aggregate from a QR of each aggregate's
+                           block of B, coarse levels have k unknowns per aggregate */
   uint64_t seed_nk, seed_agg, seed_col, seed_pow;
 } mgpbd_params;
 
@@ -219,7 +222,9 @@ mgpbd_status mgpbd_get_matrix(mgpbd_handle_t *h, int level, int64_t *ptr, int32_
 mgpbd_status mgpbd_get_map(mgpbd_handle_t *h, uint16_t *map, int mem);
 /* vertex -> incident rows, ascending: vptr [n_verts+1], vrow [2*n_dist+4*n_tet] */
 mgpbd_status mgpbd_get_incidence(mgpbd_handle_t *h, int64_t *vptr, int32_t *vrow, int mem);
-/* aggregates, MIS-2 roots, P values and near-kernel B of level `level` */
+/* aggregates, MIS-2 roots, P values and near-kernel B of level `level`:
+ * agg, root [n]; P, B [n * nk_vectors], row-major (row i of P holds the
+ * values of columns agg[i]*k .. agg[i]*k + k-1) */
 mgpbd_status mgpbd_get_aggregates(mgpbd_handle_t *h, int level, int32_t *agg, uint8_t *root,
                                   double *P, double *B, int mem);
 /* multicolour ordering of each level (Jones-Plassmann, used by the Gauss-Seidel

@@ -210,7 +210,8 @@ static mgpbd_status check_params(const mgpbd_params *p) {
       !(p->theta_s >= 0.0) || p->backtrack < 0 ||
       (p->autotune != 0 && p->autotune != 1) || (p->level0_op != 0 && p->level0_op != 1) ||
       (p->use_graphs != 0 && p->use_graphs != 1) ||
-      (p->linear_solver != 0 && p->linear_solver != 1) ||
+      (p->linear_solver != 0 && p->linear_solver != 1) || p->nk_vectors < 1 ||
+      p->nk_vectors > 8 ||
       !(p->pcg_rtol >= 0.0) || !(p->power_safety > 0.0)) {
     set_error("invalid mgpbd_params");
     return MGPBD_E_INVALID;
@@ -470,6 +471,7 @@ mgpbd_status mgpbd_default_params(mgpbd_params *p) {
   p->level0_op = 0;
   p->use_graphs = 0;
   p->linear_solver = 0;
+  p->nk_vectors = 1;
   p->seed_nk = 3;
   p->seed_agg = 4;
   p->seed_col = 5;
@@ -715,13 +717,13 @@ mgpbd_status mgpbd_get_aggregates(mgpbd_handle_t *hh, int level, int32_t *agg, u
   Handle *h = H(hh);
   if (!h || !h->have_setup || level < 0 || level >= h->L) return MGPBD_E_INVALID;
   const Level &L = h->lev[level];
-  size_t n = (size_t)L.n;
+  size_t n = (size_t)L.n, nk = n * (size_t)h->p.nk_vectors;
   if (level + 1 < h->L) {
     MG_TRY(copy_out(h, agg, L.agg, sizeof(int32_t) * n, mem));
     MG_TRY(copy_out(h, root, L.root, n, mem));
-    MG_TRY(copy_out(h, P, L.P, sizeof(double) * n, mem));
+    MG_TRY(copy_out(h, P, L.P, sizeof(double) * nk, mem));
   }
-  if (L.B) MG_TRY(copy_out(h, B, L.B, sizeof(double) * n, mem));
+  if (L.B) MG_TRY(copy_out(h, B, L.B, sizeof(double) * nk, mem));
   return MGPBD_OK;
 }
 

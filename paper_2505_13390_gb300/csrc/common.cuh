@@ -106,7 +106,13 @@ struct Level {
   int64_t *mptr = nullptr;   // members of each aggregate (ascending rows)
   int32_t *mrow = nullptr;
   int max_members = 0;
-  int max_coarse_row = 0;    // longest row of level+1 (Galerkin smem size)
+  int max_coarse_row = 0;    // longest row of level+1 (Galerkin smem size), in aggregates
+  // k > 1 near-kernel vectors: dead columns of P and the aggregate-level
+  // pattern of level+1 (kept for the Galerkin re-form)
+  uint8_t *pdead = nullptr;
+  int64_t *gbptr = nullptr;
+  int32_t *gbcol = nullptr;
+  int64_t cap_gb = 0;
   int G32 = 0, G64 = 0;      // lanes per row of the FP32 / FP64 row kernels (0 = rule)
   int32_t *color = nullptr;
   int n_colors = 0;
@@ -142,7 +148,8 @@ struct Handle {
   float *gd32 = nullptr, *gt32 = nullptr, *at32 = nullptr, *w32 = nullptr, *u32 = nullptr;
   int mf_g32 = 8, mf_g64 = 4;  // lanes per vertex of the vertex pass (autotuned)
   uint16_t *map = nullptr;
-  uint8_t *S = nullptr;  // strength mask, sized for level 0 and reused per level
+  uint8_t *S = nullptr;  // strength mask, reused per level (grown when a level has more nnz)
+  int64_t cap_S = 0;
   // hierarchy
   int L = 0;
   bool have_setup = false;

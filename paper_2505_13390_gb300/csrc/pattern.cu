@@ -304,6 +304,7 @@ mgpbd_status build_pattern(Handle *h) {
   MG_TRY(alloc_n(h->arena, &L.val, (size_t)nnz));
   MG_TRY(alloc_n(h->arena, &L.dinv, (size_t)m));
   MG_TRY(alloc_n(h->arena, &h->S, (size_t)nnz));
+  h->cap_S = nnz;
   if (h->p.precision == MGPBD_MIXED) {
     MG_TRY(alloc_n(h->arena, &L.val32, (size_t)nnz));
     MG_TRY(alloc_n(h->arena, &L.dinv32, (size_t)m));

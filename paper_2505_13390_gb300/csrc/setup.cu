@@ -604,16 +604,23 @@ static mgpbd_status ensure_level(Handle *h, int l, int n, int64_t nnz) {
       MG_TRY(alloc_n(h->arena, &L.dinv, (size_t)cap));
       if (mixed) MG_TRY(alloc_n(h->arena, &L.dinv32, (size_t)cap));
     }
-    void *olds[] = {L.agg, L.root, L.P, L.P32, L.B, L.mptr, L.mrow, L.color, L.crow,
-                    L.x, L.x2, L.b, L.r, L.t};
+    void *olds[] = {L.agg, L.root, L.P, L.P32, L.B, L.pdead, L.mptr, L.mrow, L.color, L.crow,
+                    L.x, L.x2, L.b, L.r, L.t, L.gbptr};
     for (void *o : olds) h->arena.release(o);
     L.P32 = nullptr;
     L.crow = nullptr;
+    L.pdead = nullptr;
+    L.gbptr = nullptr;
+    const size_t k = (size_t)h->p.nk_vectors;
     MG_TRY(alloc_n(h->arena, &L.agg, (size_t)cap));
     MG_TRY(alloc_n(h->arena, &L.root, (size_t)cap));
-    MG_TRY(alloc_n(h->arena, &L.P, (size_t)cap));
-    if (mixed) MG_TRY(alloc_n(h->arena, &L.P32, (size_t)cap));
-    MG_TRY(alloc_n(h->arena, &L.B, (size_t)cap));
+    MG_TRY(alloc_n(h->arena, &L.P, (size_t)cap * k));
+    if (mixed) MG_TRY(alloc_n(h->arena, &L.P32, (size_t)cap * k));
+    MG_TRY(alloc_n(h->arena, &L.B, (size_t)cap * k));
+    if (k > 1) {
+      MG_TRY(alloc_n(h->arena, &L.pdead, (size_t)cap * k));
+      MG_TRY(alloc_n(h->arena, &L.gbptr, (size_t)cap + 1));
+    }
     MG_TRY(alloc_n(h->arena, &L.mptr, (size_t)cap + 1));
     MG_TRY(alloc_n(h->arena, &L.mrow, (size_t)cap));
     MG_TRY(alloc_n(h->arena, &L.color, (size_t)cap));
@@ -743,6 +750,14 @@ static mgpbd_status aggregate_level(Handle *h, int l) {
   size_t off_f = ((off_p1 + 4 * (size_t)n + 15) / 16) * 16, off_ids = off_f + 8 * (size_t)n;
   size_t need = off_ids + 8 * ((size_t)n + 1);
   MG_TRY(ensure_tmp(h, need));
+  // with k > 1 unknowns per aggregate a coarse level can hold more nonzeros
+  // than level 0, for which the strength mask was sized
+  if (L.nnz > h->cap_S) {
+    h->arena.release(h->S);
+    h->S = nullptr;
+    MG_TRY(alloc_n(h->arena, &h->S, (size_t)L.nnz));
+    h->cap_S = L.nnz;
+  }
   char *base = (char *)h->tmp;
   uint8_t *state = (uint8_t *)(base + off_state), *e1 = (uint8_t *)(base + off_e1);
   uint64_t *m1p = (uint64_t *)(base + off_m1p);
@@ -845,6 +860,219 @@ static mgpbd_status galerkin_pattern(Handle *h, int l) {
   return MGPBD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// k > 1 near-kernel vectors (Sec. 4.3): the tentative prolongator of each
+// aggregate from a QR factorisation of its block of B, and P^T A P with k
+// unknowns per aggregate, in the canonical order of the k = 1 kernels.
+// ---------------------------------------------------------------------------
+constexpr double kQrDrop = 1e-6;  // a column below this share of |B_a[:,c]| is dropped
+
+__global__ void k_set_col(int n, int k, int c, const double *v, double *B) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    B[(int64_t)i * k + c] = v[i];
+}
+
+// Modified Gram-Schmidt with one re-orthogonalisation pass per aggregate,
+// one thread per aggregate, members in ascending order (the order of the
+// FP64 sums is that of the definition): P rows take Q, the next level's
+// near-kernel rows (a, d) take R[d][:], dead (dropped) columns are zero.
+__global__ void k_inject_k(int na, int k, const int64_t *mptr, const int32_t *mrow,
+                           const double *B, double *P, uint8_t *pdead, double *Bc, double *v) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < na; a += gridDim.x * blockDim.x) {
+    const int64_t q0 = mptr[a], q1 = mptr[a + 1];
+    double *R = Bc + (int64_t)a * k * k;
+    for (int c = 0; c < k; ++c) {
+      for (int64_t q = q0; q < q1; ++q) v[q] = B[(int64_t)mrow[q] * k + c];
+      for (int pass = 0; pass < 2; ++pass)
+        for (int d = 0; d < c; ++d) {
+          double r = 0.0;
+          for (int64_t q = q0; q < q1; ++q) r = fma(P[(int64_t)mrow[q] * k + d], v[q], r);
+          R[d * k + c] = pass ? R[d * k + c] + r : r;
+          for (int64_t q = q0; q < q1; ++q) v[q] = fma(-r, P[(int64_t)mrow[q] * k + d], v[q]);
+        }
+      double nb = 0.0, nv = 0.0;
+      for (int64_t q = q0; q < q1; ++q) {
+        const double bq = B[(int64_t)mrow[q] * k + c];
+        nb = fma(bq, bq, nb);
+        nv = fma(v[q], v[q], nv);
+      }
+      const double nrm = sqrt(nv);
+      const bool live = nv > 0.0 && nrm > kQrDrop * sqrt(nb);
+      for (int64_t q = q0; q < q1; ++q) P[(int64_t)mrow[q] * k + c] = live ? v[q] / nrm : 0.0;
+      R[c * k + c] = live ? nrm : 0.0;
+      pdead[(int64_t)a * k + c] = live ? 0 : 1;
+    }
+  }
+}
+
+// the k-unknown coarse pattern from the aggregate pattern (off-diagonal
+// aggregates ascending, the diagonal last): row (a, p) = a*k+p holds the
+// columns b*k+q of a's aggregates ascending (a included) with (a, p) moved last
+__global__ void k_expand_count(int na, int k, const int64_t *bptr, int64_t *cnt) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < (int64_t)na * k;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(r / k);
+    cnt[r] = (bptr[a + 1] - bptr[a]) * k;
+  }
+}
+
+__device__ __forceinline__ int sorted_block(const int32_t *off, int noff, int sa, int a, int s) {
+  return s < sa ? off[s] : (s == sa ? a : off[s - 1]);
+}
+
+__global__ void k_expand_fill(int na, int k, const int64_t *bptr, const int32_t *bcol,
+                              const int64_t *cptr, int32_t *ccol) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < (int64_t)na * k;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(r / k);
+    const int32_t *off = bcol + bptr[a];
+    const int noff = (int)(bptr[a + 1] - bptr[a]) - 1;
+    int sa = 0;  // position of a among its aggregates in ascending order
+    while (sa < noff && off[sa] < a) ++sa;
+    int64_t w = cptr[r];
+    for (int s = 0; s <= noff; ++s) {
+      const int b = sorted_block(off, noff, sa, a, s);
+      for (int q = 0; q < k; ++q) {
+        const int64_t c = (int64_t)b * k + q;
+        if (c != r) ccol[w++] = (int32_t)c;
+      }
+    }
+    ccol[w] = (int32_t)r;
+  }
+}
+
+// Values of the k-unknown coarse operator: warp per aggregate a, lanes over
+// the k x k pairs (p, q); each pair's sums run over member rows i of a in
+// ascending order and row i's storage order, acc = fma(P_ip * A_ij, P_jq,
+// acc), as in the definition.  Only entries (b, q) >= (a, p) are formed.
+__global__ void k_gal_values_k(int na, int k, const int64_t *mptr, const int32_t *mrow,
+                               const int64_t *ptr, const int32_t *col, const double *val,
+                               const int32_t *agg, const double *P, const int64_t *bptr,
+                               const int32_t *bcol, const int64_t *cptr, double *cval,
+                               int maxblk) {
+  extern __shared__ unsigned char smem_raw[];
+  const int wib = threadIdx.x >> 5;
+  const int per = k * maxblk * k;
+  double *acc = reinterpret_cast<double *>(smem_raw) + (size_t)wib * per;
+  WARP_LOOP(na) {
+    const int a = (int)row_;
+    const int32_t *off = bcol + bptr[a];
+    const int noff = (int)(bptr[a + 1] - bptr[a]) - 1;
+    const int nb = noff + 1;
+    int sa = 0;
+    while (sa < noff && off[sa] < a) ++sa;
+    const int width = nb * k;
+    for (int t = lane; t < k * width; t += 32) acc[t] = 0.0;
+    __syncwarp();
+    for (int64_t m = mptr[a]; m < mptr[a + 1]; ++m) {
+      const int i = mrow[m];
+      for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
+        const int j = col[e];
+        const int b = agg[j];
+        if (b < a) continue;  // uniform over the warp
+        int sb;
+        if (b == a) {
+          sb = sa;
+        } else {
+          int lo = 0, hi = noff;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] < b) lo = mid + 1;
+            else hi = mid;
+          }
+          sb = lo < sa ? lo : lo + 1;
+        }
+        const double aij = val[e];
+        for (int pq = lane; pq < k * k; pq += 32) {
+          const int p = pq / k, q = pq % k;
+          if (b == a && q < p) continue;
+          const double t = P[(int64_t)i * k + p] * aij;
+          double *cell = acc + p * width + sb * k + q;
+          *cell = fma(t, P[(int64_t)j * k + q], *cell);
+        }
+      }
+    }
+    __syncwarp();
+    for (int p = 0; p < k; ++p) {
+      const int64_t r = (int64_t)a * k + p;
+      const int64_t rb = cptr[r], len = cptr[r + 1] - rb;
+      for (int t = lane; t < width; t += 32) {
+        const int s = t / k, q = t % k;
+        const int64_t c = (int64_t)sorted_block(off, noff, sa, a, s) * k + q;
+        if (c < r) continue;
+        const int64_t pos = c == r ? len - 1 : t - 1;
+        cval[rb + pos] = acc[p * width + t];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void k_dead_diag(int64_t nc, const uint8_t *pdead, const int64_t *cptr, double *cval) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nc;
+       r += (int64_t)gridDim.x * blockDim.x)
+    if (pdead[r]) cval[cptr[r + 1] - 1] = 1.0;
+}
+
+// aggregate pattern of level l+1 (kept in L.gbptr/gbcol), then the k-unknown
+// pattern in level l+1
+static mgpbd_status galerkin_pattern_k(Handle *h, int l) {
+  Level &L = h->lev[l];
+  Level &Lc = h->lev[l + 1];
+  const int k = h->p.nk_vectors, na = L.n_agg;
+  MG_TRY(galerkin_pattern(h, l));  // aggregate pattern, in level l+1's arrays for now
+  int64_t bnnz = 0;
+  MG_TRY(read_i64(h, Lc.ptr + na, &bnnz));
+  if (bnnz > L.cap_gb) {
+    h->arena.release(L.gbcol);
+    L.gbcol = nullptr;
+    MG_TRY(alloc_n(h->arena, &L.gbcol, (size_t)bnnz));
+    L.cap_gb = bnnz;
+  }
+  MG_CUDA(cudaMemcpyAsync(L.gbptr, Lc.ptr, sizeof(int64_t) * ((size_t)na + 1),
+                          cudaMemcpyDeviceToDevice, h->stream));
+  MG_CUDA(cudaMemcpyAsync(L.gbcol, Lc.col, sizeof(int32_t) * (size_t)bnnz,
+                          cudaMemcpyDeviceToDevice, h->stream));
+  const int64_t nc = (int64_t)na * k;
+  MG_TRY(ensure_level(h, l + 1, (int)nc, 0));
+  MG_TRY(ensure_tmp(h, sizeof(int64_t) * ((size_t)nc + 1)));
+  int64_t *cnt = (int64_t *)h->tmp;
+  k_expand_count<<<blocks_for(nc, 256), 256, 0, h->stream>>>(na, k, L.gbptr, cnt);
+  MG_LAUNCH("k_expand_count");
+  MG_TRY(scan_counts(h, cnt, Lc.ptr, nc));
+  MG_TRY(ensure_level(h, l + 1, (int)nc, bnnz * k * k));
+  k_expand_fill<<<blocks_for(nc, 256), 256, 0, h->stream>>>(na, k, L.gbptr, L.gbcol, Lc.ptr,
+                                                            Lc.col);
+  MG_LAUNCH("k_expand_fill");
+  return MGPBD_OK;
+}
+
+static mgpbd_status galerkin_values_k(Handle *h, int l) {
+  Level &L = h->lev[l], &Lc = h->lev[l + 1];
+  const int k = h->p.nk_vectors;
+  const int maxblk = std::max(L.max_coarse_row, 1);
+  const size_t per = sizeof(double) * (size_t)k * maxblk * k;
+  int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (160 * 1024) / per));
+  const size_t smem = (size_t)warps * per;
+  if (smem > 200 * 1024) {
+    set_error("Galerkin: coarse block row too long for shared memory");
+    return MGPBD_E_SETUP;
+  }
+  MG_CUDA(cudaFuncSetAttribute(k_gal_values_k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem));
+  const int blocks = (int)std::min<int64_t>((L.n_agg + warps - 1) / warps, 1 << 20);
+  k_gal_values_k<<<blocks, warps * 32, smem, h->stream>>>(L.n_agg, k, L.mptr, L.mrow, L.ptr,
+                                                         L.col, L.val, L.agg, L.P, L.gbptr,
+                                                         L.gbcol, Lc.ptr, Lc.val, maxblk);
+  MG_LAUNCH("k_gal_values_k");
+  const int64_t nc = (int64_t)L.n_agg * k;
+  k_gal_mirror<<<warp_blocks(nc), 256, 0, h->stream>>>((int)nc, Lc.ptr, Lc.col, Lc.val);
+  MG_LAUNCH("k_gal_mirror");
+  k_dead_diag<<<blocks_for(nc, 256), 256, 0, h->stream>>>(nc, L.pdead, Lc.ptr, Lc.val);
+  MG_LAUNCH("k_dead_diag");
+  return level_precision_copies(h, l + 1);
+}
+
 mgpbd_status amg_setup(Handle *h) {
   if (h->m == 0) {
     h->L = 1;
@@ -862,16 +1090,26 @@ mgpbd_status amg_setup(Handle *h) {
     k_absmax<<<std::min(blocks_for(L0.nnz, th), 4 * num_sms()), th, 0, h->stream>>>(L0.nnz, L0.val,
                                                                                     amax);
     MG_LAUNCH("k_absmax");
-    double *xa = L0.B;
-    MG_TRY(ensure_tmp(h, sizeof(double) * (size_t)h->m));
-    double *xb = (double *)h->tmp;
-    k_nk_init<<<blocks_for(h->m, th), th, 0, h->stream>>>(h->m, h->p.seed_nk, amax, xa);
-    MG_LAUNCH("k_nk_init");
-    for (int s = 0; s < h->p.nk_sweeps; ++s) {
-      k_nk_sweep<<<warp_blocks(h->m), th, 0, h->stream>>>(h->m, L0.ptr, L0.col, L0.val,
-                                                          h->p.nk_omega, xa, xb);
-      MG_LAUNCH("k_nk_sweep");
-      MG_CUDA(cudaMemcpyAsync(xa, xb, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, h->stream));
+    // vector c (of k) from the generator stream seed_nk + c; B is m x k
+    const int k = h->p.nk_vectors;
+    MG_TRY(ensure_tmp(h, sizeof(double) * (size_t)h->m * (k > 1 ? 2 : 1)));
+    for (int c = 0; c < k; ++c) {
+      double *xa = k > 1 ? (double *)h->tmp : L0.B;
+      double *xb = k > 1 ? (double *)h->tmp + h->m : (double *)h->tmp;
+      k_nk_init<<<blocks_for(h->m, th), th, 0, h->stream>>>(h->m, h->p.seed_nk + (uint64_t)c,
+                                                            amax, xa);
+      MG_LAUNCH("k_nk_init");
+      for (int s = 0; s < h->p.nk_sweeps; ++s) {
+        k_nk_sweep<<<warp_blocks(h->m), th, 0, h->stream>>>(h->m, L0.ptr, L0.col, L0.val,
+                                                            h->p.nk_omega, xa, xb);
+        MG_LAUNCH("k_nk_sweep");
+        MG_CUDA(cudaMemcpyAsync(xa, xb, sizeof(double) * h->m, cudaMemcpyDeviceToDevice,
+                                h->stream));
+      }
+      if (k > 1) {
+        k_set_col<<<blocks_for(h->m, th), th, 0, h->stream>>>(h->m, k, c, xa, L0.B);
+        MG_LAUNCH("k_set_col");
+      }
     }
   }
   int l = 0;
@@ -880,17 +1118,30 @@ mgpbd_status amg_setup(Handle *h) {
     if (L.n < h->p.coarse_max || l == h->p.max_levels - 1 || l == kMaxLevels - 1) break;
     MG_TRY(aggregate_level(h, l));
     if (L.n_agg == 0 || L.n_agg == L.n) break;
-    MG_TRY(galerkin_pattern(h, l));
-    Level &Lc = h->lev[l + 1];
-    MG_CUDA(cudaMemsetAsync(L.P, 0, sizeof(double) * L.n, h->stream));  // left-alone rows
-    k_inject<<<warp_blocks(L.n_agg), th, 0, h->stream>>>(L.n_agg, L.mptr, L.mrow, L.B, L.P,
-                                                         Lc.B);
-    MG_LAUNCH("k_inject");
+    const int k = h->p.nk_vectors;
+    if (k == 1) {
+      MG_TRY(galerkin_pattern(h, l));
+      Level &Lc = h->lev[l + 1];
+      MG_CUDA(cudaMemsetAsync(L.P, 0, sizeof(double) * L.n, h->stream));  // left-alone rows
+      k_inject<<<warp_blocks(L.n_agg), th, 0, h->stream>>>(L.n_agg, L.mptr, L.mrow, L.B, L.P,
+                                                           Lc.B);
+      MG_LAUNCH("k_inject");
+    } else {
+      MG_TRY(galerkin_pattern_k(h, l));
+      Level &Lc = h->lev[l + 1];
+      MG_CUDA(cudaMemsetAsync(L.P, 0, sizeof(double) * L.n * k, h->stream));
+      MG_CUDA(cudaMemsetAsync(Lc.B, 0, sizeof(double) * Lc.n * k, h->stream));
+      MG_TRY(ensure_tmp(h, sizeof(double) * (size_t)L.n));
+      k_inject_k<<<blocks_for(L.n_agg, 128), 128, 0, h->stream>>>(
+          L.n_agg, k, L.mptr, L.mrow, L.B, L.P, L.pdead, Lc.B, (double *)h->tmp);
+      MG_LAUNCH("k_inject_k");
+    }
     if (L.P32) {
-      k_to_f32<<<blocks_for(L.n, th), th, 0, h->stream>>>(L.n, L.P, L.P32);
+      k_to_f32<<<blocks_for((int64_t)L.n * k, th), th, 0, h->stream>>>((int64_t)L.n * k, L.P,
+                                                                       L.P32);
       MG_LAUNCH("k_to_f32(P)");
     }
-    MG_TRY(galerkin_values(h, l));
+    MG_TRY(k == 1 ? galerkin_values(h, l) : galerkin_values_k(h, l));
     ++l;
   }
   h->L = l + 1;
@@ -915,7 +1166,8 @@ mgpbd_status amg_setup(Handle *h) {
 }
 
 mgpbd_status galerkin_reform(Handle *h) {
-  for (int l = 0; l + 1 < h->L; ++l) MG_TRY(galerkin_values(h, l));
+  for (int l = 0; l + 1 < h->L; ++l)
+    MG_TRY(h->p.nk_vectors == 1 ? galerkin_values(h, l) : galerkin_values_k(h, l));
   return MGPBD_OK;
 }
 

@@ -304,10 +304,11 @@ __global__ void k_resid(int n, const int64_t *ptr, const int32_t *col, const T *
   }
 }
 
-// b_c[a] = sum_{i in a} P_i r_i (warp per aggregate); with xc given, also the
-// coarse level's first Jacobi sweep from zero, xc[a] = omega_c b_c[a] / A_c,aa
+// b_c[a*k+c] = sum_{i in a} P_ic r_i (warp per aggregate, k columns of P per
+// aggregate); with xc given, also the coarse level's first Jacobi sweep from
+// zero, xc = omega_c b_c / A_c,diag
 template <class T>
-__global__ void k_restrict(int na, const int64_t *mptr, const int32_t *mrow, const T *P,
+__global__ void k_restrict(int na, int k, const int64_t *mptr, const int32_t *mrow, const T *P,
                            const T *r, T *bc, const PcgScalars *sc, const T *dinv_c = nullptr,
                            T om_c = 0, T *xc = nullptr) {
   if (is_done(sc)) return;
@@ -315,15 +316,18 @@ __global__ void k_restrict(int na, const int64_t *mptr, const int32_t *mrow, con
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t a = w; a < na; a += nw) {
-    T acc = 0;
-    for (int64_t q = mptr[a] + lane; q < mptr[a + 1]; q += 32) {
-      int i = mrow[q];
-      acc = fma(P[i], r[i], acc);
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      bc[a] = acc;
-      if (xc) xc[a] = om_c * (acc * dinv_c[a]);
+    for (int c = 0; c < k; ++c) {
+      T acc = 0;
+      for (int64_t q = mptr[a] + lane; q < mptr[a + 1]; q += 32) {
+        int i = mrow[q];
+        acc = fma(P[(int64_t)i * k + c], r[i], acc);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        const int64_t ac = a * k + c;
+        bc[ac] = acc;
+        if (xc) xc[ac] = om_c * (acc * dinv_c[ac]);
+      }
     }
   }
 }
@@ -333,7 +337,7 @@ __global__ void k_restrict(int na, const int64_t *mptr, const int32_t *mrow, con
 constexpr int kProlongRows = 4;
 template <class T>
 __global__ void k_prolong(int n, const int32_t *agg, const T *P, const T *xc, T *x,
-                          const PcgScalars *sc) {
+                          const PcgScalars *sc) {  // one column of P per aggregate
   if (is_done(sc)) return;
   const int64_t tile = (int64_t)blockDim.x * kProlongRows;
   for (int64_t base = blockIdx.x * tile + threadIdx.x; base < n; base += gridDim.x * tile) {
@@ -357,6 +361,21 @@ __global__ void k_prolong(int n, const int32_t *agg, const T *P, const T *xc, T 
       const int64_t i = base + k * (int64_t)blockDim.x;
       if (a[k] >= 0) x[i] = fma(p[k], xc[a[k]], xv[k]);
     }
+  }
+}
+
+// x_i += sum_c P_ic x_c[agg_i*k + c], c ascending (k columns of P per aggregate)
+template <class T>
+__global__ void k_prolong_k(int n, int k, const int32_t *agg, const T *P, const T *xc, T *x,
+                            const PcgScalars *sc) {
+  if (is_done(sc)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int a = agg[i];
+    if (a < 0) continue;  // left-alone rows: P_i = 0
+    T xi = x[i];
+    for (int c = 0; c < k; ++c) xi = fma(P[i * k + c], xc[(int64_t)a * k + c], xi);
+    x[i] = xi;
   }
 }
 
@@ -633,13 +652,18 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in, bool x0_ready 
   Level &Lc = h->lev[l + 1];
   // the coarse level's first Jacobi sweep from zero rides on the restriction
   const bool c_jac = !gs && !cheb && l + 2 < h->L;
+  const int nk = h->p.nk_vectors;
   k_restrict<T><<<blocks_for((int64_t)L.n_agg * 32, 256), 256, 0, h->stream>>>(
-      L.n_agg, L.mptr, L.mrow, Ps<T>(L), r, (T *)Lc.b, sc, c_jac ? dinvs<T>(Lc) : nullptr,
+      L.n_agg, nk, L.mptr, L.mrow, Ps<T>(L), r, (T *)Lc.b, sc, c_jac ? dinvs<T>(Lc) : nullptr,
       (T)Lc.omega, c_jac ? (T *)Lc.x : nullptr);
   MG_LAUNCH("k_restrict");
   MG_TRY(vcycle_level<T>(h, l + 1, (const T *)Lc.b, c_jac));
-  k_prolong<T><<<blocks_for((n + kProlongRows - 1) / kProlongRows, 256), 256, 0, h->stream>>>(
-      n, L.agg, Ps<T>(L), (const T *)Lc.x, x, sc);
+  if (nk == 1)
+    k_prolong<T><<<blocks_for((n + kProlongRows - 1) / kProlongRows, 256), 256, 0, h->stream>>>(
+        n, L.agg, Ps<T>(L), (const T *)Lc.x, x, sc);
+  else
+    k_prolong_k<T><<<blocks_for(n, 256), 256, 0, h->stream>>>(n, nk, L.agg, Ps<T>(L),
+                                                              (const T *)Lc.x, x, sc);
   MG_LAUNCH("k_prolong");
   if (gs) MG_TRY(gs_sweeps(true));
   if (cheb) MG_TRY(cheb_smooth(false));

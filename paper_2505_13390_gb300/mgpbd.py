@@ -38,7 +38,7 @@ class Params(C.Structure):
         ("power_safety", C.c_double), ("coarse_max", C.c_int), ("max_levels", C.c_int),
         ("precision", C.c_int), ("backtrack", C.c_int), ("autotune", C.c_int),
         ("level0_op", C.c_int), ("use_graphs", C.c_int), ("linear_solver", C.c_int),
-        ("seed_nk", C.c_uint64), ("seed_agg", C.c_uint64), ("seed_col", C.c_uint64),
+        ("nk_vectors", C.c_int), ("seed_nk", C.c_uint64), ("seed_agg", C.c_uint64), ("seed_col", C.c_uint64),
         ("seed_pow", C.c_uint64),
     ]
 
@@ -356,14 +356,19 @@ class Solver:
         return vptr, vrow
 
     def level_agg(self, level: int):
+        """(n_agg, agg, root, P, B); P and B are (n,) for one near-kernel
+        vector and (n, k) for k > 1."""
         li = self.level_info(level)
         n = li["n"]
+        k = int(self.params.get("nk_vectors", 1))
         agg = np.zeros(n, np.int32)
         root = np.zeros(n, np.uint8)
-        P = np.zeros(n)
-        B = np.zeros(n)
+        P = np.zeros(n * k)
+        B = np.zeros(n * k)
         _check(load().mgpbd_get_aggregates(self.h, level, _ptr(agg), _ptr(root), _ptr(P), _ptr(B),
                                            MEM_HOST), "get_aggregates")
+        if k > 1:
+            P, B = P.reshape(n, k), B.reshape(n, k)
         return li["n_agg"], agg, root, P, B
 
     def set_colouring(self, enable: bool):

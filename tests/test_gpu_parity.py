@@ -433,3 +433,67 @@ def test_empty_and_single_constraint():
     o, g = Oracle(empty, p), solver(empty, p)
     assert o.step(2)[0] == 0 and g.step(2) >= 0
     assert np.array_equal(o.get_state()[0], g.get_state()[0])
+
+
+# --------------------------------------------------------------------------
+# k = 6 near-kernel vectors (Sec. 4.3): QR prolongator, k unknowns per aggregate
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["cloth8", "hex3", "block6", "arap"])
+def test_setup_bit_exact_six_vectors(name):
+    # small coarse_max so that every case coarsens at least once
+    mesh, p, o, g = both(name, nk_vectors=6, coarse_max=30, max_levels=4)
+    o.begin_frame()
+    g.begin_frame()
+    o.eval_assemble()
+    g.eval_assemble()
+    assert o.prepare_solve() == 0
+    g.prepare_solve()
+    assert o.levels == g.levels and o.levels >= 2
+    for l in range(o.levels):
+        for a, b in zip(o.matrix(l), g.matrix(l)):
+            assert np.array_equal(a, b), f"level {l}"
+        nao, ago, ro, Po, Bo = o.level_agg(l)
+        nag, agg_, rg, Pg, Bg = g.level_agg(l)
+        assert np.array_equal(Bo, Bg), f"level {l} B"
+        if l + 1 < o.levels:
+            assert nao == nag and np.array_equal(ago, agg_) and np.array_equal(ro, rg)
+            assert np.array_equal(Po, Pg), f"level {l} P"
+            lo, wo = o.level_omega(l)
+            lg, wg = g.level_omega(l)
+            assert lg == pytest.approx(lo, rel=1e-10) and wg == pytest.approx(wo, rel=1e-10)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["cloth8", "hex3", "block6"])
+def test_vcycle_parity_six_vectors(name, prec):
+    mesh, p, o, g = both(name, nk_vectors=6, precision=prec)
+    o.begin_frame()
+    g.begin_frame()
+    o.eval_assemble()
+    g.eval_assemble()
+    o.prepare_solve()
+    g.prepare_solve()
+    r = np.random.default_rng(5).standard_normal(mesh.n_rows)
+    zo = o.vcycle(r)
+    zg = g.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
+    tol = 1e-11 if prec == 0 else 1e-4
+    assert np.linalg.norm(zg - zo) <= tol * np.linalg.norm(zo)
+    assert zg @ r > 0
+
+
+@pytest.mark.parametrize("op", [0, 1])
+@pytest.mark.parametrize("name,iters", [("cloth8", 4), ("hex3s", 4), ("arap", 3)])
+def test_iterations_parity_six_vectors(name, iters, op):
+    """Whole global iterations with six near-kernel vectors in FP64, PCG to
+    1e-10: positions within 1e-9 of the oracle."""
+    mesh, p, o, g = both(name, nk_vectors=6, pcg_rtol=1e-10, pcg_maxiter=3000, level0_op=op)
+    o.begin_frame()
+    g.begin_frame()
+    scale = np.abs(mesh.rest_pos).max() + 1e-3
+    for it in range(iters):
+        do, dg = o.iterate(), g.iterate()
+        assert do["ret"] == 0 and dg["ret"] == 0
+        xo, _ = o.get_state()
+        xg, _ = g.get_state()
+        assert np.abs(xg - xo).max() <= 1e-9 * scale, f"iteration {it}"
