@@ -949,11 +949,14 @@ __global__ void k_gal_values_k(int na, int k, const int64_t *mptr, const int32_t
                                const int64_t *ptr, const int32_t *col, const double *val,
                                const int32_t *agg, const double *P, const int64_t *bptr,
                                const int32_t *bcol, const int64_t *cptr, double *cval,
-                               int maxblk) {
+                               int maxblk, double *acc_global) {
   extern __shared__ unsigned char smem_raw[];
   const int wib = threadIdx.x >> 5;
-  const int per = k * maxblk * k;
-  double *acc = reinterpret_cast<double *>(smem_raw) + (size_t)wib * per;
+  const int64_t per = (int64_t)k * maxblk * k;
+  // accumulators: shared memory, or a global slot per warp for long block rows
+  double *acc = acc_global
+                    ? acc_global + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * per
+                    : reinterpret_cast<double *>(smem_raw) + (size_t)wib * per;
   WARP_LOOP(na) {
     const int a = (int)row_;
     const int32_t *off = bcol + bptr[a];
@@ -1053,17 +1056,23 @@ static mgpbd_status galerkin_values_k(Handle *h, int l) {
   const int maxblk = std::max(L.max_coarse_row, 1);
   const size_t per = sizeof(double) * (size_t)k * maxblk * k;
   int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (160 * 1024) / per));
-  const size_t smem = (size_t)warps * per;
-  if (smem > 200 * 1024) {
-    set_error("Galerkin: coarse block row too long for shared memory");
-    return MGPBD_E_SETUP;
+  size_t smem = (size_t)warps * per;
+  int blocks = (int)std::min<int64_t>((L.n_agg + warps - 1) / warps, 1 << 20);
+  double *acc_global = nullptr;
+  if (smem > 160 * 1024) {
+    // block rows too long for shared memory: 256 warps with a global slot each
+    warps = 4;
+    blocks = (int)std::min<int64_t>((L.n_agg + warps - 1) / warps, 64);
+    MG_TRY(ensure_tmp(h, per * (size_t)blocks * warps));
+    acc_global = (double *)h->tmp;
+    smem = 0;
   }
   MG_CUDA(cudaFuncSetAttribute(k_gal_values_k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem));
-  const int blocks = (int)std::min<int64_t>((L.n_agg + warps - 1) / warps, 1 << 20);
   k_gal_values_k<<<blocks, warps * 32, smem, h->stream>>>(L.n_agg, k, L.mptr, L.mrow, L.ptr,
                                                          L.col, L.val, L.agg, L.P, L.gbptr,
-                                                         L.gbcol, Lc.ptr, Lc.val, maxblk);
+                                                         L.gbcol, Lc.ptr, Lc.val, maxblk,
+                                                         acc_global);
   MG_LAUNCH("k_gal_values_k");
   const int64_t nc = (int64_t)L.n_agg * k;
   k_gal_mirror<<<warp_blocks(nc), 256, 0, h->stream>>>((int)nc, Lc.ptr, Lc.col, Lc.val);
