@@ -147,6 +147,7 @@ struct Handle {
   float4 *ginc4 = nullptr;  // FP32 gradient and row id (bits in .w) per incidence
   float *gd32 = nullptr, *gt32 = nullptr, *at32 = nullptr, *w32 = nullptr, *u32 = nullptr;
   int mf_g32 = 8, mf_g64 = 4;  // lanes per vertex of the vertex pass (autotuned)
+  int32_t *vorder = nullptr;   // vertex-pass order: by incidence count within windows
   uint16_t *map = nullptr;
   uint8_t *S = nullptr;  // strength mask, reused per level (grown when a level has more nnz)
   int64_t cap_S = 0;

@@ -17,6 +17,8 @@
 // 4.7 GB for the CSR pass, and about 4x fewer FP64 multiply-adds.
 
 #include <algorithm>
+#include <numeric>
+#include <vector>
 
 #include "common.cuh"
 #include "reduce.cuh"
@@ -87,14 +89,16 @@ __global__ void k_to_f32_mf(int64_t n, const double *a, float *b) {
 // Each lane loads four incidences before it uses them (four gathers in
 // flight); the sum order is the plain lane-strided order.
 template <int G>
-__global__ void k_mf_vertex64(int N, const int64_t *vptr, const int32_t *vrow, const double *ginc,
-                              const double *w, const double *x, double *u, const PcgScalars *sc) {
+__global__ void k_mf_vertex64(int N, const int32_t *vorder, const int64_t *vptr,
+                              const int32_t *vrow, const double *ginc, const double *w,
+                              const double *x, double *u, const PcgScalars *sc) {
   if (sc && is_done(sc)) return;
   GROUP_ROWS(G, N) {
     double a0 = 0, a1 = 0, a2 = 0;
+    const int v = valid ? vorder[i] : 0;
     if (valid) {
-      int64_t q = vptr[i] + g;
-      const int64_t e = vptr[i + 1];
+      int64_t q = vptr[v] + g;
+      const int64_t e = vptr[v + 1];
       for (; q + 3 * G < e; q += 4 * G) {
         double xv[4];
 #pragma unroll
@@ -116,20 +120,21 @@ __global__ void k_mf_vertex64(int N, const int64_t *vptr, const int32_t *vrow, c
     }
     double s = group_sum3<G>(a0, a1, a2, g);
     const int comp = group_sum3_component<G>(g);
-    if (valid && comp < 3 && (g & (G / 4 - 1)) == 0) u[3 * i + comp] = w[i] * s;
+    if (valid && comp < 3 && (g & (G / 4 - 1)) == 0) u[3 * (int64_t)v + comp] = w[v] * s;
   }
 }
 
 template <int G>
 __global__ void __launch_bounds__(256, 8)
-    k_mf_vertex32(int N, const int64_t *vptr, const float4 *ginc, const float *w, const float *x,
-                  float *u, const PcgScalars *sc) {
+    k_mf_vertex32(int N, const int32_t *vorder, const int64_t *vptr, const float4 *ginc,
+                  const float *w, const float *x, float *u, const PcgScalars *sc) {
   if (sc && is_done(sc)) return;
   GROUP_ROWS(G, N) {
     float a0 = 0, a1 = 0, a2 = 0;
+    const int v = valid ? vorder[i] : 0;
     if (valid) {
-      int64_t q = vptr[i] + g;
-      const int64_t e = vptr[i + 1];
+      int64_t q = vptr[v] + g;
+      const int64_t e = vptr[v + 1];
       for (; q + 3 * G < e; q += 4 * G) {
         float4 ev[4];
         float xv[4];
@@ -154,7 +159,7 @@ __global__ void __launch_bounds__(256, 8)
     }
     float s = group_sum3<G>(a0, a1, a2, g);
     const int comp = group_sum3_component<G>(g);
-    if (valid && comp < 3 && (g & (G / 4 - 1)) == 0) u[3 * i + comp] = w[i] * s;
+    if (valid && comp < 3 && (g & (G / 4 - 1)) == 0) u[3 * (int64_t)v + comp] = w[v] * s;
   }
 }
 
@@ -242,6 +247,29 @@ mgpbd_status mf_create(Handle *h) {
   k_vslot<<<blocks_for(h->N, 128), 128, 0, h->stream>>>(h->N, h->E, h->edge, h->tet, h->vptr,
                                                        h->vrow, h->vslot);
   MG_LAUNCH("k_vslot");
+  // Vertex-pass order: within windows of kOrderWindow consecutive vertices,
+  // by incidence count (then id).  A G-lane group loops over its vertex's
+  // incidences, so a warp costs its longest vertex; neighbouring vertices of
+  // the tet lattice alternate between two degrees, and grouping equal
+  // degrees inside a window removes that waste while the warp's vertices stay
+  // close in the mesh (the gathers keep their locality).
+  constexpr int kOrderWindow = 256;
+  std::vector<int64_t> vp((size_t)h->N + 1);
+  MG_CUDA(cudaMemcpyAsync(vp.data(), h->vptr, sizeof(int64_t) * vp.size(), cudaMemcpyDeviceToHost,
+                          h->stream));
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  std::vector<int32_t> ord((size_t)h->N);
+  std::iota(ord.begin(), ord.end(), 0);
+  for (int64_t w0 = 0; w0 < h->N; w0 += kOrderWindow) {
+    auto first = ord.begin() + w0, last = ord.begin() + std::min<int64_t>(h->N, w0 + kOrderWindow);
+    std::stable_sort(first, last, [&](int32_t a, int32_t b) {
+      return vp[a + 1] - vp[a] > vp[b + 1] - vp[b];
+    });
+  }
+  MG_TRY(alloc_n(h->arena, &h->vorder, (size_t)h->N));
+  MG_CUDA(cudaMemcpyAsync(h->vorder, ord.data(), sizeof(int32_t) * ord.size(),
+                          cudaMemcpyHostToDevice, h->stream));
+  MG_CUDA(cudaStreamSynchronize(h->stream));
   return MGPBD_OK;
 }
 
@@ -296,7 +324,7 @@ static mgpbd_status mf_vertex(Handle *h, const double *x, int G = 0, bool check_
   if (G == 0) G = h->mf_g64;
   const PcgScalars *sc = check_done ? h->sc : nullptr;
   MF_G_DISPATCH(G, (k_mf_vertex64<GG><<<mf_vertex_blocks(h, GG), 256, 0, h->stream>>>(
-                       h->N, h->vptr, h->vrow, h->ginc64, h->w, x, h->u64, sc)));
+                       h->N, h->vorder, h->vptr, h->vrow, h->ginc64, h->w, x, h->u64, sc)));
   MG_LAUNCH("k_mf_vertex64");
   return MGPBD_OK;
 }
@@ -305,7 +333,7 @@ static mgpbd_status mf_vertex(Handle *h, const float *x, int G = 0, bool check_d
   if (G == 0) G = h->mf_g32;
   const PcgScalars *sc = check_done ? h->sc : nullptr;
   MF_G_DISPATCH(G, (k_mf_vertex32<GG><<<mf_vertex_blocks(h, GG), 256, 0, h->stream>>>(
-                       h->N, h->vptr, h->ginc4, h->w32, x, h->u32, sc)));
+                       h->N, h->vorder, h->vptr, h->ginc4, h->w32, x, h->u32, sc)));
   MG_LAUNCH("k_mf_vertex32");
   return MGPBD_OK;
 }
