@@ -283,6 +283,15 @@ typedef struct {
   double arrival_s, start_s, finish_s;  /* latency = finish_s - arrival_s */
   int64_t global_iters, pcg_iters;
 } mgpbd_step_result;
+/* Upper estimate of the device bytes an instance of this mesh holds after
+ * create and its first setup (the figure the service admits instances by),
+ * computed on the host from the mesh alone: per nonzero of A (bounded by the
+ * sum over rows of their vertices' degrees) column, FP64 and FP32 values,
+ * assembly map and strength mask; per row, vertex and incidence entry the
+ * vectors, gradients and matrix-free arrays.  For nk_vectors = 1.  No device
+ * work.  MGPBD_E_INVALID for a malformed descriptor. */
+mgpbd_status mgpbd_workspace_size(const mgpbd_mesh_desc *mesh, const mgpbd_params *p,
+                                  size_t *bytes);
 mgpbd_status mgpbd_batch_create(const mgpbd_batch_config *cfg, mgpbd_batch_t **out);
 /* copies the mesh (host pointers) and the initial state (x0/v0 may be NULL:
  * rest positions, zero velocity); the instance is not resident until needed */

@@ -47,19 +47,24 @@ struct Batch {
   size_t resident = 0;  // bytes held by resident instances (reserved estimate while loading)
 };
 
-// upper estimate of an instance's device bytes from its mesh (before create)
-static size_t estimate_bytes(const Instance &in) {
-  const int N = in.desc.n_verts, E = in.desc.n_dist, T = in.desc.n_tet;
+// upper estimate of an instance's device bytes from its mesh (before create):
+// per nonzero of A (bounded by the sum over rows of their vertices' degrees)
+// the column, FP64 and FP32 values, assembly map and strength mask; per row,
+// vertex and incidence entry the vectors, gradients and matrix-free arrays
+static size_t estimate_bytes_desc(const mgpbd_mesh_desc *d) {
+  const int N = d->n_verts, E = d->n_dist, T = d->n_tet;
   std::vector<int64_t> deg((size_t)N, 0);
-  for (int64_t j = 0; j < 2 * (int64_t)E; ++j) deg[in.dist[j]]++;
-  for (int64_t j = 0; j < 4 * (int64_t)T; ++j) deg[in.tet[j]]++;
+  for (int64_t j = 0; j < 2 * (int64_t)E; ++j) deg[d->dist[j]]++;
+  for (int64_t j = 0; j < 4 * (int64_t)T; ++j) deg[d->tet[j]]++;
   double nnz = 0.0;
-  for (int64_t j = 0; j < 2 * (int64_t)E; ++j) nnz += (double)deg[in.dist[j]];
-  for (int64_t j = 0; j < 4 * (int64_t)T; ++j) nnz += (double)deg[in.tet[j]];
+  for (int64_t j = 0; j < 2 * (int64_t)E; ++j) nnz += (double)deg[d->dist[j]];
+  for (int64_t j = 0; j < 4 * (int64_t)T; ++j) nnz += (double)deg[d->tet[j]];
   double m = (double)E + T, ninc = 2.0 * E + 4.0 * T;
   double b = nnz * (4 + 8 + 4 + 2 + 1) + m * 400.0 + N * 200.0 + ninc * 48.0 + (2 << 20);
   return (size_t)b;
 }
+
+static size_t estimate_bytes(const Instance &in) { return estimate_bytes_desc(&in.desc); }
 
 static double now_s(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -116,6 +121,27 @@ using namespace mg;
 struct mgpbd_batch : public Batch {};
 
 extern "C" {
+
+mgpbd_status mgpbd_workspace_size(const mgpbd_mesh_desc *md, const mgpbd_params *p,
+                                  size_t *bytes) {
+  if (!md || !p || !bytes || md->n_verts <= 0 || md->n_dist < 0 || md->n_tet < 0 ||
+      (md->n_dist > 0 && !md->dist) || (md->n_tet > 0 && !md->tet)) {
+    set_error("mgpbd_workspace_size: invalid mesh descriptor");
+    return MGPBD_E_INVALID;
+  }
+  for (int64_t j = 0; j < 2 * (int64_t)md->n_dist; ++j)
+    if (md->dist[j] < 0 || md->dist[j] >= md->n_verts) {
+      set_error("mgpbd_workspace_size: distance vertex out of range");
+      return MGPBD_E_INVALID;
+    }
+  for (int64_t j = 0; j < 4 * (int64_t)md->n_tet; ++j)
+    if (md->tet[j] < 0 || md->tet[j] >= md->n_verts) {
+      set_error("mgpbd_workspace_size: tet vertex out of range");
+      return MGPBD_E_INVALID;
+    }
+  *bytes = estimate_bytes_desc(md);
+  return MGPBD_OK;
+}
 
 mgpbd_status mgpbd_batch_create(const mgpbd_batch_config *cfg, mgpbd_batch_t **out) {
   if (!cfg || !out || cfg->max_active < 1 || cfg->hbm_budget == 0) {

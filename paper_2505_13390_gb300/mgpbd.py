@@ -123,6 +123,7 @@ SIGNATURES = {
     "mgpbd_launch_count": (C.c_ulonglong, []),
     "mgpbd_true_residual_noalloc": (_i, [_vp, _vp, _vp, _vp]),
     "mgpbd_convert": (_i, [_vp, _vp, _vp, _vp, _i64, _vp]),
+    "mgpbd_workspace_size": (_i, [C.POINTER(MeshDesc), C.POINTER(Params), C.POINTER(C.c_size_t)]),
     "mgpbd_batch_create": (_i, [C.POINTER(BatchConfig), C.POINTER(_vp)]),
     "mgpbd_batch_add_instance": (_i, [_vp, C.POINTER(MeshDesc), C.POINTER(Params), _vp, _vp,
                                       C.POINTER(_i)]),
@@ -153,6 +154,21 @@ def load(path: str = LIB_PATH):
 
 def launch_count() -> int:
     return int(load().mgpbd_launch_count())
+
+
+def workspace_size(mesh, params: Dict) -> int:
+    """Upper estimate of an instance's device bytes (mgpbd_workspace_size)."""
+    keep = [np.ascontiguousarray(mesh.rest_pos, np.float64),
+            np.ascontiguousarray(mesh.inv_mass, np.float64),
+            np.ascontiguousarray(mesh.dist, np.int32).reshape(-1, 2),
+            np.ascontiguousarray(mesh.tet, np.int32).reshape(-1, 4),
+            np.ascontiguousarray(mesh.alpha, np.float64)]
+    md = MeshDesc(mesh.n_verts, _ptr(keep[0]), _ptr(keep[1]), mesh.n_dist, _ptr(keep[2]),
+                  mesh.n_tet, _ptr(keep[3]), _ptr(keep[4]), int(getattr(mesh, "tet_kind", 0)))
+    p = make_params(params)
+    out = C.c_size_t()
+    _check(load().mgpbd_workspace_size(C.byref(md), C.byref(p), C.byref(out)), "workspace_size")
+    return int(out.value)
 
 
 def convert(in64=None, out32=None, in32=None, out64=None, stream=None) -> None:

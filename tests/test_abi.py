@@ -4,6 +4,8 @@ import ctypes as C
 import os
 import re
 
+import pytest
+
 from paper_2505_13390_gb300 import build as B
 from paper_2505_13390_gb300 import mgpbd
 
@@ -38,3 +40,19 @@ def test_default_params_and_host_only_calls():
     assert not h.value
     assert lib.mgpbd_step(None, 1) == mgpbd.E_INVALID
     assert isinstance(lib.mgpbd_last_error(), bytes)
+
+
+def test_workspace_size_is_host_only_and_grows_with_the_mesh():
+    """mgpbd_workspace_size needs no device: it sizes an instance from its mesh."""
+    from paper_2505_13390_gb300 import mgpbd
+    from paper_2505_13390_gb300.meshgen import cloth, default_params, hex_block
+    p = default_params()
+    small = mgpbd.workspace_size(cloth(8, plane="xz"), p)
+    big = mgpbd.workspace_size(cloth(32, plane="xz"), p)
+    beam = mgpbd.workspace_size(hex_block(10, 4, 4, h=0.01), p)
+    assert 0 < small < big and beam > big
+    bad = cloth(8, plane="xz")
+    bad.dist = bad.dist.copy()
+    bad.dist[0, 0] = bad.n_verts  # out of range
+    with pytest.raises(mgpbd.MgpbdError):
+        mgpbd.workspace_size(bad, p)

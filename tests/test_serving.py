@@ -115,3 +115,18 @@ def test_late_arrivals_join_while_others_run():
     r0 = res[0]
     assert any(r["start_s"] < r0["finish_s"] for r in res[1:])  # overlapped on the GPU
     assert all(r["start_s"] >= r["arrival_s"] for r in res)
+
+
+def test_workspace_size_bounds_the_device_bytes():
+    """The admission estimate (mgpbd_workspace_size) is not below what an
+    instance really holds after create and its first setup."""
+    from paper_2505_13390_gb300.mgpbd import Solver, workspace_size
+    for mesh, p in meshes():
+        p = common(p, 1)
+        est = workspace_size(mesh, p)
+        g = Solver(mesh, p)
+        g.begin_frame()
+        g.iterate()
+        held = g.stats()["device_bytes"]
+        g.close()
+        assert held <= est, (mesh.name, held, est)
