@@ -288,8 +288,9 @@ typedef struct {
  * computed on the host from the mesh alone: per nonzero of A (bounded by the
  * sum over rows of their vertices' degrees) column, FP64 and FP32 values,
  * assembly map and strength mask; per row, vertex and incidence entry the
- * vectors, gradients and matrix-free arrays.  For nk_vectors = 1.  No device
- * work.  MGPBD_E_INVALID for a malformed descriptor. */
+ * vectors, gradients and matrix-free arrays; the dense coarsest factor and
+ * inverse for a coarsest level below p->coarse_max rows.  For nk_vectors = 1.
+ * No device work.  MGPBD_E_INVALID for a malformed descriptor. */
 mgpbd_status mgpbd_workspace_size(const mgpbd_mesh_desc *mesh, const mgpbd_params *p,
                                   size_t *bytes);
 mgpbd_status mgpbd_batch_create(const mgpbd_batch_config *cfg, mgpbd_batch_t **out);

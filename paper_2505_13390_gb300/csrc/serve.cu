@@ -50,8 +50,10 @@ struct Batch {
 // upper estimate of an instance's device bytes from its mesh (before create):
 // per nonzero of A (bounded by the sum over rows of their vertices' degrees)
 // the column, FP64 and FP32 values, assembly map and strength mask; per row,
-// vertex and incidence entry the vectors, gradients and matrix-free arrays
-static size_t estimate_bytes_desc(const mgpbd_mesh_desc *d) {
+// vertex and incidence entry the vectors, gradients and matrix-free arrays;
+// the dense coarsest factor and inverse (3 n_c^2 doubles, n_c below
+// coarse_max or the whole system when it is smaller)
+static size_t estimate_bytes_desc(const mgpbd_mesh_desc *d, const mgpbd_params *p) {
   const int N = d->n_verts, E = d->n_dist, T = d->n_tet;
   std::vector<int64_t> deg((size_t)N, 0);
   for (int64_t j = 0; j < 2 * (int64_t)E; ++j) deg[d->dist[j]]++;
@@ -61,10 +63,12 @@ static size_t estimate_bytes_desc(const mgpbd_mesh_desc *d) {
   for (int64_t j = 0; j < 4 * (int64_t)T; ++j) nnz += (double)deg[d->tet[j]];
   double m = (double)E + T, ninc = 2.0 * E + 4.0 * T;
   double b = nnz * (4 + 8 + 4 + 2 + 1) + m * 400.0 + N * 200.0 + ninc * 48.0 + (2 << 20);
+  const double nc = std::min(m, (double)std::max(p->coarse_max, 1));
+  b += 24.0 * nc * nc;
   return (size_t)b;
 }
 
-static size_t estimate_bytes(const Instance &in) { return estimate_bytes_desc(&in.desc); }
+static size_t estimate_bytes(const Instance &in) { return estimate_bytes_desc(&in.desc, &in.p); }
 
 static double now_s(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -139,7 +143,7 @@ mgpbd_status mgpbd_workspace_size(const mgpbd_mesh_desc *md, const mgpbd_params 
       set_error("mgpbd_workspace_size: tet vertex out of range");
       return MGPBD_E_INVALID;
     }
-  *bytes = estimate_bytes_desc(md);
+  *bytes = estimate_bytes_desc(md, p);
   return MGPBD_OK;
 }
 

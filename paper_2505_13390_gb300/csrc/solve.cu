@@ -143,15 +143,26 @@ __global__ void k_top_prep(int64_t n, const double *r, T *bl, const T *dinv, T o
 __global__ void k_p_update(int64_t n, double *p, const double *z, const PcgScalars *sc) {
   if (is_done(sc)) return;
   const double be = sc->beta;
-  const int64_t n2 = n / 2;
+  const int64_t n2 = n / 2, h2 = (n2 + 1) / 2;  // pairs k and k + h2 per thread
   double2 *p2 = reinterpret_cast<double2 *>(p);
   const double2 *z2 = reinterpret_cast<const double2 *>(z);
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n2;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < h2;
        k += (int64_t)gridDim.x * blockDim.x) {
-    double2 pv = p2[k], zv = z2[k];
-    pv.x = fma(be, pv.x, zv.x);
-    pv.y = fma(be, pv.y, zv.y);
-    p2[k] = pv;
+    const int64_t k2 = k + h2;
+    const bool two = k2 < n2;
+    double2 pa = p2[k], za = z2[k], pb = {0.0, 0.0}, zb = {0.0, 0.0};
+    if (two) {
+      pb = p2[k2];
+      zb = z2[k2];
+    }
+    pa.x = fma(be, pa.x, za.x);
+    pa.y = fma(be, pa.y, za.y);
+    p2[k] = pa;
+    if (two) {
+      pb.x = fma(be, pb.x, zb.x);
+      pb.y = fma(be, pb.y, zb.y);
+      p2[k2] = pb;
+    }
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) p[n - 1] = fma(be, p[n - 1], z[n - 1]);
 }
@@ -551,6 +562,7 @@ const double *Ps<double>(const Level &L) { return L.P; }
 template <>
 const float *Ps<float>(const Level &L) { return L.P32; }
 
+
 // V-cycle on level l in precision T: L.b -> L.x (zero start).  On level 0 of
 // a top V-cycle, `x0_ready` says the first Jacobi sweep is already in L.x,
 // and `top` lets the last matrix-free sweep write z in FP64 (and r.z)
@@ -796,7 +808,8 @@ static mgpbd_status pcg_iteration(Handle *h, double *x) {
         jac ? (double *)L.x : nullptr);
   MG_LAUNCH("k_xr_update");
   MG_TRY(vcycle_top(h, r, z, true, DOT_RZ));
-  k_p_update<<<blocks_for(std::max(1, m / 2), 256), 256, 0, h->stream>>>(m, p, z, h->sc);
+  k_p_update<<<blocks_for(std::max(1, (m / 2 + 1) / 2), 256), 256, 0, h->stream>>>(m, p, z,
+                                                                                 h->sc);
   MG_LAUNCH("k_p_update");
   return MGPBD_OK;
 }
