@@ -43,11 +43,11 @@ FULL_PCG_ITERS = 7300
 # (k_jacobi<16, float>, 494.52 MB for 59,625,809 nonzeros); the sweep's
 # traffic grows in proportion to nnz, so it scales to a full launch
 SWEEP_TRAFFIC_PER_NNZ = (489.342720e6 + 5.179904e6) / 59_625_809
-# DRAM bytes of one matrix-free level-0 FP32 sweep (k_mf_vertex32<8> 30.51 MB
+# DRAM bytes of one matrix-free level-0 FP32 sweep (k_mf_vertex32<8> 30.74 MB
 # + k_mf_row<float,0> 33.68 MB) per constraint row, from the ncu captures in
 # profiles/k_mf_sweep_level0_block40x33x40.md (593,633 rows); the passes
 # stream per-row and per-incidence arrays, so traffic scales with the rows
-MF_SWEEP_TRAFFIC_PER_ROW = (30.513152e6 + 33.678592e6) / 593_633
+MF_SWEEP_TRAFFIC_PER_ROW = (30.742016e6 + 33.679104e6) / 593_633
 SAMPLE = (4, 33, 4)     # oracle sample: cells along x, y (vertical), z
 SAMPLE_PCG = 500        # PCG iterations per sampled global iteration (cost is linear in them)
 

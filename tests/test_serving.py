@@ -86,13 +86,11 @@ def test_budget_evicts_and_restores_state():
     ms = meshes()
     reqs = trace(len(ms), 2, 0.0)
     _, _, roomy = serve(ms, 0, 2, 64 << 30, reqs)
-    # about two instances fit: the others wait, and idle ones are evicted
-    from paper_2505_13390_gb300.mgpbd import Batch
-    probe = Batch(64 << 30, 1)
-    i = probe.add(*[ms[-1][0], common(ms[-1][1], 0)])
-    probe.run([(0, i, 1, 0.0)])
-    n, one = probe.resident()
-    probe.close()
+    # about two instances fit: the others wait, and idle ones are evicted.
+    # Admission reserves an instance's estimate (mgpbd_workspace_size) while
+    # it loads, so the budget is sized from the largest estimate.
+    from paper_2505_13390_gb300.mgpbd import workspace_size
+    one = max(workspace_size(m, common(p, 0)) for m, p in ms)
     st, res, tight = serve(ms, 0, 2, int(2.5 * one), reqs)
     assert st >= 0 and all(r["status"] >= 0 for r in res)
     for (x1, v1), (x2, v2) in zip(roomy, tight):
