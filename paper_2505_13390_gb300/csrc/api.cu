@@ -1,7 +1,10 @@
 // C ABI of the GB300 MGPBD library: handle lifecycle, state I/O, the
 // Algorithm 1 driver (frame prologue, global iterations, epilogue) and the
-// inspection getters.  Compute happens in the kernels of pattern.cu,
-// physics.cu, setup.cu and solve.cu.
+// inspection getters.  Compute happens in the kernels of pattern.cu
+// (incidence, CSR pattern), physics.cu (constraints, assembly, updates),
+// setup.cu (AMG setup and Galerkin products), solve.cu (MGPCG, V-cycle,
+// smoothers) and mfree.cu (matrix-free level-0 products); serve.cu holds the
+// multi-instance service and noalloc.cu the allocation-free residual.
 #include <stdio.h>
 #include <string.h>
 

@@ -14,7 +14,9 @@
 //                their strongest pass-1 neighbour (ties: smaller aggregate
 //                id, then smaller neighbour index)
 //   inject       P_i = B_i / |B_agg|, next near-kernel B_{l+1}[a] = |B_agg|
-//                (k = 1 QR), |B_agg| summed over members in ascending order
+//                (k = 1 QR), |B_agg| summed over members in ascending order;
+//                with k > 1 vectors a modified Gram-Schmidt QR per aggregate
+//                (k columns of P, k unknowns per coarse aggregate)
 //   Galerkin     A_{l+1} = P^T A_l P; entry (a,b), b >= a, accumulates
 //                fma(P_i*A_ij, P_j, acc) over member rows i of a ascending and
 //                row i's storage order; entries with b < a copy (b,a)
