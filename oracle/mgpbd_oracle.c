@@ -988,6 +988,54 @@ static void level_alloc_work(orc_level *L) {
   L->t = (double *)xcalloc((size_t)n, sizeof(double));
 }
 
+/* Node matrix of a coarse level with k unknowns per node (k > 1): node a
+   holds rows a*k .. a*k+k-1; its row lists the nodes its rows reach (off-
+   diagonals ascending, itself last) with the Frobenius norm of each k x k
+   block, |A_ab|_F = sqrt(sum over rows p ascending and their storage order
+   of fma(v, v, .)).  Aggregating nodes keeps a node's k unknowns together
+   (smoothed-aggregation practice for several near-kernel vectors). */
+static void node_matrix(const orc_csr *A, int k, orc_csr *N) {
+  int nn = A->n / k;
+  N->n = nn;
+  N->ptr = (int64_t *)xcalloc((size_t)nn + 1, sizeof(int64_t));
+  int32_t *mark = (int32_t *)xcalloc((size_t)nn, sizeof(int32_t));
+  int32_t *slot = (int32_t *)xcalloc((size_t)nn, sizeof(int32_t));
+  for (int a = 0; a < nn; ++a) mark[a] = -1;
+  for (int a = 0; a < nn; ++a) {
+    int cnt = 0;
+    for (int p = 0; p < k; ++p)
+      for (int64_t e = A->ptr[a * k + p]; e < A->ptr[a * k + p + 1]; ++e) {
+        int b = A->col[e] / k;
+        if (mark[b] != a) { mark[b] = a; ++cnt; }
+      }
+    N->ptr[a + 1] = N->ptr[a] + cnt;
+  }
+  N->nnz = N->ptr[nn];
+  N->col = (int32_t *)xcalloc((size_t)N->nnz, sizeof(int32_t));
+  N->val = (double *)xcalloc((size_t)N->nnz, sizeof(double));
+  for (int a = 0; a < nn; ++a) mark[a] = -1;
+  for (int a = 0; a < nn; ++a) {
+    int64_t base = N->ptr[a];
+    int cnt = 0;
+    for (int p = 0; p < k; ++p)
+      for (int64_t e = A->ptr[a * k + p]; e < A->ptr[a * k + p + 1]; ++e) {
+        int b = A->col[e] / k;
+        if (b != a && mark[b] != a) { mark[b] = a; N->col[base + cnt++] = b; }
+      }
+    qsort(N->col + base, (size_t)cnt, sizeof(int32_t), cmp_i32c);
+    N->col[base + cnt] = a;
+    for (int t = 0; t <= cnt; ++t) slot[N->col[base + t]] = t;
+    for (int p = 0; p < k; ++p)
+      for (int64_t e = A->ptr[a * k + p]; e < A->ptr[a * k + p + 1]; ++e) {
+        double v = A->val[e];
+        double *c = N->val + base + slot[A->col[e] / k];
+        *c = fma(v, v, *c);
+      }
+    for (int t = 0; t <= cnt; ++t) N->val[base + t] = sqrt(N->val[base + t]);
+  }
+  free(mark); free(slot);
+}
+
 /* Full setup from the current level-0 matrix (Sec. 4.1, setup-pipeline figure): level 0 takes the
    near-kernel sweeps; each level filters, aggregates, injects and forms the
    next Galerkin operator, until the size is below coarse_max or max_levels is
@@ -1007,13 +1055,29 @@ static int setup(orc *o) {
     int n = L->A.n;
     if (!L->x) level_alloc_work(L);
     if (n < o->p.coarse_max || l == o->p.max_levels - 1 || l == ORC_MAXL - 1) break;
-    uint8_t *S = strength(&L->A, o->p.theta_s);
     L->agg = (int32_t *)xcalloc((size_t)n, sizeof(int32_t));
     L->root = (uint8_t *)xcalloc((size_t)n, 1);
-    int na = aggregate(&L->A, S, o->p.seed_agg, l, L->agg, L->root);
-    free(S);
+    const int k = o->p.nk_vectors;
+    int na, units = n;
+    if (k > 1 && l > 0) {
+      /* coarse levels with k unknowns per node aggregate whole nodes */
+      orc_csr N;
+      memset(&N, 0, sizeof(N));
+      node_matrix(&L->A, k, &N);
+      units = N.n;
+      uint8_t *S = strength(&N, o->p.theta_s);
+      int32_t *nagg = (int32_t *)xcalloc((size_t)N.n, sizeof(int32_t));
+      uint8_t *nroot = (uint8_t *)xcalloc((size_t)N.n, 1);
+      na = aggregate(&N, S, o->p.seed_agg, l, nagg, nroot);
+      for (int i = 0; i < n; ++i) { L->agg[i] = nagg[i / k]; L->root[i] = nroot[i / k]; }
+      free(S); free(nagg); free(nroot); csr_free(&N);
+    } else {
+      uint8_t *S = strength(&L->A, o->p.theta_s);
+      na = aggregate(&L->A, S, o->p.seed_agg, l, L->agg, L->root);
+      free(S);
+    }
     if (na < 0) return ORC_E_SETUP;
-    if (na == 0 || na == n) { /* nothing to coarsen: stop here */
+    if (na == 0 || na == units) { /* nothing to coarsen: stop here */
       free(L->agg); free(L->root); L->agg = NULL; L->root = NULL;
       break;
     }

@@ -139,3 +139,48 @@ def test_one_vector_is_unchanged():
     for l in range(o.levels):
         for a, b in zip(o.matrix(l), o1.matrix(l)):
             assert np.array_equal(a, b)
+
+
+def node_matrix_numpy(ptr, col, val, k):
+    """Block Frobenius norms of a k-unknowns-per-node CSR, diagonal last."""
+    n = len(ptr) - 1
+    nn = n // k
+    blocks = [dict() for _ in range(nn)]
+    for r in range(n):
+        a = r // k
+        for e in range(ptr[r], ptr[r + 1]):
+            b = col[e] // k
+            blocks[a][b] = blocks[a].get(b, 0.0) + val[e] ** 2
+    nptr, ncol, nval = [0], [], []
+    for a in range(nn):
+        off = sorted(b for b in blocks[a] if b != a)
+        for b in off + [a]:
+            ncol.append(b)
+            nval.append(np.sqrt(blocks[a][b]))
+        nptr.append(len(ncol))
+    return np.array(nptr), np.array(ncol), np.array(nval)
+
+
+def test_coarse_levels_aggregate_whole_nodes():
+    """With k > 1 the coarse levels aggregate nodes (the k unknowns of a
+    coarse aggregate stay together): the aggregates equal the pinned MIS-2
+    rule applied to the block-norm node matrix built here in numpy, and the
+    hierarchy keeps coarsening."""
+    from oracle.oracle import aggregate_csr
+    mesh = hex_block(8, 4, 4, h=0.01, jitter=0.1, alpha=1e-7, pin="x0", seed=4)
+    p = default_params(coarse_max=30, max_levels=5, nk_vectors=K)
+    o = Oracle(mesh, p)
+    o.begin_frame()
+    o.eval_assemble()
+    assert o.prepare_solve() == 0
+    sizes = [len(o.matrix(l)[0]) - 1 for l in range(o.levels)]
+    assert o.levels >= 3 and all(b < a for a, b in zip(sizes, sizes[1:]))
+    for l in range(1, o.levels - 1):
+        ptr, col, val = o.matrix(l)
+        na, agg, root, _, _ = o.level_agg(l)
+        nptr, ncol, nval = node_matrix_numpy(ptr, col, val, K)
+        ref_na, ref_agg, ref_root, _ = aggregate_csr(nptr, ncol, nval, p["theta_s"],
+                                                     p["seed_agg"], l)
+        assert na == ref_na
+        assert np.array_equal(agg, np.repeat(ref_agg, K))
+        assert np.array_equal(root, np.repeat(ref_root, K))
