@@ -741,10 +741,11 @@ static mgpbd_status colour_groups(Handle *h, int l) {
   return MGPBD_OK;
 }
 
-// aggregation of level l: fills L.agg, L.root, L.n_agg and the member lists
-static mgpbd_status aggregate_level(Handle *h, int l) {
-  Level &L = h->lev[l];
-  const int n = L.n;
+// strength filter + MIS-2 aggregation of a CSR (the rows of a level, or its
+// nodes): agg, root and the number of aggregates
+static mgpbd_status mis2_aggregate(Handle *h, int l, int n, int64_t nnz, const int64_t *ptr,
+                                   const int32_t *col, const double *val, int32_t *agg,
+                                   uint8_t *root, int64_t *na_out) {
   const int th = 256;
   // scratch: state u8 | e1 u8 | m1p u64 | m1i i32 | p1 i32 | flags i64 | ids i64 (n+1)
   size_t off_state = 0, off_e1 = (size_t)n, off_m1p = ((2 * (size_t)n + 15) / 16) * 16;
@@ -754,50 +755,47 @@ static mgpbd_status aggregate_level(Handle *h, int l) {
   MG_TRY(ensure_tmp(h, need));
   // with k > 1 unknowns per aggregate a coarse level can hold more nonzeros
   // than level 0, for which the strength mask was sized
-  if (L.nnz > h->cap_S) {
+  if (nnz > h->cap_S) {
     h->arena.release(h->S);
     h->S = nullptr;
-    MG_TRY(alloc_n(h->arena, &h->S, (size_t)L.nnz));
-    h->cap_S = L.nnz;
+    MG_TRY(alloc_n(h->arena, &h->S, (size_t)nnz));
+    h->cap_S = nnz;
   }
   char *base = (char *)h->tmp;
   uint8_t *state = (uint8_t *)(base + off_state), *e1 = (uint8_t *)(base + off_e1);
   uint64_t *m1p = (uint64_t *)(base + off_m1p);
   int *m1i = (int *)(base + off_m1i), *p1 = (int *)(base + off_p1);
   int64_t *f64 = (int64_t *)(base + off_f), *ids = (int64_t *)(base + off_ids);
-  k_strength<<<warp_blocks(n), th, 0, h->stream>>>(n, L.ptr, L.col, L.val, h->p.theta_s, h->S,
-                                                   state);
+  k_strength<<<warp_blocks(n), th, 0, h->stream>>>(n, ptr, col, val, h->p.theta_s, h->S, state);
   MG_LAUNCH("k_strength");
   for (int round = 0;; ++round) {
     if (round > 100000) {
       set_error("MIS-2 did not terminate");
       return MGPBD_E_SETUP;
     }
-    k_mis_m1<<<warp_blocks(n), th, 0, h->stream>>>(n, L.ptr, L.col, h->S, state, h->p.seed_agg,
-                                                   l, m1p, m1i);
+    k_mis_m1<<<warp_blocks(n), th, 0, h->stream>>>(n, ptr, col, h->S, state, h->p.seed_agg, l,
+                                                   m1p, m1i);
     MG_LAUNCH("k_mis_m1");
-    k_mis_m2<<<warp_blocks(n), th, 0, h->stream>>>(n, L.ptr, L.col, h->S, m1p, m1i, state);
+    k_mis_m2<<<warp_blocks(n), th, 0, h->stream>>>(n, ptr, col, h->S, m1p, m1i, state);
     MG_LAUNCH("k_mis_m2");
-    k_mis_e1<<<warp_blocks(n), th, 0, h->stream>>>(n, L.ptr, L.col, h->S, state, e1);
+    k_mis_e1<<<warp_blocks(n), th, 0, h->stream>>>(n, ptr, col, h->S, state, e1);
     MG_LAUNCH("k_mis_e1");
     MG_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
-    k_mis_e2<<<warp_blocks(n), th, 0, h->stream>>>(n, L.ptr, L.col, h->S, e1, state, h->flag);
+    k_mis_e2<<<warp_blocks(n), th, 0, h->stream>>>(n, ptr, col, h->S, e1, state, h->flag);
     MG_LAUNCH("k_mis_e2");
     int rem = 0;
     MG_TRY(read_int(h, h->flag, &rem));
     if (rem == 0) break;
   }
-  k_root_flags<<<blocks_for(n, th), th, 0, h->stream>>>(n, state, L.root, f64);
+  k_root_flags<<<blocks_for(n, th), th, 0, h->stream>>>(n, state, root, f64);
   MG_LAUNCH("k_root_flags");
   MG_TRY(scan_counts(h, f64, ids, n));
   int64_t na = 0;
   MG_TRY(read_i64(h, ids + n, &na));
-  L.n_agg = (int)na;
-  k_agg_pass1<<<warp_blocks(n), th, 0, h->stream>>>(n, L.ptr, L.col, h->S, L.root, ids, p1);
+  k_agg_pass1<<<warp_blocks(n), th, 0, h->stream>>>(n, ptr, col, h->S, root, ids, p1);
   MG_LAUNCH("k_agg_pass1");
   MG_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
-  k_agg_pass2<<<warp_blocks(n), th, 0, h->stream>>>(n, L.ptr, L.col, L.val, h->S, p1, L.agg,
-                                                    h->flag);
+  k_agg_pass2<<<warp_blocks(n), th, 0, h->stream>>>(n, ptr, col, val, h->S, p1, agg, h->flag);
   MG_LAUNCH("k_agg_pass2");
   int bad = 0;
   MG_TRY(read_int(h, h->flag, &bad));
@@ -805,8 +803,97 @@ static mgpbd_status aggregate_level(Handle *h, int l) {
     set_error("aggregation left a row unassigned");
     return MGPBD_E_SETUP;
   }
-  if (na == 0 || na == n) return MGPBD_OK;  // nothing to coarsen; caller stops here
-  // member lists
+  *na_out = na;
+  return MGPBD_OK;
+}
+
+// node matrix of a level with k unknowns per node: the Frobenius norm of each
+// k x k block of the node pattern (off-diagonal nodes ascending, the node
+// itself last), summed over rows p ascending and their storage order
+__global__ void k_node_norms(int nn, int k, const int64_t *ptr, const int32_t *col,
+                             const double *val, const int64_t *nptr, const int32_t *ncol,
+                             double *nval) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nn; a += gridDim.x * blockDim.x) {
+    const int64_t base = nptr[a];
+    const int deg = (int)(nptr[a + 1] - base), noff = deg - 1;
+    for (int t = 0; t < deg; ++t) nval[base + t] = 0.0;
+    for (int p = 0; p < k; ++p) {
+      const int64_t r = (int64_t)a * k + p;
+      for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) {
+        const int b = col[e] / k;
+        int t = noff;
+        if (b != a) {
+          int lo = 0, hi = noff;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (ncol[base + mid] < b) lo = mid + 1;
+            else hi = mid;
+          }
+          t = lo;
+        }
+        const double v = val[e];
+        nval[base + t] = fma(v, v, nval[base + t]);
+      }
+    }
+    for (int t = 0; t < deg; ++t) nval[base + t] = sqrt(nval[base + t]);
+  }
+}
+
+__global__ void k_expand_nodes(int n, int k, const int32_t *nagg, const uint8_t *nroot,
+                               int32_t *agg, uint8_t *root) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    agg[i] = nagg[i / k];
+    root[i] = nroot[i / k];
+  }
+}
+
+// aggregation of level l: fills L.agg, L.root, L.n_agg and the member lists
+// (L.n_agg = 0 when the level does not coarsen).  With k > 1 unknowns per
+// node, coarse levels aggregate whole nodes: the node matrix comes from the
+// aggregate pattern the level was built from (level l-1's gbptr/gbcol).
+static mgpbd_status aggregate_level(Handle *h, int l) {
+  Level &L = h->lev[l];
+  const int n = L.n;
+  const int th = 256;
+  const int k = h->p.nk_vectors;
+  int64_t na = 0;
+  int units = n;
+  if (k > 1 && l > 0) {
+    const Level &Lp = h->lev[l - 1];
+    const int nn = n / k;
+    units = nn;
+    int64_t nnz_n = 0;
+    MG_TRY(read_i64(h, Lp.gbptr + nn, &nnz_n));
+    double *nval = nullptr;
+    int32_t *nagg = nullptr;
+    uint8_t *nroot = nullptr;
+    MG_TRY(alloc_n(h->arena, &nval, (size_t)nnz_n));
+    MG_TRY(alloc_n(h->arena, &nagg, (size_t)nn));
+    MG_TRY(alloc_n(h->arena, &nroot, (size_t)nn));
+    k_node_norms<<<blocks_for(nn, 128), 128, 0, h->stream>>>(nn, k, L.ptr, L.col, L.val, Lp.gbptr,
+                                                            Lp.gbcol, nval);
+    MG_LAUNCH("k_node_norms");
+    mgpbd_status st =
+        mis2_aggregate(h, l, nn, nnz_n, Lp.gbptr, Lp.gbcol, nval, nagg, nroot, &na);
+    if (st >= 0) {
+      k_expand_nodes<<<blocks_for(n, th), th, 0, h->stream>>>(n, k, nagg, nroot, L.agg, L.root);
+      MG_LAUNCH("k_expand_nodes");
+    }
+    h->arena.release(nval);
+    h->arena.release(nagg);
+    h->arena.release(nroot);
+    MG_TRY(st);
+  } else {
+    MG_TRY(mis2_aggregate(h, l, n, L.nnz, L.ptr, L.col, L.val, L.agg, L.root, &na));
+  }
+  L.n_agg = (int)na;
+  if (na == 0 || na == units) {  // nothing to coarsen; caller stops here
+    L.n_agg = 0;
+    return MGPBD_OK;
+  }
+  // member lists (over rows)
+  MG_TRY(ensure_tmp(h, sizeof(int64_t) * (2 * (size_t)n + 2)));
+  int64_t *f64 = (int64_t *)h->tmp, *ids = f64 + n + 1;
   unsigned long long *cnt = (unsigned long long *)f64;  // reuse (na <= n)
   MG_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * na, h->stream));
   k_mem_count<<<blocks_for(n, th), th, 0, h->stream>>>(n, L.agg, cnt);
