@@ -925,23 +925,22 @@ mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *
 // Reads up to 256 MB of the level-0 matrix values, so that a kernel timed by
 // the autotuner starts from the cache state it meets inside a V-cycle (its
 // data evicted by the level-0 passes), not hot from its previous repetition.
-__global__ void k_evict(const double4 *p, int64_t n, int *sink) {
+__global__ void k_evict(const ulonglong2 *p, int64_t n, int *sink) {
   unsigned long long acc = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double4 v = p[i];
-    acc ^= __double_as_longlong(v.x) ^ __double_as_longlong(v.y) ^ __double_as_longlong(v.z) ^
-           __double_as_longlong(v.w);
+    const ulonglong2 v = p[i];
+    acc ^= v.x ^ v.y;
   }
   if (acc == 0x5eed5eed5eed5eedull) *sink = 1;  // keeps the loads
 }
 
 mgpbd_status evict_l2(Handle *h) {
   const Level &L = h->lev[0];
-  const int64_t n = std::min<int64_t>(L.nnz / 4, (256ll << 20) / 32);
+  const int64_t n = std::min<int64_t>(L.nnz / 2, (256ll << 20) / 16);
   if (n <= 0 || !L.val) return MGPBD_OK;
   k_evict<<<std::min<int64_t>(4 * num_sms(), (n + 255) / 256), 256, 0, h->stream>>>(
-      reinterpret_cast<const double4 *>(L.val), n, reinterpret_cast<int *>(h->partials + 4096 + 15));
+      reinterpret_cast<const ulonglong2 *>(L.val), n, reinterpret_cast<int *>(h->partials + 4096 + 15));
   MG_LAUNCH("k_evict");
   return MGPBD_OK;
 }
