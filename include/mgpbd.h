@@ -138,6 +138,7 @@ typedef struct {
   double op_complexity; /* sum nnz_l / nnz_0 (Table 1 column C) */
   size_t device_bytes;  /* device memory held by the handle */
   double ms_setup, ms_galerkin, ms_solve, ms_other; /* accumulated phase times */
+  size_t peak_device_bytes; /* high-water mark of device_bytes since create */
 } mgpbd_stats_t;
 
 typedef struct {
@@ -161,6 +162,26 @@ mgpbd_status mgpbd_default_params(mgpbd_params *p);
  * MGPBD_E_OOM, MGPBD_E_CUDA.  *out is NULL on error. */
 mgpbd_status mgpbd_create(const mgpbd_mesh_desc *mesh, const mgpbd_params *p, void *stream,
                           mgpbd_handle_t **out);
+
+/* mgpbd_create with every device array of the instance placed in a buffer
+ * the caller owns (for example a torch uint8 tensor), so that the caller
+ * decides where, and within what budget, the instance lives.
+ *   d_workspace  device memory, 256-byte aligned; the library carves its
+ *                arrays out of it (first fit, freed ranges reused) and never
+ *                frees it; it must outlive mgpbd_destroy of the handle
+ *   bytes        its size; mgpbd_workspace_size bounds what create and the
+ *                first setup hold (nk_vectors = 1); a later setup whose
+ *                coarse levels outgrow their capacity re-allocates them with
+ *                25% headroom and may need more
+ * Pinned host scalars, events and CUDA graphs are still allocated by the
+ * runtime.  Results are bitwise those of mgpbd_create: no kernel depends on
+ * where its arrays lie.  Errors: as mgpbd_create; MGPBD_E_INVALID for a NULL,
+ * misaligned or non-device workspace; MGPBD_E_BUDGET when an allocation does
+ * not fit, at create or later (a setup whose hierarchy needs more), with the
+ * handle left valid in the latter case. */
+mgpbd_status mgpbd_create_in_workspace(const mgpbd_mesh_desc *mesh, const mgpbd_params *p,
+                                       void *d_workspace, size_t bytes, void *stream,
+                                       mgpbd_handle_t **out);
 
 /* Frees everything the handle holds.  Synchronises its stream. NULL is a no-op. */
 void mgpbd_destroy(mgpbd_handle_t *h);

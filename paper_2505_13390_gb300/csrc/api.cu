@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <iterator>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -106,40 +107,88 @@ mgpbd_status cuda_fail(cudaError_t e, const char *what, const char *file, int li
   return e == cudaErrorMemoryAllocation ? MGPBD_E_OOM : MGPBD_E_CUDA;
 }
 
+void Arena::use_workspace(void *p, size_t n) {
+  base = static_cast<char *>(p);
+  cap = n & ~(size_t)255;
+  holes.clear();
+  if (cap) holes.emplace(0, cap);
+}
+
 mgpbd_status Arena::alloc(void **p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 16;
   n = (n + 255) & ~(size_t)255;  // keep every buffer 256-byte aligned
-  cudaError_t e = cudaMallocAsync(p, n, stream);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    *p = nullptr;
-    char buf[128];
-    snprintf(buf, sizeof(buf), "device allocation of %zu bytes failed: %s", n,
-             cudaGetErrorString(e));
-    set_error(buf);
-    return MGPBD_E_OOM;
+  if (base) {
+    auto it = holes.begin();
+    while (it != holes.end() && it->second < n) ++it;
+    if (it == holes.end()) {
+      char buf[160];
+      snprintf(buf, sizeof(buf),
+               "workspace of %zu bytes exhausted: %zu more bytes needed with %zu live", cap, n,
+               bytes);
+      set_error(buf);
+      return MGPBD_E_BUDGET;
+    }
+    const size_t off = it->first, len = it->second;
+    holes.erase(it);
+    if (len > n) holes.emplace(off + n, len - n);
+    *p = base + off;
+  } else {
+    cudaError_t e = cudaMallocAsync(p, n, stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      char buf[128];
+      snprintf(buf, sizeof(buf), "device allocation of %zu bytes failed: %s", n,
+               cudaGetErrorString(e));
+      set_error(buf);
+      return MGPBD_E_OOM;
+    }
   }
   bytes += n;
+  peak = std::max(peak, bytes);
   live.emplace_back(*p, n);
   return MGPBD_OK;
 }
 
 void Arena::release(void *p) {
   if (!p) return;
+  size_t n = 0;
   for (auto it = live.begin(); it != live.end(); ++it)
     if (it->first == p) {
-      bytes -= it->second;
+      n = it->second;
+      bytes -= n;
       live.erase(it);
       break;
     }
-  cudaFreeAsync(p, stream);
+  if (!base) {
+    cudaFreeAsync(p, stream);
+    return;
+  }
+  if (!n) return;  // not an array of this arena
+  size_t off = static_cast<size_t>(static_cast<char *>(p) - base), len = n;
+  auto next = holes.lower_bound(off);
+  if (next != holes.end() && off + len == next->first) {  // merge with the range after
+    len += next->second;
+    next = holes.erase(next);
+  }
+  if (next != holes.begin()) {  // merge with the range before
+    auto prev = std::prev(next);
+    if (prev->first + prev->second == off) {
+      off = prev->first;
+      len += prev->second;
+      holes.erase(prev);
+    }
+  }
+  holes.emplace(off, len);
 }
 
 void Arena::release_all() {
-  for (auto &q : live) cudaFreeAsync(q.first, stream);
+  if (!base)
+    for (auto &q : live) cudaFreeAsync(q.first, stream);
   live.clear();
   bytes = 0;
+  if (base) use_workspace(base, cap);
   cudaStreamSynchronize(stream);
 }
 
@@ -238,7 +287,7 @@ static void destroy(Handle *h) {
 }
 
 static mgpbd_status create(const mgpbd_mesh_desc *md, const mgpbd_params *p, void *stream,
-                           Handle **out) {
+                           void *ws, size_t ws_bytes, Handle **out) {
   *out = nullptr;
   if (!md || !p || md->n_verts <= 0 || md->n_dist < 0 || md->n_tet < 0 || !md->rest_pos ||
       !md->inv_mass || (md->n_dist > 0 && !md->dist) || (md->n_tet > 0 && !md->tet) ||
@@ -282,6 +331,7 @@ static mgpbd_status create(const mgpbd_mesh_desc *md, const mgpbd_params *p, voi
   Handle *h = new Handle();
   h->stream = (cudaStream_t)stream;
   h->arena.stream = h->stream;
+  if (ws) h->arena.use_workspace(ws, ws_bytes);
   h->p = *p;
   h->N = md->n_verts;
   h->E = md->n_dist;
@@ -489,7 +539,32 @@ mgpbd_status mgpbd_create(const mgpbd_mesh_desc *mesh, const mgpbd_params *p, vo
     return MGPBD_E_INVALID;
   }
   Handle *h = nullptr;
-  mgpbd_status s = create(mesh, p, stream, &h);
+  mgpbd_status s = create(mesh, p, stream, nullptr, 0, &h);
+  *out = reinterpret_cast<mgpbd_handle_t *>(h);
+  return s;
+}
+
+mgpbd_status mgpbd_create_in_workspace(const mgpbd_mesh_desc *mesh, const mgpbd_params *p,
+                                       void *d_workspace, size_t bytes, void *stream,
+                                       mgpbd_handle_t **out) {
+  if (!out) {
+    set_error("out is NULL");
+    return MGPBD_E_INVALID;
+  }
+  *out = nullptr;
+  if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255) || bytes < 256) {
+    set_error("workspace must be a non-NULL, 256-byte aligned device buffer of >= 256 bytes");
+    return MGPBD_E_INVALID;
+  }
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, d_workspace) != cudaSuccess ||
+      attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    set_error("workspace is not device memory");
+    return MGPBD_E_INVALID;
+  }
+  Handle *h = nullptr;
+  mgpbd_status s = create(mesh, p, stream, d_workspace, bytes, &h);
   *out = reinterpret_cast<mgpbd_handle_t *>(h);
   return s;
 }
@@ -612,6 +687,7 @@ mgpbd_status mgpbd_stats(mgpbd_handle_t *hh, mgpbd_stats_t *s) {
   for (int l = 0; l < h->L; ++l) tot += (double)h->lev[l].nnz;
   s->op_complexity = h->L && h->lev[0].nnz ? tot / (double)h->lev[0].nnz : 0.0;
   s->device_bytes = h->arena.bytes;
+  s->peak_device_bytes = h->arena.peak;
   s->ms_setup = h->ms_setup;
   s->ms_galerkin = h->ms_galerkin;
   s->ms_solve = h->ms_solve;

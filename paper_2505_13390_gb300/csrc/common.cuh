@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -50,10 +51,24 @@ extern unsigned long long g_launches;  // updated atomically
 // Stream-ordered allocations on the owning handle's stream (cudaMallocAsync /
 // cudaFreeAsync): freeing never synchronises the whole device, so instances
 // that run side by side on their own streams do not stall each other.
+//
+// With a caller workspace (base != nullptr) the arena instead carves every
+// array out of the caller's buffer [base, base + cap): first fit over a list
+// of free ranges, freed ranges merged with their neighbours.  A range freed
+// here is reused only by arrays the same handle allocates later, and all of
+// the handle's work is ordered on its one stream, so a reused range is never
+// written while an earlier kernel still reads it (the ordering
+// cudaFreeAsync gives the pooled mode).  Exhausting the buffer is
+// MGPBD_E_BUDGET.
 struct Arena {
-  size_t bytes = 0;
+  size_t bytes = 0;  // live bytes
+  size_t peak = 0;   // high-water mark of `bytes`
   cudaStream_t stream = nullptr;
   std::vector<std::pair<void *, size_t>> live;
+  char *base = nullptr;             // caller workspace, or nullptr (pooled)
+  size_t cap = 0;                   // usable bytes of the workspace
+  std::map<size_t, size_t> holes;   // offset -> length of each free range
+  void use_workspace(void *p, size_t n);
   mgpbd_status alloc(void **p, size_t n);
   void release(void *p);
   void release_all();

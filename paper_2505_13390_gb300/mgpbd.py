@@ -56,7 +56,7 @@ class Stats(C.Structure):
     _fields_ = [("levels", C.c_int), ("n_setups", C.c_int), ("global_iters", C.c_int64),
                 ("op_complexity", C.c_double), ("device_bytes", C.c_size_t),
                 ("ms_setup", C.c_double), ("ms_galerkin", C.c_double), ("ms_solve", C.c_double),
-                ("ms_other", C.c_double)]
+                ("ms_other", C.c_double), ("peak_device_bytes", C.c_size_t)]
 
     def as_dict(self) -> Dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,6 +94,8 @@ _vp, _i, _i64 = C.c_void_p, C.c_int, C.c_int64
 SIGNATURES = {
     "mgpbd_default_params": (_i, [C.POINTER(Params)]),
     "mgpbd_create": (_i, [C.POINTER(MeshDesc), C.POINTER(Params), _vp, C.POINTER(_vp)]),
+    "mgpbd_create_in_workspace": (_i, [C.POINTER(MeshDesc), C.POINTER(Params), _vp, C.c_size_t,
+                                       _vp, C.POINTER(_vp)]),
     "mgpbd_destroy": (None, [_vp]),
     "mgpbd_set_state": (_i, [_vp, _vp, _vp, _i]),
     "mgpbd_get_state": (_i, [_vp, _vp, _vp, _i]),
@@ -217,9 +219,13 @@ def _ptr(a) -> Optional[int]:
 
 
 class Solver:
-    """One MGPBD instance resident on the current CUDA device."""
+    """One MGPBD instance resident on the current CUDA device.
 
-    def __init__(self, mesh, params: Dict, stream=None):
+    With `workspace` (a CUDA tensor, e.g. uint8 of workspace_size(mesh, params)
+    bytes) every device array of the instance is placed in that tensor, which
+    the solver keeps alive until close()."""
+
+    def __init__(self, mesh, params: Dict, stream=None, workspace=None):
         import torch
 
         L = load()
@@ -237,8 +243,15 @@ class Solver:
         self.params = dict(params)
         self._p = make_params(params)
         h = C.c_void_p()
-        _check(L.mgpbd_create(C.byref(md), C.byref(self._p), C.c_void_p(self.stream.cuda_stream),
-                              C.byref(h)), "mgpbd_create")
+        st = C.c_void_p(self.stream.cuda_stream)
+        if workspace is None:
+            _check(L.mgpbd_create(C.byref(md), C.byref(self._p), st, C.byref(h)), "mgpbd_create")
+        else:
+            nbytes = workspace.numel() * workspace.element_size()
+            _check(L.mgpbd_create_in_workspace(C.byref(md), C.byref(self._p),
+                                               C.c_void_p(workspace.data_ptr()), nbytes, st,
+                                               C.byref(h)), "mgpbd_create_in_workspace")
+        self.workspace = workspace
         self.h = h
         self.set_state(mesh.x0, mesh.v0)
 
@@ -246,6 +259,7 @@ class Solver:
         if getattr(self, "h", None):
             load().mgpbd_destroy(self.h)
             self.h = None
+        self.workspace = None
 
     def __del__(self):
         try:

@@ -39,6 +39,14 @@ def test_default_params_and_host_only_calls():
     assert lib.mgpbd_create(None, C.byref(p), None, C.byref(h)) == mgpbd.E_INVALID
     assert not h.value
     assert lib.mgpbd_step(None, 1) == mgpbd.E_INVALID
+    # a caller workspace that is NULL, misaligned or too small is refused on the host
+    for ws, nbytes in ((None, 1 << 20), (0x1000 + 16, 1 << 20), (0x1000, 16)):
+        h = C.c_void_p()
+        assert lib.mgpbd_create_in_workspace(None, C.byref(p), ws, nbytes, None,
+                                             C.byref(h)) == mgpbd.E_INVALID
+        assert not h.value
+    assert lib.mgpbd_create_in_workspace(None, C.byref(p), 0x1000, 1 << 20, None,
+                                         None) == mgpbd.E_INVALID
     assert isinstance(lib.mgpbd_last_error(), bytes)
 
 
