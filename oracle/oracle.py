@@ -15,12 +15,17 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "mgpbd_oracle.c")
-LIB = os.path.join(HERE, "liborc.so")
+# MGPBD_ORACLE_LIB loads another build of the oracle's source instead (the
+# mutation test's copies with a planted mistake); it is never compiled here.
+OVERRIDE = os.environ.get("MGPBD_ORACLE_LIB")
+LIB = OVERRIDE or os.path.join(HERE, "liborc.so")
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-shared", "-fPIC"]
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
+    if OVERRIDE:
+        return LIB
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", *CFLAGS, SRC, "-o", tmp, "-lm"])

@@ -203,14 +203,15 @@ def test_A_symmetric_positive_definite(mi):
 # XPBD special cases (eq. 4, Alg. 1)
 # --------------------------------------------------------------------------
 
-def test_single_constraint_reduces_to_xpbd_update():
+@pytest.mark.parametrize("omega_x", [1.0, 0.25])
+def test_single_constraint_reduces_to_xpbd_update(omega_x):
     rest = np.array([[0, 0, 0], [1, 0, 0]], float)
     x0 = np.array([[0, 0, 0], [1.3, 0.1, -0.2]], float)
     w = np.array([0.5, 2.0])
     alpha = np.array([1e-3])
     mesh = Mesh("one", rest, w, np.array([[0, 1]], np.int32), np.zeros((0, 4), np.int32),
                 alpha, x0, np.zeros((2, 3)))
-    p = params_small(gravity=(0.0, 0.0, 0.0), omega_x=1.0, max_iter=1)
+    p = params_small(gravity=(0.0, 0.0, 0.0), omega_x=omega_x, max_iter=1)
     o = Oracle(mesh, p)
     o.begin_frame()
     o.eval_assemble()
@@ -224,11 +225,46 @@ def test_single_constraint_reduces_to_xpbd_update():
     expect = -(Cexp + at * 0.0) / (w[0] + w[1] + at)
     assert dl[0] == pytest.approx(expect, rel=1e-13)
     assert info["pcg_iters"] == 1
-    # eq. 5: dx = M^-1 grad C^T dlambda
+    # eq. 5: dx = M^-1 grad C^T dlambda, applied with the relaxation omega_x
     x, _ = o.get_state()
     n = d / np.linalg.norm(d)
-    assert np.allclose(x[0], x0[0] + w[0] * n * expect, rtol=0, atol=1e-15)
-    assert np.allclose(x[1], x0[1] - w[1] * n * expect, rtol=0, atol=1e-15)
+    assert np.allclose(x[0], x0[0] + omega_x * w[0] * n * expect, rtol=0, atol=1e-15)
+    assert np.allclose(x[1], x0[1] - omega_x * w[1] * n * expect, rtol=0, atol=1e-15)
+    lam, _ = o.lam()
+    assert lam[0] == dl[0]  # lambda takes the full update (Alg. 1)
+
+
+def test_single_constraint_stays_at_the_compliant_solution():
+    """Two particles and one distance constraint, omega_x = 1: the motion is
+    along n, so C is linear in lambda and the implicit equations C(x) +
+    alpha~ lambda = 0, x = x~ + M^-1 grad C^T lambda (eq. 3-5) have the closed
+    form lambda* = -C~ / (w_a + w_b + alpha~).  One global iteration reaches it
+    and later ones keep it: lambda is the running sum of the updates (Alg. 1),
+    so the right-hand side b = -C - alpha~ lambda stays 0."""
+    rest = np.array([[0, 0, 0], [1, 0, 0]], float)
+    x0 = np.array([[0.2, -0.1, 0.05], [1.3, 0.1, -0.2]], float)
+    w = np.array([0.5, 2.0])
+    alpha = np.array([1e-3])
+    mesh = Mesh("one", rest, w, np.array([[0, 1]], np.int32), np.zeros((0, 4), np.int32),
+                alpha, x0, np.zeros((2, 3)))
+    p = params_small(gravity=(0.0, 0.0, 0.0), omega_x=1.0, max_iter=6)
+    o = Oracle(mesh, p)
+    o.begin_frame()
+    at = alpha[0] / p["dt"] ** 2
+    d = x0[0] - x0[1]
+    n = d / np.linalg.norm(d)
+    C0 = np.linalg.norm(d) - 1.0
+    lam_star = -C0 / (w[0] + w[1] + at)
+    for it in range(6):
+        o.iterate()
+        lam, _ = o.lam()
+        x, _ = o.get_state()
+        assert lam[0] == pytest.approx(lam_star, rel=1e-12), it
+        assert np.allclose(x[0], x0[0] + w[0] * lam_star * n, rtol=0, atol=1e-14), it
+        assert np.allclose(x[1], x0[1] - w[1] * lam_star * n, rtol=0, atol=1e-14), it
+    o.eval_assemble()
+    _, b, _, _ = o.constraints()
+    assert abs(b[0]) <= 1e-12 * abs(C0)
 
 
 @pytest.mark.parametrize("mi", [0, 1])
@@ -379,6 +415,14 @@ def test_strength_hand_example():
     val = np.array([-1.0, 4.0, -1.0, 0.3, 4.0, 0.3, 16.0])
     _, _, _, S = aggregate_csr(ptr, col, val, 0.1, seed=4)
     assert S.tolist() == [1, 0, 1, 0, 0, 0, 0]
+    # an entry is weak only below the threshold: at equality it is strong
+    # (0.1 * sqrt(4 * 25) rounds to exactly 1.0)
+    assert 0.1 * np.sqrt(4.0 * 25.0) == 1.0
+    ptr = np.array([0, 2, 4])
+    col = np.array([1, 0, 0, 1])
+    val = np.array([-1.0, 4.0, -1.0, 25.0])
+    _, _, _, S = aggregate_csr(ptr, col, val, 0.1, seed=4)
+    assert S.tolist() == [1, 0, 1, 0]
 
 
 @pytest.mark.parametrize("seed", range(4))
