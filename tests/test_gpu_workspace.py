@@ -63,7 +63,7 @@ def test_workspace_run_equals_pooled_run(name, prec):
     x0, v0, m0, s0 = run(mesh, p)
     nbytes = workspace_size(mesh, p)
     x1, v1, m1, s1 = run(mesh, p, workspace=ws_tensor(nbytes))
-    assert s1["n_setups"] == s0["n_setups"] >= 4
+    assert s1["n_setups"] == s0["n_setups"] == 3  # global iterations 0, 2, 4
     assert np.array_equal(x0, x1) and np.array_equal(v0, v1)
     assert len(m0) == len(m1)
     for a, b in zip(m0, m1):
