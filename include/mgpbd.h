@@ -305,7 +305,8 @@ typedef struct {
   int64_t global_iters, pcg_iters;
 } mgpbd_step_result;
 /* Upper estimate of the device bytes an instance of this mesh holds after
- * create and its first setup (the figure the service admits instances by),
+ * create and its first setup (the figure the service admits instances by,
+ * and a buffer size that mgpbd_create_in_workspace accepts for them),
  * computed on the host from the mesh alone: per nonzero of A (bounded by the
  * sum over rows of their vertices' degrees) column, FP64 and FP32 values,
  * assembly map and strength mask; per row, vertex and incidence entry the
