@@ -435,6 +435,55 @@ def test_empty_and_single_constraint():
     assert np.array_equal(o.get_state()[0], g.get_state()[0])
 
 
+@pytest.mark.parametrize("prec,op", [(0, 0), (1, 1)])
+def test_degenerate_cases(prec, op):
+    """The method's degenerate cases, in the bench's launch configuration
+    (graphs on): the rest mesh (b = 0, so every update is zero and x stays
+    bitwise), a zero-length edge (n = 0: C = -L0, A_ii = alpha~, dlambda =
+    L0 / alpha~ and no motion) and a fully pinned mesh (A = diag(alpha~), no
+    coarse level, dlambda = b / alpha~ and no motion)."""
+    from paper_2505_13390_gb300.meshgen import Mesh
+    p0 = dict(default_params(gravity=(0.0, 0.0, 0.0), max_iter=3, coarse_max=20, max_levels=4),
+              precision=prec, level0_op=op, use_graphs=1)
+    mesh, _ = CASES["cloth8"]()
+    mesh.x0 = mesh.rest_pos.copy()
+    g = solver(mesh, p0)
+    assert g.step(1) >= 0
+    x, v = g.get_state()
+    assert np.array_equal(x, mesh.rest_pos) and np.all(v == 0)
+
+    rest = np.array([[0, 0, 0], [1, 0, 0]], float)
+    deg = Mesh("d", rest, np.ones(2), np.array([[0, 1]], np.int32), np.zeros((0, 4), np.int32),
+               np.array([1e-6]), np.zeros((2, 3)), np.zeros((2, 3)))
+    p1 = dict(p0, max_iter=1)
+    o, g = Oracle(deg, p1), solver(deg, p1)
+    o.begin_frame()
+    g.begin_frame()
+    do, dg = o.iterate(), g.iterate()
+    for a, b in zip(o.constraints(), g.constraints()):
+        assert np.array_equal(a, b)
+    assert np.array_equal(o.matrix(0)[2], g.matrix(0)[2])
+    at = 1e-6 / p1["dt"] ** 2
+    assert g.lam()[1][0] == pytest.approx(1.0 / at, rel=1e-14)
+    assert np.array_equal(g.get_state()[0], np.zeros((2, 3)))
+
+    pinned, _ = CASES["cloth8"]()
+    pinned.inv_mass = np.zeros_like(pinned.inv_mass)
+    o, g = Oracle(pinned, p1), solver(pinned, p1)
+    o.begin_frame()
+    g.begin_frame()
+    do, dg = o.iterate(), g.iterate()
+    assert g.stats()["levels"] == o.levels == 1
+    assert dg["ret"] >= 0 and dg["rel_res"] <= p1["pcg_rtol"]
+    lo, lg = o.lam()[1], g.lam()[1]
+    if prec == 0:  # FP64: the coarsest solve is exact, one PCG iteration
+        assert dg["pcg_iters"] == do["pcg_iters"] == 1
+        assert np.allclose(lg, lo, rtol=1e-12, atol=0)
+    else:  # FP32 V-cycle: z carries FP32 rounding, PCG converges to its tolerance
+        assert np.linalg.norm(lg - lo) <= 10 * p1["pcg_rtol"] * np.linalg.norm(lo)
+    assert np.array_equal(g.get_state()[0], pinned.x0)
+
+
 # --------------------------------------------------------------------------
 # k = 6 near-kernel vectors (Sec. 4.3): QR prolongator, k unknowns per aggregate
 # --------------------------------------------------------------------------
