@@ -12,25 +12,41 @@
  *
  * What it computes, step by step in the order of Algorithm 1:
  *   semi-implicit Euler predict and lambda reset        (Alg. 1, Sec. 3 eq. 1)
- *   constraint values C and gradients                    (Alg. 1, eq. 3)
+ *   constraint values C and gradients: distance, volume
+ *     and ARAP rows                                      (Alg. 1, eq. 3, Sec. 5.3)
  *   A = grad C  M^-1  grad C^T + alpha~ on a fixed CSR
  *     pattern, off-diagonals first, diagonal last        (eq. 3, Sec. 4.2)
  *   b = -C - alpha~ lambda                               (eq. 3)
- *   lazy UA-AMG setup: near-kernel sweeps, strength
- *     filter, aggregation, injection, next-level
- *     near-kernel, Galerkin, recursion below 400 rows    (Sec. 4.1-4.3, setup-pipeline figure)
+ *   lazy UA-AMG setup: near-kernel sweeps (k vectors),
+ *     strength filter, aggregation, injection (QR per
+ *     aggregate for k > 1), next-level near-kernel,
+ *     Galerkin, recursion below 400 rows                 (Sec. 4.1-4.3, setup-pipeline figure)
  *   Galerkin coarse operators P^T A P                    (Sec. 4.4, eq. 6)
  *   coarsest dense Cholesky                              (reading: Sec. 4.1 size rule)
  *   PCG with one V-cycle per iteration                   (Sec. 4.4)
- *   weighted-Jacobi / multicolour GS smoothing, omega
- *     from the power method and lambda_min estimate      (Sec. 4.5)
- *   dx = M^-1 grad C^T dlambda, lambda and x update      (eq. 5, Alg. 1)
+ *   weighted-Jacobi / multicolour GS / Chebyshev
+ *     smoothing, omega from the power method and the
+ *     lambda_min estimate                                (Sec. 4.5)
+ *   or XPBD's local step dlambda_j = b_j / A_jj          (eq. 4)
+ *   dx = M^-1 grad C^T dlambda, lambda and x update,
+ *     optionally with backtracking of omega_x            (eq. 5, Alg. 1, Sec. 4)
  *   velocity update                                      (Alg. 1)
  *
- * Readings where the paper is silent (distance/volume constraint forms, the
- * deterministic MIS-2 aggregation, k = 1 near-kernel vector, summation
- * orders, the coarsest solve) are listed in the design notes and restated at
- * each function below.
+ * Readings where the paper is silent (the constraint forms, the
+ * deterministic MIS-2 aggregation, the number of near-kernel vectors,
+ * summation orders, the coarsest solve) are listed in the design notes and
+ * restated at each function below.
+ *
+ * How it is pinned (tests/test_oracle_pins.py, test_oracle_arap.py,
+ * test_oracle_nearkernel.py): against published generator outputs, finite
+ * differences, closed forms, dense J M^-1 J^T + alpha~ built in numpy,
+ * brute-force patterns, aggregations and colourings, scipy's P^T A P, dense
+ * Cholesky solves, the textbook XPBD update and a compliant two-particle
+ * solution, V-cycle symmetry and the Chebyshev polynomial.
+ * tests/test_oracle_mutants.py plants 40 plausible mistakes in a copy of
+ * this file, one at a time, and each is caught by a named pin.
+ * Parity unpinned: whole-frame trajectories of the stiff meshes beyond those
+ * invariants (the paper prints no trajectory).
  */
 #include <math.h>
 #include <stdint.h>
