@@ -510,8 +510,8 @@ static uint8_t *strength(const orc_csr *A, double theta) {
    neighbours of a root join it.  Pass 2: every other row with a strong
    neighbour joins the aggregate of the pass-1 member among its strong
    neighbours with the largest |A_ij| (ties: smaller aggregate id, then
-   smaller neighbour index) -- "assign them to the neighbour aggregate with
-   the strongest connection". */
+   smaller neighbour index): a leftover row goes to the aggregate it is
+   most strongly coupled to. */
 typedef struct { uint64_t pri; int32_t i; } orc_pri;
 static int cmp_pri_desc(const void *a, const void *b) {
   const orc_pri *x = (const orc_pri *)a, *y = (const orc_pri *)b;

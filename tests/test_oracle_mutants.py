@@ -55,7 +55,7 @@ MUTANTS = [
     ("strength_equality_weak", "Sec. 4.1, weak only below the threshold",
      "S[k] = fabs(A->val[k]) >= thr;", "S[k] = fabs(A->val[k]) > thr;",
      [PINS + "test_strength_hand_example"]),
-    ("aggregation_weakest_connection", "Sec. 4.1, join the strongest connection",
+    ("aggregation_weakest_connection", "Sec. 4.1, leftover rows join the most strongly coupled aggregate",
      "double s = fabs(A->val[k]);", "double s = 1.0 / fabs(A->val[k]);",
      [PINS + "test_aggregation_brute_force[0.1-0]"]),
     ("aggregation_distance_one_roots", "Sec. 4.1, roots independent at strength distance 2",
