@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-arap", action="store_true",
                     help="skip the ARAP-constraint leg (block100arap)")
+    ap.add_argument("--no-xpbd", action="store_true",
+                    help="skip the XPBD-versus-MGPBD frame on cloth512")
     ap.add_argument("--arap-steps", type=int, default=3)
     ap.add_argument("--arap-warmup", type=int, default=3)
     ap.add_argument("--assembled-steps", type=int, default=1)
@@ -369,6 +371,43 @@ def cpu_sample_baseline(iters=2, warm=1, gpu_pcg=None):
                        f"ratio {pscale:.2f} to 376.5M nnz")}, dt, scale
 
 
+def xpbd_comparison():
+    """One frame of the 512x512 cloth (1,306,625 rows, per-row compliance over
+    four decades) with MGPBD and with XPBD's local step (eq. 4, the solver
+    the paper compares against on the GPU): the dual residual |b| before each
+    of the 20 global iterations and after the last, relative to the first,
+    and the time of a global iteration (median over iterations 2-20; the
+    first carries the AMG setup)."""
+    import numpy as np
+    import torch
+
+    from paper_2505_13390_gb300.meshgen import workload
+    from paper_2505_13390_gb300.mgpbd import Solver
+    mesh, p = workload("cloth512")
+    out = {"workload": "cloth512: 512x512 cloth with bend edges, top row pinned, "
+                       "alpha = 10^U(-10,-6) per row, one frame of 20 global iterations",
+           "rows": mesh.n_rows}
+    for name, ls in (("mgpbd", 0), ("xpbd", 1)):
+        q = dict(p, precision=1, level0_op=1, use_graphs=1, autotune=1, linear_solver=ls)
+        g = Solver(mesh, q, stream=torch.cuda.Stream())
+        g.begin_frame()
+        bn, ms, pcg = [], [], 0
+        for _ in range(q["max_iter"]):
+            t0 = time.perf_counter()
+            d = g.iterate()
+            ms.append(1e3 * (time.perf_counter() - t0))
+            bn.append(d["bnorm"])
+            pcg += d["pcg_iters"]
+        g.eval_assemble()
+        bn.append(float(np.linalg.norm(g.constraints()[1])))
+        g.close()
+        rel = [b / bn[0] for b in bn]
+        out[name] = {"bnorm_rel_after": {str(k): rel[k] for k in (1, 2, 5, 10, 20)},
+                     "ms_per_iter": float(np.median(ms[1:])), "pcg_iters": pcg}
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, ws, rank):
     import torch
 
@@ -455,6 +494,9 @@ def run_ours(args, ws, rank):
         rar["solver"].close()
         del rar
         torch.cuda.empty_cache()
+    xpbd = None
+    if not args.no_xpbd:
+        xpbd = xpbd_comparison()
     serve = None
     if not args.no_serve:
         serve = serving(args)
@@ -510,6 +552,7 @@ def run_ours(args, ws, rank):
         "fp64": fp64,
         "assembled": assembled,
         "arap": arap,
+        "xpbd_vs_mgpbd": xpbd,
         "serving": serve,
         "create_s": res["create_s"],
         "stats": {k: res["stats"][k] for k in ("levels", "op_complexity", "device_bytes")},
