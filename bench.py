@@ -495,7 +495,7 @@ def run_ours(args, ws, rank):
         del rar
         torch.cuda.empty_cache()
     xpbd = None
-    if not args.no_xpbd:
+    if not args.no_xpbd and ws == 1:  # a single-GPU comparison: not repeated per rank
         xpbd = xpbd_comparison()
     serve = None
     if not args.no_serve:
