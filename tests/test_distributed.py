@@ -45,3 +45,26 @@ def test_two_replica_ranks_gloo():
         assert (got_ws, got_rank) == (ws, r)
         assert ms == 2000.0  # max over ranks
         assert rate == pytest.approx(ws * 3 / 2.0)  # whole-job iterations per second
+
+
+@pytest.mark.timeout(300)
+def test_reference_arm_under_two_ranks_prints_once():
+    """bench.py --impl reference under torch.distributed.run with two gloo
+    ranks: rank 0 alone times the oracle and prints one JSON line; the other
+    rank exits 0 without work."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, MGPBD_DIST_BACKEND="gloo", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+                        "--nproc-per-node", "2", "--master-addr", "127.0.0.1",
+                        "--master-port", str(_free_port()), "bench.py", "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"],
+                       cwd=root, env=env, capture_output=True, text=True, timeout=280)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
