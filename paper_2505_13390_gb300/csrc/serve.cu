@@ -306,7 +306,9 @@ mgpbd_status mgpbd_batch_run(mgpbd_batch_t *bb, const mgpbd_step_request *req, i
           int victim = -1;
           for (size_t i = 0; i < b->inst.size(); ++i) {
             Instance &q = b->inst[i];
-            if (!q.h || q.busy || (int)i == best) continue;
+            // busy first: a busy instance's handle is being written by its
+            // worker outside the lock, so it must not be read here
+            if (q.busy || !q.h || (int)i == best) continue;
             if (victim < 0 || q.last_used < b->inst[victim].last_used) victim = (int)i;
           }
           if (victim < 0) break;
