@@ -43,7 +43,7 @@
  * brute-force patterns, aggregations and colourings, scipy's P^T A P, dense
  * Cholesky solves, the textbook XPBD update and a compliant two-particle
  * solution, V-cycle symmetry and the Chebyshev polynomial.
- * tests/test_oracle_mutants.py plants 40 plausible mistakes in a copy of
+ * tests/test_oracle_mutants.py plants 58 plausible mistakes in a copy of
  * this file, one at a time, and each is caught by a named pin.
  * Parity unpinned: whole-frame trajectories of the stiff meshes beyond those
  * invariants (the paper prints no trajectory).

@@ -80,10 +80,10 @@ MUTANTS = [
      "for (int i = 0; i < n; ++i) B[i] = u01(h64(hkey(seed, 0, i))) * amax;",
      "for (int i = 0; i < n; ++i) B[i] = u01(h64(hkey(seed, 0, i)));",
      [PINS + "test_near_kernel_is_weighted_jacobi_on_homogeneous_system"]),
-    ("six_vectors_R_not_accumulated", "Sec. 4.3, six B: QR of each aggregate",
+    ("six_vectors_R_not_accumulated", "Sec. 4.3, k vectors: QR of each aggregate",
      "R[d * k + c] = pass ? R[d * k + c] + r : r;", "R[d * k + c] = r;",
      [NK + "test_qr_of_each_aggregate[c8]"]),
-    ("six_vectors_prolong_first_column", "Sec. 4.3, six B: k coarse unknowns per aggregate",
+    ("six_vectors_prolong_first_column", "Sec. 4.3, k vectors: k coarse unknowns per aggregate",
      "L->x[i] = fma(L->P[(size_t)i * k + c], Lc->x[L->agg[i] * k + c], L->x[i]);",
      "L->x[i] = fma(L->P[(size_t)i * k + c], Lc->x[L->agg[i] * k], L->x[i]);",
      [NK + "test_vcycle_symmetric_with_k_columns[c8]"]),
@@ -164,6 +164,68 @@ MUTANTS = [
     ("arap_gradient_without_two", "Sec. 5.3, dC/dF = 2 (F - R)",
      "g[3 * (k + 1) + a] = 2.0 * t;", "g[3 * (k + 1) + a] = t;",
      [ARAP + "test_gradient_matches_finite_differences"]),
+    ("six_vectors_one_seed", "Sec. 4.3, k near-kernel vectors from independent starts",
+     "near_kernel_one(A, p, p->seed_nk + (uint64_t)c, v);", "near_kernel_one(A, p, p->seed_nk, v);",
+     [NK + "test_near_kernel_columns_are_the_single_vector_procedure"]),
+    ("node_norm_one_norm", "Sec. 4.3, k vectors: node strength from k x k block norms",
+     "        *c = fma(v, v, *c);", "        *c = *c + fabs(v);",
+     [NK + "test_coarse_levels_aggregate_whole_nodes"]),
+    ("node_norm_without_sqrt", "Sec. 4.3, k vectors: Frobenius norm of a block",
+     "for (int t = 0; t <= cnt; ++t) N->val[base + t] = sqrt(N->val[base + t]);",
+     "for (int t = 0; t <= cnt; ++t) N->val[base + t] = N->val[base + t];",
+     [NK + "test_coarse_levels_aggregate_whole_nodes"]),
+    ("galerkin_k_wrong_column", "Eq. 6 with k columns, P_ip A_ij P_jq",
+     "*cell = fma(t, L->P[(size_t)j * k + qq], *cell);",
+     "*cell = fma(t, L->P[(size_t)j * k + p], *cell);",
+     [NK + "test_galerkin_with_k_columns[c8]"]),
+    ("galerkin_k_dead_diagonal_zero", "Sec. 4.3, k vectors: dropped columns keep the coarse matrix SPD",
+     "if (L->pdead[r]) Ac->val[Ac->ptr[r + 1] - 1] = 1.0;",
+     "if (L->pdead[r]) Ac->val[Ac->ptr[r + 1] - 1] = 0.0;",
+     [NK + "test_galerkin_with_k_columns[c8]"]),
+    ("qr_without_drop_tolerance", "Sec. 4.3, k vectors: numerically dependent columns dropped",
+     "int live = nv > 0.0 && nrm > ORC_QR_DROP * sqrt(nb);", "int live = nv > 0.0;",
+     [NK + "test_qr_of_each_aggregate[c8]"]),
+    ("chebyshev_start_unscaled", "Sec. 4.5, Chebyshev smoother's first step r/theta",
+     "d[i] = r[i] / theta;", "d[i] = r[i];",
+     [PINS + "test_chebyshev_matches_the_chebyshev_polynomial"]),
+    ("backtracking_stops_on_growth", "Sec. 4, omega halves while the residual grows",
+     "if (nb < info->bnorm || t == o->p.backtrack) break;",
+     "if (nb > info->bnorm || t == o->p.backtrack) break;",
+     [PINS + "test_backtracking_never_accepts_a_growing_residual_when_a_halving_helps"]),
+    ("position_update_without_inverse_mass", "Eq. 5, dx = M^-1 grad C^T dlambda",
+     "o->dx[3 * (int64_t)v + k] = o->w[v] * acc[k];", "o->dx[3 * (int64_t)v + k] = acc[k];",
+     [PINS + "test_single_constraint_reduces_to_xpbd_update[1.0]"]),
+    ("cholesky_without_pivot_check", "coarsest level: a zero pivot is singular",
+     "if (!(d > 0.0)) return ORC_E_SINGULAR;", "if (0) return ORC_E_SINGULAR;",
+     [PINS + "test_singular_system_is_reported"]),
+    ("arap_rest_inverse_transposed", "Sec. 5.3, F = Ds Dm^-1",
+     "for (int k = 0; k < 3; ++k) B[3 * r + k] = det != 0.0 ? c[r][k] / det : 0.0;",
+     "for (int k = 0; k < 3; ++k) B[3 * r + k] = det != 0.0 ? c[k][r] / det : 0.0;",
+     [ARAP + "test_polar_factor_on_a_skewed_rest_shape"]),
+    ("arap_singular_deformation_unhandled", "Sec. 5.3, no polar factor for a singular F",
+     "  if (detF == 0.0) {", "  if (0) {",
+     [ARAP + "test_singular_and_reflected_deformations"]),
+    ("jacobi_without_weight", "Sec. 4.5, omega-weighted Jacobi",
+     "x[i] = fma(L->omega, (b[i] - t[i]) / diag_of(&L->A, i), x[i]);",
+     "x[i] = x[i] + (b[i] - t[i]) / diag_of(&L->A, i);",
+     [PINS + "test_chebyshev_degree_one_is_optimal_weighted_jacobi"]),
+    ("pcg_alpha_wrong_denominator", "Sec. 4.4, PCG alpha = r.z / p.Ap",
+     "double al = rz / pq;", "double al = rz / rr;",
+     [PINS + "test_one_level_hierarchy_converges_in_one_iteration"]),
+    ("true_residual_sign", "Sec. 4.4, true residual b - A dlambda",
+     "for (int i = 0; i < n; ++i) q[i] = b[i] - q[i];",
+     "for (int i = 0; i < n; ++i) q[i] = b[i] + q[i];",
+     [PINS + "test_pcg_matches_dense_cholesky[c8-0]"]),
+    ("lambda_not_reset_per_frame", "Alg. 1, lambda = 0 at the start of a time step",
+     "  memset(o->lambda, 0, sizeof(double) * (size_t)o->m);\n}", "}",
+     [PINS + "test_single_constraint_stays_at_the_compliant_solution"]),
+    ("strength_with_signed_scaled_diagonal", "Sec. 4.1, strength uses |A_ii|",
+     "double aii = fabs(diag_of(A, i));", "double aii = diag_of(A, i) * 0.5;",
+     [PINS + "test_aggregation_brute_force[0.1-0]"]),
+    ("six_vectors_restrict_first_column", "Sec. 4.3, k vectors: restriction by every column of P",
+     "acc = fma(L->P[(size_t)i * k + c], L->r[i], acc);\n      }\n      Lc->b[a * k + c] = acc;",
+     "acc = fma(L->P[(size_t)i * k], L->r[i], acc);\n      }\n      Lc->b[a * k + c] = acc;",
+     [NK + "test_pcg_with_k_columns_matches_dense_cholesky[c8]"]),
     ("splitmix_shift", "counter-based generator (SplitMix64 finaliser)",
      "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBULL;",
      [PINS + "test_splitmix64_reference_values"]),

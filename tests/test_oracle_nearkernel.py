@@ -1,4 +1,4 @@
-"""Pins of the oracle with k > 1 near-kernel vectors (Sec. 4.3, six B).
+"""Pins of the oracle with k > 1 near-kernel vectors (Sec. 4.3, six in the paper).
 
 With k vectors the tentative prolongator has k columns per aggregate, from
 a QR factorisation of each aggregate's block of B, and the next level's

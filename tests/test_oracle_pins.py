@@ -265,6 +265,38 @@ def test_single_constraint_stays_at_the_compliant_solution():
     o.eval_assemble()
     _, b, _, _ = o.constraints()
     assert abs(b[0]) <= 1e-12 * abs(C0)
+    # the next frame starts again from lambda = 0 (Alg. 1); its prediction
+    # x~ = x + dt v moves along n as well, so the same closed form holds there
+    o.end_frame()
+    o.begin_frame()
+    xt, _ = o.get_state()
+    d2 = xt[0] - xt[1]
+    n2 = d2 / np.linalg.norm(d2)
+    C2 = np.linalg.norm(d2) - 1.0
+    lam2 = -C2 / (w[0] + w[1] + at)
+    assert np.allclose(n2, n, rtol=0, atol=1e-14) and abs(C2) > 1e-3
+    for it in range(4):
+        o.iterate()
+        lam, _ = o.lam()
+        x, _ = o.get_state()
+        assert lam[0] == pytest.approx(lam2, rel=1e-12), it
+        assert np.allclose(x[0], xt[0] + w[0] * lam2 * n2, rtol=0, atol=1e-14), it
+        assert np.allclose(x[1], xt[1] - w[1] * lam2 * n2, rtol=0, atol=1e-14), it
+
+
+def test_singular_system_is_reported():
+    """A = 0: one distance row between two pinned vertices with zero
+    compliance.  The coarsest Cholesky meets a zero pivot and the solve is
+    refused as singular instead of returning non-finite values."""
+    rest = np.array([[0, 0, 0], [1, 0, 0]], float)
+    x0 = np.array([[0, 0, 0], [1.2, 0, 0]], float)
+    mesh = Mesh("s", rest, np.zeros(2), np.array([[0, 1]], np.int32), np.zeros((0, 4), np.int32),
+                np.array([0.0]), x0, np.zeros((2, 3)))
+    o = Oracle(mesh, params_small(gravity=(0.0, 0.0, 0.0)))
+    o.begin_frame()
+    o.eval_assemble()
+    assert np.array_equal(o.matrix(0)[2], [0.0])
+    assert o.prepare_solve() == -4  # singular
 
 
 @pytest.mark.parametrize("mi", [0, 1])
@@ -655,6 +687,33 @@ def test_backtracking_never_accepts_a_growing_residual_when_a_halving_helps():
         assert d["omega"] == 2.0 ** -halvings
         if halvings < p["backtrack"]:
             assert d["bnorm_after"] < d["bnorm"]
+    # each trial re-evaluated in a second instance (state before the iteration
+    # plus omega dx, lambda after it): the accepted omega is the first of
+    # omega_x, omega_x/2, ... whose trial lowers |b|
+    o = Oracle(mesh, p)
+    probe = Oracle(mesh, p)
+    o.begin_frame()
+    accepted = []
+    for _ in range(6):
+        x0, v0 = o.get_state()
+        d = o.iterate()
+        x1, _ = o.get_state()
+        lam1, _ = o.lam()
+        om = d["omega"]
+        accepted.append(om)
+        dx = (x1 - x0) / om
+        trial = p["omega_x"]
+        while True:
+            probe.set_state(x0 + trial * dx, v0)
+            probe.set_lambda(lam1)
+            probe.eval_assemble()
+            ratio = np.linalg.norm(probe.constraints()[1]) / d["bnorm"]
+            if trial == om:
+                assert ratio < 1.0
+                break
+            assert ratio >= 1.0, (trial, om, ratio)
+            trial /= 2
+    assert max(accepted) == p["omega_x"] and min(accepted) < p["omega_x"]  # both cases met
     # fixed relaxation leaves omega untouched and reports no trial residual
     o2 = Oracle(mesh, default_params(omega_x=0.25, coarse_max=40))
     o2.begin_frame()
