@@ -658,7 +658,7 @@ static void member_lists(orc_level *L) {
   free(f);
 }
 
-/* Injection with k > 1 (Sec. 4.3, six B; the tentative prolongator of
+/* Injection with k > 1 (Sec. 4.3, six vectors in the paper; the tentative prolongator of
    smoothed-aggregation AMG): per aggregate a the member rows of B (|a| x k)
    are factored B_a = Q R by modified Gram-Schmidt with one re-orthogonal-
    isation pass (the smoothed near-kernel columns are close to dependent on
