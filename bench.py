@@ -432,9 +432,12 @@ def run_ours(args, ws, rank):
     achieved = prof["bytes_per_launch"] / (avg_ms / 1e3) / 1e9
     e2e_val = None
     e2e_bytes = 0
+    e2e_pcg = []
     if not args.no_e2e:
+        pcg0 = len(res["runner"].pcg)
         e2e_val, e2e_bytes = e2e(g, res["runner"], args.e2e_steps)
         e2e_val = e2e_val * ws
+        e2e_pcg = list(res["runner"].pcg[pcg0:])
     fp64 = None
     assembled = None
     levels = [g.level_info(l) for l in range(g.levels)]
@@ -545,8 +548,10 @@ def run_ours(args, ws, rank):
                      "bytes_per_launch": prof["bytes_per_launch"], "avg_launch_ms": avg_ms,
                      "launches": prof["launches"]},
         "cpu_baseline": cpu,
+        # the end-to-end steps are the global iterations after the timed ones
+        # (same frame); their PCG counts differ from the timed steps'
         "e2e": {"value": e2e_val, "unit": "global_iters/s", "h2d_bytes_per_step": e2e_bytes,
-                "d2h_bytes_per_step": e2e_bytes} if e2e_val else None,
+                "d2h_bytes_per_step": e2e_bytes, "pcg_iters": e2e_pcg} if e2e_val else None,
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
         "fp64": fp64,
