@@ -1,0 +1,70 @@
+"""Host logic of bench.py that needs no GPU: the clock sampler's parsing
+(the throttle reasons decide whether a run is kept) and the JSON line of the
+reference arm at N = 1."""
+import json
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+class _FakeProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_samples_and_throttle_reasons():
+    import bench
+    c = bench.Clocks()
+    fd, c.path = tempfile.mkstemp(suffix=".csv")
+    with os.fdopen(fd, "w") as f:
+        f.write("0, 2070, 2070, 812.3, 0x0000000000000000, Not Active, Not Active, "
+                "Not Active, Not Active\n")
+        f.write("0, 1980, 2070, 1399.0, 0x0000000000000004, Not Active, Not Active, "
+                "Not Active, Active\n")
+        f.write("0, [N/A], 2070, 10.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("a line nvidia-smi did not finish\n")
+    c.proc = _FakeProc()
+    d = c.stop()
+    assert d["samples"] == 2
+    assert d["sm_mhz"] == 2025.0 and d["sm_max_mhz"] == 2070.0 and d["power_w_max"] == 1399.0
+    assert d["reasons"] == ["sw_power_cap"]  # kept and noted; no slowdown reason
+    assert not os.path.exists(c.path)
+
+
+def test_clocks_without_nvidia_smi():
+    import bench
+    c = bench.Clocks()
+    assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+@pytest.mark.timeout(300)
+def test_reference_arm_line_carries_every_key():
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=280)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 1
+    assert d["higher_is_better"] is True and d["scaling"] == "weak" and d["vs_baseline"] is None
+    assert d["ms_per_step"] == pytest.approx(1e3 / d["value"])
+    assert d["config"]["workload"] == "block100" and d["config"]["nnz"] == 376_541_249
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"]
+    assert "4x33x4" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
