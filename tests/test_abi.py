@@ -64,3 +64,36 @@ def test_workspace_size_is_host_only_and_grows_with_the_mesh():
     bad.dist[0, 0] = bad.n_verts  # out of range
     with pytest.raises(mgpbd.MgpbdError):
         mgpbd.workspace_size(bad, p)
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes mirror in the binding has the size and field offsets that
+    a C compiler gives the header's struct (a mismatch would corrupt memory)."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    pairs = {"mgpbd_mesh_desc": mgpbd.MeshDesc, "mgpbd_params": mgpbd.Params,
+             "mgpbd_solve_info": mgpbd.SolveInfo, "mgpbd_stats_t": mgpbd.Stats,
+             "mgpbd_level_info": mgpbd.LevelInfo, "mgpbd_batch_config": mgpbd.BatchConfig,
+             "mgpbd_step_request": mgpbd.StepRequest, "mgpbd_step_result": mgpbd.StepResult}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mgpbd.h"', 'int main(void) {']
+    for cname, py in pairs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                               check=True).stdout.splitlines():
+        cname, field, val = line.split()
+        got[(cname, field)] = int(val)
+    for cname, py in pairs.items():
+        assert got[(cname, "sizeof")] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
