@@ -97,3 +97,17 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(cname, "sizeof")] == C.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_missing_library_fails_loudly():
+    """No CPU fallback: without libmgpbd.so the binding raises on first use."""
+    import subprocess
+    import sys
+    code = ("from paper_2505_13390_gb300 import mgpbd\n"
+            "try:\n"
+            "    mgpbd.load('/nonexistent/libmgpbd.so')\n"
+            "except ImportError as e:\n"
+            "    print('raised', e)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0 and r.stdout.startswith("raised") and "missing" in r.stdout
