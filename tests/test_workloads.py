@@ -45,3 +45,29 @@ def test_workload_sizes(name, verts, dist, tets, nnz):
         assert np.all(np.linalg.det(e) > 0)
     if nnz is not None:
         assert pattern_nnz(mesh) == nnz
+
+
+def test_serving_trace_recipe():
+    """The seeded serving trace: half cloth N x N with N in 16..256, half beams
+    L x 10 x 10 with L in 10..80, alpha = 10^U(-9,-6); Poisson arrivals at the
+    given rate (exponential gaps, so mean gap 1/rate and coefficient of
+    variation 1), instances drawn uniformly; the same seed gives the same trace."""
+    from paper_2505_13390_gb300.meshgen import instance_mesh, serving_trace
+    inst, reqs = serving_trace(n_requests=4000, n_instances=400, rate_hz=2.0, seed=6)
+    kinds = np.array([i["kind"] == "cloth" for i in inst])
+    assert abs(kinds.mean() - 0.5) < 4 * np.sqrt(0.25 / len(inst))
+    for i in inst:
+        lo, hi = (16, 256) if i["kind"] == "cloth" else (10, 80)
+        assert lo <= i["size"] <= hi and 1e-9 <= i["alpha"] <= 1e-6
+    t = np.array([r["t"] for r in reqs])
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert np.all(gaps > 0)
+    assert abs(gaps.mean() - 0.5) < 4 * 0.5 / np.sqrt(len(gaps))
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.1
+    counts = np.bincount([r["instance"] for r in reqs], minlength=len(inst))
+    assert counts.max() < 30  # uniform: about 10 each
+    assert serving_trace(n_requests=50, n_instances=8, seed=6) == \
+        serving_trace(n_requests=50, n_instances=8, seed=6)
+    # an instance's mesh follows its kind and size
+    mesh, p = instance_mesh(next(i for i in inst if i["kind"] == "beam"))
+    assert mesh.n_tet == 5 * 100 * next(i for i in inst if i["kind"] == "beam")["size"]
