@@ -55,6 +55,14 @@
 
 #define ORC_MAXL 16
 
+/* Loops over independent rows carry ORC_ROWS.  The plain build ignores it;
+   the -fopenmp build (liborc_omp.so, used to time the oracle on all host
+   cores and to run it at test sizes where one core is too slow) splits the
+   rows among threads.  Each row's arithmetic is the same in both, so both
+   builds give the same bits.  Sums across rows (dot products, norms) stay
+   sequential. */
+#define ORC_ROWS _Pragma("omp parallel for schedule(static)")
+
 enum {
   ORC_OK = 0,
   ORC_W_NOT_CONVERGED = 1,
@@ -169,6 +177,20 @@ static uint64_t hkey(uint64_t seed, int l, int i) {
 static double u01(uint64_t h) { return ((double)(h >> 11) + 0.5) * 0x1p-53; }
 
 uint64_t orc_h64(uint64_t k) { return h64(k); }
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+/* threads the row loops use (1 in the plain build); n > 0 sets them */
+int orc_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 static void *xcalloc(size_t n, size_t s) { return calloc(n ? n : 1, s ? s : 1); }
 
@@ -312,11 +334,13 @@ static double arap_eval(const double *x0, const double *x1, const double *x2, co
 
 /* Alg. 1 (calculate C and grad C), eq. 3 (b = -C - alpha~ lambda) */
 static void eval_constraints(orc *o) {
+  ORC_ROWS
   for (int j = 0; j < o->E; ++j) {
     const double *xa = o->x + 3 * (int64_t)o->edge[2 * j];
     const double *xb = o->x + 3 * (int64_t)o->edge[2 * j + 1];
     o->C[j] = dist_eval(xa, xb, o->L0[j], o->gd + 3 * (int64_t)j);
   }
+  ORC_ROWS
   for (int t = 0; t < o->T; ++t) {
     const int32_t *tv = o->tet + 4 * (int64_t)t;
     const double *p0 = o->x + 3 * (int64_t)tv[0], *p1 = o->x + 3 * (int64_t)tv[1];
@@ -325,6 +349,7 @@ static void eval_constraints(orc *o) {
                          ? arap_eval(p0, p1, p2, p3, o->Dminv + 9 * (int64_t)t, o->gt + 12 * (int64_t)t)
                          : tet_eval(p0, p1, p2, p3, o->V0[t], o->gt + 12 * (int64_t)t);
   }
+  ORC_ROWS
   for (int j = 0; j < o->m; ++j) {
     double t = o->alpha_t[j] * o->lambda[j];
     o->b[j] = (-o->C[j]) - t;
@@ -435,8 +460,9 @@ static double gdot(const double *a, const double *b) {
 }
 
 static void assemble(orc *o) {
-  int32_t vv[4];
+  ORC_ROWS
   for (int i = 0; i < o->m; ++i) {
+    int32_t vv[4];
     int c = row_verts(o, i, vv);
     double gi[4][3];
     for (int s = 0; s < c; ++s) row_grad(o, i, s, gi[s]);
@@ -467,6 +493,7 @@ static double diag_of(const orc_csr *A, int i) { return A->val[A->ptr[i + 1] - 1
 
 /* y_i = sum over row i in storage order of fma(A_ij, x_j, s) */
 static void spmv(const orc_csr *A, const double *x, double *y) {
+  ORC_ROWS
   for (int i = 0; i < A->n; ++i) {
     double s = 0.0;
     for (int64_t k = A->ptr[i]; k < A->ptr[i + 1]; ++k) s = fma(A->val[k], x[A->col[k]], s);
@@ -593,6 +620,7 @@ static void near_kernel_one(const orc_csr *A, const orc_params *p, uint64_t seed
   double *s = (double *)xcalloc((size_t)n, sizeof(double));
   for (int sw = 0; sw < p->nk_sweeps; ++sw) {
     spmv(A, B, s);
+    ORC_ROWS
     for (int i = 0; i < n; ++i) B[i] = fma(-p->nk_omega, s[i] / diag_of(A, i), B[i]);
   }
   free(s);
@@ -945,10 +973,12 @@ static double power_lmax(const orc_csr *A, const orc_params *p, int l) {
   double lam = 0.0;
   for (int it = 0; it < p->power_iters; ++it) {
     spmv(A, y, z);
+    ORC_ROWS
     for (int i = 0; i < n; ++i) z[i] = z[i] / diag_of(A, i);
     double nz = sqrt(dot(n, z, z)), ny = sqrt(dot(n, y, y));
     lam = nz / ny;
     if (!(nz > 0.0)) break;
+    ORC_ROWS
     for (int i = 0; i < n; ++i) y[i] = z[i] / nz;
   }
   free(y); free(z);
@@ -1139,6 +1169,7 @@ static void reform(orc *o) {
 /* weighted Jacobi: x_i <- fma(omega, (b_i - s_i)/A_ii, x_i), s = A x */
 static void jacobi(const orc_level *L, double *x, const double *b, double *t) {
   spmv(&L->A, x, t);
+  ORC_ROWS
   for (int i = 0; i < L->A.n; ++i) x[i] = fma(L->omega, (b[i] - t[i]) / diag_of(&L->A, i), x[i]);
 }
 
@@ -1171,17 +1202,21 @@ static void chebyshev(const orc *o, const orc_level *L, double *x, const double 
   double *r = (double *)xcalloc((size_t)n, sizeof(double));
   double *d = (double *)xcalloc((size_t)n, sizeof(double));
   spmv(&L->A, x, t);
+  ORC_ROWS
   for (int i = 0; i < n; ++i) {
     r[i] = (b[i] - t[i]) / diag_of(&L->A, i);
     d[i] = r[i] / theta;
   }
   for (int k = 0; k < o->p.smooth_sweeps; ++k) {
+    ORC_ROWS
     for (int i = 0; i < n; ++i) x[i] = x[i] + d[i];
     if (k + 1 == o->p.smooth_sweeps) break;
     spmv(&L->A, d, t);
+    ORC_ROWS
     for (int i = 0; i < n; ++i) r[i] = r[i] - t[i] / diag_of(&L->A, i);
     double rho2 = 1.0 / (2.0 * sigma - rho);
     double c1 = rho2 * rho, c2 = 2.0 * rho2 / delta;
+    ORC_ROWS
     for (int i = 0; i < n; ++i) d[i] = fma(c1, d[i], c2 * r[i]);
     rho = rho2;
   }
@@ -1214,9 +1249,11 @@ static void vcycle_level(orc *o, int l) {
   memset(L->x, 0, sizeof(double) * (size_t)n);
   smooth(o, L, L->x, L->b, L->t, 0);
   spmv(&L->A, L->x, L->t);
+  ORC_ROWS
   for (int i = 0; i < n; ++i) L->r[i] = L->b[i] - L->t[i];
   orc_level *Lc = &o->lev[l + 1];
   const int k = o->p.nk_vectors;
+  ORC_ROWS
   for (int a = 0; a < L->n_agg; ++a)
     for (int c = 0; c < k; ++c) {
       double acc = 0.0;
@@ -1227,6 +1264,7 @@ static void vcycle_level(orc *o, int l) {
       Lc->b[a * k + c] = acc;
     }
   vcycle_level(o, l + 1);
+  ORC_ROWS
   for (int i = 0; i < n; ++i)
     if (L->agg[i] >= 0)
       for (int c = 0; c < k; ++c)
@@ -1262,6 +1300,7 @@ static int pcg(orc *o, const double *b, double *x, orc_solve_info *info) {
     double pq = dot(n, p, q);
     if (!(pq > 0.0) || !(rz > 0.0)) { status = ORC_E_BREAKDOWN; break; }
     double al = rz / pq;
+    ORC_ROWS
     for (int i = 0; i < n; ++i) { x[i] = fma(al, p[i], x[i]); r[i] = fma(-al, q[i], r[i]); }
     rr = dot(n, r, r);
     if (sqrt(rr) <= o->p.pcg_rtol * bnorm) { status = ORC_OK; break; }
@@ -1269,11 +1308,13 @@ static int pcg(orc *o, const double *b, double *x, orc_solve_info *info) {
     double rz2 = dot(n, r, z);
     double be = rz2 / rz;
     rz = rz2;
+    ORC_ROWS
     for (int i = 0; i < n; ++i) p[i] = fma(be, p[i], z[i]);
   }
   info->pcg_iters = k > o->p.pcg_maxiter ? o->p.pcg_maxiter : k;
   info->rel_res = sqrt(rr) / bnorm;
   spmv(A, x, q);
+  ORC_ROWS
   for (int i = 0; i < n; ++i) q[i] = b[i] - q[i];
   info->true_rel_res = sqrt(dot(n, q, q)) / bnorm;
   info->status = status;

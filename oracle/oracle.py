@@ -19,17 +19,26 @@ SRC = os.path.join(HERE, "mgpbd_oracle.c")
 # mutation test's copies with a planted mistake); it is never compiled here.
 OVERRIDE = os.environ.get("MGPBD_ORACLE_LIB")
 LIB = OVERRIDE or os.path.join(HERE, "liborc.so")
+# the same source built with -fopenmp: its row-independent loops run on all
+# host cores and give the same bits as the plain build
+LIB_OMP = os.path.join(HERE, "liborc_omp.so")
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-shared", "-fPIC"]
 
 
+def _compile(out: str, extra, force: bool) -> None:
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, *extra, SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, out)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
+    """Compile the oracle with gcc (no FMA contraction, no fast-math), plain
+    and with OpenMP."""
     if OVERRIDE:
         return LIB
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, SRC, "-o", tmp, "-lm"])
-        os.replace(tmp, LIB)
+    _compile(LIB, [], force)
+    _compile(LIB_OMP, ["-fopenmp"], force)
     return LIB
 
 
@@ -56,14 +65,14 @@ class SolveInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-_lib = None
+_libs: Dict[bool, object] = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
+def lib(omp: bool = False):
+    """The plain oracle library, or with omp=True its OpenMP build."""
+    if omp not in _libs:
         build()
-        L = C.CDLL(LIB)
+        L = C.CDLL(LIB_OMP if omp and not OVERRIDE else LIB)
         vp = C.c_void_p
         L.orc_create.restype = vp
         L.orc_create.argtypes = [C.c_int, vp, vp, C.c_int, vp, C.c_int, vp, C.c_int, vp,
@@ -107,10 +116,17 @@ def lib():
         L.orc_smooth_test.argtypes = [vp, C.c_int, vp, vp]
         L.orc_h64.argtypes = [C.c_uint64]
         L.orc_h64.restype = C.c_uint64
+        L.orc_threads.argtypes = [C.c_int]
+        L.orc_threads.restype = C.c_int
         assert L.orc_sizeof_params() == C.sizeof(Params)
         assert L.orc_sizeof_info() == C.sizeof(SolveInfo)
-        _lib = L
-    return _lib
+        _libs[omp] = L
+    return _libs[omp]
+
+
+def threads(n: int = 0) -> int:
+    """Threads of the OpenMP build's row loops (n > 0 sets them)."""
+    return int(lib(True).orc_threads(n))
 
 
 def _p(a: Optional[np.ndarray]):
@@ -161,10 +177,12 @@ def h64(k: int) -> int:
 
 
 class Oracle:
-    """One oracle instance of a mesh (plain FP64 CPU reference)."""
+    """One oracle instance of a mesh (plain FP64 CPU reference).  omp=True
+    runs it in the OpenMP build (same bits, row loops on all host cores)."""
 
-    def __init__(self, mesh, params: Dict):
-        L = lib()
+    def __init__(self, mesh, params: Dict, omp: bool = False):
+        L = lib(omp)
+        self.L = L
         self.mesh = mesh
         self.params = dict(params)
         self.N, self.E, self.T = mesh.n_verts, mesh.n_dist, mesh.n_tet
@@ -187,77 +205,77 @@ class Oracle:
     def __del__(self):
         h = getattr(self, "h", None)
         if h:
-            lib().orc_destroy(h)
+            self.L.orc_destroy(h)
             self.h = None
 
     # state ---------------------------------------------------------------
     def set_state(self, x, v):
         x = np.ascontiguousarray(x, np.float64)
         v = np.ascontiguousarray(v, np.float64)
-        lib().orc_set_state(self.h, _p(x), _p(v))
+        self.L.orc_set_state(self.h, _p(x), _p(v))
 
     def get_state(self):
         x = np.zeros((self.N, 3))
         v = np.zeros((self.N, 3))
-        lib().orc_get_state(self.h, _p(x), _p(v))
+        self.L.orc_get_state(self.h, _p(x), _p(v))
         return x, v
 
     # integrator ----------------------------------------------------------
     def begin_frame(self):
-        lib().orc_begin_frame(self.h)
+        self.L.orc_begin_frame(self.h)
 
     def end_frame(self):
-        lib().orc_end_frame(self.h)
+        self.L.orc_end_frame(self.h)
 
     def iterate(self) -> Dict:
         inf = SolveInfo()
-        st = lib().orc_iterate(self.h, C.byref(inf))
+        st = self.L.orc_iterate(self.h, C.byref(inf))
         d = inf.as_dict()
         d["ret"] = st
         return d
 
     def step(self, n_frames: int):
         hist = (SolveInfo * (n_frames * self.params["max_iter"]))()
-        st = lib().orc_step(self.h, n_frames, C.cast(hist, C.c_void_p))
+        st = self.L.orc_step(self.h, n_frames, C.cast(hist, C.c_void_p))
         return st, [h.as_dict() for h in hist]
 
     def eval_assemble(self):
-        lib().orc_eval_assemble(self.h)
+        self.L.orc_eval_assemble(self.h)
 
     def setup(self) -> int:
-        return lib().orc_setup(self.h)
+        return self.L.orc_setup(self.h)
 
     def prepare_solve(self) -> int:
-        return lib().orc_prepare_solve(self.h)
+        return self.L.orc_prepare_solve(self.h)
 
     def solve(self, b):
         b = np.ascontiguousarray(b, np.float64)
         x = np.zeros(self.m)
         inf = SolveInfo()
-        lib().orc_solve(self.h, _p(b), _p(x), C.byref(inf))
+        self.L.orc_solve(self.h, _p(b), _p(x), C.byref(inf))
         return x, inf.as_dict()
 
     def smooth(self, level: int, b):
         """Test-only: one pre-smoothing of `level` from x = 0."""
         b = np.ascontiguousarray(b, np.float64)
         x = np.zeros_like(b)
-        lib().orc_smooth_test(self.h, level, _p(b), _p(x))
+        self.L.orc_smooth_test(self.h, level, _p(b), _p(x))
         return x
 
     def vcycle(self, r):
         r = np.ascontiguousarray(r, np.float64)
         z = np.zeros(self.m)
-        lib().orc_vcycle(self.h, _p(r), _p(z))
+        self.L.orc_vcycle(self.h, _p(r), _p(z))
         return z
 
     # inspection ----------------------------------------------------------
     @property
     def levels(self) -> int:
-        return lib().orc_levels(self.h)
+        return self.L.orc_levels(self.h)
 
     @property
     def n_setups(self) -> int:
-        return lib().orc_n_setups(self.h)
+        return self.L.orc_n_setups(self.h)
 
     def matrix(self, level: int = 0):
         L = lib()
@@ -270,9 +288,9 @@ class Oracle:
         return ptr, col, val
 
     def assembly_map(self):
-        nnz = lib().orc_nnz(self.h, 0)
+        nnz = self.L.orc_nnz(self.h, 0)
         m = np.zeros(nnz, np.uint16)
-        lib().orc_map(self.h, _p(m))
+        self.L.orc_map(self.h, _p(m))
         return m
 
     def incidence(self):
@@ -280,32 +298,32 @@ class Oracle:
         tot = 2 * self.E + 4 * self.T
         vptr = np.zeros(self.N + 1, np.int64)
         vrow = np.zeros(tot, np.int32)
-        lib().orc_incidence(self.h, _p(vptr), _p(vrow))
+        self.L.orc_incidence(self.h, _p(vptr), _p(vrow))
         return vptr, vrow
 
     def level_agg(self, level: int):
         """(n_agg, agg, root, P, B); P and B are (n,) for one near-kernel
         vector and (n, k) for k > 1."""
-        n = lib().orc_rows(self.h, level)
+        n = self.L.orc_rows(self.h, level)
         k = int(self.params.get("nk_vectors", 1))
         agg = np.zeros(n, np.int32)
         root = np.zeros(n, np.uint8)
         P = np.zeros(n * k)
         B = np.zeros(n * k)
-        na = lib().orc_level_agg(self.h, level, _p(agg), _p(root), _p(P), _p(B))
+        na = self.L.orc_level_agg(self.h, level, _p(agg), _p(root), _p(P), _p(B))
         if k > 1:
             P, B = P.reshape(n, k), B.reshape(n, k)
         return na, agg, root, P, B
 
     def level_color(self, level: int):
-        n = lib().orc_rows(self.h, level)
+        n = self.L.orc_rows(self.h, level)
         c = np.zeros(n, np.int32)
-        nc = lib().orc_level_color(self.h, level, _p(c))
+        nc = self.L.orc_level_color(self.h, level, _p(c))
         return nc, c
 
     def level_omega(self, level: int):
         a, b = C.c_double(), C.c_double()
-        lib().orc_level_omega(self.h, level, C.byref(a), C.byref(b))
+        self.L.orc_level_omega(self.h, level, C.byref(a), C.byref(b))
         return a.value, b.value
 
     def constraints(self):
@@ -313,21 +331,21 @@ class Oracle:
         b = np.zeros(self.m)
         gd = np.zeros((self.E, 3))
         gt = np.zeros((self.T, 4, 3))
-        lib().orc_constraints(self.h, _p(Cv), _p(b), _p(gd), _p(gt))
+        self.L.orc_constraints(self.h, _p(Cv), _p(b), _p(gd), _p(gt))
         return Cv, b, gd, gt
 
     def rest(self):
         L0 = np.zeros(self.E)
         V0 = np.zeros(self.T)
-        lib().orc_rest(self.h, _p(L0), _p(V0))
+        self.L.orc_rest(self.h, _p(L0), _p(V0))
         return L0, V0
 
     def lam(self):
         lam = np.zeros(self.m)
         dl = np.zeros(self.m)
-        lib().orc_lambda(self.h, _p(lam), _p(dl))
+        self.L.orc_lambda(self.h, _p(lam), _p(dl))
         return lam, dl
 
     def set_lambda(self, lam):
         lam = np.ascontiguousarray(lam, np.float64)
-        lib().orc_set_lambda(self.h, _p(lam))
+        self.L.orc_set_lambda(self.h, _p(lam))
