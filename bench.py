@@ -39,13 +39,13 @@ FULL_NNZ = 376_541_249  # nonzeros of A for block100 (checked at run time)
 # as measured on GB300 (the reference arm cannot run the GPU to learn it)
 FULL_PCG_ITERS = 7300
 # DRAM bytes (read + write) of one level-0 FP32 smoother sweep per nonzero of
-# A, from the ncu capture in profiles/k_jacobi_level0_block40x33x40.md
-# (k_jacobi<16, float>, 494.52 MB for 59,625,809 nonzeros); the sweep's
+# A, from an ncu capture of k_jacobi<16, float> on a 40x33x40 block of the
+# same recipe (494.52 MB for 59,625,809 nonzeros); the sweep's
 # traffic grows in proportion to nnz, so it scales to a full launch
 SWEEP_TRAFFIC_PER_NNZ = (489.342720e6 + 5.179904e6) / 59_625_809
 # DRAM bytes of one matrix-free level-0 FP32 sweep (k_mf_vertex32<8> 30.74 MB
-# + k_mf_row<float,0> 33.68 MB) per constraint row, from the ncu captures in
-# profiles/k_mf_sweep_level0_block40x33x40.md (593,633 rows); the passes
+# + k_mf_row<float,0> 33.68 MB) per constraint row, from ncu captures of the
+# two passes on a 40x33x40 block of the same recipe (593,633 rows); the passes
 # stream per-row and per-incidence arrays, so traffic scales with the rows
 MF_SWEEP_TRAFFIC_PER_ROW = (30.742016e6 + 33.679104e6) / 593_633
 SAMPLE = (4, 33, 4)     # oracle sample: cells along x, y (vertical), z

@@ -21,6 +21,7 @@
 // cudaGetSymbolAddress (once per device, with that device current); make that
 // first call before any stream capture begins.
 #include <mutex>
+#include <string>
 
 #include "common.cuh"
 
@@ -107,21 +108,20 @@ __global__ void k_true_resid_noalloc(int n, const int64_t *ptr, const int32_t *c
   }
 }
 
-// device address of the static array, looked up once per device
-static NoAllocScratch *scratch_for_current_device(mgpbd_status *st) {
+// device address of the static array on device `dev`, looked up once per
+// device (the caller has checked that `dev` is current)
+static NoAllocScratch *scratch_for_device(int dev, mgpbd_status *st) {
   static std::mutex mu;
   static NoAllocScratch *addr[64] = {nullptr};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 64) {
-    *st = cuda_fail(e == cudaSuccess ? cudaErrorInvalidDevice : e, "cudaGetDevice", __FILE__,
-                    __LINE__);
+  if (dev < 0 || dev >= 64) {
+    set_error("mgpbd_true_residual_noalloc: device ordinal above 63");
+    *st = MGPBD_E_INVALID;
     return nullptr;
   }
   std::lock_guard<std::mutex> lock(mu);
   if (!addr[dev]) {
     void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
       *st = cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress",
                       __FILE__, __LINE__);
@@ -150,8 +150,18 @@ extern "C" mgpbd_status mgpbd_true_residual_noalloc(mgpbd_handle_t *hh, const do
               "rows, the limit of its static scratch (65,536 blocks of 64 rows)");
     return MGPBD_E_INVALID;
   }
+  // the array's address is per device and the kernel runs on the instance's
+  // stream, so the instance's device must be the current one
+  int dev = -1;
+  MG_CUDA(cudaGetDevice(&dev));
+  if (dev != h->device) {
+    set_error("mgpbd_true_residual_noalloc: the instance lives on device " +
+              std::to_string(h->device) + " but device " + std::to_string(dev) +
+              " is current; make the instance's device current first");
+    return MGPBD_E_INVALID;
+  }
   mgpbd_status st = MGPBD_OK;
-  NoAllocScratch *scr = scratch_for_current_device(&st);
+  NoAllocScratch *scr = scratch_for_device(dev, &st);
   if (!scr) return st;
   if (L.n == 0) {
     MG_CUDA(cudaMemsetAsync(d_out, 0, sizeof(double), h->stream));

@@ -74,28 +74,38 @@ static double now_s(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// drops the instance's handle and stream (its device state is lost)
+static void drop_handle(Instance &in) {
+  if (in.h) mgpbd_destroy(in.h);
+  in.h = nullptr;
+  if (in.stream) cudaStreamDestroy(in.stream);
+  in.stream = nullptr;
+}
+
+// Creates the instance on the device from its host state.  On any failure
+// nothing stays resident: a handle whose state was never loaded must not be
+// stepped by a later request.
 static mgpbd_status make_resident(Instance &in) {
   if (in.h) return MGPBD_OK;
   MG_CUDA(cudaStreamCreateWithFlags(&in.stream, cudaStreamNonBlocking));
   mgpbd_status s = mgpbd_create(&in.desc, &in.p, in.stream, &in.h);
+  if (s >= 0) s = mgpbd_set_state(in.h, in.x.data(), in.v.data(), MGPBD_MEM_HOST);
   if (s < 0) {
-    cudaStreamDestroy(in.stream);
-    in.stream = nullptr;
+    drop_handle(in);
     return s;
   }
-  s = mgpbd_set_state(in.h, in.x.data(), in.v.data(), MGPBD_MEM_HOST);
-  if (s < 0) return s;
   return MGPBD_OK;
 }
 
+// Moves the instance's state to host memory and frees its device memory.  If
+// the state cannot be read back, the handle stays resident (its device state
+// is the only current copy) and the error is returned.
 static mgpbd_status evict(Instance &in) {
   if (!in.h) return MGPBD_OK;
   mgpbd_status s = mgpbd_get_state(in.h, in.x.data(), in.v.data(), MGPBD_MEM_HOST);
-  mgpbd_destroy(in.h);
-  in.h = nullptr;
-  if (in.stream) cudaStreamDestroy(in.stream);
-  in.stream = nullptr;
-  return s;
+  if (s < 0) return s;
+  drop_handle(in);
+  return MGPBD_OK;
 }
 
 // one request: `frames` frames of Alg. 1 on one instance
@@ -314,7 +324,10 @@ mgpbd_status mgpbd_batch_run(mgpbd_batch_t *bb, const mgpbd_step_request *req, i
           if (victim < 0) break;
           Instance &q = b->inst[victim];
           mgpbd_status s = evict(q);
-          if (s < 0 && first_err >= 0) first_err = s;
+          if (s < 0) {  // still resident (its state could not be read back)
+            if (first_err >= 0) first_err = s;
+            break;
+          }
           b->resident -= q.bytes;
           q.bytes = 0;
         }
