@@ -234,6 +234,20 @@ mgpbd_status mgpbd_stats(mgpbd_handle_t *h, mgpbd_stats_t *s);
 /* ---- inspection (host or device destinations per `mem`; synchronise) ---- */
 mgpbd_status mgpbd_sizes(mgpbd_handle_t *h, int *n_verts, int *n_rows, int64_t *nnz);
 mgpbd_status mgpbd_level_info_get(mgpbd_handle_t *h, int level, mgpbd_level_info *info);
+/* Shapes of the row kernels (not in the paper: they decide only how the
+ * GPU splits a row sum or a vertex sum among threads, which changes the
+ * rounding order of that sum).  mgpbd_set_lanes forces, for every level,
+ *   csr32, csr64    lanes per CSR row of the FP32 and FP64 row kernels
+ *                   (sweeps, residuals, A.p): 4, 8, 16 or 32
+ *   vert32, vert64  lanes per vertex of the matrix-free vertex pass
+ *                   u = W J^T x in FP32 and FP64: 4, 8 or 16
+ * with 0 meaning "the autotuner's pick, else the fixed rule".  Forced shapes
+ * take precedence over params.autotune and stay in force across setups.  No
+ * device work.  MGPBD_E_INVALID for another value.  mgpbd_get_lanes returns
+ * the shapes in effect on level `level` (the vertex shapes are level 0's). */
+mgpbd_status mgpbd_set_lanes(mgpbd_handle_t *h, int csr32, int csr64, int vert32, int vert64);
+mgpbd_status mgpbd_get_lanes(mgpbd_handle_t *h, int level, int *csr32, int *csr64, int *vert32,
+                             int *vert64);
 /* CSR of level `level`: ptr [n+1] int64, col [nnz] int32, val [nnz] double
  * (diagonal last in each row); any pointer may be NULL. */
 mgpbd_status mgpbd_get_matrix(mgpbd_handle_t *h, int level, int64_t *ptr, int32_t *col,
@@ -359,7 +373,8 @@ mgpbd_status mgpbd_convert(const double *d_in64, float *d_out32, const float *d_
  * (the block counter is cleared before each launch), so calls that overlap
  * on the GPU race and must be serialised by the caller.  The first call on a
  * device looks up the array's address (once per device); make it before any
- * stream capture starts.  Instances with more than 4,194,304 constraint rows
+ * stream capture starts.  The instance's device (current at its create) must
+ * be the current device, else MGPBD_E_INVALID.  Instances with more than 4,194,304 constraint rows
  * are rejected with MGPBD_E_INVALID (the array holds 65,536 blocks of 64 rows). */
 mgpbd_status mgpbd_true_residual_noalloc(mgpbd_handle_t *h, const double *d_b, const double *d_x,
                                          double *d_out);

@@ -330,6 +330,12 @@ static mgpbd_status create(const mgpbd_mesh_desc *md, const mgpbd_params *p, voi
 
   Handle *h = new Handle();
   h->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    set_error("create: cudaGetDevice failed");
+    return MGPBD_E_CUDA;
+  }
   h->arena.stream = h->stream;
   if (ws) h->arena.use_workspace(ws, ws_bytes);
   h->p = *p;
@@ -763,6 +769,35 @@ mgpbd_status mgpbd_level_info_get(mgpbd_handle_t *hh, int level, mgpbd_level_inf
   info->omega = L.omega;
   info->lanes_fp32 = L.G32;
   info->lanes_fp64 = L.G64;
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_set_lanes(mgpbd_handle_t *hh, int csr32, int csr64, int vert32, int vert64) {
+  Handle *h = H(hh);
+  auto csr_ok = [](int g) { return g == 0 || g == 4 || g == 8 || g == 16 || g == 32; };
+  auto vert_ok = [](int g) { return g == 0 || g == 4 || g == 8 || g == 16; };
+  if (!h || !csr_ok(csr32) || !csr_ok(csr64) || !vert_ok(vert32) || !vert_ok(vert64)) {
+    set_error("mgpbd_set_lanes: lanes per CSR row must be 0, 4, 8, 16 or 32 and lanes per "
+              "vertex 0, 4, 8 or 16");
+    return MGPBD_E_INVALID;
+  }
+  h->force_csr32 = csr32;
+  h->force_csr64 = csr64;
+  h->force_vert32 = vert32;
+  h->force_vert64 = vert64;
+  h->gen++;  // a captured PCG graph holds the previous shapes
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_get_lanes(mgpbd_handle_t *hh, int level, int *csr32, int *csr64, int *vert32,
+                             int *vert64) {
+  Handle *h = H(hh);
+  if (!h || level < 0 || level >= std::max(h->L, 1)) return MGPBD_E_INVALID;
+  const Level &L = h->lev[level];
+  if (csr32) *csr32 = group_for(h, L, false);
+  if (csr64) *csr64 = group_for(h, L, true);
+  if (vert32) *vert32 = h->force_vert32 ? h->force_vert32 : h->mf_g32;
+  if (vert64) *vert64 = h->force_vert64 ? h->force_vert64 : h->mf_g64;
   return MGPBD_OK;
 }
 

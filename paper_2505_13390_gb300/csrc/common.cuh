@@ -140,6 +140,7 @@ struct Level {
 
 struct Handle {
   cudaStream_t stream = nullptr;
+  int device = 0;            // CUDA device that was current at create
   mgpbd_params p{};
   int N = 0, E = 0, T = 0, m = 0;
   Arena arena;
@@ -162,6 +163,9 @@ struct Handle {
   float4 *ginc4 = nullptr;  // FP32 gradient and row id (bits in .w) per incidence
   float *gd32 = nullptr, *gt32 = nullptr, *at32 = nullptr, *w32 = nullptr, *u32 = nullptr;
   int mf_g32 = 8, mf_g64 = 4;  // lanes per vertex of the vertex pass (autotuned)
+  // lanes forced by mgpbd_set_lanes (0 = autotuned or rule): CSR rows in FP32
+  // and FP64, matrix-free vertices in FP32 and FP64
+  int force_csr32 = 0, force_csr64 = 0, force_vert32 = 0, force_vert64 = 0;
   int32_t *vorder = nullptr;   // vertex-pass order: by incidence count within windows
   uint16_t *map = nullptr;
   uint8_t *S = nullptr;  // strength mask, reused per level (grown when a level has more nnz)
@@ -270,6 +274,7 @@ mgpbd_status mf_create(Handle *h);
 mgpbd_status mf_prepare(Handle *h);
 
 // solve.cu
+int group_for(const Handle *h, const Level &L, bool fp64);  // lanes per row in effect
 mgpbd_status autotune_levels(Handle *h);
 mgpbd_status coarsest_factor(Handle *h);
 mgpbd_status pcg_solve(Handle *h, const double *d_b, double *d_x, mgpbd_solve_info *info);

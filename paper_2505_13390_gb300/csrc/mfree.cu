@@ -321,7 +321,7 @@ static int mf_vertex_blocks(const Handle *h, int G) {
 
 // u = W J^T x (FP64: u64; FP32: u32); G = 0 takes the tuned lanes per vertex
 static mgpbd_status mf_vertex(Handle *h, const double *x, int G = 0, bool check_done = true) {
-  if (G == 0) G = h->mf_g64;
+  if (G == 0) G = h->force_vert64 ? h->force_vert64 : h->mf_g64;
   const PcgScalars *sc = check_done ? h->sc : nullptr;
   MF_G_DISPATCH(G, (k_mf_vertex64<GG><<<mf_vertex_blocks(h, GG), 256, 0, h->stream>>>(
                        h->N, h->vorder, h->vptr, h->vrow, h->ginc64, h->w, x, h->u64, sc)));
@@ -330,7 +330,7 @@ static mgpbd_status mf_vertex(Handle *h, const double *x, int G = 0, bool check_
 }
 
 static mgpbd_status mf_vertex(Handle *h, const float *x, int G = 0, bool check_done = true) {
-  if (G == 0) G = h->mf_g32;
+  if (G == 0) G = h->force_vert32 ? h->force_vert32 : h->mf_g32;
   const PcgScalars *sc = check_done ? h->sc : nullptr;
   MF_G_DISPATCH(G, (k_mf_vertex32<GG><<<mf_vertex_blocks(h, GG), 256, 0, h->stream>>>(
                        h->N, h->vorder, h->vptr, h->ginc4, h->w32, x, h->u32, sc)));

@@ -111,6 +111,9 @@ SIGNATURES = {
     "mgpbd_stats": (_i, [_vp, C.POINTER(Stats)]),
     "mgpbd_sizes": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i64)]),
     "mgpbd_level_info_get": (_i, [_vp, _i, C.POINTER(LevelInfo)]),
+    "mgpbd_set_lanes": (_i, [_vp, _i, _i, _i, _i]),
+    "mgpbd_get_lanes": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i),
+                             C.POINTER(_i)]),
     "mgpbd_get_matrix": (_i, [_vp, _i, _vp, _vp, _vp, _i]),
     "mgpbd_get_map": (_i, [_vp, _vp, _i]),
     "mgpbd_get_incidence": (_i, [_vp, _vp, _vp, _i]),
@@ -346,6 +349,17 @@ class Solver:
         li = LevelInfo()
         _check(load().mgpbd_level_info_get(self.h, level, C.byref(li)), "level_info")
         return li.as_dict()
+
+    def set_lanes(self, csr32: int = 0, csr64: int = 0, vert32: int = 0, vert64: int = 0):
+        """Force the row-kernel shapes (lanes per CSR row, lanes per vertex of
+        the matrix-free vertex pass; 0 = autotuned or rule) on every level."""
+        _check(load().mgpbd_set_lanes(self.h, csr32, csr64, vert32, vert64), "set_lanes")
+
+    def lanes(self, level: int = 0) -> Dict:
+        """The row-kernel shapes in effect on a level."""
+        v = [C.c_int() for _ in range(4)]
+        _check(load().mgpbd_get_lanes(self.h, level, *[C.byref(x) for x in v]), "get_lanes")
+        return dict(zip(("csr32", "csr64", "vert32", "vert64"), (x.value for x in v)))
 
     @property
     def levels(self) -> int:
