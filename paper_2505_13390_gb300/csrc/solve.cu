@@ -415,64 +415,163 @@ __global__ void k_dense_fill(int n, const int64_t *ptr, const int32_t *col, cons
       Ad[(int64_t)i * n + col[k]] = val[k];
 }
 
-// right-looking Cholesky in place (lower triangle), one block
-__global__ void k_cholesky(int n, double *A, int *status) {
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
+// Tiled over 16 x 16 tiles, one tile per block of 256 threads (one entry per
+// thread).  FP64 throughput per SM is low on this part (about 1.6 fused
+// multiply-adds per clock), so the n^3 work is spread over many blocks:
+//   Cholesky, right-looking: for each tile column k, a panel launch factors
+//     the diagonal tile in shared memory (every block of the launch redundantly,
+//     so no block waits on another) and forms L_ik = A_ik L_kk^-T below it,
+//     then a trailing launch applies A_ij -= L_ik L_jk^T to the tiles right of it;
+//   L^-1, by tile rows: step p adds -L_ip Li_pj into the tiles of rows below
+//     p, after which row p + 1 is complete: Li_{p+1,j} = L_{p+1,p+1}^-1 times
+//     its sum (the inverses of the diagonal tiles come from the panels);
+//   A^-1 = L^-T L^-1, one launch, tile (i, j) summing Li_ki^T Li_kj over
+//     k >= max(i, j) in ascending k (so A^-1 is bitwise symmetric).
+// Entries outside the n x n matrix read as 0 (1 on the diagonal of the last
+// diagonal tile), i.e. the factorisation of diag(A, I), whose leading block
+// is A's; they are never stored.  A pivot <= 0 sets *status to
+// MGPBD_E_SINGULAR and every later launch returns at once.
+constexpr int kCT = 16;
+constexpr int kCThreads = kCT * kCT;
+
+__device__ __forceinline__ bool chol_failed(const int *status) {
+  return *(volatile const int *)status != MGPBD_OK;
+}
+
+__device__ __forceinline__ double tile_get(const double *M, int n, int ti, int tj, int r, int c,
+                                           bool ident) {
+  const int gr = ti * kCT + r, gc = tj * kCT + c;
+  if (gr < n && gc < n) return M[(int64_t)gr * n + gc];
+  return (ident && gr == gc) ? 1.0 : 0.0;
+}
+
+__device__ __forceinline__ void tile_put(double *M, int n, int ti, int tj, int r, int c,
+                                         double v) {
+  const int gr = ti * kCT + r, gc = tj * kCT + c;
+  if (gr < n && gc < n) M[(int64_t)gr * n + gc] = v;
+}
+
+// Cholesky of the tile in D (lower part, in place) and the inverse X of the
+// lower factor (zero above the diagonal); false on a pivot <= 0 (the same in
+// every thread of the block)
+__device__ bool tile_factor(double (*D)[kCT + 1], double (*X)[kCT + 1], int *bad) {
+  const int t = threadIdx.x, r = t / kCT, c = t % kCT;
+  for (int j = 0; j < kCT; ++j) {
+    if (t == 0) {
+      const double d = D[j][j];
+      if (!(d > 0.0)) *bad = 1;
+      else D[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    if (*bad) return false;
+    if (c == j && r > j) D[r][j] = D[r][j] / D[j][j];
+    __syncthreads();
+    if (c > j && r >= c) D[r][c] = fma(-D[r][j], D[c][j], D[r][c]);
+    __syncthreads();
+  }
+  if (t < kCT) {  // column t of the inverse by forward substitution
+    for (int i = 0; i < kCT; ++i) {
+      if (i < t) {
+        X[i][t] = 0.0;
+        continue;
+      }
+      double s = i == t ? 1.0 : 0.0;
+      for (int q = t; q < i; ++q) s = fma(-D[i][q], X[q][t], s);
+      X[i][t] = s / D[i][i];
+    }
+  }
   __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) {
-      double d = A[(int64_t)j * n + j];
-      if (!(d > 0.0)) bad = 1;
-      else A[(int64_t)j * n + j] = sqrt(d);
-    }
-    __syncthreads();
-    if (bad) break;
-    double ljj = A[(int64_t)j * n + j];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(int64_t)i * n + j] /= ljj;
-    __syncthreads();
-    // trailing update of the lower triangle: A_ik -= L_ij L_kj, j < k <= i
-    int64_t m = n - j - 1;
-    int64_t tri = m * (m + 1) / 2;
-    for (int64_t t = threadIdx.x; t < tri; t += blockDim.x) {
-      // t -> (ii, kk) with 0 <= kk <= ii < m, row-major over the triangle
-      int64_t ii = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-      while (ii * (ii + 1) / 2 > t) --ii;
-      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-      int64_t kk = t - ii * (ii + 1) / 2;
-      int64_t i = j + 1 + ii, k = j + 1 + kk;
-      A[i * n + k] = fma(-A[i * n + j], A[k * n + j], A[i * n + k]);
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *status = bad ? MGPBD_E_SINGULAR : MGPBD_OK;
+  return true;
 }
 
-// column c of L^-1 (thread per column, forward substitution), row-major Li[k][c]
-__global__ void k_tri_inverse(int n, const double *Lm, double *Li, const int *status) {
-  if (*status != MGPBD_OK) return;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-    for (int i = 0; i < c; ++i) Li[(int64_t)i * n + c] = 0.0;
-    for (int i = c; i < n; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int k = c; k < i; ++k) s = fma(-Lm[(int64_t)i * n + k], Li[(int64_t)k * n + c], s);
-      Li[(int64_t)i * n + c] = s / Lm[(int64_t)i * n + i];
-    }
+// panel of tile column k: block b handles tile row k + b.  Block 0 stores the
+// inverse of the diagonal factor into Li; the others store L_ik = A_ik L_kk^-T
+// over A_ik.  (A_kk itself is read by every block and written by none.)
+__global__ void __launch_bounds__(kCThreads) k_chol_panel(int n, int k, double *A, double *Li,
+                                                          int *status) {
+  __shared__ double D[kCT][kCT + 1], X[kCT][kCT + 1];
+  __shared__ int bad;
+  if (chol_failed(status)) return;
+  const int t = threadIdx.x, r = t / kCT, c = t % kCT;
+  const int i = k + blockIdx.x;
+  if (t == 0) bad = 0;
+  D[r][c] = tile_get(A, n, k, k, r, c, true);
+  __syncthreads();
+  if (!tile_factor(D, X, &bad)) {
+    if (blockIdx.x == 0 && t == 0) *status = MGPBD_E_SINGULAR;
+    return;
   }
+  if (blockIdx.x == 0) {
+    tile_put(Li, n, k, k, r, c, X[r][c]);
+    return;
+  }
+  D[r][c] = tile_get(A, n, i, k, r, c, false);  // D is free after the factor
+  __syncthreads();
+  double s = 0.0;
+  for (int q = 0; q <= c; ++q) s = fma(D[r][q], X[c][q], s);
+  tile_put(A, n, i, k, r, c, s);
 }
 
-// A^-1 = L^-T L^-1: inv[i][j] = sum_{k >= max(i,j)} Li[k][i] Li[k][j]
-__global__ void k_inv_gram(int n, const double *Li, double *inv, const int *status) {
-  if (*status != MGPBD_OK) return;
-  int64_t tot = (int64_t)n * n;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int i = (int)(t / n), j = (int)(t % n);
-    int k0 = max(i, j);
-    double s = 0.0;
-    for (int k = k0; k < n; ++k) s = fma(Li[(int64_t)k * n + i], Li[(int64_t)k * n + j], s);
-    inv[t] = s;
+// trailing update after tile column k: block (x, y) is tile (k+1+y, k+1+x)
+// of the lower triangle (blocks above the diagonal return)
+__global__ void __launch_bounds__(kCThreads) k_chol_trail(int n, int k, double *A,
+                                                          const int *status) {
+  __shared__ double Lr[kCT][kCT + 1], Lc[kCT][kCT + 1];
+  if (chol_failed(status)) return;
+  const int i = k + 1 + blockIdx.y, j = k + 1 + blockIdx.x;
+  if (j > i) return;
+  const int t = threadIdx.x, r = t / kCT, c = t % kCT;
+  Lr[r][c] = tile_get(A, n, i, k, r, c, false);
+  Lc[r][c] = tile_get(A, n, j, k, r, c, false);
+  __syncthreads();
+  double a = tile_get(A, n, i, j, r, c, false);
+  for (int q = 0; q < kCT; ++q) a = fma(-Lr[r][q], Lc[c][q], a);
+  tile_put(A, n, i, j, r, c, a);
+}
+
+// step p of L^-1 (Li's off-diagonal tiles start at zero): block (x, y) is
+// tile (p+1+y, x), x <= p; it adds -L_ip Li_pj and, on row p + 1, finishes
+// the tile with the diagonal inverse
+__global__ void __launch_bounds__(kCThreads) k_trtri_step(int n, int p, const double *A,
+                                                          double *Li, const int *status) {
+  __shared__ double L1[kCT][kCT + 1], M[kCT][kCT + 1];
+  if (chol_failed(status)) return;
+  const int i = p + 1 + blockIdx.y, j = blockIdx.x;
+  const int t = threadIdx.x, r = t / kCT, c = t % kCT;
+  L1[r][c] = tile_get(A, n, i, p, r, c, false);
+  M[r][c] = tile_get(Li, n, p, j, r, c, false);
+  __syncthreads();
+  double s = tile_get(Li, n, i, j, r, c, false);
+  for (int q = 0; q < kCT; ++q) s = fma(-L1[r][q], M[q][c], s);
+  if (i != p + 1) {
+    tile_put(Li, n, i, j, r, c, s);
+    return;
   }
+  __syncthreads();
+  M[r][c] = s;
+  L1[r][c] = tile_get(Li, n, i, i, r, c, false);
+  __syncthreads();
+  double v = 0.0;
+  for (int q = 0; q <= r; ++q) v = fma(L1[r][q], M[q][c], v);
+  tile_put(Li, n, i, j, r, c, v);
+}
+
+// A^-1 = L^-T L^-1: block (x, y) is tile (y, x)
+__global__ void __launch_bounds__(kCThreads) k_inv_gram(int n, int T, const double *Li,
+                                                        double *inv, const int *status) {
+  __shared__ double Pt[kCT][kCT + 1], Qt[kCT][kCT + 1];
+  if (chol_failed(status)) return;
+  const int i = blockIdx.y, j = blockIdx.x;
+  const int t = threadIdx.x, r = t / kCT, c = t % kCT;
+  double s = 0.0;
+  for (int k = max(i, j); k < T; ++k) {
+    Pt[r][c] = tile_get(Li, n, k, i, r, c, false);
+    Qt[r][c] = tile_get(Li, n, k, j, r, c, false);
+    __syncthreads();
+    for (int q = 0; q < kCT; ++q) s = fma(Pt[q][r], Qt[q][c], s);
+    __syncthreads();
+  }
+  tile_put(inv, n, i, j, r, c, s);
 }
 
 mgpbd_status coarsest_factor(Handle *h) {
@@ -492,12 +591,25 @@ mgpbd_status coarsest_factor(Handle *h) {
   k_dense_fill<<<std::max(1, std::min(n, 4096)), 128, 0, h->stream>>>(n, L.ptr, L.col, L.val,
                                                                       h->cdense);
   MG_LAUNCH("k_dense_fill");
-  k_cholesky<<<1, 1024, 0, h->stream>>>(n, h->cdense, h->cstat);
-  MG_LAUNCH("k_cholesky");
   double *Li = h->cinv + (size_t)n * n;
-  k_tri_inverse<<<blocks_for(n, 32), 32, 0, h->stream>>>(n, h->cdense, Li, h->cstat);
-  MG_LAUNCH("k_tri_inverse");
-  k_inv_gram<<<blocks_for((int64_t)n * n, 256), 256, 0, h->stream>>>(n, Li, h->cinv, h->cstat);
+  MG_CUDA(cudaMemsetAsync(Li, 0, sizeof(double) * (size_t)n * n, h->stream));
+  MG_CUDA(cudaMemsetAsync(h->cstat, 0, sizeof(int), h->stream));  // MGPBD_OK
+  const int T = (n + kCT - 1) / kCT;
+  for (int k = 0; k < T; ++k) {
+    k_chol_panel<<<T - k, kCThreads, 0, h->stream>>>(n, k, h->cdense, Li, h->cstat);
+    MG_LAUNCH("k_chol_panel");
+    if (k + 1 < T) {
+      k_chol_trail<<<dim3(T - k - 1, T - k - 1), kCThreads, 0, h->stream>>>(n, k, h->cdense,
+                                                                            h->cstat);
+      MG_LAUNCH("k_chol_trail");
+    }
+  }
+  for (int p = 0; p + 1 < T; ++p) {
+    k_trtri_step<<<dim3(p + 1, T - 1 - p), kCThreads, 0, h->stream>>>(n, p, h->cdense, Li,
+                                                                      h->cstat);
+    MG_LAUNCH("k_trtri_step");
+  }
+  k_inv_gram<<<dim3(T, T), kCThreads, 0, h->stream>>>(n, T, Li, h->cinv, h->cstat);
   MG_LAUNCH("k_inv_gram");
   int st = 0;
   MG_CUDA(cudaMemcpyAsync(h->flag_host, h->cstat, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -523,7 +635,10 @@ static int group_rule(const Level &L, bool fp64) {
   return avg <= 12 ? 4 : (avg <= 24 ? 8 : (avg <= 48 ? 16 : 32));
 }
 
-static int group_for(const Level &L, bool fp64 = false) {
+// lanes per row in effect: forced (mgpbd_set_lanes), else autotuned, else the rule
+int group_for(const Handle *h, const Level &L, bool fp64) {
+  const int f = fp64 ? h->force_csr64 : h->force_csr32;
+  if (f) return f;
   int g = fp64 ? L.G64 : L.G32;
   return g ? g : group_rule(L, fp64);
 }
@@ -580,7 +695,7 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in, bool x0_ready 
     MG_LAUNCH("k_coarse_apply");
     return MGPBD_OK;
   }
-  const int G = group_for(L, sizeof(T) == 8);
+  const int G = group_for(h, L, sizeof(T) == 8);
   const T om = (T)L.omega;
   const T *val = vals<T>(L);
   const T *dinv = dinvs<T>(L);
@@ -777,7 +892,7 @@ static mgpbd_status pcg_iteration(Handle *h, double *x) {
   Level &L = h->lev[0];
   const int m = h->m;
   double *r = h->pr, *z = h->pz, *p = h->pp, *q = h->pq;
-  const int G = group_for(L, true);
+  const int G = group_for(h, L, true);
   DotCtx cpq = make_ctx(h, DOT_PQ);
   // A.p is part of the Krylov recurrence, not of the preconditioner, and stays
   // FP64 in both modes: rounding A's values to FP32 perturbs entries of size

@@ -546,3 +546,71 @@ def test_iterations_parity_six_vectors(name, iters, op):
         xo, _ = o.get_state()
         xg, _ = g.get_state()
         assert np.abs(xg - xo).max() <= 1e-9 * scale, f"iteration {it}"
+
+
+def chain(n_rows, alpha, pin_last_two=False):
+    """A straight chain of n_rows distance rows (n_rows + 1 unit-mass
+    vertices 1 cm apart), slightly stretched."""
+    from paper_2505_13390_gb300.meshgen import Mesh
+    nv = n_rows + 1
+    rest = np.zeros((nv, 3))
+    rest[:, 0] = 0.01 * np.arange(nv)
+    w = np.ones(nv)
+    if pin_last_two:
+        w[-2:] = 0.0
+    edges = np.stack([np.arange(n_rows), np.arange(1, nv)], 1).astype(np.int32)
+    x0 = rest.copy()
+    x0[:, 0] *= 1.001
+    return Mesh("chain", rest, w, edges, np.zeros((0, 4), np.int32), np.asarray(alpha, float),
+                x0, np.zeros((nv, 3)))
+
+
+@pytest.mark.parametrize("n_rows", [1, 16, 17, 300])
+def test_coarsest_inverse_against_dense_solve(n_rows):
+    """A one-level hierarchy (coarse_max above the row count): the V-cycle is
+    the coarsest solve alone, z = A^-1 r through the tiled Cholesky and
+    inverse, and equals a dense solve of the oracle's A (one tile, a ragged
+    second tile, 19 tiles with a ragged tail)."""
+    mesh = chain(n_rows, np.full(n_rows, 1e-6))
+    p = default_params(coarse_max=1000, gravity=(0.0, 0.0, 0.0))
+    o, g = Oracle(mesh, p), solver(mesh, p)
+    for s_ in (o, g):
+        s_.begin_frame()
+        s_.eval_assemble()
+        assert s_.prepare_solve() in (0, None)
+    assert g.levels == 1
+    ptr, col, val = o.matrix(0)
+    assert np.array_equal(val, g.matrix(0)[2])
+    A = np.zeros((n_rows, n_rows))
+    for i in range(n_rows):
+        A[i, col[ptr[i]:ptr[i + 1]]] = val[ptr[i]:ptr[i + 1]]
+    r = np.random.default_rng(5).standard_normal(n_rows)
+    ref = np.linalg.solve(A, r)
+    zg = g.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
+    assert np.linalg.norm(zg - ref) <= 1e-12 * np.linalg.cond(A) * np.linalg.norm(ref)
+    assert np.linalg.norm(zg - o.vcycle(r)) <= 1e-12 * np.linalg.cond(A) * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("n_rows", [1, 40])
+def test_singular_coarsest_is_reported(n_rows):
+    """A singular coarsest system: the last row joins two pinned vertices
+    with zero compliance, so A = diag(A', 0).  Both sides refuse it as
+    MGPBD_E_SINGULAR (for 40 rows the zero pivot lies in the third tile), and
+    the device stays usable afterwards."""
+    from paper_2505_13390_gb300 import mgpbd
+    alpha = np.full(n_rows, 1e-6)
+    alpha[-1] = 0.0
+    mesh = chain(n_rows, alpha, pin_last_two=True)
+    p = default_params(coarse_max=1000, gravity=(0.0, 0.0, 0.0))
+    o, g = Oracle(mesh, p), solver(mesh, p)
+    for s_ in (o, g):
+        s_.begin_frame()
+        s_.eval_assemble()
+    assert o.prepare_solve() == mgpbd.E_SINGULAR
+    with pytest.raises(mgpbd.MgpbdError) as e:
+        g.prepare_solve()
+    assert e.value.status == mgpbd.E_SINGULAR
+    g.close()
+    ok = solver(*CASES["cloth8"]())
+    ok.begin_frame()
+    assert ok.iterate()["ret"] == 0
