@@ -69,10 +69,10 @@ def parse():
                     help="1: matrix-free level-0 products (headline); 0: assembled CSR")
     ap.add_argument("--no-assembled", action="store_true",
                     help="skip the assembled-CSR comparison line")
-    ap.add_argument("--serve-requests", type=int, default=8,
+    ap.add_argument("--serve-requests", type=int, default=64,
                     help="step requests of the serving trace (the full trace has 512)")
-    ap.add_argument("--serve-instances", type=int, default=4)
-    ap.add_argument("--serve-rate", type=float, default=0.5, help="arrivals per second")
+    ap.add_argument("--serve-instances", type=int, default=8)
+    ap.add_argument("--serve-rate", type=float, default=1.0, help="arrivals per second")
     ap.add_argument("--serve-active", type=int, default=8)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-arap", action="store_true",
@@ -296,45 +296,78 @@ def e2e(g, run, steps):
     return steps / dt, nbytes
 
 
-def serving(args):
-    """Serving load: step requests of uneven instances with Poisson arrivals.
-
-    Batched: mixed precision, matrix-free level 0, CUDA graphs, up to
-    --serve-active instances at once, admission by a device-memory budget.
-    Plain: FP64, assembled CSR, plain launches, one instance at a time.  Both
-    serve the same seeded trace; latency = finish - arrival of each request."""
+def serve_arm(meshes, reqs, prec, op, graphs, active, budget):
+    """Serves the trace through the request loop: each request is admitted
+    (mgpbd_batch_admit) when its arrival time has passed on the wall clock,
+    results are collected with mgpbd_batch_tick.  Latency = finish - arrival
+    on the batch's clock."""
     import numpy as np
     import torch
 
-    from paper_2505_13390_gb300.meshgen import instance_mesh, serving_trace
     from paper_2505_13390_gb300.mgpbd import Batch
+    b = Batch(budget, active)
+    for m, p in meshes:
+        b.add(m, dict(p, precision=prec, level0_op=op, use_graphs=graphs, autotune=0,
+                      setup_interval=20))
+    torch.cuda.synchronize()
+    pending = sorted(reqs, key=lambda r: r["t"])
+    t0 = b.counts()["clock"]
+    ticket_of, results, i = {}, {}, 0
+    while len(results) < len(pending):
+        now = b.counts()["clock"] - t0
+        while i < len(pending) and pending[i]["t"] <= now:
+            ticket_of[b.admit(pending[i]["instance"], pending[i]["frames"])] = pending[i]["id"]
+            i += 1
+        wait = 0.05 if i >= len(pending) else max(0.0, min(0.05, pending[i]["t"] - now))
+        for r in b.tick(wait_s=wait):
+            results[ticket_of[r["id"]]] = r
+    b.close()
+    res = [results[r["id"]] for r in reqs]
+    lat = np.array([r["finish_s"] - r["arrival_s"] for r in res])
+    wait_q = np.array([r["start_s"] - r["arrival_s"] for r in res])
+    span = max(r["finish_s"] for r in res) - t0
+    iters = sum(r["global_iters"] for r in res)
+    st = min([0] + [r["status"] for r in res])
+    return {"status": st, "requests": len(res),
+            "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_latency_s": float(lat.mean()), "mean_queue_wait_s": float(wait_q.mean()),
+            "global_iters_per_s": iters / span, "makespan_s": span,
+            "pcg_iters_per_request": [int(r["pcg_iters"]) for r in res], "max_active": active}
+
+
+def serving(args):
+    """Serving load: step requests of uneven instances with Poisson arrivals,
+    driven through the request loop with wall-clock arrivals.  Three arms on
+    the same seeded trace, all at PCG rtol 1e-6:
+      batched_mixed  mixed precision, matrix-free level 0, CUDA graphs, up to
+                     --serve-active requests at once (the served form);
+      serial_mixed   the same solver settings, one request at a time (isolates
+                     the batching);
+      plain_fp64     FP64, assembled CSR, plain launches, one at a time (the
+                     plain solver).
+    Admission budget: half of the free device memory."""
+    import torch
+
+    from paper_2505_13390_gb300.meshgen import instance_mesh, serving_trace
     inst, reqs = serving_trace(args.serve_requests, args.serve_instances, args.serve_rate)
     meshes = [instance_mesh(d) for d in inst]
-    free, total = torch.cuda.mem_get_info()
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.5 * free)
     out = {}
     for name, prec, op, graphs, active in (("batched_mixed", 1, 1, 1, args.serve_active),
+                                            ("serial_mixed", 1, 1, 1, 1),
                                             ("plain_fp64", 0, 0, 0, 1)):
-        b = Batch(int(0.5 * free), active)
-        for m, p in meshes:
-            b.add(m, dict(p, precision=prec, level0_op=op, use_graphs=graphs, autotune=0,
-                          setup_interval=20))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st, res = b.run([(r["id"], r["instance"], r["frames"], r["t"]) for r in reqs])
-        wall = time.perf_counter() - t0
-        b.close()
-        lat = np.array([r["finish_s"] - r["arrival_s"] for r in res])
-        iters = sum(r["global_iters"] for r in res)
-        out[name] = {"status": st, "p50_latency_s": float(np.percentile(lat, 50)),
-                     "p99_latency_s": float(np.percentile(lat, 99)),
-                     "global_iters_per_s": iters / wall, "makespan_s": wall,
-                     "pcg_iters_per_request": [int(r["pcg_iters"]) for r in res],
-                     "max_active": active}
+        out[name] = serve_arm(meshes, reqs, prec, op, graphs, active, budget)
+        torch.cuda.empty_cache()
     out["trace"] = {"requests": len(reqs), "instances": len(inst),
-                    "rate_hz": args.serve_rate, "meshes": [f"{d['kind']}{d['size']}" for d in inst],
-                    "budget": "half of free device memory", "frames_per_request": 1}
-    out["speedup_iters_per_s"] = (out["batched_mixed"]["global_iters_per_s"] /
-                                  out["plain_fp64"]["global_iters_per_s"])
+                    "rate_hz": args.serve_rate,
+                    "meshes": [f"{d['kind']}{d['size']}" for d in inst],
+                    "budget": "half of free device memory", "frames_per_request": 1,
+                    "iters_per_frame": 20, "pcg_rtol": 1e-6, "arrivals": "Poisson, seed 6"}
+    b = out["batched_mixed"]["global_iters_per_s"]
+    out["speedup_vs_plain_fp64"] = b / out["plain_fp64"]["global_iters_per_s"]
+    out["speedup_vs_serial_mixed"] = b / out["serial_mixed"]["global_iters_per_s"]
     return out
 
 

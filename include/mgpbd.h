@@ -291,30 +291,33 @@ unsigned long long mgpbd_launch_count(void);
 /* ---- serving: continuous batching of many instances ----
  * Not in the paper, which steps one instance at a time.  A batch holds many
  * instances (meshes with their parameters and state) and serves step
- * requests: one request = `frames` frames of Alg. 1 on one instance.
- * mgpbd_batch_run admits a request once its arrival time has passed, its
- * instance is idle, a worker is free and the instance fits the device-memory
- * budget (idle resident instances are evicted least recently used first;
- * their state moves to host memory and back on their next admission).  Up to
- * max_active instances run at the same time on their own streams and host
- * worker threads.  Requests of one instance run in arrival order.  The call
- * returns when every request has finished; results carry arrival, start and
- * finish times (seconds from the start of the call) for latency statistics.
- * A request whose instance can never fit the budget fails with
- * MGPBD_E_BUDGET.  Instances must not be added while a run is in progress. */
+ * requests: one request = `frames` frames of Alg. 1 on one instance.  It is
+ * a request loop: mgpbd_batch_admit submits a request at any time, from any
+ * thread, also while other requests run; mgpbd_batch_tick returns the
+ * requests that have finished since the previous tick.  A request starts as
+ * soon as its instance is idle, one of max_active worker threads is free and
+ * the instance fits the device-memory budget (idle resident instances are
+ * evicted least recently used first; their state moves to host memory and
+ * back on their next admission).  Running requests step on their instances'
+ * own CUDA streams, so their kernels overlap on the GPU.  Requests of one
+ * instance run in submission order.  Times are seconds on the batch's clock,
+ * which starts at mgpbd_batch_create.  A request whose instance can never fit
+ * the budget finishes at once with MGPBD_E_BUDGET.  Instances may be added
+ * at any time; their indices are 0, 1, 2, ... in order of addition. */
 typedef struct mgpbd_batch mgpbd_batch_t;
 typedef struct {
   size_t hbm_budget;  /* bytes of device memory the resident instances may hold */
-  int max_active;     /* instances stepping at the same time (worker threads) */
+  int max_active;     /* requests stepping at the same time (worker threads), 1..256 */
 } mgpbd_batch_config;
 typedef struct {
-  int id;             /* caller's request id, copied to the result */
+  int id;             /* caller's request id, copied to the result (mgpbd_batch_run) */
   int instance;       /* instance index returned by mgpbd_batch_add_instance */
   int frames;         /* frames of Alg. 1 to run (each max_iter global iterations) */
   double arrival_s;   /* arrival time, seconds after mgpbd_batch_run starts */
 } mgpbd_step_request;
 typedef struct {
-  int id, instance, status;
+  int id;             /* ticket of mgpbd_batch_admit (the request's id under mgpbd_batch_run) */
+  int instance, status;
   double arrival_s, start_s, finish_s;  /* latency = finish_s - arrival_s */
   int64_t global_iters, pcg_iters;
 } mgpbd_step_result;
@@ -335,12 +338,35 @@ mgpbd_status mgpbd_batch_create(const mgpbd_batch_config *cfg, mgpbd_batch_t **o
 mgpbd_status mgpbd_batch_add_instance(mgpbd_batch_t *b, const mgpbd_mesh_desc *mesh,
                                       const mgpbd_params *p, const double *x0, const double *v0,
                                       int *instance);
+/* Submits one request now (its arrival time is the call's time on the
+ * batch's clock) and returns at once with its ticket (0, 1, 2, ... per
+ * batch), which its result carries as `id`.  Thread-safe.  MGPBD_E_INVALID
+ * for an unknown instance or frames < 1. */
+mgpbd_status mgpbd_batch_admit(mgpbd_batch_t *b, int instance, int frames, int *ticket);
+/* Copies up to `max` results of requests that finished since the previous
+ * tick into res[0 .. *n), in finishing order, waiting up to wait_s seconds for
+ * the first one when none is ready (0: poll).  A result is returned once. */
+mgpbd_status mgpbd_batch_tick(mgpbd_batch_t *b, double wait_s, mgpbd_step_result *res, int max,
+                              int *n);
+/* Requests queued (not started), running, finished but not yet returned by a
+ * tick, and the batch's clock now (seconds); any pointer may be NULL. */
+mgpbd_status mgpbd_batch_counts(mgpbd_batch_t *b, int *queued, int *running, int *unreported,
+                                double *clock);
+/* Replays a list of timed requests through the request loop: admits each
+ * when its arrival time (seconds after the call) has passed and returns
+ * when all have finished, res[i] holding request i's result (its caller id,
+ * times in seconds after the call; arrival_s is the time it was admitted).
+ * Results of requests admitted by other calls stay for mgpbd_batch_tick.
+ * Returns the first error of a request, else MGPBD_OK. */
 mgpbd_status mgpbd_batch_run(mgpbd_batch_t *b, const mgpbd_step_request *req, int n_req,
                              mgpbd_step_result *res);
-/* host copy of an instance's positions/velocities (synchronises if resident) */
+/* host copy of an instance's positions/velocities (waits while a request steps
+ * the instance; synchronises if it is resident) */
 mgpbd_status mgpbd_batch_get_state(mgpbd_batch_t *b, int instance, double *x, double *v);
 /* resident instances and bytes held now */
 mgpbd_status mgpbd_batch_resident(mgpbd_batch_t *b, int *n_resident, size_t *bytes);
+/* Waits for the requests that have started, drops the queued ones, frees
+ * every instance. */
 void mgpbd_batch_destroy(mgpbd_batch_t *b);
 
 /* ---- precision conversions of the mixed-precision path ----

@@ -1,16 +1,21 @@
 // Continuous-batching service of many simulation instances on one GPU.
 //
 // The paper runs one instance at a time; this layer serves step requests
-// (one request = one frame of Alg. 1 for one instance) for many instances of
-// different meshes.  Instance state stays on the device between its
-// requests while memory allows.  Admission is by a device-memory budget:
-// an instance is made resident only if its bytes fit, after evicting idle
-// resident instances (least recently used first; their positions and
-// velocities go to host memory and come back when they are next admitted).
-// Up to `max_active` instances step at the same time, each on its own CUDA
-// stream driven by its own worker thread, so their kernels overlap on the
-// GPU and requests that arrive while others run are admitted as soon as a
-// worker and memory are free.
+// (one request = `frames` frames of Alg. 1 for one instance) for many
+// instances of different meshes, as a request loop: mgpbd_batch_admit
+// submits a request at any time, also while others run, and
+// mgpbd_batch_tick returns the requests that finished since the previous
+// tick.  Instance state stays on the device between its requests while
+// memory allows.  Admission is by a device-memory budget: an instance is
+// made resident only if its bytes fit, after evicting idle resident
+// instances (least recently used first; their positions and velocities go to
+// host memory and come back when they are next admitted).  Up to
+// `max_active` requests run at the same time, each on its instance's own
+// CUDA stream driven by one of `max_active` worker threads, so their kernels
+// overlap on the GPU.  A dispatcher runs under the batch lock whenever a
+// request arrives or a worker finishes: it starts the earliest queued
+// request whose instance is idle while a worker and memory are free.
+// mgpbd_batch_run replays a list of timed requests through the same loop.
 #include <stdio.h>
 #include <string.h>
 
@@ -18,8 +23,10 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -34,17 +41,32 @@ struct Instance {
   mgpbd_handle_t *h = nullptr;  // resident when not null
   cudaStream_t stream = nullptr;
   size_t est_bytes = 0, bytes = 0;
-  bool busy = false;
+  bool busy = false;  // a worker steps it (or a state read holds it)
   double last_used = 0.0;
-  std::deque<int> pending;  // request indices in arrival order
+};
+
+struct Req {
+  int ticket, instance, frames;
+  double arrival;  // seconds on the batch's clock
 };
 
 struct Batch {
   mgpbd_batch_config cfg{};
-  std::vector<Instance> inst;
+  int device = 0;
+  std::chrono::steady_clock::time_point t0;  // the batch's clock starts at create
+  // instances are held by pointer: adding one never moves another
+  std::vector<std::unique_ptr<Instance>> inst;
   std::mutex mu;
-  std::condition_variable cv;
+  std::condition_variable cv_work;  // workers wait for jobs
+  std::condition_variable cv_done;  // tick and state reads wait for results
   size_t resident = 0;  // bytes held by resident instances (reserved estimate while loading)
+  int next_ticket = 0;
+  std::deque<Req> queue;  // submitted, not started, in arrival order
+  std::deque<Req> jobs;   // started, waiting for a worker
+  int running = 0;        // requests in `jobs` or in a worker
+  std::vector<mgpbd_step_result> finished;  // not yet returned by a tick
+  bool stop = false;
+  std::vector<std::thread> workers;
 };
 
 // upper estimate of an instance's device bytes from its mesh (before create):
@@ -66,12 +88,6 @@ static size_t estimate_bytes_desc(const mgpbd_mesh_desc *d, const mgpbd_params *
   const double nc = std::min(m, (double)std::max(p->coarse_max, 1));
   b += 24.0 * nc * nc;
   return (size_t)b;
-}
-
-static size_t estimate_bytes(const Instance &in) { return estimate_bytes_desc(&in.desc, &in.p); }
-
-static double now_s(std::chrono::steady_clock::time_point t0) {
-  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
 // drops the instance's handle and stream (its device state is lost)
@@ -128,6 +144,138 @@ static mgpbd_status run_request(Instance &in, int frames, mgpbd_step_result *r) 
   return worst;
 }
 
+static double clock_s(const Batch *b) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - b->t0).count();
+}
+
+// a request that never ran (its instance can never fit)
+static void fail_request(Batch *b, const Req &q, mgpbd_status s) {
+  mgpbd_step_result r{};
+  r.id = q.ticket;
+  r.instance = q.instance;
+  r.status = s;
+  r.arrival_s = q.arrival;
+  r.start_s = r.finish_s = clock_s(b);
+  b->finished.push_back(r);
+  b->cv_done.notify_all();
+}
+
+// Starts queued requests while a worker and memory are free (lock held).
+// Queue order is arrival order; a request whose instance is busy waits, and
+// so do the later requests of that instance, so each instance's requests run
+// in submission order.
+static void dispatch(Batch *b) {
+  while (b->running < b->cfg.max_active) {
+    auto it = b->queue.begin();
+    for (; it != b->queue.end(); ++it)
+      if (!b->inst[it->instance]->busy) break;
+    if (it == b->queue.end()) return;
+    const Req q = *it;
+    Instance &in = *b->inst[q.instance];
+    if (!in.h) {
+      const size_t need = in.bytes ? in.bytes : in.est_bytes;
+      if (need > b->cfg.hbm_budget) {  // can never fit: fail the request
+        b->queue.erase(it);
+        fail_request(b, q, MGPBD_E_BUDGET);
+        continue;
+      }
+      mgpbd_status evict_err = MGPBD_OK;
+      while (b->resident + need > b->cfg.hbm_budget) {
+        int victim = -1;
+        for (size_t i = 0; i < b->inst.size(); ++i) {
+          const Instance &v = *b->inst[i];
+          if (v.busy || !v.h || (int)i == q.instance) continue;
+          if (victim < 0 || v.last_used < b->inst[victim]->last_used) victim = (int)i;
+        }
+        if (victim < 0) break;
+        Instance &v = *b->inst[victim];
+        mgpbd_status s = evict(v);
+        if (s < 0) {  // still resident: its state could not be read back
+          evict_err = s;
+          break;
+        }
+        b->resident -= v.bytes;
+        v.bytes = 0;
+      }
+      if (b->resident + need > b->cfg.hbm_budget) {
+        if (b->running > 0) return;  // memory frees up when a request finishes
+        b->queue.erase(it);          // nothing runs and nothing more can be evicted
+        fail_request(b, q, evict_err < 0 ? evict_err : MGPBD_E_BUDGET);
+        continue;
+      }
+      b->resident += need;  // reserved until the worker measures the real size
+      in.bytes = need;
+    }
+    b->queue.erase(it);
+    in.busy = true;
+    ++b->running;
+    b->jobs.push_back(q);
+    b->cv_work.notify_one();
+  }
+}
+
+static void worker(Batch *b) {
+  cudaSetDevice(b->device);
+  std::unique_lock<std::mutex> lock(b->mu);
+  for (;;) {
+    b->cv_work.wait(lock, [&] { return b->stop || !b->jobs.empty(); });
+    if (b->jobs.empty()) return;  // stopping
+    const Req q = b->jobs.front();
+    b->jobs.pop_front();
+    Instance &in = *b->inst[q.instance];
+    lock.unlock();
+    mgpbd_step_result r{};
+    r.id = q.ticket;
+    r.instance = q.instance;
+    r.arrival_s = q.arrival;
+    r.start_s = clock_s(b);
+    mgpbd_status s = make_resident(in);
+    if (s >= 0) s = run_request(in, q.frames, &r);
+    size_t held = 0;
+    if (in.h) {
+      mgpbd_stats_t st{};
+      mgpbd_stats(in.h, &st);
+      held = st.device_bytes;
+    }
+    r.finish_s = clock_s(b);
+    r.status = s;
+    lock.lock();
+    b->resident = b->resident - in.bytes + held;  // the measured size replaces the estimate
+    in.bytes = held;
+    in.busy = false;
+    in.last_used = r.finish_s;
+    --b->running;
+    b->finished.push_back(r);
+    dispatch(b);
+    b->cv_done.notify_all();
+  }
+}
+
+// Moves up to `max` finished results that `want` accepts into `out`, in
+// finishing order, waiting up to wait_s seconds for the first one (lock held
+// by the caller through `lock`).
+template <class Pred>
+static int take_results(Batch *b, std::unique_lock<std::mutex> &lock, double wait_s,
+                        mgpbd_step_result *out, int max, Pred want) {
+  auto any = [&] {
+    for (const auto &r : b->finished)
+      if (want(r)) return true;
+    return false;
+  };
+  if (wait_s > 0 && !any())
+    b->cv_done.wait_for(lock, std::chrono::duration<double>(wait_s), any);
+  int k = 0;
+  for (auto it = b->finished.begin(); it != b->finished.end() && k < max;) {
+    if (want(*it)) {
+      out[k++] = *it;
+      it = b->finished.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  return k;
+}
+
 }  // namespace mg
 
 using namespace mg;
@@ -158,14 +306,23 @@ mgpbd_status mgpbd_workspace_size(const mgpbd_mesh_desc *md, const mgpbd_params 
 }
 
 mgpbd_status mgpbd_batch_create(const mgpbd_batch_config *cfg, mgpbd_batch_t **out) {
-  if (!cfg || !out || cfg->max_active < 1 || cfg->hbm_budget == 0) {
+  if (!cfg || !out || cfg->max_active < 1 || cfg->max_active > 256 || cfg->hbm_budget == 0) {
     set_error("mgpbd_batch_create: invalid configuration");
     return MGPBD_E_INVALID;
   }
+  *out = nullptr;
+  num_sms();  // query once before worker threads exist
   Batch *b = new Batch();
   b->cfg = *cfg;
+  b->t0 = std::chrono::steady_clock::now();
+  if (cudaGetDevice(&b->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    set_error("mgpbd_batch_create: cudaGetDevice failed");
+    return MGPBD_E_CUDA;
+  }
+  for (int t = 0; t < cfg->max_active; ++t) b->workers.emplace_back(worker, b);
   *out = reinterpret_cast<mgpbd_batch_t *>(b);
-  num_sms();  // query once before worker threads exist
   return MGPBD_OK;
 }
 
@@ -173,44 +330,81 @@ mgpbd_status mgpbd_batch_add_instance(mgpbd_batch_t *bb, const mgpbd_mesh_desc *
                                       const mgpbd_params *p, const double *x0, const double *v0,
                                       int *id) {
   Batch *b = reinterpret_cast<Batch *>(bb);
-  if (!b || !md || !p || !id || md->n_verts <= 0 || md->n_dist < 0 || md->n_tet < 0) {
+  if (!b || !md || !p || !id || md->n_verts <= 0 || md->n_dist < 0 || md->n_tet < 0 ||
+      !md->rest_pos || !md->inv_mass || (md->n_dist > 0 && !md->dist) ||
+      (md->n_tet > 0 && !md->tet) || (md->n_dist + md->n_tet > 0 && !md->alpha)) {
     set_error("mgpbd_batch_add_instance: invalid argument");
     return MGPBD_E_INVALID;
   }
-  Instance in;
+  size_t est = 0;
+  MG_TRY(mgpbd_workspace_size(md, p, &est));  // also range-checks the indices
+  auto in = std::make_unique<Instance>();
   const int N = md->n_verts, E = md->n_dist, T = md->n_tet;
-  in.rest.assign(md->rest_pos, md->rest_pos + 3 * (size_t)N);
-  in.w.assign(md->inv_mass, md->inv_mass + (size_t)N);
-  if (E) in.dist.assign(md->dist, md->dist + 2 * (size_t)E);
-  if (T) in.tet.assign(md->tet, md->tet + 4 * (size_t)T);
-  if (E + T) in.alpha.assign(md->alpha, md->alpha + (size_t)E + T);
-  in.x.assign(x0 ? x0 : md->rest_pos, (x0 ? x0 : md->rest_pos) + 3 * (size_t)N);
-  in.v.assign(3 * (size_t)N, 0.0);
-  if (v0) in.v.assign(v0, v0 + 3 * (size_t)N);
-  in.p = *p;
+  in->rest.assign(md->rest_pos, md->rest_pos + 3 * (size_t)N);
+  in->w.assign(md->inv_mass, md->inv_mass + (size_t)N);
+  if (E) in->dist.assign(md->dist, md->dist + 2 * (size_t)E);
+  if (T) in->tet.assign(md->tet, md->tet + 4 * (size_t)T);
+  if (E + T) in->alpha.assign(md->alpha, md->alpha + (size_t)E + T);
+  in->x.assign(x0 ? x0 : md->rest_pos, (x0 ? x0 : md->rest_pos) + 3 * (size_t)N);
+  in->v.assign(3 * (size_t)N, 0.0);
+  if (v0) in->v.assign(v0, v0 + 3 * (size_t)N);
+  in->p = *p;
+  in->desc.n_verts = N;
+  in->desc.rest_pos = in->rest.data();
+  in->desc.inv_mass = in->w.data();
+  in->desc.n_dist = E;
+  in->desc.dist = E ? in->dist.data() : nullptr;
+  in->desc.n_tet = T;
+  in->desc.tet = T ? in->tet.data() : nullptr;
+  in->desc.alpha = (E + T) ? in->alpha.data() : nullptr;
+  in->desc.tet_kind = md->tet_kind;
+  in->est_bytes = est;
   std::lock_guard<std::mutex> lock(b->mu);
   b->inst.push_back(std::move(in));
-  Instance &r = b->inst.back();
-  r.desc.n_verts = N;
-  r.desc.rest_pos = r.rest.data();
-  r.desc.inv_mass = r.w.data();
-  r.desc.n_dist = E;
-  r.desc.dist = E ? r.dist.data() : nullptr;
-  r.desc.n_tet = T;
-  r.desc.tet = T ? r.tet.data() : nullptr;
-  r.desc.alpha = (E + T) ? r.alpha.data() : nullptr;
-  r.desc.tet_kind = md->tet_kind;
-  r.est_bytes = estimate_bytes(r);
   *id = (int)b->inst.size() - 1;
-  // descriptors of earlier instances stay valid: vectors own their storage and
-  // std::vector<Instance> moves the element vectors without reallocating them
-  for (Instance &q : b->inst) {
-    q.desc.rest_pos = q.rest.data();
-    q.desc.inv_mass = q.w.data();
-    q.desc.dist = q.desc.n_dist ? q.dist.data() : nullptr;
-    q.desc.tet = q.desc.n_tet ? q.tet.data() : nullptr;
-    q.desc.alpha = (q.desc.n_dist + q.desc.n_tet) ? q.alpha.data() : nullptr;
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_batch_admit(mgpbd_batch_t *bb, int instance, int frames, int *ticket) {
+  Batch *b = reinterpret_cast<Batch *>(bb);
+  if (!b || !ticket || frames < 1) {
+    set_error("mgpbd_batch_admit: invalid argument");
+    return MGPBD_E_INVALID;
   }
+  std::lock_guard<std::mutex> lock(b->mu);
+  if (instance < 0 || instance >= (int)b->inst.size()) {
+    set_error("mgpbd_batch_admit: unknown instance");
+    return MGPBD_E_INVALID;
+  }
+  Req q{b->next_ticket++, instance, frames, clock_s(b)};
+  b->queue.push_back(q);
+  *ticket = q.ticket;
+  dispatch(b);
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_batch_tick(mgpbd_batch_t *bb, double wait_s, mgpbd_step_result *res, int max,
+                              int *n) {
+  Batch *b = reinterpret_cast<Batch *>(bb);
+  if (!b || !n || max < 0 || (max > 0 && !res) || !(wait_s >= 0.0)) {
+    set_error("mgpbd_batch_tick: invalid argument");
+    return MGPBD_E_INVALID;
+  }
+  std::unique_lock<std::mutex> lock(b->mu);
+  *n = take_results(b, lock, max > 0 ? wait_s : 0.0, res, max,
+                    [](const mgpbd_step_result &) { return true; });
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_batch_counts(mgpbd_batch_t *bb, int *queued, int *running, int *unreported,
+                                double *clock) {
+  Batch *b = reinterpret_cast<Batch *>(bb);
+  if (!b) return MGPBD_E_INVALID;
+  std::lock_guard<std::mutex> lock(b->mu);
+  if (queued) *queued = (int)b->queue.size();
+  if (running) *running = b->running;
+  if (unreported) *unreported = (int)b->finished.size();
+  if (clock) *clock = clock_s(b);
   return MGPBD_OK;
 }
 
@@ -218,157 +412,82 @@ mgpbd_status mgpbd_batch_run(mgpbd_batch_t *bb, const mgpbd_step_request *req, i
                              mgpbd_step_result *res) {
   Batch *b = reinterpret_cast<Batch *>(bb);
   if (!b || n_req < 0 || (n_req && (!req || !res))) return MGPBD_E_INVALID;
-  for (int i = 0; i < n_req; ++i)
-    if (req[i].instance < 0 || req[i].instance >= (int)b->inst.size() || req[i].frames < 1) {
-      set_error("mgpbd_batch_run: request names an unknown instance or no frames");
-      return MGPBD_E_INVALID;
-    }
-  int dev = 0;
-  MG_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lock(b->mu);
+    for (int i = 0; i < n_req; ++i)
+      if (req[i].instance < 0 || req[i].instance >= (int)b->inst.size() || req[i].frames < 1) {
+        set_error("mgpbd_batch_run: request names an unknown instance or no frames");
+        return MGPBD_E_INVALID;
+      }
+  }
   std::vector<int> order((size_t)n_req);
   for (int i = 0; i < n_req; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int c) { return req[a].arrival_s < req[c].arrival_s; });
-  for (int i = 0; i < n_req; ++i) {
-    memset(&res[i], 0, sizeof(res[i]));
-    res[i].id = req[i].id;
-    res[i].instance = req[i].instance;
-    res[i].arrival_s = req[i].arrival_s;
-    res[i].start_s = res[i].finish_s = -1.0;
-  }
-  auto t0 = std::chrono::steady_clock::now();
-  std::deque<int> jobs;  // requests whose instance is resident/being loaded, ready to run
-  int done = 0, next_arrival = 0, active = 0;
-  bool stop = false;
+  std::unordered_map<int, int> index;  // ticket -> request
+  const double t_run = clock_s(b);
+  int next = 0, got = 0;
   mgpbd_status first_err = MGPBD_OK;
-
-  auto worker = [&]() {
-    cudaSetDevice(dev);
-    std::unique_lock<std::mutex> lock(b->mu);
-    for (;;) {
-      b->cv.wait(lock, [&] { return stop || !jobs.empty(); });
-      if (jobs.empty() && stop) return;
-      int k = jobs.front();
-      jobs.pop_front();
-      Instance &in = b->inst[req[k].instance];
-      lock.unlock();
-      res[k].start_s = now_s(t0);
-      mgpbd_status s = make_resident(in);
-      if (s >= 0) s = run_request(in, req[k].frames, &res[k]);
-      res[k].finish_s = now_s(t0);
-      res[k].status = s;
-      size_t held = 0;
-      if (in.h) {
-        mgpbd_stats_t st{};
-        mgpbd_stats(in.h, &st);
-        held = st.device_bytes;
-      }
-      lock.lock();
-      if (s < 0 && first_err >= 0) first_err = s;
-      // replace the admission estimate by the measured bytes
-      b->resident = b->resident - in.bytes + held;
-      in.bytes = held;
-      in.busy = false;
-      in.last_used = now_s(t0);
-      --active;
-      ++done;
-      b->cv.notify_all();
+  std::vector<mgpbd_step_result> buf(64);
+  while (got < n_req) {
+    while (next < n_req && req[order[next]].arrival_s <= clock_s(b) - t_run) {
+      const int k = order[next++];
+      int ticket = -1;
+      MG_TRY(mgpbd_batch_admit(bb, req[k].instance, req[k].frames, &ticket));
+      index[ticket] = k;
     }
-  };
-
-  std::vector<std::thread> pool;
-  for (int t = 0; t < b->cfg.max_active; ++t) pool.emplace_back(worker);
-
-  std::unique_lock<std::mutex> lock(b->mu);
-  while (done < n_req) {
-    double now = now_s(t0);
-    while (next_arrival < n_req && req[order[next_arrival]].arrival_s <= now) {
-      int k = order[next_arrival++];
-      b->inst[req[k].instance].pending.push_back(k);
-    }
-    // admit: earliest pending request of an idle instance, while memory and
-    // workers allow
-    for (;;) {
-      if (active >= b->cfg.max_active) break;
-      int best = -1;
-      for (size_t i = 0; i < b->inst.size(); ++i) {
-        Instance &in = b->inst[i];
-        if (in.busy || in.pending.empty()) continue;
-        if (best < 0 || req[in.pending.front()].arrival_s <
-                            req[b->inst[best].pending.front()].arrival_s)
-          best = (int)i;
-      }
-      if (best < 0) break;
-      Instance &in = b->inst[best];
-      if (!in.h) {
-        size_t need = in.bytes ? in.bytes : in.est_bytes;
-        if (need > b->cfg.hbm_budget) {  // can never fit: fail the request
-          int k = in.pending.front();
-          in.pending.pop_front();
-          res[k].status = MGPBD_E_BUDGET;
-          res[k].start_s = res[k].finish_s = now_s(t0);
-          if (first_err >= 0) first_err = MGPBD_E_BUDGET;
-          ++done;
-          set_error("mgpbd_batch_run: an instance needs more memory than the budget");
-          continue;
-        }
-        while (b->resident + need > b->cfg.hbm_budget) {
-          int victim = -1;
-          for (size_t i = 0; i < b->inst.size(); ++i) {
-            Instance &q = b->inst[i];
-            // busy first: a busy instance's handle is being written by its
-            // worker outside the lock, so it must not be read here
-            if (q.busy || !q.h || (int)i == best) continue;
-            if (victim < 0 || q.last_used < b->inst[victim].last_used) victim = (int)i;
-          }
-          if (victim < 0) break;
-          Instance &q = b->inst[victim];
-          mgpbd_status s = evict(q);
-          if (s < 0) {  // still resident (its state could not be read back)
-            if (first_err >= 0) first_err = s;
-            break;
-          }
-          b->resident -= q.bytes;
-          q.bytes = 0;
-        }
-        if (b->resident + need > b->cfg.hbm_budget && active > 0) break;  // wait for memory
-        b->resident += need;  // reserved until the worker measures the real size
-        in.bytes = need;
-      }
-      int k = in.pending.front();
-      in.pending.pop_front();
-      in.busy = true;
-      ++active;
-      jobs.push_back(k);
-      b->cv.notify_all();
-    }
-    if (done >= n_req) break;
     double wait = 0.05;
-    if (next_arrival < n_req) wait = std::min(wait, std::max(0.0, req[order[next_arrival]].arrival_s - now));
-    b->cv.wait_for(lock, std::chrono::duration<double>(wait));
+    if (next < n_req)
+      wait = std::min(wait, std::max(0.0, req[order[next]].arrival_s - (clock_s(b) - t_run)));
+    int n = 0;
+    {
+      std::unique_lock<std::mutex> lock(b->mu);
+      n = take_results(b, lock, wait, buf.data(), (int)buf.size(),
+                       [&](const mgpbd_step_result &r) { return index.count(r.id) != 0; });
+    }
+    for (int j = 0; j < n; ++j) {
+      const int k = index[buf[j].id];
+      mgpbd_step_result r = buf[j];
+      r.id = req[k].id;
+      r.arrival_s -= t_run;
+      r.start_s -= t_run;
+      r.finish_s -= t_run;
+      res[k] = r;
+      if (r.status < 0 && first_err >= 0) first_err = r.status;
+      ++got;
+    }
   }
-  stop = true;
-  b->cv.notify_all();
-  lock.unlock();
-  for (auto &t : pool) t.join();
   return first_err;
 }
 
 mgpbd_status mgpbd_batch_get_state(mgpbd_batch_t *bb, int id, double *x, double *v) {
   Batch *b = reinterpret_cast<Batch *>(bb);
-  if (!b || id < 0 || id >= (int)b->inst.size()) return MGPBD_E_INVALID;
-  Instance &in = b->inst[id];
-  if (in.h) MG_TRY(mgpbd_get_state(in.h, in.x.data(), in.v.data(), MGPBD_MEM_HOST));
-  if (x) memcpy(x, in.x.data(), sizeof(double) * in.x.size());
-  if (v) memcpy(v, in.v.data(), sizeof(double) * in.v.size());
-  return MGPBD_OK;
+  if (!b) return MGPBD_E_INVALID;
+  std::unique_lock<std::mutex> lock(b->mu);
+  if (id < 0 || id >= (int)b->inst.size()) return MGPBD_E_INVALID;
+  Instance &in = *b->inst[id];
+  b->cv_done.wait(lock, [&] { return !in.busy; });  // not while a worker steps it
+  in.busy = true;
+  lock.unlock();
+  mgpbd_status s = MGPBD_OK;
+  if (in.h) s = mgpbd_get_state(in.h, in.x.data(), in.v.data(), MGPBD_MEM_HOST);
+  if (s >= 0) {
+    if (x) memcpy(x, in.x.data(), sizeof(double) * in.x.size());
+    if (v) memcpy(v, in.v.data(), sizeof(double) * in.v.size());
+  }
+  lock.lock();
+  in.busy = false;
+  dispatch(b);
+  b->cv_done.notify_all();
+  return s;
 }
 
 mgpbd_status mgpbd_batch_resident(mgpbd_batch_t *bb, int *n_resident, size_t *bytes) {
   Batch *b = reinterpret_cast<Batch *>(bb);
   if (!b) return MGPBD_E_INVALID;
+  std::lock_guard<std::mutex> lock(b->mu);
   int n = 0;
-  for (Instance &in : b->inst) n += in.h != nullptr;
+  for (auto &in : b->inst) n += in->h != nullptr;
   if (n_resident) *n_resident = n;
   if (bytes) *bytes = b->resident;
   return MGPBD_OK;
@@ -377,7 +496,17 @@ mgpbd_status mgpbd_batch_resident(mgpbd_batch_t *bb, int *n_resident, size_t *by
 void mgpbd_batch_destroy(mgpbd_batch_t *bb) {
   Batch *b = reinterpret_cast<Batch *>(bb);
   if (!b) return;
-  for (Instance &in : b->inst) evict(in);
+  {
+    std::lock_guard<std::mutex> lock(b->mu);
+    b->stop = true;
+    b->queue.clear();  // requests that have not started are dropped
+  }
+  b->cv_work.notify_all();
+  for (auto &t : b->workers) t.join();  // workers finish the jobs they hold first
+  for (auto &in : b->inst) {
+    evict(*in);
+    drop_handle(*in);
+  }
   delete b;
 }
 

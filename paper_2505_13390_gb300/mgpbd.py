@@ -132,6 +132,10 @@ SIGNATURES = {
     "mgpbd_batch_create": (_i, [C.POINTER(BatchConfig), C.POINTER(_vp)]),
     "mgpbd_batch_add_instance": (_i, [_vp, C.POINTER(MeshDesc), C.POINTER(Params), _vp, _vp,
                                       C.POINTER(_i)]),
+    "mgpbd_batch_admit": (_i, [_vp, _i, _i, C.POINTER(_i)]),
+    "mgpbd_batch_tick": (_i, [_vp, C.c_double, _vp, _i, C.POINTER(_i)]),
+    "mgpbd_batch_counts": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i),
+                                C.POINTER(C.c_double)]),
     "mgpbd_batch_run": (_i, [_vp, _vp, _i, _vp]),
     "mgpbd_batch_get_state": (_i, [_vp, _i, _vp, _vp]),
     "mgpbd_batch_resident": (_i, [_vp, C.POINTER(_i), C.POINTER(C.c_size_t)]),
@@ -470,6 +474,26 @@ class Batch:
                                                _ptr(keep[6]), C.byref(i)), "batch_add_instance")
         self.sizes.append(mesh.n_verts)
         return i.value
+
+    def admit(self, instance: int, frames: int = 1) -> int:
+        """Submits a request now (mgpbd_batch_admit); returns its ticket."""
+        t = C.c_int()
+        _check(load().mgpbd_batch_admit(self.h, instance, frames, C.byref(t)), "batch_admit")
+        return t.value
+
+    def tick(self, wait_s: float = 0.0, max_results: int = 256):
+        """Results of the requests finished since the previous tick."""
+        rs = (StepResult * max_results)()
+        n = C.c_int()
+        _check(load().mgpbd_batch_tick(self.h, float(wait_s), C.cast(rs, C.c_void_p),
+                                       max_results, C.byref(n)), "batch_tick")
+        return [rs[i].as_dict() for i in range(n.value)]
+
+    def counts(self) -> Dict:
+        q, r, u, t = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+        _check(load().mgpbd_batch_counts(self.h, C.byref(q), C.byref(r), C.byref(u),
+                                         C.byref(t)), "batch_counts")
+        return {"queued": q.value, "running": r.value, "unreported": u.value, "clock": t.value}
 
     def run(self, requests):
         """requests: iterable of (id, instance, frames, arrival_s)."""

@@ -128,3 +128,62 @@ def test_workspace_size_bounds_the_device_bytes():
         held = g.stats()["device_bytes"]
         g.close()
         assert held <= est, (mesh.name, held, est)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_admit_while_running_mix_equals_alone(prec):
+    """The request loop: a long request starts, and while it is on the GPU the
+    host thread admits requests for the other instances one by one and
+    collects results with tick.  The late requests run while the long one is
+    still running, each result is returned once, and every instance ends in
+    the state of a one-at-a-time run of the same requests, bit for bit."""
+    import time
+
+    from paper_2505_13390_gb300.mgpbd import Batch
+    ms = meshes()
+    ref = serve(ms, prec, 1, 64 << 30, [(0, 3, 6, 0.0)] + [(1 + k, k, 1, 0.0) for k in range(3)])
+    b = Batch(64 << 30, 4)
+    ids = [b.add(m, common(p, prec)) for m, p in ms]
+    long_ticket = b.admit(ids[3], 6)
+    t0 = time.perf_counter()
+    while b.counts()["running"] == 0 and time.perf_counter() - t0 < 10:
+        time.sleep(0.001)
+    tickets = []
+    for k in range(3):
+        assert b.counts()["running"] >= 1
+        tickets.append(b.admit(ids[k], 1))
+        time.sleep(0.002)
+    got = []
+    while len(got) < 4 and time.perf_counter() - t0 < 300:
+        got += b.tick(wait_s=0.5)
+    assert sorted(r["id"] for r in got) == sorted([long_ticket] + tickets)
+    assert all(r["status"] >= 0 for r in got)
+    assert b.tick() == [] and b.counts()["unreported"] == 0
+    by = {r["id"]: r for r in got}
+    long_r = by[long_ticket]
+    assert any(by[t]["start_s"] < long_r["finish_s"] for t in tickets)  # overlapped
+    assert all(r["start_s"] >= r["arrival_s"] for r in got)
+    states = [b.state(i) for i in ids]
+    b.close()
+    for (x1, v1), (x2, v2) in zip(ref[2], states):
+        assert np.array_equal(x1, x2) and np.array_equal(v1, v2)
+
+
+def test_admit_rejects_unknown_instance_and_tick_polls():
+    from paper_2505_13390_gb300 import mgpbd
+    from paper_2505_13390_gb300.mgpbd import Batch
+    b = Batch(64 << 30, 2)
+    m, p = meshes()[0]
+    i = b.add(m, common(p, 0))
+    with pytest.raises(mgpbd.MgpbdError):
+        b.admit(i + 1, 1)
+    with pytest.raises(mgpbd.MgpbdError):
+        b.admit(i, 0)
+    assert b.tick() == []
+    t = b.admit(i, 1)
+    res = []
+    while not res:
+        res = b.tick(wait_s=1.0)
+    assert [r["id"] for r in res] == [t] and res[0]["status"] >= 0
+    assert res[0]["arrival_s"] <= res[0]["start_s"] <= res[0]["finish_s"] <= b.counts()["clock"]
+    b.close()
