@@ -35,9 +35,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FULL_NNZ = 376_541_249  # nonzeros of A for block100 (checked at run time)
-# PCG iterations per global iteration on block100 at frame 0, iterations 1-5,
-# as measured on GB300 (the reference arm cannot run the GPU to learn it)
-FULL_PCG_ITERS = 7300
+# PCG iterations of one block100 global iteration at PCG rtol 1e-6 as
+# measured on GB300 (mixed precision, frame 0: 6,340-6,580 over the timed
+# iterations).  Both CPU legs (the cpu_baseline of this arm and the
+# reference arm, which cannot run the GPU) scale the oracle sample by this
+# one number, so they agree.
+FULL_PCG_ITERS = 6450
 # DRAM bytes (read + write) of one level-0 FP32 smoother sweep per nonzero of
 # A, from an ncu capture of k_jacobi<16, float> on a 40x33x40 block of the
 # same recipe (494.52 MB for 59,625,809 nonzeros); the sweep's
@@ -64,6 +67,8 @@ def parse():
     ap.add_argument("--workload", default="block100")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="also time beam40 on one oracle thread (about 3 minutes)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--level0-op", type=int, default=1,
                     help="1: matrix-free level-0 products (headline); 0: assembled CSR")
@@ -74,6 +79,8 @@ def parse():
     ap.add_argument("--serve-instances", type=int, default=8)
     ap.add_argument("--serve-rate", type=float, default=1.0, help="arrivals per second")
     ap.add_argument("--serve-active", type=int, default=8)
+    ap.add_argument("--serve-arms", default="batched_cohort,serial_mixed,plain_fp64",
+                    help="comma list of: " + ", ".join(SERVE_ARMS))
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-arap", action="store_true",
                     help="skip the ARAP-constraint leg (block100arap)")
@@ -296,7 +303,7 @@ def e2e(g, run, steps):
     return steps / dt, nbytes
 
 
-def serve_arm(meshes, reqs, prec, op, graphs, active, budget):
+def serve_arm(meshes, reqs, prec, op, graphs, active, budget, cohort=False):
     """Serves the trace through the request loop: each request is admitted
     (mgpbd_batch_admit) when its arrival time has passed on the wall clock,
     results are collected with mgpbd_batch_tick.  Latency = finish - arrival
@@ -305,7 +312,7 @@ def serve_arm(meshes, reqs, prec, op, graphs, active, budget):
     import torch
 
     from paper_2505_13390_gb300.mgpbd import Batch
-    b = Batch(budget, active)
+    b = Batch(budget, active, cohort=cohort)
     for m, p in meshes:
         b.add(m, dict(p, precision=prec, level0_op=op, use_graphs=graphs, autotune=0,
                       setup_interval=20))
@@ -333,19 +340,32 @@ def serve_arm(meshes, reqs, prec, op, graphs, active, budget):
             "p99_latency_s": float(np.percentile(lat, 99)),
             "mean_latency_s": float(lat.mean()), "mean_queue_wait_s": float(wait_q.mean()),
             "global_iters_per_s": iters / span, "makespan_s": span,
-            "pcg_iters_per_request": [int(r["pcg_iters"]) for r in res], "max_active": active}
+            "pcg_iters_per_request": [int(r["pcg_iters"]) for r in res], "max_active": active,
+            "cohort": bool(cohort)}
+
+
+SERVE_ARMS = {
+    # name: (precision, level0_op, graphs, concurrent, cohort)
+    "batched_cohort": (1, 1, 1, True, True),
+    "batched_streams": (1, 1, 1, True, False),
+    "serial_mixed": (1, 1, 1, False, False),
+    "plain_fp64": (0, 0, 0, False, False),
+}
 
 
 def serving(args):
     """Serving load: step requests of uneven instances with Poisson arrivals,
-    driven through the request loop with wall-clock arrivals.  Three arms on
-    the same seeded trace, all at PCG rtol 1e-6:
-      batched_mixed  mixed precision, matrix-free level 0, CUDA graphs, up to
-                     --serve-active requests at once (the served form);
-      serial_mixed   the same solver settings, one request at a time (isolates
-                     the batching);
-      plain_fp64     FP64, assembled CSR, plain launches, one at a time (the
-                     plain solver).
+    driven through the request loop with wall-clock arrivals, all at PCG rtol
+    1e-6 on the same seeded trace.  Arms (--serve-arms):
+      batched_cohort   the served form: mixed precision, matrix-free level 0,
+                       up to --serve-active requests at once, the PCG
+                       iterations of all of them one launch per step;
+      batched_streams  the same settings, each request on its own stream and
+                       worker thread with CUDA graphs;
+      serial_mixed     the same solver settings, one request at a time
+                       (isolates the batching);
+      plain_fp64       FP64, assembled CSR, plain launches, one at a time (the
+                       plain solver).
     Admission budget: half of the free device memory."""
     import torch
 
@@ -355,53 +375,113 @@ def serving(args):
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.5 * free)
     out = {}
-    for name, prec, op, graphs, active in (("batched_mixed", 1, 1, 1, args.serve_active),
-                                            ("serial_mixed", 1, 1, 1, 1),
-                                            ("plain_fp64", 0, 0, 0, 1)):
-        out[name] = serve_arm(meshes, reqs, prec, op, graphs, active, budget)
+    for name in args.serve_arms.split(","):
+        prec, op, graphs, conc, cohort = SERVE_ARMS[name]
+        out[name] = serve_arm(meshes, reqs, prec, op, graphs, args.serve_active if conc else 1,
+                              budget, cohort)
         torch.cuda.empty_cache()
     out["trace"] = {"requests": len(reqs), "instances": len(inst),
                     "rate_hz": args.serve_rate,
                     "meshes": [f"{d['kind']}{d['size']}" for d in inst],
                     "budget": "half of free device memory", "frames_per_request": 1,
                     "iters_per_frame": 20, "pcg_rtol": 1e-6, "arrivals": "Poisson, seed 6"}
-    b = out["batched_mixed"]["global_iters_per_s"]
-    out["speedup_vs_plain_fp64"] = b / out["plain_fp64"]["global_iters_per_s"]
-    out["speedup_vs_serial_mixed"] = b / out["serial_mixed"]["global_iters_per_s"]
+    served = next((n for n in ("batched_cohort", "batched_streams") if n in out), None)
+    if served:
+        b = out[served]["global_iters_per_s"]
+        for base in ("plain_fp64", "serial_mixed", "batched_streams"):
+            if base in out and base != served:
+                out[f"speedup_vs_{base}"] = b / out[base]["global_iters_per_s"]
     return out
 
 
-def cpu_sample_baseline(iters=2, warm=1, gpu_pcg=None):
-    """The FP64 oracle on the host cores (1 thread) on the bounded sample.
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
-    The time per global iteration is scaled to the full workload by the nnz
-    ratio and, when the GPU run's PCG iteration count is known, by the ratio
-    of PCG iterations (the cost of an iteration is the PCG iterations times
-    the A-passes per PCG iteration)."""
+
+def oracle_sample(steps=2, warm=1, omp=False):
+    """The FP64 oracle on a bounded sample of block100: a 4x33x4-cell block of
+    the same recipe, `steps` global iterations timed after `warm`, PCG capped
+    at SAMPLE_PCG iterations (it does not reach 1e-6 there; its cost is
+    linear in the iterations).  The time per global iteration is scaled to
+    block100 by the nnz ratio and by FULL_PCG_ITERS over the sample's PCG
+    iterations.  omp=True runs the OpenMP build (same bits) on all host cores."""
+    from oracle import oracle
     from oracle.oracle import Oracle
     from paper_2505_13390_gb300.meshgen import default_params, hex_block
     mesh = hex_block(*SAMPLE, h=0.005, jitter=0.1, alpha=1e-10, pin="y0", seed=1,
                      name="block-sample")
     p = default_params(omega_x=0.1, setup_interval=20, pcg_maxiter=SAMPLE_PCG)
-    o = Oracle(mesh, p)
+    cores = oracle.threads(host_cores()) if omp else 1
+    o = Oracle(mesh, p, omp=omp)
     nnz = int(o.matrix(0)[0][-1])
     o.begin_frame()
     for _ in range(warm):
         o.iterate()
     t0 = time.perf_counter()
-    pcg = []
-    for _ in range(iters):
-        pcg.append(o.iterate()["pcg_iters"])
-    dt = (time.perf_counter() - t0) / iters
+    pcg = [o.iterate()["pcg_iters"] for _ in range(steps)]
+    dt = (time.perf_counter() - t0) / steps
     scale = FULL_NNZ / nnz
-    pscale = (sum(gpu_pcg) / len(gpu_pcg)) / (sum(pcg) / len(pcg)) if gpu_pcg else 1.0
-    return {"value": 1.0 / (dt * scale * pscale), "unit": "global_iters/s", "cores": 1,
-            "kind": "oracle",
-            "sample": (f"FP64 C oracle, {iters} global iteration(s) (after {warm} with setup) on a "
-                       f"{SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]}-cell block of the same recipe "
-                       f"({mesh.n_rows} rows, {nnz} nnz, PCG iterations {pcg}), {dt:.2f} s per "
-                       f"iteration, scaled by the nnz ratio {scale:.1f} and the PCG-iteration "
-                       f"ratio {pscale:.2f} to 376.5M nnz")}, dt, scale
+    pscale = FULL_PCG_ITERS / (sum(pcg) / len(pcg))
+    value = 1.0 / (dt * scale * pscale)
+    sample = (f"block100 extrapolated: FP64 C oracle ({'OpenMP build, ' if omp else ''}{cores} "
+              f"thread(s)), {steps} global iteration(s) after {warm} on a "
+              f"{SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]}-cell block of the same recipe ({mesh.n_rows} "
+              f"rows, {nnz} nnz, PCG iterations {pcg}, capped), {dt:.2f} s per iteration, scaled "
+              f"by the nnz ratio {scale:.1f} and the PCG-iteration ratio {pscale:.2f} to "
+              f"{FULL_NNZ} nnz and {FULL_PCG_ITERS} PCG iterations")
+    return {"value": value, "unit": "global_iters/s", "cores": cores, "kind": "oracle",
+            "sample": sample}
+
+
+def direct_pair(name, iters, oracle_builds=(False, True)):
+    """The oracle and the GPU on the same full-size workload and inputs, timed
+    directly: the first `iters` global iterations of frame 0, PCG to 1e-6.
+    Oracle in its plain build (1 thread) and/or its OpenMP build (all host
+    cores); GPU in FP64 (assembled CSR, plain launches) and in the benchmark's
+    configuration (mixed, matrix-free, CUDA graphs, autotuned).  Reports
+    global iterations/s of each and the largest position difference from
+    the oracle (relative to the largest coordinate)."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle
+    from oracle.oracle import Oracle
+    from paper_2505_13390_gb300.meshgen import workload
+    from paper_2505_13390_gb300.mgpbd import Solver
+    mesh, p = workload(name)
+    out = {"workload": name, "rows": mesh.n_rows, "global_iters": iters, "pcg_rtol": 1e-6}
+    xo = None
+    for omp in oracle_builds:
+        cores = oracle.threads(host_cores()) if omp else 1
+        o = Oracle(mesh, p, omp=omp)
+        o.begin_frame()
+        t0 = time.perf_counter()
+        pcg = [o.iterate()["pcg_iters"] for _ in range(iters)]
+        dt = time.perf_counter() - t0
+        out["oracle_omp" if omp else "oracle_1core"] = {
+            "value": iters / dt, "cores": cores, "pcg_iters": pcg}
+        xo = o.get_state()[0]
+        del o
+    scale = float(np.abs(mesh.rest_pos).max())
+    for leg, q in (("gpu_fp64", dict(p, precision=0, level0_op=0, use_graphs=0)),
+                   ("gpu_mixed", dict(p, precision=1, level0_op=1, use_graphs=1, autotune=1))):
+        g = Solver(mesh, q, stream=torch.cuda.Stream())
+        g.begin_frame()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pcg = [g.iterate()["pcg_iters"] for _ in range(iters)]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        xg = g.get_state()[0]
+        g.close()
+        out[leg] = {"value": iters / dt, "pcg_iters": pcg,
+                    "max_dx_vs_oracle": float(np.abs(xg - xo).max() / scale)}
+    ref = out.get("oracle_1core") or out.get("oracle_omp")
+    out["gpu_mixed_over_oracle"] = out["gpu_mixed"]["value"] / ref["value"]
+    return out
 
 
 def xpbd_comparison():
@@ -538,8 +618,12 @@ def run_ours(args, ws, rank):
         serve = serving(args)
     if rank != 0:
         return
+    cpu_all = cpu_direct = None
     if not args.no_cpu:
-        cpu, _, _ = cpu_sample_baseline(gpu_pcg=res["pcg"])
+        cpu = oracle_sample(omp=False)
+        cpu_all = oracle_sample(omp=True)
+        cpu_direct = [direct_pair("cloth32", 2)]
+        cpu_direct.append(direct_pair("beam40", 1, (False, True) if args.cpu_full else (True,)))
     line = {
         "metric": "global XPBD iters/s at 1.65M tets (mixed precision; FP64 under fp64; "
                   "p50/p99 step latency under serving)",
@@ -581,6 +665,11 @@ def run_ours(args, ws, rank):
                      "bytes_per_launch": prof["bytes_per_launch"], "avg_launch_ms": avg_ms,
                      "launches": prof["launches"]},
         "cpu_baseline": cpu,
+        # the same sample on all host cores (the oracle's OpenMP build, same bits)
+        "cpu_baseline_all_cores": cpu_all,
+        # oracle and GPU timed directly, without extrapolation, on full-size
+        # workloads the oracle finishes (cloth32, beam40), on the same inputs
+        "cpu_direct": cpu_direct,
         # the end-to-end steps are the global iterations after the timed ones
         # (same frame); their PCG counts differ from the timed steps'
         "e2e": {"value": e2e_val, "unit": "global_iters/s", "h2d_bytes_per_step": e2e_bytes,
@@ -598,44 +687,14 @@ def run_ours(args, ws, rank):
     print(json.dumps(line))
 
 
-_ORACLE_PCG = []
-
-
 def run_reference(args, ws, rank):
+    """The reference arm: the FP64 oracle as it stands (plain build, one
+    thread) on the bounded block100 sample, args.steps global iterations
+    timed after args.warmup, scaled as in oracle_sample."""
     if rank != 0:
         return
-    from oracle.oracle import Oracle
-    from paper_2505_13390_gb300.meshgen import default_params, hex_block
-    mesh = hex_block(*SAMPLE, h=0.005, jitter=0.1, alpha=1e-10, pin="y0", seed=1)
-    p = default_params(omega_x=0.1, setup_interval=20, pcg_maxiter=SAMPLE_PCG)
-    o = Oracle(mesh, p)
-    nnz = int(o.matrix(0)[0][-1])
-    scale = FULL_NNZ / nnz
-    o.begin_frame()
-    k = 0
-    _ORACLE_PCG.clear()
-
-    def step():
-        nonlocal k
-        _ORACLE_PCG.append(o.iterate()["pcg_iters"])
-        k += 1
-        if k % p["max_iter"] == 0:
-            o.end_frame()
-            o.begin_frame()
-
-    for _ in range(args.warmup):
-        step()
-    _ORACLE_PCG.clear()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
-    pscale = FULL_PCG_ITERS / max(1.0, sum(o_pcg) / len(o_pcg)) if (o_pcg := _ORACLE_PCG) else 1.0
-    value = args.steps / (dt * scale * pscale)
-    sample = (f"FP64 C oracle (1 thread) on a {SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]}-cell block of "
-              f"the same recipe ({mesh.n_rows} rows, {nnz} nnz, PCG iterations {_ORACLE_PCG}); "
-              f"time per global iteration scaled by the nnz ratio {scale:.1f} and the "
-              f"PCG-iteration ratio {pscale:.2f} to 376.5M nnz and {FULL_PCG_ITERS} PCG iterations")
+    cpu = oracle_sample(steps=max(1, args.steps), warm=max(0, args.warmup), omp=False)
+    value = cpu["value"]
     line = {
         "impl": "reference",
         "metric": "global XPBD iters/s at 1.65M tets (mixed precision; FP64 under fp64; "
@@ -644,11 +703,12 @@ def run_reference(args, ws, rank):
         "warmup": args.warmup, "ms_per_step": 1e3 / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "rows": 3_680_033, "nnz": FULL_NNZ,
-                   "tets": 1_650_000, "verts": 346_834, "iters_per_frame": 20,
-                   "setup_interval": 20, "pcg_rtol": 1e-6, "parallelism": f"replicas{ws}"},
-        "cpu_baseline": {"value": value, "unit": "global_iters/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "config": {"workload": f"block100, extrapolated from a {SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]}"
+                               f"-cell sample of the same recipe",
+                   "rows": 3_680_033, "nnz": FULL_NNZ, "tets": 1_650_000, "verts": 346_834,
+                   "iters_per_frame": 20, "setup_interval": 20, "pcg_rtol": 1e-6,
+                   "pcg_iters_scaled_to": FULL_PCG_ITERS, "parallelism": f"replicas{ws}"},
+        "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": "global_iters/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

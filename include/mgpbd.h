@@ -248,6 +248,22 @@ mgpbd_status mgpbd_level_info_get(mgpbd_handle_t *h, int level, mgpbd_level_info
 mgpbd_status mgpbd_set_lanes(mgpbd_handle_t *h, int csr32, int csr64, int vert32, int vert64);
 mgpbd_status mgpbd_get_lanes(mgpbd_handle_t *h, int level, int *csr32, int *csr64, int *vert32,
                              int *vert64);
+/* The V-cycle below level 0 (Sec. 4.4: smoothing, residual and restriction
+ * down to the coarsest level, its dense solve, prolongation and smoothing back
+ * up to level 1).  Where it applies (weighted-Jacobi smoother, one
+ * near-kernel vector, a level between level 0 and the coarsest) it runs by
+ * default as one cooperative kernel over every SM, with a grid barrier
+ * between dependent steps, instead of one launch per step; the results are
+ * the same bits either way (no step of it sums across rows).
+ * mgpbd_set_coarse_tail(h, 0) launches the steps separately, 1 restores the
+ * default.  No device work; MGPBD_E_INVALID for another value.
+ * mgpbd_set_wait_limit bounds how many times a block of that kernel polls a
+ * grid barrier (default 2^24, one to two seconds); when a wait runs out the
+ * solve stops and returns MGPBD_E_DEVICE_TIMEOUT, and the next solve starts
+ * from a reset barrier.  0 makes every waiting block give up at once (to test
+ * that path).  MGPBD_E_INVALID for polls < 0. */
+mgpbd_status mgpbd_set_coarse_tail(mgpbd_handle_t *h, int enable);
+mgpbd_status mgpbd_set_wait_limit(mgpbd_handle_t *h, long long polls);
 /* CSR of level `level`: ptr [n+1] int64, col [nnz] int32, val [nnz] double
  * (diagonal last in each row); any pointer may be NULL. */
 mgpbd_status mgpbd_get_matrix(mgpbd_handle_t *h, int level, int64_t *ptr, int32_t *col,
@@ -307,7 +323,18 @@ unsigned long long mgpbd_launch_count(void);
 typedef struct mgpbd_batch mgpbd_batch_t;
 typedef struct {
   size_t hbm_budget;  /* bytes of device memory the resident instances may hold */
-  int max_active;     /* requests stepping at the same time (worker threads), 1..256 */
+  int max_active;     /* requests stepping at the same time, 1..256 (1..64 with cohort) */
+  int cohort;         /* 0: each running request on its own stream and worker thread;
+                         1: one stepping thread runs every running request together:
+                         the PCG iterations of all of them run as ONE launch per step
+                         (A.p passes, x/r update, level-0 sweeps and residual,
+                         restriction, the V-cycle below level 0 as one cooperative
+                         kernel, prolongation, final sweep, p update), each instance
+                         keeping the grid and reduction order of its own solve, so
+                         its results are bit for bit those of running alone.  Covers
+                         mixed precision, matrix-free level 0, two weighted-Jacobi
+                         sweeps, one near-kernel vector and at least two levels;
+                         other instances solve alone on the same thread. */
 } mgpbd_batch_config;
 typedef struct {
   int id;             /* caller's request id, copied to the result (mgpbd_batch_run) */

@@ -381,6 +381,7 @@ static mgpbd_status create(const mgpbd_mesh_desc *md, const mgpbd_params *p, voi
   CK(alloc_n(h->arena, &h->sc, 1));
   CK(alloc_n(h->arena, &h->partials, 4096 + 16));
   CK(alloc_n(h->arena, &h->counter, 16));
+  CK(alloc_n(h->arena, &h->gbar, 16));
   CK(alloc_n(h->arena, &h->flag, 16));
   CK(alloc_n(h->arena, &h->cstat, 4));
   if (cudaMallocHost((void **)&h->sc_host, sizeof(PcgScalars)) != cudaSuccess ||
@@ -414,7 +415,8 @@ static mgpbd_status create(const mgpbd_mesh_desc *md, const mgpbd_params *p, voi
   }
   if (cudaMemsetAsync(h->v, 0, sizeof(double) * 3 * N, st) != cudaSuccess ||
       cudaMemsetAsync(h->lambda, 0, sizeof(double) * m, st) != cudaSuccess ||
-      cudaMemsetAsync(h->counter, 0, 16 * sizeof(unsigned), st) != cudaSuccess)
+      cudaMemsetAsync(h->counter, 0, 16 * sizeof(unsigned), st) != cudaSuccess ||
+      cudaMemsetAsync(h->gbar, 0, 16 * sizeof(unsigned), st) != cudaSuccess)
     return fail(MGPBD_E_CUDA);
   CK(rest_shape(h));
   CK(build_incidence(h));
@@ -441,11 +443,54 @@ static mgpbd_status timed_end(Handle *h, double *acc) {
   return MGPBD_OK;
 }
 
-// One global iteration of Alg. 1.
-static mgpbd_status iterate(Handle *h, mgpbd_solve_info *info) {
+// The parts of one global iteration of Alg. 1 around its MGPCG solve.
+// Before: C and grad C, assembly, the matrix-free arrays, the lazy setup when
+// due (else the Galerkin re-form) and the coarsest factorisation.
+mgpbd_status iterate_prepare(Handle *h, bool *due) {
   MG_TRY(launch_eval(h));
   MG_TRY(launch_assemble(h));
+  if (h->p.level0_op == 1) MG_TRY(mf_prepare(h));
+  *due = !h->have_setup || (h->p.setup_interval > 0 && h->it_global % h->p.setup_interval == 0);
+  if (*due) {
+    MG_TRY(timed_begin(h));
+    MG_TRY(amg_setup(h));
+    MG_TRY(timed_end(h, &h->ms_setup));
+  } else {
+    MG_TRY(galerkin_reform(h));
+  }
+  return coarsest_factor(h);
+}
+
+// After the solve (status st, inf): a breakdown on a reused hierarchy (omega
+// or P built for an A that has since changed) sets up afresh for the current
+// A and solves once more; then dlambda, lambda and x are applied (eq. 5).
+mgpbd_status iterate_complete(Handle *h, mgpbd_status st, mgpbd_solve_info *inf, bool due,
+                              mgpbd_solve_info *info) {
+  if (st == MGPBD_E_BREAKDOWN && !due) {
+    MG_TRY(timed_begin(h));
+    MG_TRY(amg_setup(h));
+    MG_TRY(timed_end(h, &h->ms_setup));
+    MG_TRY(coarsest_factor(h));
+    *inf = mgpbd_solve_info{};
+    st = pcg_solve(h, h->b, h->dl, inf);
+  }
+  h->it_global++;
+  if (st < 0) {
+    h->last = *inf;
+    if (info) *info = *inf;
+    return st;
+  }
+  MG_TRY(launch_update(h, inf));
+  h->last = *inf;
+  if (info) *info = *inf;
+  return inf->status;
+}
+
+// One global iteration of Alg. 1.
+static mgpbd_status iterate(Handle *h, mgpbd_solve_info *info) {
   if (h->p.linear_solver == 1) {  // XPBD's local step (eq. 4)
+    MG_TRY(launch_eval(h));
+    MG_TRY(launch_assemble(h));
     mgpbd_solve_info inf{};
     MG_TRY(xpbd_step(h, &inf));
     h->it_global++;
@@ -454,39 +499,11 @@ static mgpbd_status iterate(Handle *h, mgpbd_solve_info *info) {
     if (info) *info = inf;
     return MGPBD_OK;
   }
-  if (h->p.level0_op == 1) MG_TRY(mf_prepare(h));
-  bool due = !h->have_setup ||
-             (h->p.setup_interval > 0 && h->it_global % h->p.setup_interval == 0);
-  if (due) {
-    MG_TRY(timed_begin(h));
-    MG_TRY(amg_setup(h));
-    MG_TRY(timed_end(h, &h->ms_setup));
-  } else {
-    MG_TRY(galerkin_reform(h));
-  }
-  MG_TRY(coarsest_factor(h));
+  bool due = false;
+  MG_TRY(iterate_prepare(h, &due));
   mgpbd_solve_info inf{};
   mgpbd_status st = pcg_solve(h, h->b, h->dl, &inf);
-  // a breakdown on a reused hierarchy (omega or P built for an A that has
-  // since changed): set up afresh for the current A and solve once more
-  if (st == MGPBD_E_BREAKDOWN && !due) {
-    MG_TRY(timed_begin(h));
-    MG_TRY(amg_setup(h));
-    MG_TRY(timed_end(h, &h->ms_setup));
-    MG_TRY(coarsest_factor(h));
-    inf = mgpbd_solve_info{};
-    st = pcg_solve(h, h->b, h->dl, &inf);
-  }
-  h->it_global++;
-  if (st < 0) {
-    h->last = inf;
-    if (info) *info = inf;
-    return st;
-  }
-  MG_TRY(launch_update(h, &inf));
-  h->last = inf;
-  if (info) *info = inf;
-  return inf.status;
+  return iterate_complete(h, st, &inf, due, info);
 }
 
 }  // namespace mg
@@ -786,6 +803,22 @@ mgpbd_status mgpbd_set_lanes(mgpbd_handle_t *hh, int csr32, int csr64, int vert3
   h->force_vert32 = vert32;
   h->force_vert64 = vert64;
   h->gen++;  // a captured PCG graph holds the previous shapes
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_set_coarse_tail(mgpbd_handle_t *hh, int enable) {
+  Handle *h = H(hh);
+  if (!h || (enable != 0 && enable != 1)) return MGPBD_E_INVALID;
+  h->tail = enable == 1;
+  h->gen++;  // a captured PCG graph holds the other form
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_set_wait_limit(mgpbd_handle_t *hh, long long polls) {
+  Handle *h = H(hh);
+  if (!h || polls < 0) return MGPBD_E_INVALID;
+  h->wait_limit = polls;
+  h->gen++;  // the limit is a launch argument of captured graphs
   return MGPBD_OK;
 }
 

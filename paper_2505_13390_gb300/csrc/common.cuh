@@ -183,6 +183,10 @@ struct Handle {
   double *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr;
   PcgScalars *sc = nullptr;
   PcgScalars *sc_host = nullptr;  // pinned mirror for polls
+  // the V-cycle below level 0 as one cooperative kernel (solve.cu)
+  bool tail = true;                  // use it where it applies
+  unsigned int *gbar = nullptr;      // its grid barrier: arrivals, generation
+  long long wait_limit = 1ll << 24;  // polls a block waits at the barrier
   double *partials = nullptr;     // dot-product block partials
   unsigned int *counter = nullptr;
   // scratch for setup
@@ -264,6 +268,11 @@ mgpbd_status launch_eval(Handle *h);
 mgpbd_status launch_assemble(Handle *h);
 mgpbd_status launch_update(Handle *h, mgpbd_solve_info *info);
 
+// api.cu: one global iteration of Alg. 1 around its MGPCG solve
+mgpbd_status iterate_prepare(Handle *h, bool *due);
+mgpbd_status iterate_complete(Handle *h, mgpbd_status st, mgpbd_solve_info *inf, bool due,
+                              mgpbd_solve_info *info);
+
 // setup.cu
 mgpbd_status amg_setup(Handle *h);
 mgpbd_status galerkin_reform(Handle *h);
@@ -278,6 +287,10 @@ int group_for(const Handle *h, const Level &L, bool fp64);  // lanes per row in 
 mgpbd_status autotune_levels(Handle *h);
 mgpbd_status coarsest_factor(Handle *h);
 mgpbd_status pcg_solve(Handle *h, const double *d_b, double *d_x, mgpbd_solve_info *info);
+// the solve's start (x = 0, r = b, z = V(r), p = z) and end (true residual,
+// status into info; synchronises), between which chunks of iterations run
+mgpbd_status pcg_begin(Handle *h, const double *d_b, double *d_x);
+mgpbd_status pcg_finish(Handle *h, const double *d_b, double *d_x, mgpbd_solve_info *info);
 mgpbd_status vcycle_apply(Handle *h, const double *d_r, double *d_z);
 mgpbd_status dot_dd(Handle *h, const double *x, const double *y, int64_t n, double *d_out);
 mgpbd_status xpbd_step(Handle *h, mgpbd_solve_info *info);

@@ -20,6 +20,7 @@
 #include <numeric>
 #include <vector>
 
+#include "cohort.cuh"
 #include "common.cuh"
 #include "reduce.cuh"
 
@@ -89,11 +90,11 @@ __global__ void k_to_f32_mf(int64_t n, const double *a, float *b) {
 // Each lane loads four incidences before it uses them (four gathers in
 // flight); the sum order is the plain lane-strided order.
 template <int G>
-__global__ void k_mf_vertex64(int N, const int32_t *vorder, const int64_t *vptr,
-                              const int32_t *vrow, const double *ginc, const double *w,
-                              const double *x, double *u, const PcgScalars *sc) {
-  if (sc && is_done(sc)) return;
-  GROUP_ROWS(G, N) {
+__device__ __forceinline__ void mf_vertex64_rows(int64_t w0, int64_t nw, int N,
+                                                 const int32_t *vorder, const int64_t *vptr,
+                                                 const int32_t *vrow, const double *ginc,
+                                                 const double *w, const double *x, double *u) {
+  GROUP_ROWS_OVER(G, N, w0, nw) {
     double a0 = 0, a1 = 0, a2 = 0;
     const int v = valid ? vorder[i] : 0;
     if (valid) {
@@ -125,11 +126,19 @@ __global__ void k_mf_vertex64(int N, const int32_t *vorder, const int64_t *vptr,
 }
 
 template <int G>
-__global__ void __launch_bounds__(256, 8)
-    k_mf_vertex32(int N, const int32_t *vorder, const int64_t *vptr, const float4 *ginc,
-                  const float *w, const float *x, float *u, const PcgScalars *sc) {
+__global__ void k_mf_vertex64(int N, const int32_t *vorder, const int64_t *vptr,
+                              const int32_t *vrow, const double *ginc, const double *w,
+                              const double *x, double *u, const PcgScalars *sc) {
   if (sc && is_done(sc)) return;
-  GROUP_ROWS(G, N) {
+  mf_vertex64_rows<G>(HW_WARPS, N, vorder, vptr, vrow, ginc, w, x, u);
+}
+
+template <int G>
+__device__ __forceinline__ void mf_vertex32_rows(int64_t w0, int64_t nw, int N,
+                                                 const int32_t *vorder, const int64_t *vptr,
+                                                 const float4 *ginc, const float *w,
+                                                 const float *x, float *u) {
+  GROUP_ROWS_OVER(G, N, w0, nw) {
     float a0 = 0, a1 = 0, a2 = 0;
     const int v = valid ? vorder[i] : 0;
     if (valid) {
@@ -163,6 +172,14 @@ __global__ void __launch_bounds__(256, 8)
   }
 }
 
+template <int G>
+__global__ void __launch_bounds__(256, 8)
+    k_mf_vertex32(int N, const int32_t *vorder, const int64_t *vptr, const float4 *ginc,
+                  const float *w, const float *x, float *u, const PcgScalars *sc) {
+  if (sc && is_done(sc)) return;
+  mf_vertex32_rows<G>(HW_WARPS, N, vorder, vptr, ginc, w, x, u);
+}
+
 enum {
   MF_SWEEP = kMfSweep,
   MF_RESID = kMfResid,
@@ -179,14 +196,14 @@ enum {
 //   MF_SWEEP_Z    z = x + omega D^-1 (b - y) widened to FP64
 //   MF_SWEEP_ZDOT the same, with r.z folded into the PCG scalars
 template <class T, int MODE>
-__global__ void k_mf_row(int E, int m, const int32_t *edge, const int32_t *tet, const T *gd,
-                         const T *gt, const T *u, const T *at, const T *x, const T *b,
-                         const T *dinv, T omega, T *out, DotCtx c, double *z = nullptr,
-                         const double *rr = nullptr) {
-  if (is_done(c.sc)) return;
+__device__ __forceinline__ void mf_row_body(int vb, int vn, int E, int m, const int32_t *edge,
+                                            const int32_t *tet, const T *gd, const T *gt,
+                                            const T *u, const T *at, const T *x, const T *b,
+                                            const T *dinv, T omega, T *out, const DotCtx &c,
+                                            double *z, const double *rr) {
   double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = vb * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)vn * blockDim.x) {
     T y;
     if (i < E) {
       const T *n = gd + 3 * i;
@@ -221,7 +238,17 @@ __global__ void k_mf_row(int E, int m, const int32_t *edge, const int32_t *tet, 
       if (MODE == MF_SWEEP_ZDOT) acc = fma(rr[i], zi, acc);
     }
   }
-  if (MODE == MF_APPLY_DOT || MODE == MF_SWEEP_ZDOT) block_dot_finish(acc, c);
+  if (MODE == MF_APPLY_DOT || MODE == MF_SWEEP_ZDOT) block_dot_finish_vg(acc, c, vb, vn);
+}
+
+template <class T, int MODE>
+__global__ void k_mf_row(int E, int m, const int32_t *edge, const int32_t *tet, const T *gd,
+                         const T *gt, const T *u, const T *at, const T *x, const T *b,
+                         const T *dinv, T omega, T *out, DotCtx c, double *z = nullptr,
+                         const double *rr = nullptr) {
+  if (is_done(c.sc)) return;
+  mf_row_body<T, MODE>(blockIdx.x, gridDim.x, E, m, edge, tet, gd, gt, u, at, x, b, dinv, omega,
+                       out, c, z, rr);
 }
 
 // ---------------------------------------------------------------------------
@@ -318,6 +345,95 @@ static int mf_vertex_blocks(const Handle *h, int G) {
       launch;                    \
     } break;                     \
   }
+
+// ---------------------------------------------------------------------------
+// the same passes for every instance of a cohort in one launch
+// ---------------------------------------------------------------------------
+#define COHORT_BLOCK(step)                                                        \
+  const int *bs_ = bstart + (step) * (K + 1);                                     \
+  const int k_ = cohort_member(bs_, K, blockIdx.x);                               \
+  const CohortMember &M = mem[k_];                                                \
+  const int vb = blockIdx.x - bs_[k_], vn = bs_[k_ + 1] - bs_[k_]
+
+__global__ void kb_vertex64(const CohortMember *mem, const int *bstart, int K) {
+  COHORT_BLOCK(CS_VERT64);
+  if (is_done(M.sc)) return;
+  MF_G_DISPATCH(M.gv64, (mf_vertex64_rows<GG>(VG_WARPS(vb, vn), M.N, M.vorder, M.vptr, M.vrow,
+                                               M.ginc64, M.w, M.p, M.u64)));
+}
+
+__global__ void __launch_bounds__(256, 8)
+    kb_vertex32(const CohortMember *mem, const int *bstart, int K, int sel) {
+  COHORT_BLOCK(CS_VERT32);
+  if (is_done(M.sc)) return;
+  MF_G_DISPATCH(M.gv32, (mf_vertex32_rows<GG>(VG_WARPS(vb, vn), M.N, M.vorder, M.vptr, M.ginc4,
+                                               M.w32, sel ? M.x20 : M.x0, M.u32)));
+}
+
+__global__ void kb_row_pq(const CohortMember *mem, const int *bstart, int K) {
+  COHORT_BLOCK(CS_ROW_PQ);
+  if (is_done(M.sc)) return;
+  mf_row_body<double, MF_APPLY_DOT>(vb, vn, M.E, M.m, M.edge, M.tet, M.gd, M.gt, M.u64, M.at,
+                                    M.p, nullptr, nullptr, 0.0, M.q, M.c_pq, nullptr, nullptr);
+}
+
+// sel 0: pre-sweep x0 -> x20; 1: residual x20 -> r0; 2: post-sweep x20 -> x0
+__global__ void kb_row(const CohortMember *mem, const int *bstart, int K, int sel) {
+  COHORT_BLOCK(CS_ROW);
+  if (is_done(M.sc)) return;
+  DotCtx c{};
+  c.sc = M.sc;
+  if (sel == 1)
+    mf_row_body<float, MF_RESID>(vb, vn, M.E, M.m, M.edge, M.tet, M.gd32, M.gt32, M.u32, M.at32,
+                                 M.x20, M.b0, M.dinv0, M.om0, M.r0, c, nullptr, nullptr);
+  else
+    mf_row_body<float, MF_SWEEP>(vb, vn, M.E, M.m, M.edge, M.tet, M.gd32, M.gt32, M.u32, M.at32,
+                                 sel == 0 ? M.x0 : M.x20, M.b0, M.dinv0, M.om0,
+                                 sel == 0 ? M.x20 : M.x0, c, nullptr, nullptr);
+}
+
+__global__ void kb_row_final(const CohortMember *mem, const int *bstart, int K) {
+  COHORT_BLOCK(CS_ROW_FINAL);
+  if (is_done(M.sc)) return;
+  mf_row_body<float, MF_SWEEP_ZDOT>(vb, vn, M.E, M.m, M.edge, M.tet, M.gd32, M.gt32, M.u32,
+                                    M.at32, M.x0, M.b0, M.dinv0, M.om0, nullptr, M.c_rz, M.z,
+                                    M.r);
+}
+
+void mf_cohort_grids(const Handle *h, int grid[CS_STEPS]) {
+  const int g64 = h->force_vert64 ? h->force_vert64 : h->mf_g64;
+  const int g32 = h->force_vert32 ? h->force_vert32 : h->mf_g32;
+  MF_G_DISPATCH(g64, (grid[CS_VERT64] = mf_vertex_blocks(h, GG)));
+  MF_G_DISPATCH(g32, (grid[CS_VERT32] = mf_vertex_blocks(h, GG)));
+  grid[CS_ROW_PQ] = std::min(mf_grid(h->m, 256),
+                             wave_blocks((const void *)k_mf_row<double, MF_APPLY_DOT>, 256));
+  grid[CS_ROW] = mf_grid(h->m, 256);
+  grid[CS_ROW_FINAL] = std::min(mf_grid(h->m, 256),
+                                wave_blocks((const void *)k_mf_row<float, MF_SWEEP_ZDOT>, 256));
+}
+
+mgpbd_status mf_cohort_step(int which, int sel, const CohortMember *d_mem, const int *d_bstart,
+                            int K, int blocks, cudaStream_t st) {
+  switch (which) {
+    case CS_VERT64:
+      kb_vertex64<<<blocks, 256, 0, st>>>(d_mem, d_bstart, K);
+      break;
+    case CS_ROW_PQ:
+      kb_row_pq<<<blocks, 256, 0, st>>>(d_mem, d_bstart, K);
+      break;
+    case CS_VERT32:
+      kb_vertex32<<<blocks, 256, 0, st>>>(d_mem, d_bstart, K, sel);
+      break;
+    case CS_ROW:
+      kb_row<<<blocks, 256, 0, st>>>(d_mem, d_bstart, K, sel);
+      break;
+    default:
+      kb_row_final<<<blocks, 256, 0, st>>>(d_mem, d_bstart, K);
+      break;
+  }
+  MG_LAUNCH("kb_mf");
+  return MGPBD_OK;
+}
 
 // u = W J^T x (FP64: u64; FP32: u32); G = 0 takes the tuned lanes per vertex
 static mgpbd_status mf_vertex(Handle *h, const double *x, int G = 0, bool check_done = true) {

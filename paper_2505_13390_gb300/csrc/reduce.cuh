@@ -96,8 +96,11 @@ static __device__ void dot_finalize(const DotCtx &c, double s) {
 }
 
 // block reduce of one value per thread in a fixed order, then the last block
-// folds the partials (fixed order) and finalizes
-static __device__ void block_dot_finish(double v, const DotCtx &c) {
+// folds the partials (fixed order) and finalizes.  vb and vn are the block's
+// index and the number of blocks of its reduction: the launch's own, or one
+// instance's share of a launch that serves several instances (the partition
+// into blocks, and so every rounding, is the instance's own either way).
+static __device__ void block_dot_finish_vg(double v, const DotCtx &c, int vb, int vn) {
   __shared__ double ws[32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -107,16 +110,16 @@ static __device__ void block_dot_finish(double v, const DotCtx &c) {
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
-    c.partials[blockIdx.x] = s;
+    c.partials[vb] = s;
     __threadfence();
     unsigned t = atomicAdd(c.counter, 1u);
-    last = (t == gridDim.x - 1);
+    last = (t == (unsigned)vn - 1);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   double s = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+  for (int b = threadIdx.x; b < vn; b += blockDim.x)
     s += ((volatile double *)c.partials)[b];
   s = warp_sum(s);
   if (lane == 0) ws[wid] = s;
@@ -127,6 +130,10 @@ static __device__ void block_dot_finish(double v, const DotCtx &c) {
     dot_finalize(c, t);
     *c.counter = 0;
   }
+}
+
+static __device__ __forceinline__ void block_dot_finish(double v, const DotCtx &c) {
+  block_dot_finish_vg(v, c, blockIdx.x, gridDim.x);
 }
 
 static __device__ __forceinline__ bool is_done(const PcgScalars *sc) {
@@ -189,19 +196,33 @@ __device__ __forceinline__ AT row_dot(const int64_t *ptr, const int32_t *col, co
   return acc;
 }
 
-// Rows handled by G-lane groups, 32/G rows per warp per trip.  The loop bound
-// is uniform across the warp, so full-mask shuffles inside are safe; `valid`
-// marks groups past the last row.
-#define GROUP_ROWS(G, n)                                                          \
+// Rows handled by G-lane groups, 32/G rows per warp per trip, over warps
+// w0, w0 + nw, ...  The loop bound is uniform across the warp, so full-mask
+// shuffles inside are safe; `valid` marks groups past the last row.  Which
+// warp takes a row never changes that row's arithmetic.
+#define GROUP_ROWS_OVER(G, n, w0, nw)                                             \
   const int lane_ = threadIdx.x & 31;                                             \
   const int g = lane_ & ((G) - 1);                                                \
   const int sub_ = lane_ / (G);                                                   \
-  const int64_t warp_ = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;    \
-  const int64_t nwarp_ = ((int64_t)gridDim.x * blockDim.x) >> 5;                  \
+  const int64_t warp_ = (w0);                                                     \
+  const int64_t nwarp_ = (nw);                                                    \
   for (int64_t base_ = warp_ * (32 / (G)), i = base_ + sub_; base_ < (n);         \
        base_ += nwarp_ * (32 / (G)), i = base_ + sub_)                            \
     if (const bool valid = i < (n); true)
 
+// the same over every warp of the launch
+#define GROUP_ROWS(G, n)                                                          \
+  GROUP_ROWS_OVER(G, n, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,    \
+                  ((int64_t)gridDim.x * blockDim.x) >> 5)
+
+// the launch's own warps as (first warp, number of warps)
+#define HW_WARPS                                                                  \
+  (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,                          \
+      ((int64_t)gridDim.x * blockDim.x) >> 5
+
+// the warps of virtual block vb of a grid of vn blocks
+#define VG_WARPS(vb, vn)                                                          \
+  ((int64_t)(vb) * blockDim.x + threadIdx.x) >> 5, ((int64_t)(vn) * blockDim.x) >> 5
 
 // matrix-free level-0 products (mfree.cu)
 mgpbd_status mf_apply_pq(Handle *h, const double *p, double *q, const DotCtx &c);

@@ -29,6 +29,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "cohort.cuh"
 #include "common.cuh"
 
 namespace mg {
@@ -67,6 +68,10 @@ struct Batch {
   std::vector<mgpbd_step_result> finished;  // not yet returned by a tick
   bool stop = false;
   std::vector<std::thread> workers;
+  // cohort mode: the stream of the batched launches (only the stepping thread
+  // uses it; instances keep their own streams)
+  cudaStream_t cohort_stream = nullptr;
+  unsigned long long submitted = 0;  // requests submitted so far
 };
 
 // upper estimate of an instance's device bytes from its mesh (before create):
@@ -251,6 +256,216 @@ static void worker(Batch *b) {
   }
 }
 
+// ---- cohort mode ------------------------------------------------------------
+// One stepping thread runs every started request.  Each round it advances
+// the requests that are between solves (frame prologue, C, A, setup or
+// Galerkin re-form, coarsest factorisation, the solve's start) with their
+// own launches on their own streams, then runs eight PCG iterations of every
+// solving instance as one launch per step on the batch's cohort stream
+// (which first waits for each member's start), then finishes the solves that
+// have converged (true residual, position update, frame epilogue).  Only the
+// stepping thread uses the cohort stream, so no other thread's work can fall
+// into its graph capture.  Instances whose configuration the batched kernels
+// do not cover solve alone, one global iteration per round.  An instance's
+// arithmetic is its standalone solve's, bit for bit, whatever else runs.
+struct CohortRun {
+  Req q;
+  Instance *in;
+  mgpbd_step_result r;
+  int frame = 0, it = 0;     // frame of the request and global iteration within it
+  bool frame_open = false;   // begin_frame ran for `frame`
+  bool solving = false;      // a batched solve is in progress
+  bool due = false;          // the iteration set up afresh (breakdown retry rule)
+  bool done = false;
+  mgpbd_status worst = MGPBD_OK;
+  cudaEvent_t started = nullptr;  // recorded after the solve's start
+};
+
+// counts one finished global iteration and closes the frame or the request
+static void cohort_advance(CohortRun &c, const mgpbd_solve_info &inf, mgpbd_status st) {
+  c.r.global_iters++;
+  c.r.pcg_iters += inf.pcg_iters;
+  if (st < 0) {
+    c.worst = st;
+    c.done = true;
+    return;
+  }
+  c.worst = std::max(c.worst, st);
+  c.it++;
+  if (c.it >= c.in->p.max_iter || inf.bnorm < c.in->p.eps_b) {
+    mgpbd_status e = mgpbd_end_frame(c.in->h);
+    if (e < 0) {
+      c.worst = e;
+      c.done = true;
+      return;
+    }
+    c.frame++;
+    c.it = 0;
+    c.frame_open = false;
+    if (c.frame >= c.q.frames) c.done = true;
+  }
+}
+
+// the part of a global iteration before its solve; starts a batched solve or
+// runs the whole iteration alone
+static void cohort_prepare(CohortRun &c) {
+  Handle *h = reinterpret_cast<Handle *>(c.in->h);
+  if (!c.frame_open) {
+    mgpbd_status e = mgpbd_begin_frame(c.in->h);
+    if (e < 0) {
+      c.worst = e;
+      c.done = true;
+      return;
+    }
+    c.frame_open = true;
+  }
+  if (h->p.max_iter <= 0) {  // a frame without iterations
+    cohort_advance(c, mgpbd_solve_info{}, MGPBD_OK);
+    return;
+  }
+  if (h->p.linear_solver == 0) {
+    mgpbd_status e = iterate_prepare(h, &c.due);
+    if (e < 0) {
+      c.r.global_iters++;
+      c.worst = e;
+      c.done = true;
+      return;
+    }
+    if (cohort_eligible(h)) {
+      e = h->m > 0 ? pcg_begin(h, h->b, h->dl) : MGPBD_OK;
+      if (e < 0) {
+        c.worst = e;
+        c.done = true;
+        return;
+      }
+      c.solving = true;
+      return;
+    }
+    mgpbd_solve_info inf{}, info{};
+    mgpbd_status st = pcg_solve(h, h->b, h->dl, &inf);
+    st = iterate_complete(h, st, &inf, c.due, &info);
+    cohort_advance(c, info, st);
+    return;
+  }
+  mgpbd_solve_info info{};
+  mgpbd_status st = mgpbd_iterate(c.in->h, &info);
+  cohort_advance(c, info, st);
+}
+
+static void cohort_stepper(Batch *b) {
+  cudaSetDevice(b->device);
+  Cohort co;
+  co.stream = b->cohort_stream;
+  std::vector<CohortRun> runs;
+  unsigned long long seen = 0;
+  std::unique_lock<std::mutex> lock(b->mu);
+  for (;;) {
+    dispatch(b);
+    seen = b->submitted;
+    if (runs.empty() && b->jobs.empty()) {
+      b->cv_work.wait(lock, [&] { return b->stop || !b->jobs.empty() || b->submitted != seen; });
+      if (b->stop && b->jobs.empty()) return;
+      continue;
+    }
+    std::vector<CohortRun> fresh;
+    while (!b->jobs.empty()) {
+      CohortRun c;
+      c.q = b->jobs.front();
+      b->jobs.pop_front();
+      c.in = b->inst[c.q.instance].get();
+      c.r = mgpbd_step_result{};
+      c.r.id = c.q.ticket;
+      c.r.instance = c.q.instance;
+      c.r.arrival_s = c.q.arrival;
+      c.r.start_s = clock_s(b);
+      fresh.push_back(c);
+    }
+    lock.unlock();
+    for (CohortRun &c : fresh) {
+      mgpbd_status e = make_resident(*c.in);
+      if (e >= 0 && cudaEventCreateWithFlags(&c.started, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        e = MGPBD_E_CUDA;
+      }
+      if (e < 0) {
+        c.worst = e;
+        c.done = true;
+      }
+      runs.push_back(c);
+    }
+    // requests between solves: the next global iteration up to its solve
+    for (CohortRun &c : runs)
+      if (!c.done && !c.solving) cohort_prepare(c);
+    // the batched chunk over every instance that is solving
+    std::vector<Handle *> members;
+    for (CohortRun &c : runs)
+      if (!c.done && c.solving) members.push_back(reinterpret_cast<Handle *>(c.in->h));
+    if (!members.empty()) {
+      mgpbd_status e = MGPBD_OK;
+      if (members != co.hs || cohort_stale(&co)) {
+        co.hs = members;
+        e = cohort_build(&co);
+      }
+      // the chunk follows each member's own work (its solve's start)
+      for (CohortRun &c : runs)
+        if (e >= 0 && !c.done && c.solving &&
+            (cudaEventRecord(c.started, c.in->stream) != cudaSuccess ||
+             cudaStreamWaitEvent(b->cohort_stream, c.started, 0) != cudaSuccess))
+          e = cuda_fail(cudaGetLastError(), "cohort: ordering a member's start", __FILE__,
+                        __LINE__);
+      if (e >= 0) e = cohort_chunk(&co, 8);
+      for (CohortRun &c : runs) {
+        if (c.done || !c.solving) continue;
+        Handle *h = reinterpret_cast<Handle *>(c.in->h);
+        if (e < 0) {
+          c.worst = e;
+          c.done = true;
+          continue;
+        }
+        const int k = (int)(std::find(co.hs.begin(), co.hs.end(), h) - co.hs.begin());
+        if (!co.h_sc[k].done) continue;
+        c.solving = false;
+        mgpbd_solve_info inf{}, info{};
+        mgpbd_status st = pcg_finish(h, h->b, h->dl, &inf);
+        st = iterate_complete(h, st, &inf, c.due, &info);
+        cohort_advance(c, info, st);
+      }
+    }
+    // finished requests leave
+    std::vector<CohortRun> left;
+    std::vector<std::pair<CohortRun, size_t>> fin;
+    for (CohortRun &c : runs) {
+      if (!c.done) {
+        left.push_back(c);
+        continue;
+      }
+      size_t held = 0;
+      if (c.in->h) {
+        mgpbd_stats_t st{};
+        mgpbd_stats(c.in->h, &st);
+        held = st.device_bytes;
+      }
+      if (c.started) cudaEventDestroy(c.started);
+      c.r.finish_s = clock_s(b);
+      c.r.status = c.worst;
+      fin.emplace_back(c, held);
+    }
+    runs.swap(left);
+    if (runs.empty()) co.hs.clear();  // no member holds a handle that may be evicted
+    lock.lock();
+    for (auto &f : fin) {
+      Instance &in = *f.first.in;
+      b->resident = b->resident - in.bytes + f.second;
+      in.bytes = f.second;
+      in.busy = false;
+      in.last_used = f.first.r.finish_s;
+      --b->running;
+      b->finished.push_back(f.first.r);
+    }
+    if (!fin.empty()) b->cv_done.notify_all();
+  }
+}
+
 // Moves up to `max` finished results that `want` accepts into `out`, in
 // finishing order, waiting up to wait_s seconds for the first one (lock held
 // by the caller through `lock`).
@@ -306,7 +521,8 @@ mgpbd_status mgpbd_workspace_size(const mgpbd_mesh_desc *md, const mgpbd_params 
 }
 
 mgpbd_status mgpbd_batch_create(const mgpbd_batch_config *cfg, mgpbd_batch_t **out) {
-  if (!cfg || !out || cfg->max_active < 1 || cfg->max_active > 256 || cfg->hbm_budget == 0) {
+  if (!cfg || !out || cfg->max_active < 1 || cfg->max_active > 256 || cfg->hbm_budget == 0 ||
+      (cfg->cohort != 0 && cfg->cohort != 1) || (cfg->cohort && cfg->max_active > kCohortMax)) {
     set_error("mgpbd_batch_create: invalid configuration");
     return MGPBD_E_INVALID;
   }
@@ -321,7 +537,17 @@ mgpbd_status mgpbd_batch_create(const mgpbd_batch_config *cfg, mgpbd_batch_t **o
     set_error("mgpbd_batch_create: cudaGetDevice failed");
     return MGPBD_E_CUDA;
   }
-  for (int t = 0; t < cfg->max_active; ++t) b->workers.emplace_back(worker, b);
+  if (cfg->cohort) {
+    if (cudaStreamCreateWithFlags(&b->cohort_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete b;
+      set_error("mgpbd_batch_create: cudaStreamCreate failed");
+      return MGPBD_E_CUDA;
+    }
+    b->workers.emplace_back(cohort_stepper, b);
+  } else {
+    for (int t = 0; t < cfg->max_active; ++t) b->workers.emplace_back(worker, b);
+  }
   *out = reinterpret_cast<mgpbd_batch_t *>(b);
   return MGPBD_OK;
 }
@@ -379,7 +605,9 @@ mgpbd_status mgpbd_batch_admit(mgpbd_batch_t *bb, int instance, int frames, int 
   Req q{b->next_ticket++, instance, frames, clock_s(b)};
   b->queue.push_back(q);
   *ticket = q.ticket;
+  b->submitted++;
   dispatch(b);
+  b->cv_work.notify_all();
   return MGPBD_OK;
 }
 
@@ -507,6 +735,7 @@ void mgpbd_batch_destroy(mgpbd_batch_t *bb) {
     evict(*in);
     drop_handle(*in);
   }
+  if (b->cohort_stream) cudaStreamDestroy(b->cohort_stream);
   delete b;
 }
 

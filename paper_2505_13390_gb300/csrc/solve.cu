@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "cohort.cuh"
 #include "reduce.cuh"
 
 namespace mg {
@@ -85,15 +86,15 @@ __device__ __forceinline__ T xr_entry(double al, double &xi, double &ri, double 
 }
 
 template <class T>
-__global__ void k_xr_update(int64_t n, double *x, double *r, const double *p, const double *q,
-                            DotCtx c, T *bl, const T *dinv, T om, T *x0) {
+__device__ __forceinline__ void xr_update_body(int vb, int vn, int64_t n, double *x, double *r,
+                                               const double *p, const double *q, const DotCtx &c,
+                                               T *bl, const T *dinv, T om, T *x0) {
   using V = typename Pair<T>::V;
-  if (is_done(c.sc)) return;
   const double al = c.sc->alpha;
   T acc = 0;
   const int64_t n2 = n / 2;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n2;
-       k += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t k = vb * (int64_t)blockDim.x + threadIdx.x; k < n2;
+       k += (int64_t)vn * blockDim.x) {
     double2 xv = reinterpret_cast<const double2 *>(x)[k];
     double2 rv = reinterpret_cast<const double2 *>(r)[k];
     const double2 pv = reinterpret_cast<const double2 *>(p)[k];
@@ -110,7 +111,7 @@ __global__ void k_xr_update(int64_t n, double *x, double *r, const double *p, co
     if (bl) reinterpret_cast<V *>(bl)[k] = bv;
     if (x0) reinterpret_cast<V *>(x0)[k] = xv0;
   }
-  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+  if ((n & 1) && vb == 0 && threadIdx.x == 0) {
     const int64_t i = n - 1;
     double xi = x[i], ri = r[i];
     T bi, x0i;
@@ -121,7 +122,14 @@ __global__ void k_xr_update(int64_t n, double *x, double *r, const double *p, co
     if (bl) bl[i] = bi;
     if (x0) x0[i] = x0i;
   }
-  block_dot_finish(widen(acc), c);
+  block_dot_finish_vg(widen(acc), c, vb, vn);
+}
+
+template <class T>
+__global__ void k_xr_update(int64_t n, double *x, double *r, const double *p, const double *q,
+                            DotCtx c, T *bl, const T *dinv, T om, T *x0) {
+  if (is_done(c.sc)) return;
+  xr_update_body<T>(blockIdx.x, gridDim.x, n, x, r, p, q, c, bl, dinv, om, x0);
 }
 
 // the same start of a V-cycle on its own: bl = r in the V-cycle's precision,
@@ -140,14 +148,14 @@ __global__ void k_top_prep(int64_t n, const double *r, T *bl, const T *dinv, T o
 
 // p = z + beta p, two entries per thread (16-byte loads; p and z are
 // 256-byte aligned)
-__global__ void k_p_update(int64_t n, double *p, const double *z, const PcgScalars *sc) {
-  if (is_done(sc)) return;
+__device__ __forceinline__ void p_update_body(int vb, int vn, int64_t n, double *p,
+                                              const double *z, const PcgScalars *sc) {
   const double be = sc->beta;
   const int64_t n2 = n / 2, h2 = (n2 + 1) / 2;  // pairs k and k + h2 per thread
   double2 *p2 = reinterpret_cast<double2 *>(p);
   const double2 *z2 = reinterpret_cast<const double2 *>(z);
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < h2;
-       k += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t k = vb * (int64_t)blockDim.x + threadIdx.x; k < h2;
+       k += (int64_t)vn * blockDim.x) {
     const int64_t k2 = k + h2;
     const bool two = k2 < n2;
     double2 pa = p2[k], za = z2[k], pb = {0.0, 0.0}, zb = {0.0, 0.0};
@@ -164,10 +172,16 @@ __global__ void k_p_update(int64_t n, double *p, const double *z, const PcgScala
       p2[k2] = pb;
     }
   }
-  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) p[n - 1] = fma(be, p[n - 1], z[n - 1]);
+  if ((n & 1) && vb == 0 && threadIdx.x == 0) p[n - 1] = fma(be, p[n - 1], z[n - 1]);
 }
 
-__global__ void k_pcg_init(PcgScalars *sc) {
+__global__ void k_p_update(int64_t n, double *p, const double *z, const PcgScalars *sc) {
+  if (is_done(sc)) return;
+  p_update_body(blockIdx.x, gridDim.x, n, p, z, sc);
+}
+
+__global__ void k_pcg_init(PcgScalars *sc, unsigned int *bar) {
+  bar[0] = 0;  // no block waits at the coarse tail's barrier between solves
   sc->done = 0;
   sc->iters = 0;
   sc->status = MGPBD_W_NOT_CONVERGED;
@@ -290,13 +304,14 @@ __global__ void k_cheb_step(int n, const T *Ad, const T *dinv, T c1, T c2, T *r,
   }
 }
 
+// Row bodies of the CSR-level V-cycle steps, over the warps w0, w0 + nw, ...
+// (a launch's own warps, or every warp of the cooperative coarse tail).
 // weighted Jacobi sweep: xn = x + omega D^-1 (b - A x)
 template <int G, class T>
-__global__ void k_jacobi(int n, const int64_t *ptr, const int32_t *col, const T *val,
-                         const T *dinv, T omega, const T *b, const T *x, T *xn,
-                         const PcgScalars *sc) {
-  if (is_done(sc)) return;
-  GROUP_ROWS(G, n) {
+__device__ __forceinline__ void jacobi_rows(int64_t w0, int64_t nw, int n, const int64_t *ptr,
+                                            const int32_t *col, const T *val, const T *dinv,
+                                            T omega, const T *b, const T *x, T *xn) {
+  GROUP_ROWS_OVER(G, n, w0, nw) {
     T s = valid ? row_dot<G, T, T, T>(ptr, col, val, x, (int)i, g) : (T)0;
     s = group_sum<G>(s);
     if (valid && g == 0) xn[i] = fma(omega, (b[i] - s) * dinv[i], x[i]);
@@ -305,27 +320,40 @@ __global__ void k_jacobi(int n, const int64_t *ptr, const int32_t *col, const T 
 
 // r = b - A x
 template <int G, class T>
-__global__ void k_resid(int n, const int64_t *ptr, const int32_t *col, const T *val, const T *b,
-                        const T *x, T *r, const PcgScalars *sc) {
-  if (sc && is_done(sc)) return;
-  GROUP_ROWS(G, n) {
+__device__ __forceinline__ void resid_rows(int64_t w0, int64_t nw, int n, const int64_t *ptr,
+                                           const int32_t *col, const T *val, const T *b,
+                                           const T *x, T *r) {
+  GROUP_ROWS_OVER(G, n, w0, nw) {
     T s = valid ? row_dot<G, T, T, T>(ptr, col, val, x, (int)i, g) : (T)0;
     s = group_sum<G>(s);
     if (valid && g == 0) r[i] = b[i] - s;
   }
 }
 
+template <int G, class T>
+__global__ void k_jacobi(int n, const int64_t *ptr, const int32_t *col, const T *val,
+                         const T *dinv, T omega, const T *b, const T *x, T *xn,
+                         const PcgScalars *sc) {
+  if (is_done(sc)) return;
+  jacobi_rows<G, T>(HW_WARPS, n, ptr, col, val, dinv, omega, b, x, xn);
+}
+
+template <int G, class T>
+__global__ void k_resid(int n, const int64_t *ptr, const int32_t *col, const T *val, const T *b,
+                        const T *x, T *r, const PcgScalars *sc) {
+  if (sc && is_done(sc)) return;
+  resid_rows<G, T>(HW_WARPS, n, ptr, col, val, b, x, r);
+}
+
 // b_c[a*k+c] = sum_{i in a} P_ic r_i (warp per aggregate, k columns of P per
 // aggregate); with xc given, also the coarse level's first Jacobi sweep from
 // zero, xc = omega_c b_c / A_c,diag
 template <class T>
-__global__ void k_restrict(int na, int k, const int64_t *mptr, const int32_t *mrow, const T *P,
-                           const T *r, T *bc, const PcgScalars *sc, const T *dinv_c = nullptr,
-                           T om_c = 0, T *xc = nullptr) {
-  if (is_done(sc)) return;
+__device__ __forceinline__ void restrict_aggs(int64_t w, int64_t nw, int na, int k,
+                                              const int64_t *mptr, const int32_t *mrow,
+                                              const T *P, const T *r, T *bc, const T *dinv_c,
+                                              T om_c, T *xc) {
   const int lane = threadIdx.x & 31;
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t a = w; a < na; a += nw) {
     for (int c = 0; c < k; ++c) {
       T acc = 0;
@@ -343,15 +371,22 @@ __global__ void k_restrict(int na, int k, const int64_t *mptr, const int32_t *mr
   }
 }
 
+template <class T>
+__global__ void k_restrict(int na, int k, const int64_t *mptr, const int32_t *mrow, const T *P,
+                           const T *r, T *bc, const PcgScalars *sc, const T *dinv_c = nullptr,
+                           T om_c = 0, T *xc = nullptr) {
+  if (is_done(sc)) return;
+  restrict_aggs<T>(HW_WARPS, na, k, mptr, mrow, P, r, bc, dinv_c, om_c, xc);
+}
+
 // x_i += P_i x_c[agg_i] (rows left alone have no aggregate); each thread
 // takes four rows a block-width apart so that its loads are in flight together
 constexpr int kProlongRows = 4;
 template <class T>
-__global__ void k_prolong(int n, const int32_t *agg, const T *P, const T *xc, T *x,
-                          const PcgScalars *sc) {  // one column of P per aggregate
-  if (is_done(sc)) return;
+__device__ __forceinline__ void prolong_rows(int64_t blk, int64_t nblk, int n, const int32_t *agg,
+                                             const T *P, const T *xc, T *x) {
   const int64_t tile = (int64_t)blockDim.x * kProlongRows;
-  for (int64_t base = blockIdx.x * tile + threadIdx.x; base < n; base += gridDim.x * tile) {
+  for (int64_t base = blk * tile + threadIdx.x; base < n; base += nblk * tile) {
     int a[kProlongRows];
     T p[kProlongRows], xv[kProlongRows];
 #pragma unroll
@@ -375,6 +410,13 @@ __global__ void k_prolong(int n, const int32_t *agg, const T *P, const T *xc, T 
   }
 }
 
+template <class T>
+__global__ void k_prolong(int n, const int32_t *agg, const T *P, const T *xc, T *x,
+                          const PcgScalars *sc) {  // one column of P per aggregate
+  if (is_done(sc)) return;
+  prolong_rows<T>(blockIdx.x, gridDim.x, n, agg, P, xc, x);
+}
+
 // x_i += sum_c P_ic x_c[agg_i*k + c], c ascending (k columns of P per aggregate)
 template <class T>
 __global__ void k_prolong_k(int n, int k, const int32_t *agg, const T *P, const T *xc, T *x,
@@ -392,17 +434,21 @@ __global__ void k_prolong_k(int n, int k, const int32_t *agg, const T *P, const 
 
 // coarsest: x = A_c^-1 b with the explicit FP64 inverse (warp per row)
 template <class T>
-__global__ void k_coarse_apply(int n, const double *inv, const T *b, T *x, const PcgScalars *sc) {
-  if (sc && is_done(sc)) return;
+__device__ __forceinline__ void coarse_rows(int64_t w, int64_t nw, int n, const double *inv,
+                                            const T *b, T *x) {
   const int lane = threadIdx.x & 31;
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = w; i < n; i += nw) {
     double acc = 0.0;
     for (int j = lane; j < n; j += 32) acc = fma(inv[i * (int64_t)n + j], widen(b[j]), acc);
     acc = warp_sum(acc);
     if (lane == 0) x[i] = narrow<T>(acc);
   }
+}
+
+template <class T>
+__global__ void k_coarse_apply(int n, const double *inv, const T *b, T *x, const PcgScalars *sc) {
+  if (sc && is_done(sc)) return;
+  coarse_rows<T>(HW_WARPS, n, inv, b, x);
 }
 
 // ---------------------------------------------------------------------------
@@ -417,20 +463,21 @@ __global__ void k_dense_fill(int n, const int64_t *ptr, const int32_t *col, cons
 
 // Tiled over 16 x 16 tiles, one tile per block of 256 threads (one entry per
 // thread).  FP64 throughput per SM is low on this part (about 1.6 fused
-// multiply-adds per clock), so the n^3 work is spread over many blocks:
-//   Cholesky, right-looking: for each tile column k, a panel launch factors
-//     the diagonal tile in shared memory (every block of the launch redundantly,
-//     so no block waits on another) and forms L_ik = A_ik L_kk^-T below it,
-//     then a trailing launch applies A_ij -= L_ik L_jk^T to the tiles right of it;
-//   L^-1, by tile rows: step p adds -L_ip Li_pj into the tiles of rows below
-//     p, after which row p + 1 is complete: Li_{p+1,j} = L_{p+1,p+1}^-1 times
-//     its sum (the inverses of the diagonal tiles come from the panels);
-//   A^-1 = L^-T L^-1, one launch, tile (i, j) summing Li_ki^T Li_kj over
-//     k >= max(i, j) in ascending k (so A^-1 is bitwise symmetric).
-// Entries outside the n x n matrix read as 0 (1 on the diagonal of the last
-// diagonal tile), i.e. the factorisation of diag(A, I), whose leading block
-// is A's; they are never stored.  A pivot <= 0 sets *status to
-// MGPBD_E_SINGULAR and every later launch returns at once.
+// multiply-adds per clock), so the n^3 work is spread over many blocks and
+// the dependent chains inside a tile are kept short.  Right-looking, for each
+// tile column k (Li holds L^-1; its tiles start at zero):
+//   panel launch: every block factors the diagonal tile A_kk in shared memory
+//     (redundantly, so no block waits on another), getting L_kk and L_kk^-1;
+//     blocks below form L_ik = A_ik L_kk^-T, block 0 stores Li_kk = L_kk^-1,
+//     and blocks left of the diagonal finish Li_kj = L_kk^-1 S_kj;
+//   trailing launch: A_ij -= L_ik L_jk^T right of column k, and the running
+//     sums S_ij -= L_ik Li_kj of L^-1's tiles in the rows below k;
+// then A^-1 = L^-T L^-1 in one launch, tile (i, j) summing Li_ki^T Li_kj over
+// k >= max(i, j) in ascending k (so A^-1 is bitwise symmetric).  Entries
+// outside the n x n matrix read as 0 (1 on the diagonal of the last diagonal
+// tile), i.e. the factorisation of diag(A, I), whose leading block is A's;
+// they are never stored.  A pivot <= 0 sets *status to MGPBD_E_SINGULAR and
+// every later launch returns at once.
 constexpr int kCT = 16;
 constexpr int kCThreads = kCT * kCT;
 
@@ -451,109 +498,101 @@ __device__ __forceinline__ void tile_put(double *M, int n, int ti, int tj, int r
   if (gr < n && gc < n) M[(int64_t)gr * n + gc] = v;
 }
 
-// Cholesky of the tile in D (lower part, in place) and the inverse X of the
-// lower factor (zero above the diagonal); false on a pivot <= 0 (the same in
-// every thread of the block)
-__device__ bool tile_factor(double (*D)[kCT + 1], double (*X)[kCT + 1], int *bad) {
+// Cholesky of the tile in D (lower part, in place) and, in the same
+// right-looking loop, the inverse X of the lower factor (X starts as the
+// identity; step j scales row j of X by 1/L_jj and subtracts L_ij times it
+// from the rows below).  False on a pivot <= 0 (the same in every thread).
+__device__ bool tile_factor(double (*D)[kCT + 1], double (*X)[kCT + 1], double *rinv, int *bad) {
   const int t = threadIdx.x, r = t / kCT, c = t % kCT;
+  X[r][c] = r == c ? 1.0 : 0.0;
   for (int j = 0; j < kCT; ++j) {
     if (t == 0) {
       const double d = D[j][j];
-      if (!(d > 0.0)) *bad = 1;
-      else D[j][j] = sqrt(d);
+      if (!(d > 0.0)) {
+        *bad = 1;
+      } else {
+        const double l = sqrt(d);
+        D[j][j] = l;
+        *rinv = 1.0 / l;
+      }
     }
     __syncthreads();
     if (*bad) return false;
-    if (c == j && r > j) D[r][j] = D[r][j] / D[j][j];
+    const double inv = *rinv;
+    if (c == j && r > j) D[r][j] = D[r][j] * inv;
+    if (r == j && c <= j) X[j][c] = X[j][c] * inv;
     __syncthreads();
     if (c > j && r >= c) D[r][c] = fma(-D[r][j], D[c][j], D[r][c]);
+    if (r > j && c <= j) X[r][c] = fma(-D[r][j], X[j][c], X[r][c]);
     __syncthreads();
   }
-  if (t < kCT) {  // column t of the inverse by forward substitution
-    for (int i = 0; i < kCT; ++i) {
-      if (i < t) {
-        X[i][t] = 0.0;
-        continue;
-      }
-      double s = i == t ? 1.0 : 0.0;
-      for (int q = t; q < i; ++q) s = fma(-D[i][q], X[q][t], s);
-      X[i][t] = s / D[i][i];
-    }
-  }
-  __syncthreads();
   return true;
 }
 
-// panel of tile column k: block b handles tile row k + b.  Block 0 stores the
-// inverse of the diagonal factor into Li; the others store L_ik = A_ik L_kk^-T
-// over A_ik.  (A_kk itself is read by every block and written by none.)
-__global__ void __launch_bounds__(kCThreads) k_chol_panel(int n, int k, double *A, double *Li,
-                                                          int *status) {
+// panel of tile column k: blocks 0 .. T-k-1 handle tile rows k .. T-1 of L
+// (block 0 stores L_kk^-1 into Li), blocks T-k .. T-1 finish the tiles
+// Li_kj, j = 0 .. k-1, of L^-1's row k.  A_kk is read by every block and
+// written by none.
+__global__ void __launch_bounds__(kCThreads) k_chol_panel(int n, int T, int k, double *A,
+                                                          double *Li, int *status) {
   __shared__ double D[kCT][kCT + 1], X[kCT][kCT + 1];
+  __shared__ double rinv;
   __shared__ int bad;
   if (chol_failed(status)) return;
   const int t = threadIdx.x, r = t / kCT, c = t % kCT;
-  const int i = k + blockIdx.x;
   if (t == 0) bad = 0;
   D[r][c] = tile_get(A, n, k, k, r, c, true);
   __syncthreads();
-  if (!tile_factor(D, X, &bad)) {
+  if (!tile_factor(D, X, &rinv, &bad)) {
     if (blockIdx.x == 0 && t == 0) *status = MGPBD_E_SINGULAR;
     return;
   }
-  if (blockIdx.x == 0) {
+  const int b = blockIdx.x;
+  if (b == 0) {
     tile_put(Li, n, k, k, r, c, X[r][c]);
     return;
   }
-  D[r][c] = tile_get(A, n, i, k, r, c, false);  // D is free after the factor
-  __syncthreads();
-  double s = 0.0;
-  for (int q = 0; q <= c; ++q) s = fma(D[r][q], X[c][q], s);
-  tile_put(A, n, i, k, r, c, s);
-}
-
-// trailing update after tile column k: block (x, y) is tile (k+1+y, k+1+x)
-// of the lower triangle (blocks above the diagonal return)
-__global__ void __launch_bounds__(kCThreads) k_chol_trail(int n, int k, double *A,
-                                                          const int *status) {
-  __shared__ double Lr[kCT][kCT + 1], Lc[kCT][kCT + 1];
-  if (chol_failed(status)) return;
-  const int i = k + 1 + blockIdx.y, j = k + 1 + blockIdx.x;
-  if (j > i) return;
-  const int t = threadIdx.x, r = t / kCT, c = t % kCT;
-  Lr[r][c] = tile_get(A, n, i, k, r, c, false);
-  Lc[r][c] = tile_get(A, n, j, k, r, c, false);
-  __syncthreads();
-  double a = tile_get(A, n, i, j, r, c, false);
-  for (int q = 0; q < kCT; ++q) a = fma(-Lr[r][q], Lc[c][q], a);
-  tile_put(A, n, i, j, r, c, a);
-}
-
-// step p of L^-1 (Li's off-diagonal tiles start at zero): block (x, y) is
-// tile (p+1+y, x), x <= p; it adds -L_ip Li_pj and, on row p + 1, finishes
-// the tile with the diagonal inverse
-__global__ void __launch_bounds__(kCThreads) k_trtri_step(int n, int p, const double *A,
-                                                          double *Li, const int *status) {
-  __shared__ double L1[kCT][kCT + 1], M[kCT][kCT + 1];
-  if (chol_failed(status)) return;
-  const int i = p + 1 + blockIdx.y, j = blockIdx.x;
-  const int t = threadIdx.x, r = t / kCT, c = t % kCT;
-  L1[r][c] = tile_get(A, n, i, p, r, c, false);
-  M[r][c] = tile_get(Li, n, p, j, r, c, false);
-  __syncthreads();
-  double s = tile_get(Li, n, i, j, r, c, false);
-  for (int q = 0; q < kCT; ++q) s = fma(-L1[r][q], M[q][c], s);
-  if (i != p + 1) {
-    tile_put(Li, n, i, j, r, c, s);
+  if (b < T - k) {  // L_ik = A_ik L_kk^-T, i = k + b
+    const int i = k + b;
+    D[r][c] = tile_get(A, n, i, k, r, c, false);  // D is free after the factor
+    __syncthreads();
+    double s = 0.0;
+    for (int q = 0; q <= c; ++q) s = fma(D[r][q], X[c][q], s);
+    tile_put(A, n, i, k, r, c, s);
     return;
   }
+  const int j = b - (T - k);  // Li_kj = L_kk^-1 S_kj
+  D[r][c] = tile_get(Li, n, k, j, r, c, false);
   __syncthreads();
-  M[r][c] = s;
-  L1[r][c] = tile_get(Li, n, i, i, r, c, false);
-  __syncthreads();
-  double v = 0.0;
-  for (int q = 0; q <= r; ++q) v = fma(L1[r][q], M[q][c], v);
-  tile_put(Li, n, i, j, r, c, v);
+  double s = 0.0;
+  for (int q = 0; q <= r; ++q) s = fma(X[r][q], D[q][c], s);
+  tile_put(Li, n, k, j, r, c, s);
+}
+
+// trailing update after tile column k: block (x, y) is tile column x of tile
+// row i = k+1+y: A_ix -= L_ik L_xk^T for k < x <= i (blocks with x > i
+// return), S_ix -= L_ik Li_kx for x <= k
+__global__ void __launch_bounds__(kCThreads) k_chol_trail(int n, int k, double *A, double *Li,
+                                                          const int *status) {
+  __shared__ double Lr[kCT][kCT + 1], M[kCT][kCT + 1];
+  if (chol_failed(status)) return;
+  const int i = k + 1 + blockIdx.y, x = blockIdx.x;
+  if (x > i) return;
+  const int t = threadIdx.x, r = t / kCT, c = t % kCT;
+  Lr[r][c] = tile_get(A, n, i, k, r, c, false);
+  if (x > k) {
+    M[r][c] = tile_get(A, n, x, k, r, c, false);
+    __syncthreads();
+    double a = tile_get(A, n, i, x, r, c, false);
+    for (int q = 0; q < kCT; ++q) a = fma(-Lr[r][q], M[c][q], a);
+    tile_put(A, n, i, x, r, c, a);
+  } else {
+    M[r][c] = tile_get(Li, n, k, x, r, c, false);
+    __syncthreads();
+    double a = tile_get(Li, n, i, x, r, c, false);
+    for (int q = 0; q < kCT; ++q) a = fma(-Lr[r][q], M[q][c], a);
+    tile_put(Li, n, i, x, r, c, a);
+  }
 }
 
 // A^-1 = L^-T L^-1: block (x, y) is tile (y, x)
@@ -596,18 +635,13 @@ mgpbd_status coarsest_factor(Handle *h) {
   MG_CUDA(cudaMemsetAsync(h->cstat, 0, sizeof(int), h->stream));  // MGPBD_OK
   const int T = (n + kCT - 1) / kCT;
   for (int k = 0; k < T; ++k) {
-    k_chol_panel<<<T - k, kCThreads, 0, h->stream>>>(n, k, h->cdense, Li, h->cstat);
+    k_chol_panel<<<T, kCThreads, 0, h->stream>>>(n, T, k, h->cdense, Li, h->cstat);
     MG_LAUNCH("k_chol_panel");
     if (k + 1 < T) {
-      k_chol_trail<<<dim3(T - k - 1, T - k - 1), kCThreads, 0, h->stream>>>(n, k, h->cdense,
-                                                                            h->cstat);
+      k_chol_trail<<<dim3(T, T - k - 1), kCThreads, 0, h->stream>>>(n, k, h->cdense, Li,
+                                                                    h->cstat);
       MG_LAUNCH("k_chol_trail");
     }
-  }
-  for (int p = 0; p + 1 < T; ++p) {
-    k_trtri_step<<<dim3(p + 1, T - 1 - p), kCThreads, 0, h->stream>>>(n, p, h->cdense, Li,
-                                                                      h->cstat);
-    MG_LAUNCH("k_trtri_step");
   }
   k_inv_gram<<<dim3(T, T), kCThreads, 0, h->stream>>>(n, T, Li, h->cinv, h->cstat);
   MG_LAUNCH("k_inv_gram");
@@ -677,6 +711,520 @@ const double *Ps<double>(const Level &L) { return L.P; }
 template <>
 const float *Ps<float>(const Level &L) { return L.P32; }
 
+
+// ---------------------------------------------------------------------------
+// the V-cycle below level 0 in one cooperative launch
+// ---------------------------------------------------------------------------
+// Levels 1 .. coarsest of a V-cycle (weighted Jacobi, one column of P per
+// aggregate) are small: as separate launches each step costs a launch's
+// latency, not its bytes.  Here every block of one cooperative launch (all
+// resident at once) runs the same steps over the same row bodies as the
+// separate launches -- pre-sweeps, residual, restriction on the way down, the
+// coarsest solve, prolongation and post-sweeps on the way up -- with a grid
+// barrier between dependent steps.  No step reduces across rows, so the
+// results are the same bits as the separate launches'.
+// Grid-wide barrier of a cooperative launch.  Thread 0 of each block arrives
+// on bar[0]; the last arrival resets it and advances the generation bar[1];
+// the others poll the generation at most `limit` times.  False in every
+// thread of a block whose wait ran out (the solve then fails with
+// MGPBD_E_DEVICE_TIMEOUT; every other block gives up at its next barrier).
+__device__ bool grid_barrier(unsigned int *bar, long long limit) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int *vgen = bar + 1;
+    const unsigned int gen = *vgen;
+    __threadfence();
+    ok = 1;
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long polls = 0;
+      while (*vgen == gen) {
+        if (polls++ >= limit) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_coarse_tail(TailDesc<T> d, unsigned int *bar,
+                                                      long long limit, PcgScalars *sc) {
+  if (is_done(sc)) return;  // the scalars do not change during this kernel
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  auto sync = [&]() -> bool {
+    if (grid_barrier(bar, limit)) return true;
+    if (threadIdx.x == 0) {
+      sc->status = MGPBD_E_DEVICE_TIMEOUT;
+      __threadfence();
+      sc->done = 1;
+    }
+    return false;
+  };
+  T *cur[kMaxLevels];  // the buffer holding each level's iterate
+  for (int l = d.first; l < d.coarsest; ++l) {
+    const TailLevel<T> &L = d.lev[l];
+    T *x = L.x, *x2 = L.x2;  // x holds the first sweep from zero
+    for (int s = 1; s < d.sweeps; ++s) {
+      DISPATCH_G(L.G, (jacobi_rows<GG, T>(w0, nw, L.n, L.ptr, L.col, L.val, L.dinv, L.omega,
+                                          L.b, x, x2)));
+      if (!sync()) return;
+      T *t = x;
+      x = x2;
+      x2 = t;
+    }
+    DISPATCH_G(L.G, (resid_rows<GG, T>(w0, nw, L.n, L.ptr, L.col, L.val, L.b, x, L.r)));
+    if (!sync()) return;
+    const TailLevel<T> &Lc = d.lev[l + 1];
+    const bool c_jac = l + 1 < d.coarsest;  // the coarse level's first sweep rides along
+    restrict_aggs<T>(w0, nw, L.n_agg, 1, L.mptr, L.mrow, L.P, L.r, Lc.b,
+                     c_jac ? Lc.dinv : nullptr, Lc.omega, c_jac ? Lc.x : nullptr);
+    if (!sync()) return;
+    cur[l] = x;
+  }
+  const TailLevel<T> &C = d.lev[d.coarsest];
+  coarse_rows<T>(w0, nw, C.n, d.cinv, C.b, C.x);
+  const T *xc = C.x;
+  for (int l = d.coarsest - 1; l >= d.first; --l) {
+    if (!sync()) return;
+    const TailLevel<T> &L = d.lev[l];
+    T *x = cur[l], *x2 = x == L.x ? L.x2 : L.x;
+    prolong_rows<T>(blockIdx.x, gridDim.x, L.n, L.agg, L.P, xc, x);
+    for (int s = 0; s < d.sweeps; ++s) {
+      if (!sync()) return;
+      DISPATCH_G(L.G, (jacobi_rows<GG, T>(w0, nw, L.n, L.ptr, L.col, L.val, L.dinv, L.omega,
+                                          L.b, x, x2)));
+      T *t = x;
+      x = x2;
+      x2 = t;
+    }
+    xc = x;
+  }
+}
+
+// the tail applies from level `first` down: Jacobi smoothing, one column of
+// P per aggregate, and at least one level above the coarsest
+static bool tail_applies(const Handle *h, int first) {
+  return h->tail && h->p.smoother == MGPBD_SMOOTH_JACOBI && h->p.nk_vectors == 1 &&
+         h->p.smooth_sweeps >= 1 && first >= 1 && first < h->L - 1;
+}
+
+// level `first`'s result lies in x after an even number of buffer swaps (2
+// sweeps - 1 of them), else in x2
+template <class T>
+static T *tail_result(Handle *h, int first) {
+  Level &L = h->lev[first];
+  return (T *)((2 * h->p.smooth_sweeps - 1) % 2 == 0 ? L.x : L.x2);
+}
+
+template <class T>
+static mgpbd_status launch_tail(Handle *h, int first) {
+  TailDesc<T> d;
+  memset(&d, 0, sizeof(d));
+  d.first = first;
+  d.coarsest = h->L - 1;
+  d.sweeps = h->p.smooth_sweeps;
+  d.cinv = h->cinv;
+  for (int l = first; l <= d.coarsest; ++l) {
+    const Level &L = h->lev[l];
+    TailLevel<T> &t = d.lev[l];
+    t.n = L.n;
+    t.G = group_for(h, L, sizeof(T) == 8);
+    t.n_agg = L.n_agg;
+    t.omega = (T)L.omega;
+    t.ptr = L.ptr;
+    t.col = L.col;
+    t.val = vals<T>(L);
+    t.dinv = dinvs<T>(L);
+    t.x = (T *)L.x;
+    t.x2 = (T *)L.x2;
+    t.b = (T *)L.b;
+    t.r = (T *)L.r;
+    t.agg = L.agg;
+    t.P = Ps<T>(L);
+    t.mptr = L.mptr;
+    t.mrow = L.mrow;
+  }
+  // at most two blocks per SM: every barrier waits for each block
+  const int blocks = std::min(wave_blocks((const void *)k_coarse_tail<T>, 256), 2 * num_sms());
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(256);
+  cfg.stream = h->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  MG_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_tail<T>, d, h->gbar, h->wait_limit, h->sc));
+  MG_LAUNCH("k_coarse_tail");
+  return MGPBD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched PCG of a cohort: every step one launch for every member
+// ---------------------------------------------------------------------------
+#define COHORT_BLOCK(step)                                                        \
+  const int *bs_ = bstart + (step) * (K + 1);                                     \
+  const int k_ = cohort_member(bs_, K, blockIdx.x);                               \
+  const CohortMember &M = mem[k_];                                                \
+  const int vb = blockIdx.x - bs_[k_], vn = bs_[k_ + 1] - bs_[k_]
+
+__global__ void kb_xr(const CohortMember *mem, const int *bstart, int K) {
+  COHORT_BLOCK(CS_XR);
+  if (is_done(M.sc)) return;
+  xr_update_body<float>(vb, vn, M.m, M.x, M.r, M.p, M.q, M.c_rr, M.b0, M.dinv0, M.om0, M.x0);
+}
+
+__global__ void kb_restrict0(const CohortMember *mem, const int *bstart, int K) {
+  COHORT_BLOCK(CS_RESTRICT);
+  if (is_done(M.sc)) return;
+  const TailLevel<float> &L1 = M.tail.lev[1];
+  const bool c_jac = M.tail.coarsest > 1;  // level 1 smooths: its first sweep rides along
+  restrict_aggs<float>(VG_WARPS(vb, vn), M.n_agg0, 1, M.mptr0, M.mrow0, M.P0, M.r0, L1.b,
+                       c_jac ? L1.dinv : nullptr, L1.omega, c_jac ? L1.x : nullptr);
+}
+
+__global__ void kb_prolong0(const CohortMember *mem, const int *bstart, int K) {
+  COHORT_BLOCK(CS_PROLONG);
+  if (is_done(M.sc)) return;
+  prolong_rows<float>(vb, vn, M.m, M.agg0, M.P0, M.xc1, M.x20);
+}
+
+__global__ void kb_pupdate(const CohortMember *mem, const int *bstart, int K) {
+  COHORT_BLOCK(CS_PUPD);
+  if (is_done(M.sc)) return;
+  p_update_body(vb, vn, M.m, M.p, M.z, M.sc);
+}
+
+// The V-cycle below level 0 of every member in one cooperative launch, depth
+// by depth: at depth d the members whose coarsest level is deeper pre-smooth,
+// take the residual and restrict; a member whose coarsest level is d solves
+// it there; on the way back up each member prolongs and post-smooths its
+// levels.  A member's own steps run in its standalone order over the same row
+// bodies, so its results are its standalone bits.
+__global__ void __launch_bounds__(256) kb_tail(const CohortMember *mem, int K, int maxc,
+                                                unsigned int *bar, long long limit) {
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long act = 0;  // members still iterating (the same in every block)
+  for (int k = 0; k < K; ++k)
+    if (!is_done(mem[k].sc)) act |= 1ull << k;
+  if (!act) return;
+  auto sync = [&]() -> bool {
+    if (grid_barrier(bar, limit)) return true;
+    if (threadIdx.x == 0)
+      for (int k = 0; k < K; ++k)
+        if (act >> k & 1) {
+          mem[k].sc->status = MGPBD_E_DEVICE_TIMEOUT;
+          __threadfence();
+          mem[k].sc->done = 1;
+        }
+    return false;
+  };
+  auto jacobi = [&](const TailLevel<float> &L, const float *x, float *xn) {
+    DISPATCH_G(L.G, (jacobi_rows<GG, float>(w0, nw, L.n, L.ptr, L.col, L.val, L.dinv, L.omega,
+                                            L.b, x, xn)));
+  };
+  for (int d = 1; d <= maxc; ++d) {
+    for (int s = 1; s < 2; ++s) {  // pre-sweeps after the first (two sweeps per side)
+      for (int k = 0; k < K; ++k) {
+        const TailDesc<float> &T = mem[k].tail;
+        if ((act >> k & 1) && d < T.coarsest) jacobi(T.lev[d], T.lev[d].x, T.lev[d].x2);
+      }
+      if (!sync()) return;
+    }
+    for (int k = 0; k < K; ++k) {
+      const TailDesc<float> &T = mem[k].tail;
+      if (!(act >> k & 1)) continue;
+      const TailLevel<float> &L = T.lev[d];
+      if (d < T.coarsest) {
+        DISPATCH_G(L.G, (resid_rows<GG, float>(w0, nw, L.n, L.ptr, L.col, L.val, L.b, L.x2,
+                                                L.r)));
+      } else if (d == T.coarsest) {
+        coarse_rows<float>(w0, nw, L.n, T.cinv, L.b, L.x);
+      }
+    }
+    if (!sync()) return;
+    if (d == maxc) break;
+    for (int k = 0; k < K; ++k) {
+      const TailDesc<float> &T = mem[k].tail;
+      if (!(act >> k & 1) || d >= T.coarsest) continue;
+      const TailLevel<float> &L = T.lev[d], &Lc = T.lev[d + 1];
+      const bool c_jac = d + 1 < T.coarsest;
+      restrict_aggs<float>(w0, nw, L.n_agg, 1, L.mptr, L.mrow, L.P, L.r, Lc.b,
+                           c_jac ? Lc.dinv : nullptr, Lc.omega, c_jac ? Lc.x : nullptr);
+    }
+    if (!sync()) return;
+  }
+  for (int d = maxc - 1; d >= 1; --d) {
+    for (int k = 0; k < K; ++k) {
+      const TailDesc<float> &T = mem[k].tail;
+      if (!(act >> k & 1) || d >= T.coarsest) continue;
+      const TailLevel<float> &L = T.lev[d], &Lc = T.lev[d + 1];
+      const float *xc = d + 1 == T.coarsest ? Lc.x : Lc.x2;  // the coarser level's result
+      prolong_rows<float>(blockIdx.x, gridDim.x, L.n, L.agg, L.P, xc, L.x2);
+    }
+    if (!sync()) return;
+    for (int s = 0; s < 2; ++s) {
+      for (int k = 0; k < K; ++k) {
+        const TailDesc<float> &T = mem[k].tail;
+        if ((act >> k & 1) && d < T.coarsest)
+          jacobi(T.lev[d], s == 0 ? T.lev[d].x2 : T.lev[d].x, s == 0 ? T.lev[d].x : T.lev[d].x2);
+      }
+      if ((d > 1 || s == 0) && !sync()) return;
+    }
+  }
+}
+
+__global__ void kb_gather(const CohortMember *mem, int K, PcgScalars *out) {
+  for (int k = threadIdx.x; k < K; k += blockDim.x) out[k] = *mem[k].sc;
+}
+
+// ---- host side -------------------------------------------------------------
+bool cohort_eligible(const Handle *h) {
+  const mgpbd_params &p = h->p;
+  return p.precision == MGPBD_MIXED && p.level0_op == 1 && p.smoother == MGPBD_SMOOTH_JACOBI &&
+         p.smooth_sweeps == 2 && p.nk_vectors == 1 && p.linear_solver == 0 && h->have_setup &&
+         h->L >= 2 && h->m > 0;
+}
+
+Cohort::~Cohort() {
+  if (graph) cudaGraphExecDestroy(graph);
+  if (d_mem) cudaFree(d_mem);
+  if (d_bstart) cudaFree(d_bstart);
+  if (d_sc) cudaFree(d_sc);
+  if (bar) cudaFree(bar);
+  if (h_sc) cudaFreeHost(h_sc);
+}
+
+// Member records and block tables for the handles in c->hs (all eligible,
+// all on c->stream).  Rebuilt when a member joins or leaves or its device
+// arrays change (a new setup).
+mgpbd_status cohort_build(Cohort *c) {
+  const int K = (int)c->hs.size();
+  if (K > kCohortMax) {
+    set_error("cohort: more than 64 instances");
+    return MGPBD_E_INVALID;
+  }
+  if (K > c->cap) {
+    if (c->d_mem) cudaFree(c->d_mem);
+    if (c->d_bstart) cudaFree(c->d_bstart);
+    if (c->d_sc) cudaFree(c->d_sc);
+    if (c->h_sc) cudaFreeHost(c->h_sc);
+    c->d_mem = nullptr;
+    c->d_bstart = nullptr;
+    c->d_sc = nullptr;
+    c->h_sc = nullptr;
+    c->cap = 0;
+    MG_CUDA(cudaMalloc(&c->d_mem, sizeof(CohortMember) * kCohortMax));
+    MG_CUDA(cudaMalloc(&c->d_bstart, sizeof(int) * CS_STEPS * (kCohortMax + 1)));
+    MG_CUDA(cudaMalloc(&c->d_sc, sizeof(PcgScalars) * kCohortMax));
+    MG_CUDA(cudaMallocHost(&c->h_sc, sizeof(PcgScalars) * kCohortMax));
+    c->cap = kCohortMax;
+  }
+  if (!c->bar) {
+    MG_CUDA(cudaMalloc(&c->bar, 16 * sizeof(unsigned int)));
+    MG_CUDA(cudaMemsetAsync(c->bar, 0, 16 * sizeof(unsigned int), c->stream));
+  }
+  std::vector<CohortMember> mem((size_t)K);
+  std::vector<int> bstart((size_t)CS_STEPS * (K + 1), 0);
+  c->maxc = 1;
+  c->gens.assign(K, 0);
+  for (int k = 0; k < K; ++k) {
+    Handle *h = c->hs[k];
+    CohortMember &M = mem[k];
+    memset(&M, 0, sizeof(M));
+    const Level &L0 = h->lev[0];
+    M.m = h->m;
+    M.N = h->N;
+    M.E = h->E;
+    M.gv64 = h->force_vert64 ? h->force_vert64 : h->mf_g64;
+    M.gv32 = h->force_vert32 ? h->force_vert32 : h->mf_g32;
+    M.edge = h->edge;
+    M.tet = h->tet;
+    M.vorder = h->vorder;
+    M.vptr = h->vptr;
+    M.vrow = h->vrow;
+    M.ginc64 = h->ginc64;
+    M.w = h->w;
+    M.gd = h->gd;
+    M.gt = h->gt;
+    M.at = h->alpha_t;
+    M.ginc4 = h->ginc4;
+    M.w32 = h->w32;
+    M.gd32 = h->gd32;
+    M.gt32 = h->gt32;
+    M.at32 = h->at32;
+    M.u64 = h->u64;
+    M.u32 = h->u32;
+    M.x = h->dl;
+    M.r = h->pr;
+    M.z = h->pz;
+    M.p = h->pp;
+    M.q = h->pq;
+    M.sc = h->sc;
+    M.c_pq = make_ctx(h, DOT_PQ);
+    M.c_rr = make_ctx(h, DOT_RR);
+    M.c_rz = make_ctx(h, DOT_RZ);
+    M.b0 = (float *)L0.b;
+    M.x0 = (float *)L0.x;
+    M.x20 = (float *)L0.x2;
+    M.r0 = (float *)L0.r;
+    M.dinv0 = L0.dinv32;
+    M.om0 = (float)L0.omega;
+    M.n_agg0 = L0.n_agg;
+    M.mptr0 = L0.mptr;
+    M.mrow0 = L0.mrow;
+    M.P0 = L0.P32;
+    M.agg0 = L0.agg;
+    TailDesc<float> &T = M.tail;
+    T.first = 1;
+    T.coarsest = h->L - 1;
+    T.sweeps = h->p.smooth_sweeps;
+    T.cinv = h->cinv;
+    for (int l = 1; l <= T.coarsest; ++l) {
+      const Level &L = h->lev[l];
+      TailLevel<float> &t = T.lev[l];
+      t.n = L.n;
+      t.G = group_for(h, L, false);
+      t.n_agg = L.n_agg;
+      t.omega = (float)L.omega;
+      t.ptr = L.ptr;
+      t.col = L.col;
+      t.val = L.val32;
+      t.dinv = L.dinv32;
+      t.x = (float *)L.x;
+      t.x2 = (float *)L.x2;
+      t.b = (float *)L.b;
+      t.r = (float *)L.r;
+      t.agg = L.agg;
+      t.P = L.P32;
+      t.mptr = L.mptr;
+      t.mrow = L.mrow;
+    }
+    M.xc1 = T.coarsest > 1 ? T.lev[1].x2 : T.lev[1].x;
+    c->maxc = std::max(c->maxc, T.coarsest);
+    mf_cohort_grids(h, M.grid);
+    const int m = h->m;
+    M.grid[CS_XR] = std::min(dot_grid(m), wave_blocks((const void *)k_xr_update<float>, kDotThreads));
+    M.grid[CS_RESTRICT] = blocks_for((int64_t)L0.n_agg * 32, 256);
+    M.grid[CS_PROLONG] = blocks_for((m + kProlongRows - 1) / kProlongRows, 256);
+    M.grid[CS_PUPD] = blocks_for(std::max(1, (m / 2 + 1) / 2), 256);
+    for (int s = 0; s < CS_STEPS; ++s)
+      bstart[(size_t)s * (K + 1) + k + 1] = bstart[(size_t)s * (K + 1) + k] + M.grid[s];
+    c->gens[k] = h->gen;
+  }
+  for (int s = 0; s < CS_STEPS; ++s) c->blocks[s] = bstart[(size_t)s * (K + 1) + K];
+  MG_CUDA(cudaMemcpyAsync(c->d_mem, mem.data(), sizeof(CohortMember) * K, cudaMemcpyHostToDevice,
+                          c->stream));
+  MG_CUDA(cudaMemcpyAsync(c->d_bstart, bstart.data(), sizeof(int) * bstart.size(),
+                          cudaMemcpyHostToDevice, c->stream));
+  MG_CUDA(cudaStreamSynchronize(c->stream));
+  c->K = K;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return MGPBD_OK;
+}
+
+// true when a member's device arrays changed since the build
+bool cohort_stale(const Cohort *c) {
+  if ((int)c->hs.size() != c->K) return true;
+  for (int k = 0; k < c->K; ++k)
+    if (c->gens[k] != c->hs[k]->gen) return true;
+  return false;
+}
+
+// one batched PCG iteration (the launch sequence of pcg_iteration for the
+// configuration every member has)
+static mgpbd_status cohort_iteration(Cohort *c) {
+  const int K = c->K;
+  cudaStream_t st = c->stream;
+  MG_TRY(mf_cohort_step(CS_VERT64, 0, c->d_mem, c->d_bstart, K, c->blocks[CS_VERT64], st));
+  MG_TRY(mf_cohort_step(CS_ROW_PQ, 0, c->d_mem, c->d_bstart, K, c->blocks[CS_ROW_PQ], st));
+  kb_xr<<<c->blocks[CS_XR], kDotThreads, 0, st>>>(c->d_mem, c->d_bstart, K);
+  MG_LAUNCH("kb_xr");
+  MG_TRY(mf_cohort_step(CS_VERT32, 0, c->d_mem, c->d_bstart, K, c->blocks[CS_VERT32], st));
+  MG_TRY(mf_cohort_step(CS_ROW, 0, c->d_mem, c->d_bstart, K, c->blocks[CS_ROW], st));
+  MG_TRY(mf_cohort_step(CS_VERT32, 1, c->d_mem, c->d_bstart, K, c->blocks[CS_VERT32], st));
+  MG_TRY(mf_cohort_step(CS_ROW, 1, c->d_mem, c->d_bstart, K, c->blocks[CS_ROW], st));
+  kb_restrict0<<<c->blocks[CS_RESTRICT], 256, 0, st>>>(c->d_mem, c->d_bstart, K);
+  MG_LAUNCH("kb_restrict0");
+  {
+    const int blocks = std::min(wave_blocks((const void *)kb_tail, 256), 2 * num_sms());
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    MG_CUDA(cudaLaunchKernelEx(&cfg, kb_tail, (const CohortMember *)c->d_mem, K, c->maxc, c->bar,
+                               c->wait_limit));
+    MG_LAUNCH("kb_tail");
+  }
+  kb_prolong0<<<c->blocks[CS_PROLONG], 256, 0, st>>>(c->d_mem, c->d_bstart, K);
+  MG_LAUNCH("kb_prolong0");
+  MG_TRY(mf_cohort_step(CS_VERT32, 1, c->d_mem, c->d_bstart, K, c->blocks[CS_VERT32], st));
+  MG_TRY(mf_cohort_step(CS_ROW, 2, c->d_mem, c->d_bstart, K, c->blocks[CS_ROW], st));
+  MG_TRY(mf_cohort_step(CS_VERT32, 0, c->d_mem, c->d_bstart, K, c->blocks[CS_VERT32], st));
+  MG_TRY(mf_cohort_step(CS_ROW_FINAL, 0, c->d_mem, c->d_bstart, K, c->blocks[CS_ROW_FINAL], st));
+  kb_pupdate<<<c->blocks[CS_PUPD], 256, 0, st>>>(c->d_mem, c->d_bstart, K);
+  MG_LAUNCH("kb_pupdate");
+  return MGPBD_OK;
+}
+
+// `iters` batched PCG iterations of every member (captured into a CUDA graph
+// once per build and replayed), then every member's scalars into c->h_sc
+// (synchronises)
+mgpbd_status cohort_chunk(Cohort *c, int iters) {
+  if (c->K == 0) return MGPBD_OK;
+  if (!c->graph || c->graph_iters != iters) {
+    if (c->graph) {
+      cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+    }
+    cudaGraph_t gr = nullptr;
+    unsigned long long n0 = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+    MG_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    mgpbd_status cs = MGPBD_OK;
+    for (int k = 0; k < iters && cs >= 0; ++k) cs = cohort_iteration(c);
+    cudaError_t ce = cudaStreamEndCapture(c->stream, &gr);
+    c->graph_kernels = __atomic_load_n(&g_launches, __ATOMIC_RELAXED) - n0;
+    __atomic_fetch_sub(&g_launches, c->graph_kernels, __ATOMIC_RELAXED);
+    if (cs < 0) {
+      if (gr) cudaGraphDestroy(gr);
+      return cs;
+    }
+    MG_CUDA(ce);
+    ce = cudaGraphInstantiate(&c->graph, gr, 0);
+    cudaGraphDestroy(gr);
+    MG_CUDA(ce);
+    c->graph_iters = iters;
+  }
+  MG_CUDA(cudaGraphLaunch(c->graph, c->stream));
+  __atomic_fetch_add(&g_launches, c->graph_kernels, __ATOMIC_RELAXED);
+  kb_gather<<<1, 64, 0, c->stream>>>(c->d_mem, c->K, c->d_sc);
+  MG_LAUNCH("kb_gather");
+  MG_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(PcgScalars) * c->K, cudaMemcpyDeviceToHost,
+                          c->stream));
+  MG_CUDA(cudaStreamSynchronize(c->stream));
+  return MGPBD_OK;
+}
 
 // V-cycle on level l in precision T: L.b -> L.x (zero start).  On level 0 of
 // a top V-cycle, `x0_ready` says the first Jacobi sweep is already in L.x,
@@ -784,10 +1332,16 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in, bool x0_ready 
       L.n_agg, nk, L.mptr, L.mrow, Ps<T>(L), r, (T *)Lc.b, sc, c_jac ? dinvs<T>(Lc) : nullptr,
       (T)Lc.omega, c_jac ? (T *)Lc.x : nullptr);
   MG_LAUNCH("k_restrict");
-  MG_TRY(vcycle_level<T>(h, l + 1, (const T *)Lc.b, c_jac));
+  const T *xc = (const T *)Lc.x;  // where the coarser level leaves its result
+  if (tail_applies(h, l + 1)) {
+    MG_TRY(launch_tail<T>(h, l + 1));
+    xc = tail_result<T>(h, l + 1);
+  } else {
+    MG_TRY(vcycle_level<T>(h, l + 1, (const T *)Lc.b, c_jac));
+  }
   if (nk == 1)
     k_prolong<T><<<blocks_for((n + kProlongRows - 1) / kProlongRows, 256), 256, 0, h->stream>>>(
-        n, L.agg, Ps<T>(L), (const T *)Lc.x, x, sc);
+        n, L.agg, Ps<T>(L), xc, x, sc);
   else
     k_prolong_k<T><<<blocks_for(n, 256), 256, 0, h->stream>>>(n, nk, L.agg, Ps<T>(L),
                                                               (const T *)Lc.x, x, sc);
@@ -878,7 +1432,7 @@ static mgpbd_status vcycle_top(Handle *h, const double *r, double *z, bool prepa
 }
 
 mgpbd_status vcycle_apply(Handle *h, const double *d_r, double *d_z) {
-  k_pcg_init<<<1, 1, 0, h->stream>>>(h->sc);
+  k_pcg_init<<<1, 1, 0, h->stream>>>(h->sc, h->gbar);
   MG_LAUNCH("k_pcg_init");
   return vcycle_top(h, d_r, d_z, false, -1);
 }
@@ -929,21 +1483,28 @@ static mgpbd_status pcg_iteration(Handle *h, double *x) {
   return MGPBD_OK;
 }
 
-mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *info) {
+// start of MGPCG: x = 0, r = b, |b|^2, z = V(r), r.z, p = z
+mgpbd_status pcg_begin(Handle *h, const double *b, double *x) {
   const int m = h->m;
-  memset(info, 0, sizeof(*info));
-  if (m == 0) return MGPBD_OK;
   MG_CUDA(cudaEventRecord(h->ev0, h->stream));
   double *r = h->pr, *z = h->pz, *p = h->pp;
   h->pcg_k = -1;
   h->pev_used = 0;
-  k_pcg_init<<<1, 1, 0, h->stream>>>(h->sc);
+  k_pcg_init<<<1, 1, 0, h->stream>>>(h->sc, h->gbar);
   MG_LAUNCH("k_pcg_init");
   MG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * m, h->stream));
   MG_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->stream));
   MG_TRY(launch_dot(h, b, b, m, DOT_BNORM, 0));
   MG_TRY(vcycle_top(h, r, z, false, DOT_RZ0));
   MG_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->stream));
+  return MGPBD_OK;
+}
+
+mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *info) {
+  const int m = h->m;
+  memset(info, 0, sizeof(*info));
+  if (m == 0) return MGPBD_OK;
+  MG_TRY(pcg_begin(h, b, x));
   const int chunk = 8;
   int launched = 0;
   // Chunks of PCG iterations replay a captured CUDA graph (one launch instead
@@ -1008,7 +1569,14 @@ mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *
     if (replay && h->graph_prof) MG_TRY(prof_harvest_graph(h, launched - c));
     if (h->sc_host->done) break;
   }
-  // true residual in FP64
+  return pcg_finish(h, b, x, info);
+}
+
+// end of MGPCG: the FP64 true residual |b - A x|, the scalars, the solve's
+// time and status (synchronises)
+mgpbd_status pcg_finish(Handle *h, const double *b, double *x, mgpbd_solve_info *info) {
+  const int m = h->m;
+  memset(info, 0, sizeof(*info));
   k_true_resid<<<std::min(row_blocks(m, 4), wave_blocks((const void *)k_true_resid, 256)), 256, 0,
                  h->stream>>>(
       m, h->lev[0].ptr, h->lev[0].col, h->lev[0].val, x, b, make_ctx(h, DOT_TR));
@@ -1031,6 +1599,8 @@ mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *
   if (bn == 0.0) info->status = MGPBD_OK;
   h->last_pcg_iters = s.iters;
   if (info->status == MGPBD_E_BREAKDOWN) set_error("PCG breakdown (p.Ap <= 0, r.z <= 0 or NaN)");
+  if (info->status == MGPBD_E_DEVICE_TIMEOUT)
+    set_error("a grid barrier of the coarse V-cycle kernel waited longer than its limit");
   return info->status;
 }
 

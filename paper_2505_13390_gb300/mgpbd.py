@@ -72,7 +72,7 @@ class LevelInfo(C.Structure):
 
 
 class BatchConfig(C.Structure):
-    _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int)]
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int), ("cohort", C.c_int)]
 
 
 class StepRequest(C.Structure):
@@ -112,6 +112,8 @@ SIGNATURES = {
     "mgpbd_sizes": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i64)]),
     "mgpbd_level_info_get": (_i, [_vp, _i, C.POINTER(LevelInfo)]),
     "mgpbd_set_lanes": (_i, [_vp, _i, _i, _i, _i]),
+    "mgpbd_set_coarse_tail": (_i, [_vp, _i]),
+    "mgpbd_set_wait_limit": (_i, [_vp, C.c_longlong]),
     "mgpbd_get_lanes": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i),
                              C.POINTER(_i)]),
     "mgpbd_get_matrix": (_i, [_vp, _i, _vp, _vp, _vp, _i]),
@@ -359,6 +361,16 @@ class Solver:
         the matrix-free vertex pass; 0 = autotuned or rule) on every level."""
         _check(load().mgpbd_set_lanes(self.h, csr32, csr64, vert32, vert64), "set_lanes")
 
+    def set_coarse_tail(self, enable: bool):
+        """The V-cycle below level 0 as one cooperative kernel (default) or as
+        separate launches; the same bits either way."""
+        _check(load().mgpbd_set_coarse_tail(self.h, 1 if enable else 0), "set_coarse_tail")
+
+    def set_wait_limit(self, polls: int):
+        """Polls a block of the cooperative kernel waits at a grid barrier
+        before the solve fails with MGPBD_E_DEVICE_TIMEOUT."""
+        _check(load().mgpbd_set_wait_limit(self.h, int(polls)), "set_wait_limit")
+
     def lanes(self, level: int = 0) -> Dict:
         """The row-kernel shapes in effect on a level."""
         v = [C.c_int() for _ in range(4)]
@@ -451,8 +463,8 @@ class Solver:
 class Batch:
     """Continuous-batching service of many instances (mgpbd_batch_*)."""
 
-    def __init__(self, hbm_budget: int, max_active: int):
-        self.cfg = BatchConfig(int(hbm_budget), int(max_active))
+    def __init__(self, hbm_budget: int, max_active: int, cohort: bool = False):
+        self.cfg = BatchConfig(int(hbm_budget), int(max_active), 1 if cohort else 0)
         h = C.c_void_p()
         _check(load().mgpbd_batch_create(C.byref(self.cfg), C.byref(h)), "batch_create")
         self.h = h

@@ -187,3 +187,86 @@ def test_admit_rejects_unknown_instance_and_tick_polls():
     assert [r["id"] for r in res] == [t] and res[0]["status"] >= 0
     assert res[0]["arrival_s"] <= res[0]["start_s"] <= res[0]["finish_s"] <= b.counts()["clock"]
     b.close()
+
+
+def cohort_meshes():
+    """Instances of different hierarchy depths for the batched (cohort) form:
+    a 12x12 cloth (one level: solved alone by the stepping thread), a 20x20
+    cloth (two levels), a 16x16 cloth with coarse_max 20 (three levels), a
+    6x5x7 block with coarse_max 40 (three levels) and a 20x33x20 block (four
+    levels)."""
+    from paper_2505_13390_gb300.meshgen import workload
+    out = [(cloth(12, plane="xz", alpha=1e-6, pin="corners", seed=10), default_params()),
+           (cloth(20, plane="xz", alpha=1e-6, pin="corners", seed=11), default_params()),
+           (cloth(16, plane="xz", alpha=1e-6, pin="corners", noise=1e-3, seed=3),
+            default_params(coarse_max=20, max_levels=4)),
+           (hex_block(6, 5, 7, h=0.005, jitter=0.1, alpha=1e-10, pin="y0", seed=1),
+            default_params(omega_x=0.1, coarse_max=40)),
+           workload("block20x33x20")]
+    return out
+
+
+def serve_cohort(ms, max_active, requests, cohort):
+    from paper_2505_13390_gb300.mgpbd import Batch
+    b = Batch(64 << 30, max_active, cohort=cohort)
+    ids = [b.add(m, common(p, 1)) for m, p in ms]
+    st, res = b.run(requests)
+    states = [b.state(i) for i in ids]
+    b.close()
+    return st, res, states
+
+
+def test_cohort_mix_equals_alone_bitwise():
+    """The batched form: every running request's PCG iterations run as one
+    launch per step.  Each instance keeps its own grids and reduction order,
+    so its states and PCG iteration counts are bit for bit those of serving
+    one request at a time on its own stream, and of a plain solver."""
+    ms = cohort_meshes()
+    reqs = trace(len(ms), 2, 0.0)
+    st1, res1, alone = serve_cohort(ms, 1, reqs, False)
+    stc, resc, mixed = serve_cohort(ms, 8, reqs, True)
+    assert st1 >= 0 and stc >= 0
+    assert [r["pcg_iters"] for r in res1] == [r["pcg_iters"] for r in resc]
+    for (x1, v1), (xc, vc) in zip(alone, mixed):
+        assert np.array_equal(x1, xc) and np.array_equal(v1, vc)
+    from paper_2505_13390_gb300.mgpbd import Solver
+    m, p = ms[4]
+    g = Solver(m, common(p, 1), stream=torch.cuda.Stream())
+    for _ in range(2):
+        g.begin_frame()
+        for _ in range(4):
+            g.iterate()
+        g.end_frame()
+    assert g.levels == 4
+    x, v = g.get_state()
+    g.close()
+    assert np.array_equal(x, mixed[4][0]) and np.array_equal(v, mixed[4][1])
+
+
+def test_cohort_admit_while_running():
+    """Requests admitted while the cohort is stepping join it at the next
+    chunk; each result comes back once and every state equals the
+    one-at-a-time run."""
+    import time
+
+    from paper_2505_13390_gb300.mgpbd import Batch
+    ms = cohort_meshes()
+    ref = serve_cohort(ms, 1, [(0, 4, 3, 0.0)] + [(1 + k, k, 1, 0.0) for k in range(4)], False)
+    b = Batch(64 << 30, 8, cohort=True)
+    ids = [b.add(m, common(p, 1)) for m, p in ms]
+    first = b.admit(ids[4], 3)
+    t0 = time.perf_counter()
+    while b.counts()["running"] == 0 and time.perf_counter() - t0 < 10:
+        time.sleep(0.001)
+    tickets = [b.admit(ids[k], 1) for k in range(4)]
+    got = []
+    while len(got) < 5 and time.perf_counter() - t0 < 300:
+        got += b.tick(wait_s=0.5)
+    assert sorted(r["id"] for r in got) == sorted([first] + tickets)
+    assert all(r["status"] >= 0 for r in got)
+    by = {r["id"]: r for r in got}
+    assert any(by[t]["start_s"] < by[first]["finish_s"] for t in tickets)
+    states = [b.state(i) for i in ids]
+    b.close()
+    for (x1, v1), (x2, v2) in zip(ref[2], states):
+        assert np.array_equal(x1, x2) and np.array_equal(v1, v2)
