@@ -184,8 +184,8 @@ struct Handle {
   PcgScalars *sc = nullptr;
   PcgScalars *sc_host = nullptr;  // pinned mirror for polls
   // the V-cycle below level 0 as one cooperative kernel (solve.cu)
-  bool tail = true;                  // use it where it applies
-  unsigned int *gbar = nullptr;      // its grid barrier: arrivals, generation
+  bool tail = false;                 // use it where it applies (mgpbd_set_coarse_tail)
+  unsigned int *gbar = nullptr;      // its grid barrier word
   long long wait_limit = 1ll << 24;  // polls a block waits at the barrier
   double *partials = nullptr;     // dot-product block partials
   unsigned int *counter = nullptr;

@@ -181,7 +181,7 @@ __global__ void k_p_update(int64_t n, double *p, const double *z, const PcgScala
 }
 
 __global__ void k_pcg_init(PcgScalars *sc, unsigned int *bar) {
-  bar[0] = 0;  // no block waits at the coarse tail's barrier between solves
+  bar[0] = 0;  // the coarse tail's barrier word starts each solve at zero
   sc->done = 0;
   sc->iters = 0;
   sc->status = MGPBD_W_NOT_CONVERGED;
@@ -723,31 +723,26 @@ const float *Ps<float>(const Level &L) { return L.P32; }
 // coarsest solve, prolongation and post-sweeps on the way up -- with a grid
 // barrier between dependent steps.  No step reduces across rows, so the
 // results are the same bits as the separate launches'.
-// Grid-wide barrier of a cooperative launch.  Thread 0 of each block arrives
-// on bar[0]; the last arrival resets it and advances the generation bar[1];
-// the others poll the generation at most `limit` times.  False in every
-// thread of a block whose wait ran out (the solve then fails with
-// MGPBD_E_DEVICE_TIMEOUT; every other block gives up at its next barrier).
+// Grid-wide barrier of a cooperative launch, on one word: thread 0 of block
+// 0 adds 2^31 - (blocks - 1), every other block's adds 1, so the top bit of
+// the word flips exactly when the last block arrives; each block polls the
+// word until its top bit differs from the value it found, at most `limit`
+// polls.  False in every thread of a block whose wait ran out (the solve
+// then fails with MGPBD_E_DEVICE_TIMEOUT; every other block gives up at its
+// next barrier).  The word is reset to 0 between solves.
 __device__ bool grid_barrier(unsigned int *bar, long long limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int *vgen = bar + 1;
-    const unsigned int gen = *vgen;
+    const unsigned int add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
     __threadfence();
+    const unsigned int old = atomicAdd(bar, add);
     ok = 1;
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long polls = 0;
-      while (*vgen == gen) {
-        if (polls++ >= limit) {
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
+    long long polls = 0;
+    while (((*(volatile unsigned int *)bar ^ old) & 0x80000000u) == 0) {
+      if (polls++ >= limit) {
+        ok = 0;
+        break;
       }
     }
     __threadfence();

@@ -1,4 +1,5 @@
-"""The V-cycle below level 0 as one cooperative kernel (the coarse tail).
+"""The V-cycle below level 0 as one cooperative kernel (the coarse tail,
+mgpbd_set_coarse_tail; off by default).
 
 Its steps run the same row bodies as the separate launches, with a grid
 barrier between dependent steps, so a V-cycle, a whole PCG solve and whole
@@ -51,6 +52,7 @@ def test_tail_vcycle_is_bitwise_the_separate_launches(name, prec, op):
     mesh, g = make(name, precision=prec, level0_op=op)
     assert g.levels >= 3, "the tail needs a level between level 0 and the coarsest"
     r = torch.tensor(np.random.default_rng(3).standard_normal(mesh.n_rows), device="cuda")
+    g.set_coarse_tail(True)
     z1 = g.vcycle(r).cpu().numpy()
     g.set_coarse_tail(False)
     z0 = g.vcycle(r).cpu().numpy()
@@ -81,6 +83,7 @@ def test_tail_solve_and_iterations_bitwise(name, graphs):
 def test_tail_wait_limit_zero_times_out_and_recovers(graphs):
     from paper_2505_13390_gb300 import mgpbd
     mesh, g = make("block6", precision=1, level0_op=1, use_graphs=graphs, pcg_maxiter=5000)
+    g.set_coarse_tail(True)
     b = torch.tensor(g.constraints()[1], device="cuda")
     x_ref, info_ref = g.solve(b)
     g.set_wait_limit(0)
@@ -107,6 +110,7 @@ def test_tail_vcycle_against_the_oracle(name, prec):
     o.eval_assemble()
     o.prepare_solve()
     _, g = make(name, precision=prec, level0_op=prec)
+    g.set_coarse_tail(True)
     assert g.levels == o.levels >= 3
     r = np.random.default_rng(3).standard_normal(mesh.n_rows)
     zo = o.vcycle(r)
@@ -124,6 +128,7 @@ def test_tail_iterations_against_the_oracle(op):
     mesh, p = CASES["cloth16"]()
     p = dict(p, pcg_rtol=1e-10, pcg_maxiter=3000, level0_op=op)
     o, g = Oracle(mesh, p), Solver(mesh, p)
+    g.set_coarse_tail(True)
     o.begin_frame()
     g.begin_frame()
     scale = np.abs(mesh.rest_pos).max() + 1e-3
