@@ -381,6 +381,18 @@ mgpbd_status mgpbd_batch_tick(mgpbd_batch_t *b, double wait_s, mgpbd_step_result
  * tick, and the batch's clock now (seconds); any pointer may be NULL. */
 mgpbd_status mgpbd_batch_counts(mgpbd_batch_t *b, int *queued, int *running, int *unreported,
                                 double *clock);
+/* Text of the error of the most recently failed request of the batch ("" if
+ * none), valid until the calling thread's next call of this function.  The
+ * failure itself is the request's status. */
+const char *mgpbd_batch_error(mgpbd_batch_t *b);
+/* Cohort mode only (zeros otherwise): rounds of the stepping thread, batched
+ * PCG iterations launched (eight per round that has a solving instance), and
+ * the wall time in seconds spent in the batched chunks (launch, completion,
+ * scalar read-back) and in everything else of the rounds (the instances' own
+ * work between solves: frame steps, C and A, setup or re-form, coarsest
+ * factorisation, the start and end of each solve).  Any pointer may be NULL. */
+mgpbd_status mgpbd_batch_cohort_stats(mgpbd_batch_t *b, int64_t *rounds, int64_t *batched_iters,
+                                      double *chunk_s, double *other_s);
 /* Replays a list of timed requests through the request loop: admits each
  * when its arrival time (seconds after the call) has passed and returns
  * when all have finished, res[i] holding request i's result (its caller id,

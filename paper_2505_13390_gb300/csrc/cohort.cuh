@@ -5,9 +5,9 @@
 // update, the level-0 sweeps and residual, restriction, the V-cycle below
 // level 0, prolongation, the final sweep and the p update) runs as ONE launch
 // for every instance of the cohort.  Each instance keeps the grid its own
-// launch would have: a block finds its instance in a prefix table of block
-// counts and runs the standalone kernel's body with its index among that
-// instance's blocks.  Every reduction is therefore partitioned, and every sum
+// launch would have: a block reads its instance, its index among that
+// instance's blocks and their number from a per-block table and runs the
+// standalone kernel's body with them.  Every reduction is therefore partitioned, and every sum
 // rounded, exactly as in the instance's standalone solve.
 #pragma once
 
@@ -83,17 +83,14 @@ struct CohortMember {
   int grid[CS_STEPS];    // blocks of each step in the instance's standalone solve
 };
 
-// the instance that block `blk` of a batched launch works for: bstart holds
-// the prefix sums of the instances' block counts (K + 1 entries)
-__device__ __forceinline__ int cohort_member(const int *bstart, int K, int blk) {
-  int lo = 0, hi = K;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (bstart[mid] <= blk) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
+// one block of a batched launch: its instance, its index among that
+// instance's blocks and their number, and the instance's PCG scalars (read
+// first: a finished instance's blocks leave after one load)
+struct __align__(16) CohortBlock {
+  int k, vb, vn, pad;
+  const PcgScalars *sc;
+  const void *pad2;
+};
 
 // ---- host side (solve.cu and mfree.cu) ----
 constexpr int kCohortMax = 64;
@@ -106,9 +103,12 @@ struct Cohort {
   std::vector<Handle *> hs;                 // members, in table order
   std::vector<unsigned long long> gens;     // each member's arrays at the build
   int K = 0, cap = 0, maxc = 1;
+  int gv32 = 0;                             // the members' common lanes per FP32 vertex (0: mixed)
   int blocks[CS_STEPS] = {};                // blocks of each batched step
   CohortMember *d_mem = nullptr;
-  int *d_bstart = nullptr;                  // [CS_STEPS][K + 1] block prefix sums
+  CohortBlock *d_blk = nullptr;             // the blocks of every step, step after step
+  int blk_off[CS_STEPS] = {};               // first block record of each step
+  size_t blk_cap = 0;
   PcgScalars *d_sc = nullptr, *h_sc = nullptr;  // members' scalars after a chunk
   unsigned int *bar = nullptr;              // grid barrier of the batched tail
   long long wait_limit = 1ll << 24;
@@ -125,8 +125,9 @@ mgpbd_status cohort_chunk(Cohort *c, int iters);
 void mf_cohort_grids(const Handle *h, int grid[CS_STEPS]);
 // one batched matrix-free step for every member: which = CS_VERT64,
 // CS_ROW_PQ, CS_VERT32 (sel 0: from x0, 1: from x20), CS_ROW (sel 0: sweep
-// x0 -> x20, 1: residual x20 -> r0, 2: sweep x20 -> x0) or CS_ROW_FINAL
-mgpbd_status mf_cohort_step(int which, int sel, const CohortMember *d_mem, const int *d_bstart,
-                            int K, int blocks, cudaStream_t st);
+// x0 -> x20, 1: residual x20 -> r0, 2: sweep x20 -> x0) or CS_ROW_FINAL;
+// gv32 is the members' common lanes per FP32 vertex, 0 when they differ
+mgpbd_status mf_cohort_step(int which, int sel, const CohortMember *d_mem,
+                            const CohortBlock *d_blk, int blocks, int gv32, cudaStream_t st);
 
 }  // namespace mg

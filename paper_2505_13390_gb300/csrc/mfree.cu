@@ -349,38 +349,45 @@ static int mf_vertex_blocks(const Handle *h, int G) {
 // ---------------------------------------------------------------------------
 // the same passes for every instance of a cohort in one launch
 // ---------------------------------------------------------------------------
-#define COHORT_BLOCK(step)                                                        \
-  const int *bs_ = bstart + (step) * (K + 1);                                     \
-  const int k_ = cohort_member(bs_, K, blockIdx.x);                               \
-  const CohortMember &M = mem[k_];                                                \
-  const int vb = blockIdx.x - bs_[k_], vn = bs_[k_ + 1] - bs_[k_]
+#define COHORT_BLOCK                                                              \
+  const CohortBlock cb_ = blk[blockIdx.x];                                        \
+  if (is_done(cb_.sc)) return;                                                    \
+  const CohortMember &M = mem[cb_.k];                                             \
+  const int vb = cb_.vb, vn = cb_.vn
 
-__global__ void kb_vertex64(const CohortMember *mem, const int *bstart, int K) {
-  COHORT_BLOCK(CS_VERT64);
-  if (is_done(M.sc)) return;
+__global__ void kb_vertex64(const CohortMember *mem, const CohortBlock *blk) {
+  COHORT_BLOCK;
   MF_G_DISPATCH(M.gv64, (mf_vertex64_rows<GG>(VG_WARPS(vb, vn), M.N, M.vorder, M.vptr, M.vrow,
                                                M.ginc64, M.w, M.p, M.u64)));
 }
 
+// every member with G lanes per vertex (the usual case), with the standalone
+// kernel's register budget
+template <int G>
 __global__ void __launch_bounds__(256, 8)
-    kb_vertex32(const CohortMember *mem, const int *bstart, int K, int sel) {
-  COHORT_BLOCK(CS_VERT32);
-  if (is_done(M.sc)) return;
+    kb_vertex32(const CohortMember *mem, const CohortBlock *blk, int sel) {
+  COHORT_BLOCK;
+  mf_vertex32_rows<G>(VG_WARPS(vb, vn), M.N, M.vorder, M.vptr, M.ginc4, M.w32,
+                      sel ? M.x20 : M.x0, M.u32);
+}
+
+// members with different lanes per vertex: the shape is chosen per block
+__global__ void __launch_bounds__(256, 4)
+    kb_vertex32_any(const CohortMember *mem, const CohortBlock *blk, int sel) {
+  COHORT_BLOCK;
   MF_G_DISPATCH(M.gv32, (mf_vertex32_rows<GG>(VG_WARPS(vb, vn), M.N, M.vorder, M.vptr, M.ginc4,
                                                M.w32, sel ? M.x20 : M.x0, M.u32)));
 }
 
-__global__ void kb_row_pq(const CohortMember *mem, const int *bstart, int K) {
-  COHORT_BLOCK(CS_ROW_PQ);
-  if (is_done(M.sc)) return;
+__global__ void kb_row_pq(const CohortMember *mem, const CohortBlock *blk) {
+  COHORT_BLOCK;
   mf_row_body<double, MF_APPLY_DOT>(vb, vn, M.E, M.m, M.edge, M.tet, M.gd, M.gt, M.u64, M.at,
                                     M.p, nullptr, nullptr, 0.0, M.q, M.c_pq, nullptr, nullptr);
 }
 
 // sel 0: pre-sweep x0 -> x20; 1: residual x20 -> r0; 2: post-sweep x20 -> x0
-__global__ void kb_row(const CohortMember *mem, const int *bstart, int K, int sel) {
-  COHORT_BLOCK(CS_ROW);
-  if (is_done(M.sc)) return;
+__global__ void kb_row(const CohortMember *mem, const CohortBlock *blk, int sel) {
+  COHORT_BLOCK;
   DotCtx c{};
   c.sc = M.sc;
   if (sel == 1)
@@ -392,9 +399,8 @@ __global__ void kb_row(const CohortMember *mem, const int *bstart, int K, int se
                                  sel == 0 ? M.x20 : M.x0, c, nullptr, nullptr);
 }
 
-__global__ void kb_row_final(const CohortMember *mem, const int *bstart, int K) {
-  COHORT_BLOCK(CS_ROW_FINAL);
-  if (is_done(M.sc)) return;
+__global__ void kb_row_final(const CohortMember *mem, const CohortBlock *blk) {
+  COHORT_BLOCK;
   mf_row_body<float, MF_SWEEP_ZDOT>(vb, vn, M.E, M.m, M.edge, M.tet, M.gd32, M.gt32, M.u32,
                                     M.at32, M.x0, M.b0, M.dinv0, M.om0, nullptr, M.c_rz, M.z,
                                     M.r);
@@ -412,23 +418,27 @@ void mf_cohort_grids(const Handle *h, int grid[CS_STEPS]) {
                                 wave_blocks((const void *)k_mf_row<float, MF_SWEEP_ZDOT>, 256));
 }
 
-mgpbd_status mf_cohort_step(int which, int sel, const CohortMember *d_mem, const int *d_bstart,
-                            int K, int blocks, cudaStream_t st) {
+mgpbd_status mf_cohort_step(int which, int sel, const CohortMember *d_mem,
+                            const CohortBlock *d_blk, int blocks, int gv32, cudaStream_t st) {
   switch (which) {
     case CS_VERT64:
-      kb_vertex64<<<blocks, 256, 0, st>>>(d_mem, d_bstart, K);
+      kb_vertex64<<<blocks, 256, 0, st>>>(d_mem, d_blk);
       break;
     case CS_ROW_PQ:
-      kb_row_pq<<<blocks, 256, 0, st>>>(d_mem, d_bstart, K);
+      kb_row_pq<<<blocks, 256, 0, st>>>(d_mem, d_blk);
       break;
     case CS_VERT32:
-      kb_vertex32<<<blocks, 256, 0, st>>>(d_mem, d_bstart, K, sel);
+      if (gv32 == 4 || gv32 == 8 || gv32 == 16) {
+        MF_G_DISPATCH(gv32, (kb_vertex32<GG><<<blocks, 256, 0, st>>>(d_mem, d_blk, sel)));
+      } else {
+        kb_vertex32_any<<<blocks, 256, 0, st>>>(d_mem, d_blk, sel);
+      }
       break;
     case CS_ROW:
-      kb_row<<<blocks, 256, 0, st>>>(d_mem, d_bstart, K, sel);
+      kb_row<<<blocks, 256, 0, st>>>(d_mem, d_blk, sel);
       break;
     default:
-      kb_row_final<<<blocks, 256, 0, st>>>(d_mem, d_bstart, K);
+      kb_row_final<<<blocks, 256, 0, st>>>(d_mem, d_blk);
       break;
   }
   MG_LAUNCH("kb_mf");

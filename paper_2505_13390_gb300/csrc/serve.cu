@@ -25,6 +25,7 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -72,6 +73,12 @@ struct Batch {
   // uses it; instances keep their own streams)
   cudaStream_t cohort_stream = nullptr;
   unsigned long long submitted = 0;  // requests submitted so far
+  // cohort mode: rounds of the stepping thread, batched PCG iterations
+  // launched, and the wall time spent in the batched chunks and in the
+  // instances' own work between solves
+  long long rounds = 0, batched_iters = 0;
+  double chunk_s = 0.0, phase_s = 0.0;
+  std::string last_err;  // text of the most recent failed request's error
 };
 
 // upper estimate of an instance's device bytes from its mesh (before create):
@@ -110,6 +117,10 @@ static mgpbd_status make_resident(Instance &in) {
   if (in.h) return MGPBD_OK;
   MG_CUDA(cudaStreamCreateWithFlags(&in.stream, cudaStreamNonBlocking));
   mgpbd_status s = mgpbd_create(&in.desc, &in.p, in.stream, &in.h);
+  // served instances run beside each other: a cooperative coarse tail would
+  // wait for every SM, so their V-cycles keep separate launches (the cohort
+  // form has its own batched tail)
+  if (s >= 0) s = mgpbd_set_coarse_tail(in.h, 0);
   if (s >= 0) s = mgpbd_set_state(in.h, in.x.data(), in.v.data(), MGPBD_MEM_HOST);
   if (s < 0) {
     drop_handle(in);
@@ -244,7 +255,9 @@ static void worker(Batch *b) {
     }
     r.finish_s = clock_s(b);
     r.status = s;
+    const std::string msg = s < 0 ? std::string(mgpbd_last_error()) : std::string();
     lock.lock();
+    if (s < 0) b->last_err = "request " + std::to_string(q.ticket) + ": " + msg;
     b->resident = b->resident - in.bytes + held;  // the measured size replaces the estimate
     in.bytes = held;
     in.busy = false;
@@ -394,8 +407,10 @@ static void cohort_stepper(Batch *b) {
       runs.push_back(c);
     }
     // requests between solves: the next global iteration up to its solve
+    const double t_phase0 = clock_s(b);
     for (CohortRun &c : runs)
       if (!c.done && !c.solving) cohort_prepare(c);
+    double t_chunk = 0.0;
     // the batched chunk over every instance that is solving
     std::vector<Handle *> members;
     for (CohortRun &c : runs)
@@ -413,7 +428,9 @@ static void cohort_stepper(Batch *b) {
              cudaStreamWaitEvent(b->cohort_stream, c.started, 0) != cudaSuccess))
           e = cuda_fail(cudaGetLastError(), "cohort: ordering a member's start", __FILE__,
                         __LINE__);
+      const double t0 = clock_s(b);
       if (e >= 0) e = cohort_chunk(&co, 8);
+      t_chunk = clock_s(b) - t0;
       for (CohortRun &c : runs) {
         if (c.done || !c.solving) continue;
         Handle *h = reinterpret_cast<Handle *>(c.in->h);
@@ -431,6 +448,7 @@ static void cohort_stepper(Batch *b) {
         cohort_advance(c, info, st);
       }
     }
+    const double t_round = clock_s(b) - t_phase0;
     // finished requests leave
     std::vector<CohortRun> left;
     std::vector<std::pair<CohortRun, size_t>> fin;
@@ -448,11 +466,19 @@ static void cohort_stepper(Batch *b) {
       if (c.started) cudaEventDestroy(c.started);
       c.r.finish_s = clock_s(b);
       c.r.status = c.worst;
+      if (c.worst < 0) {
+        std::lock_guard<std::mutex> g(b->mu);
+        b->last_err = "request " + std::to_string(c.q.ticket) + ": " + mgpbd_last_error();
+      }
       fin.emplace_back(c, held);
     }
     runs.swap(left);
     if (runs.empty()) co.hs.clear();  // no member holds a handle that may be evicted
     lock.lock();
+    b->rounds++;
+    if (!members.empty()) b->batched_iters += 8;
+    b->chunk_s += t_chunk;
+    b->phase_s += t_round - t_chunk;
     for (auto &f : fin) {
       Instance &in = *f.first.in;
       b->resident = b->resident - in.bytes + f.second;
@@ -633,6 +659,27 @@ mgpbd_status mgpbd_batch_counts(mgpbd_batch_t *bb, int *queued, int *running, in
   if (running) *running = b->running;
   if (unreported) *unreported = (int)b->finished.size();
   if (clock) *clock = clock_s(b);
+  return MGPBD_OK;
+}
+
+const char *mgpbd_batch_error(mgpbd_batch_t *bb) {
+  Batch *b = reinterpret_cast<Batch *>(bb);
+  if (!b) return "";
+  thread_local std::string copy;
+  std::lock_guard<std::mutex> lock(b->mu);
+  copy = b->last_err;
+  return copy.c_str();
+}
+
+mgpbd_status mgpbd_batch_cohort_stats(mgpbd_batch_t *bb, int64_t *rounds, int64_t *batched_iters,
+                                      double *chunk_s, double *other_s) {
+  Batch *b = reinterpret_cast<Batch *>(bb);
+  if (!b) return MGPBD_E_INVALID;
+  std::lock_guard<std::mutex> lock(b->mu);
+  if (rounds) *rounds = b->rounds;
+  if (batched_iters) *batched_iters = b->batched_iters;
+  if (chunk_s) *chunk_s = b->chunk_s;
+  if (other_s) *other_s = b->phase_s;
   return MGPBD_OK;
 }
 

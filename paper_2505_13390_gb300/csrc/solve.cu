@@ -807,11 +807,15 @@ __global__ void __launch_bounds__(256) k_coarse_tail(TailDesc<T> d, unsigned int
   }
 }
 
-// the tail applies from level `first` down: Jacobi smoothing, one column of
-// P per aggregate, and at least one level above the coarsest
+// The tail applies from level `first` down: Jacobi smoothing, one column of
+// P per aggregate, at least one level above the coarsest, and a level small
+// enough that two blocks per SM cover its rows in about one pass (larger
+// levels keep their own full-width launches; the tail then starts below them).
+constexpr int kTailMaxRows = 16384;
 static bool tail_applies(const Handle *h, int first) {
   return h->tail && h->p.smoother == MGPBD_SMOOTH_JACOBI && h->p.nk_vectors == 1 &&
-         h->p.smooth_sweeps >= 1 && first >= 1 && first < h->L - 1;
+         h->p.smooth_sweeps >= 1 && first >= 1 && first < h->L - 1 &&
+         h->lev[first].n <= kTailMaxRows;
 }
 
 // level `first`'s result lies in x after an even number of buffer swaps (2
@@ -869,36 +873,32 @@ static mgpbd_status launch_tail(Handle *h, int first) {
 // ---------------------------------------------------------------------------
 // batched PCG of a cohort: every step one launch for every member
 // ---------------------------------------------------------------------------
-#define COHORT_BLOCK(step)                                                        \
-  const int *bs_ = bstart + (step) * (K + 1);                                     \
-  const int k_ = cohort_member(bs_, K, blockIdx.x);                               \
-  const CohortMember &M = mem[k_];                                                \
-  const int vb = blockIdx.x - bs_[k_], vn = bs_[k_ + 1] - bs_[k_]
+#define COHORT_BLOCK                                                              \
+  const CohortBlock cb_ = blk[blockIdx.x];                                        \
+  if (is_done(cb_.sc)) return;                                                    \
+  const CohortMember &M = mem[cb_.k];                                             \
+  const int vb = cb_.vb, vn = cb_.vn
 
-__global__ void kb_xr(const CohortMember *mem, const int *bstart, int K) {
-  COHORT_BLOCK(CS_XR);
-  if (is_done(M.sc)) return;
+__global__ void kb_xr(const CohortMember *mem, const CohortBlock *blk) {
+  COHORT_BLOCK;
   xr_update_body<float>(vb, vn, M.m, M.x, M.r, M.p, M.q, M.c_rr, M.b0, M.dinv0, M.om0, M.x0);
 }
 
-__global__ void kb_restrict0(const CohortMember *mem, const int *bstart, int K) {
-  COHORT_BLOCK(CS_RESTRICT);
-  if (is_done(M.sc)) return;
+__global__ void kb_restrict0(const CohortMember *mem, const CohortBlock *blk) {
+  COHORT_BLOCK;
   const TailLevel<float> &L1 = M.tail.lev[1];
   const bool c_jac = M.tail.coarsest > 1;  // level 1 smooths: its first sweep rides along
   restrict_aggs<float>(VG_WARPS(vb, vn), M.n_agg0, 1, M.mptr0, M.mrow0, M.P0, M.r0, L1.b,
                        c_jac ? L1.dinv : nullptr, L1.omega, c_jac ? L1.x : nullptr);
 }
 
-__global__ void kb_prolong0(const CohortMember *mem, const int *bstart, int K) {
-  COHORT_BLOCK(CS_PROLONG);
-  if (is_done(M.sc)) return;
+__global__ void kb_prolong0(const CohortMember *mem, const CohortBlock *blk) {
+  COHORT_BLOCK;
   prolong_rows<float>(vb, vn, M.m, M.agg0, M.P0, M.xc1, M.x20);
 }
 
-__global__ void kb_pupdate(const CohortMember *mem, const int *bstart, int K) {
-  COHORT_BLOCK(CS_PUPD);
-  if (is_done(M.sc)) return;
+__global__ void kb_pupdate(const CohortMember *mem, const CohortBlock *blk) {
+  COHORT_BLOCK;
   p_update_body(vb, vn, M.m, M.p, M.z, M.sc);
 }
 
@@ -906,77 +906,77 @@ __global__ void kb_pupdate(const CohortMember *mem, const int *bstart, int K) {
 // by depth: at depth d the members whose coarsest level is deeper pre-smooth,
 // take the residual and restrict; a member whose coarsest level is d solves
 // it there; on the way back up each member prolongs and post-smooths its
-// levels.  A member's own steps run in its standalone order over the same row
-// bodies, so its results are its standalone bits.
+// levels.  The warps (and, for the prolongation, the blocks) are split among
+// the members in contiguous shares, so each warp reads one member's record and
+// works only on its rows, and the members' small levels run side by side.  A
+// member's own steps run in its standalone order over the same row bodies
+// (no row's arithmetic depends on the warp that takes it), so its results are
+// its standalone bits.
 __global__ void __launch_bounds__(256) kb_tail(const CohortMember *mem, int K, int maxc,
                                                 unsigned int *bar, long long limit) {
-  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // this warp's member, its index among the member's warps and their number
+  const int k = (int)((w * K) / nw);
+  const int64_t w_lo = ((int64_t)k * nw + K - 1) / K, w_hi = ((int64_t)(k + 1) * nw + K - 1) / K;
+  const int64_t lw = w - w_lo, nlw = w_hi - w_lo;
+  // the same split of the blocks for the prolongation
+  const int kb = (int)(((int64_t)blockIdx.x * K) / gridDim.x);
+  const int64_t b_lo = ((int64_t)kb * gridDim.x + K - 1) / K,
+                b_hi = ((int64_t)(kb + 1) * gridDim.x + K - 1) / K;
   unsigned long long act = 0;  // members still iterating (the same in every block)
-  for (int k = 0; k < K; ++k)
-    if (!is_done(mem[k].sc)) act |= 1ull << k;
+  for (int j = 0; j < K; ++j)
+    if (!is_done(mem[j].sc)) act |= 1ull << j;
   if (!act) return;
   auto sync = [&]() -> bool {
     if (grid_barrier(bar, limit)) return true;
     if (threadIdx.x == 0)
-      for (int k = 0; k < K; ++k)
-        if (act >> k & 1) {
-          mem[k].sc->status = MGPBD_E_DEVICE_TIMEOUT;
+      for (int j = 0; j < K; ++j)
+        if (act >> j & 1) {
+          mem[j].sc->status = MGPBD_E_DEVICE_TIMEOUT;
           __threadfence();
-          mem[k].sc->done = 1;
+          mem[j].sc->done = 1;
         }
     return false;
   };
+  const bool mine = act >> k & 1;           // this warp's member iterates
+  const TailDesc<float> &T = mem[k].tail;  // its levels
+  const int ck = T.coarsest;
+  const bool mine_b = act >> kb & 1;
+  const TailDesc<float> &Tb = mem[kb].tail;
   auto jacobi = [&](const TailLevel<float> &L, const float *x, float *xn) {
-    DISPATCH_G(L.G, (jacobi_rows<GG, float>(w0, nw, L.n, L.ptr, L.col, L.val, L.dinv, L.omega,
+    DISPATCH_G(L.G, (jacobi_rows<GG, float>(lw, nlw, L.n, L.ptr, L.col, L.val, L.dinv, L.omega,
                                             L.b, x, xn)));
   };
   for (int d = 1; d <= maxc; ++d) {
-    for (int s = 1; s < 2; ++s) {  // pre-sweeps after the first (two sweeps per side)
-      for (int k = 0; k < K; ++k) {
-        const TailDesc<float> &T = mem[k].tail;
-        if ((act >> k & 1) && d < T.coarsest) jacobi(T.lev[d], T.lev[d].x, T.lev[d].x2);
-      }
-      if (!sync()) return;
-    }
-    for (int k = 0; k < K; ++k) {
-      const TailDesc<float> &T = mem[k].tail;
-      if (!(act >> k & 1)) continue;
+    if (mine && d < ck) jacobi(T.lev[d], T.lev[d].x, T.lev[d].x2);  // the pre-sweep after the first
+    if (!sync()) return;
+    if (mine && d < ck) {
       const TailLevel<float> &L = T.lev[d];
-      if (d < T.coarsest) {
-        DISPATCH_G(L.G, (resid_rows<GG, float>(w0, nw, L.n, L.ptr, L.col, L.val, L.b, L.x2,
-                                                L.r)));
-      } else if (d == T.coarsest) {
-        coarse_rows<float>(w0, nw, L.n, T.cinv, L.b, L.x);
-      }
+      DISPATCH_G(L.G, (resid_rows<GG, float>(lw, nlw, L.n, L.ptr, L.col, L.val, L.b, L.x2, L.r)));
+    } else if (mine && d == ck) {
+      coarse_rows<float>(lw, nlw, T.lev[d].n, T.cinv, T.lev[d].b, T.lev[d].x);
     }
     if (!sync()) return;
     if (d == maxc) break;
-    for (int k = 0; k < K; ++k) {
-      const TailDesc<float> &T = mem[k].tail;
-      if (!(act >> k & 1) || d >= T.coarsest) continue;
+    if (mine && d < ck) {
       const TailLevel<float> &L = T.lev[d], &Lc = T.lev[d + 1];
-      const bool c_jac = d + 1 < T.coarsest;
-      restrict_aggs<float>(w0, nw, L.n_agg, 1, L.mptr, L.mrow, L.P, L.r, Lc.b,
+      const bool c_jac = d + 1 < ck;
+      restrict_aggs<float>(lw, nlw, L.n_agg, 1, L.mptr, L.mrow, L.P, L.r, Lc.b,
                            c_jac ? Lc.dinv : nullptr, Lc.omega, c_jac ? Lc.x : nullptr);
     }
     if (!sync()) return;
   }
   for (int d = maxc - 1; d >= 1; --d) {
-    for (int k = 0; k < K; ++k) {
-      const TailDesc<float> &T = mem[k].tail;
-      if (!(act >> k & 1) || d >= T.coarsest) continue;
-      const TailLevel<float> &L = T.lev[d], &Lc = T.lev[d + 1];
-      const float *xc = d + 1 == T.coarsest ? Lc.x : Lc.x2;  // the coarser level's result
-      prolong_rows<float>(blockIdx.x, gridDim.x, L.n, L.agg, L.P, xc, L.x2);
+    if (mine_b && d < Tb.coarsest) {
+      const TailLevel<float> &L = Tb.lev[d], &Lc = Tb.lev[d + 1];
+      const float *xc = d + 1 == Tb.coarsest ? Lc.x : Lc.x2;  // the coarser level's result
+      prolong_rows<float>(blockIdx.x - b_lo, b_hi - b_lo, L.n, L.agg, L.P, xc, L.x2);
     }
     if (!sync()) return;
     for (int s = 0; s < 2; ++s) {
-      for (int k = 0; k < K; ++k) {
-        const TailDesc<float> &T = mem[k].tail;
-        if ((act >> k & 1) && d < T.coarsest)
-          jacobi(T.lev[d], s == 0 ? T.lev[d].x2 : T.lev[d].x, s == 0 ? T.lev[d].x : T.lev[d].x2);
-      }
+      if (mine && d < ck)
+        jacobi(T.lev[d], s == 0 ? T.lev[d].x2 : T.lev[d].x, s == 0 ? T.lev[d].x : T.lev[d].x2);
       if ((d > 1 || s == 0) && !sync()) return;
     }
   }
@@ -997,7 +997,7 @@ bool cohort_eligible(const Handle *h) {
 Cohort::~Cohort() {
   if (graph) cudaGraphExecDestroy(graph);
   if (d_mem) cudaFree(d_mem);
-  if (d_bstart) cudaFree(d_bstart);
+  if (d_blk) cudaFree(d_blk);
   if (d_sc) cudaFree(d_sc);
   if (bar) cudaFree(bar);
   if (h_sc) cudaFreeHost(h_sc);
@@ -1014,16 +1014,13 @@ mgpbd_status cohort_build(Cohort *c) {
   }
   if (K > c->cap) {
     if (c->d_mem) cudaFree(c->d_mem);
-    if (c->d_bstart) cudaFree(c->d_bstart);
     if (c->d_sc) cudaFree(c->d_sc);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     c->d_mem = nullptr;
-    c->d_bstart = nullptr;
     c->d_sc = nullptr;
     c->h_sc = nullptr;
     c->cap = 0;
     MG_CUDA(cudaMalloc(&c->d_mem, sizeof(CohortMember) * kCohortMax));
-    MG_CUDA(cudaMalloc(&c->d_bstart, sizeof(int) * CS_STEPS * (kCohortMax + 1)));
     MG_CUDA(cudaMalloc(&c->d_sc, sizeof(PcgScalars) * kCohortMax));
     MG_CUDA(cudaMallocHost(&c->h_sc, sizeof(PcgScalars) * kCohortMax));
     c->cap = kCohortMax;
@@ -1033,7 +1030,6 @@ mgpbd_status cohort_build(Cohort *c) {
     MG_CUDA(cudaMemsetAsync(c->bar, 0, 16 * sizeof(unsigned int), c->stream));
   }
   std::vector<CohortMember> mem((size_t)K);
-  std::vector<int> bstart((size_t)CS_STEPS * (K + 1), 0);
   c->maxc = 1;
   c->gens.assign(K, 0);
   for (int k = 0; k < K; ++k) {
@@ -1116,14 +1112,30 @@ mgpbd_status cohort_build(Cohort *c) {
     M.grid[CS_RESTRICT] = blocks_for((int64_t)L0.n_agg * 32, 256);
     M.grid[CS_PROLONG] = blocks_for((m + kProlongRows - 1) / kProlongRows, 256);
     M.grid[CS_PUPD] = blocks_for(std::max(1, (m / 2 + 1) / 2), 256);
-    for (int s = 0; s < CS_STEPS; ++s)
-      bstart[(size_t)s * (K + 1) + k + 1] = bstart[(size_t)s * (K + 1) + k] + M.grid[s];
     c->gens[k] = h->gen;
   }
-  for (int s = 0; s < CS_STEPS; ++s) c->blocks[s] = bstart[(size_t)s * (K + 1) + K];
+  c->gv32 = mem.empty() ? 0 : mem[0].gv32;
+  for (const CohortMember &M : mem)
+    if (M.gv32 != c->gv32) c->gv32 = 0;
+  // per step, each member's blocks in member order: (member, index, count)
+  std::vector<CohortBlock> blk;
+  for (int s = 0; s < CS_STEPS; ++s) {
+    c->blk_off[s] = (int)blk.size();
+    for (int k = 0; k < K; ++k)
+      for (int b = 0; b < mem[k].grid[s]; ++b)
+        blk.push_back(CohortBlock{k, b, mem[k].grid[s], 0, mem[k].sc, nullptr});
+    c->blocks[s] = (int)blk.size() - c->blk_off[s];
+  }
+  if (blk.size() > c->blk_cap) {
+    if (c->d_blk) cudaFree(c->d_blk);
+    c->d_blk = nullptr;
+    c->blk_cap = 0;
+    MG_CUDA(cudaMalloc(&c->d_blk, sizeof(CohortBlock) * blk.size()));
+    c->blk_cap = blk.size();
+  }
   MG_CUDA(cudaMemcpyAsync(c->d_mem, mem.data(), sizeof(CohortMember) * K, cudaMemcpyHostToDevice,
                           c->stream));
-  MG_CUDA(cudaMemcpyAsync(c->d_bstart, bstart.data(), sizeof(int) * bstart.size(),
+  MG_CUDA(cudaMemcpyAsync(c->d_blk, blk.data(), sizeof(CohortBlock) * blk.size(),
                           cudaMemcpyHostToDevice, c->stream));
   MG_CUDA(cudaStreamSynchronize(c->stream));
   c->K = K;
@@ -1147,15 +1159,20 @@ bool cohort_stale(const Cohort *c) {
 static mgpbd_status cohort_iteration(Cohort *c) {
   const int K = c->K;
   cudaStream_t st = c->stream;
-  MG_TRY(mf_cohort_step(CS_VERT64, 0, c->d_mem, c->d_bstart, K, c->blocks[CS_VERT64], st));
-  MG_TRY(mf_cohort_step(CS_ROW_PQ, 0, c->d_mem, c->d_bstart, K, c->blocks[CS_ROW_PQ], st));
-  kb_xr<<<c->blocks[CS_XR], kDotThreads, 0, st>>>(c->d_mem, c->d_bstart, K);
+  const CohortMember *m = c->d_mem;
+  auto blk = [&](int step) { return c->d_blk + c->blk_off[step]; };
+  auto mf = [&](int step, int sel) {
+    return mf_cohort_step(step, sel, m, blk(step), c->blocks[step], c->gv32, st);
+  };
+  MG_TRY(mf(CS_VERT64, 0));
+  MG_TRY(mf(CS_ROW_PQ, 0));
+  kb_xr<<<c->blocks[CS_XR], kDotThreads, 0, st>>>(m, blk(CS_XR));
   MG_LAUNCH("kb_xr");
-  MG_TRY(mf_cohort_step(CS_VERT32, 0, c->d_mem, c->d_bstart, K, c->blocks[CS_VERT32], st));
-  MG_TRY(mf_cohort_step(CS_ROW, 0, c->d_mem, c->d_bstart, K, c->blocks[CS_ROW], st));
-  MG_TRY(mf_cohort_step(CS_VERT32, 1, c->d_mem, c->d_bstart, K, c->blocks[CS_VERT32], st));
-  MG_TRY(mf_cohort_step(CS_ROW, 1, c->d_mem, c->d_bstart, K, c->blocks[CS_ROW], st));
-  kb_restrict0<<<c->blocks[CS_RESTRICT], 256, 0, st>>>(c->d_mem, c->d_bstart, K);
+  MG_TRY(mf(CS_VERT32, 0));
+  MG_TRY(mf(CS_ROW, 0));
+  MG_TRY(mf(CS_VERT32, 1));
+  MG_TRY(mf(CS_ROW, 1));
+  kb_restrict0<<<c->blocks[CS_RESTRICT], 256, 0, st>>>(m, blk(CS_RESTRICT));
   MG_LAUNCH("kb_restrict0");
   {
     const int blocks = std::min(wave_blocks((const void *)kb_tail, 256), 2 * num_sms());
@@ -1168,17 +1185,16 @@ static mgpbd_status cohort_iteration(Cohort *c) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    MG_CUDA(cudaLaunchKernelEx(&cfg, kb_tail, (const CohortMember *)c->d_mem, K, c->maxc, c->bar,
-                               c->wait_limit));
+    MG_CUDA(cudaLaunchKernelEx(&cfg, kb_tail, m, K, c->maxc, c->bar, c->wait_limit));
     MG_LAUNCH("kb_tail");
   }
-  kb_prolong0<<<c->blocks[CS_PROLONG], 256, 0, st>>>(c->d_mem, c->d_bstart, K);
+  kb_prolong0<<<c->blocks[CS_PROLONG], 256, 0, st>>>(m, blk(CS_PROLONG));
   MG_LAUNCH("kb_prolong0");
-  MG_TRY(mf_cohort_step(CS_VERT32, 1, c->d_mem, c->d_bstart, K, c->blocks[CS_VERT32], st));
-  MG_TRY(mf_cohort_step(CS_ROW, 2, c->d_mem, c->d_bstart, K, c->blocks[CS_ROW], st));
-  MG_TRY(mf_cohort_step(CS_VERT32, 0, c->d_mem, c->d_bstart, K, c->blocks[CS_VERT32], st));
-  MG_TRY(mf_cohort_step(CS_ROW_FINAL, 0, c->d_mem, c->d_bstart, K, c->blocks[CS_ROW_FINAL], st));
-  kb_pupdate<<<c->blocks[CS_PUPD], 256, 0, st>>>(c->d_mem, c->d_bstart, K);
+  MG_TRY(mf(CS_VERT32, 1));
+  MG_TRY(mf(CS_ROW, 2));
+  MG_TRY(mf(CS_VERT32, 0));
+  MG_TRY(mf(CS_ROW_FINAL, 0));
+  kb_pupdate<<<c->blocks[CS_PUPD], 256, 0, st>>>(m, blk(CS_PUPD));
   MG_LAUNCH("kb_pupdate");
   return MGPBD_OK;
 }

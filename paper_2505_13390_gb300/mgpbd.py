@@ -138,6 +138,9 @@ SIGNATURES = {
     "mgpbd_batch_tick": (_i, [_vp, C.c_double, _vp, _i, C.POINTER(_i)]),
     "mgpbd_batch_counts": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i),
                                 C.POINTER(C.c_double)]),
+    "mgpbd_batch_error": (C.c_char_p, [_vp]),
+    "mgpbd_batch_cohort_stats": (_i, [_vp, C.POINTER(_i64), C.POINTER(_i64),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mgpbd_batch_run": (_i, [_vp, _vp, _i, _vp]),
     "mgpbd_batch_get_state": (_i, [_vp, _i, _vp, _vp]),
     "mgpbd_batch_resident": (_i, [_vp, C.POINTER(_i), C.POINTER(C.c_size_t)]),
@@ -506,6 +509,19 @@ class Batch:
         _check(load().mgpbd_batch_counts(self.h, C.byref(q), C.byref(r), C.byref(u),
                                          C.byref(t)), "batch_counts")
         return {"queued": q.value, "running": r.value, "unreported": u.value, "clock": t.value}
+
+    def error(self) -> str:
+        """Text of the most recently failed request's error."""
+        return load().mgpbd_batch_error(self.h).decode(errors="replace")
+
+    def cohort_stats(self) -> Dict:
+        """Cohort mode: rounds, batched PCG iterations, seconds in the batched
+        chunks and in the rest of the rounds."""
+        r, n, c, o = C.c_int64(), C.c_int64(), C.c_double(), C.c_double()
+        _check(load().mgpbd_batch_cohort_stats(self.h, C.byref(r), C.byref(n), C.byref(c),
+                                               C.byref(o)), "batch_cohort_stats")
+        return {"rounds": r.value, "batched_iters": n.value, "chunk_s": c.value,
+                "other_s": o.value}
 
     def run(self, requests):
         """requests: iterable of (id, instance, frames, arrival_s)."""
