@@ -76,10 +76,11 @@ def parse():
                     help="skip the assembled-CSR comparison line")
     ap.add_argument("--serve-requests", type=int, default=64,
                     help="step requests of the serving trace (the full trace has 512)")
-    ap.add_argument("--serve-instances", type=int, default=8)
+    ap.add_argument("--serve-instances", type=int, default=64,
+                    help="instances the requests draw from uniformly")
     ap.add_argument("--serve-rate", type=float, default=1.0, help="arrivals per second")
     ap.add_argument("--serve-active", type=int, default=8)
-    ap.add_argument("--serve-arms", default="batched_cohort,serial_mixed,plain_fp64",
+    ap.add_argument("--serve-arms", default="batched_streams,batched_cohort,serial_mixed,plain_fp64",
                     help="comma list of: " + ", ".join(SERVE_ARMS))
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-serve-saturated", action="store_true",
@@ -88,6 +89,10 @@ def parse():
                     help="skip the ARAP-constraint leg (block100arap)")
     ap.add_argument("--no-xpbd", action="store_true",
                     help="skip the XPBD-versus-MGPBD frame on cloth512")
+    ap.add_argument("--no-smoothers", action="store_true",
+                    help="skip the Chebyshev-smoother leg on the same block")
+    ap.add_argument("--smoother-steps", type=int, default=3)
+    ap.add_argument("--smoother-warmup", type=int, default=3)
     ap.add_argument("--arap-steps", type=int, default=3)
     ap.add_argument("--arap-warmup", type=int, default=3)
     ap.add_argument("--assembled-steps", type=int, default=1)
@@ -347,23 +352,25 @@ def serve_arm(meshes, reqs, prec, op, graphs, active, budget, cohort=False):
 
 
 SERVE_ARMS = {
-    # name: (precision, level0_op, graphs, concurrent, cohort)
-    "batched_cohort": (1, 1, 1, True, True),
-    "batched_streams": (1, 1, 1, True, False),
-    "serial_mixed": (1, 1, 1, False, False),
-    "plain_fp64": (0, 0, 0, False, False),
+    # name: (precision, level0_op, graphs, concurrent, cohort, open-loop run)
+    "batched_streams": (1, 1, 1, True, False, True),
+    "batched_cohort": (1, 1, 1, True, True, False),
+    "serial_mixed": (1, 1, 1, False, False, True),
+    "plain_fp64": (0, 0, 0, False, False, True),
 }
 
 
 def serving(args):
     """Serving load: step requests of uneven instances with Poisson arrivals,
     driven through the request loop with wall-clock arrivals, all at PCG rtol
-    1e-6 on the same seeded trace.  Arms (--serve-arms):
-      batched_cohort   the served form: mixed precision, matrix-free level 0,
-                       up to --serve-active requests at once, the PCG
-                       iterations of all of them one launch per step;
-      batched_streams  the same settings, each request on its own stream and
-                       worker thread with CUDA graphs;
+    1e-6 on the same seeded trace (by default every request has an instance
+    of its own).  Arms (--serve-arms):
+      batched_streams  the served form: mixed precision, matrix-free level 0,
+                       up to --serve-active requests at once, each on its own
+                       stream and worker thread with CUDA graphs;
+      batched_cohort   the same settings with the PCG iterations of all
+                       running requests one launch per step (only its
+                       saturated run, for capacity);
       serial_mixed     the same solver settings, one request at a time
                        (isolates the batching);
       plain_fp64       FP64, assembled CSR, plain launches, one at a time (the
@@ -378,10 +385,11 @@ def serving(args):
     budget = int(0.5 * free)
     out = {}
     for name in args.serve_arms.split(","):
-        prec, op, graphs, conc, cohort = SERVE_ARMS[name]
-        out[name] = serve_arm(meshes, reqs, prec, op, graphs, args.serve_active if conc else 1,
-                              budget, cohort)
-        torch.cuda.empty_cache()
+        prec, op, graphs, conc, cohort, open_loop = SERVE_ARMS[name]
+        if open_loop:
+            out[name] = serve_arm(meshes, reqs, prec, op, graphs,
+                                  args.serve_active if conc else 1, budget, cohort)
+            torch.cuda.empty_cache()
         if conc and not args.no_serve_saturated:
             # the same requests all at t = 0: the batched arm's capacity (at the
             # open-loop rate it is not saturated, and its throughput is the
@@ -395,12 +403,12 @@ def serving(args):
                     "meshes": [f"{d['kind']}{d['size']}" for d in inst],
                     "budget": "half of free device memory", "frames_per_request": 1,
                     "iters_per_frame": 20, "pcg_rtol": 1e-6, "arrivals": "Poisson, seed 6"}
-    served = next((n for n in ("batched_cohort", "batched_streams") if n in out), None)
-    if served:
-        key = served + "_saturated" if served + "_saturated" in out else served
+    if "batched_streams" in out:
+        key = "batched_streams_saturated" if "batched_streams_saturated" in out else \
+            "batched_streams"
         b = out[key]["global_iters_per_s"]
-        for base in ("plain_fp64", "serial_mixed", "batched_streams_saturated"):
-            if base in out and base != key:
+        for base in ("plain_fp64", "serial_mixed", "batched_cohort_saturated"):
+            if base in out:
                 out[f"capacity_speedup_vs_{base}"] = b / out[base]["global_iters_per_s"]
     return out
 
@@ -621,6 +629,25 @@ def run_ours(args, ws, rank):
         rar["solver"].close()
         del rar
         torch.cuda.empty_cache()
+    smoothers = None
+    if not args.no_smoothers:
+        # the paper's other smoother (Sec. 4.5: Chebyshev, its choice for
+        # cloth) on the same block, two and three sweeps per side, timed the
+        # same way from the same start (the headline keeps weighted Jacobi,
+        # its choice for soft bodies)
+        smoothers = {}
+        for sweeps in (2, 3):
+            ps = dict(params, smoother=2, smooth_sweeps=sweeps)
+            rs = measure(mesh, ps, args.smoother_steps, args.smoother_warmup, ws, profile=False)
+            mss = max_over_ranks(ws, rs["ms"])
+            smoothers[f"chebyshev{sweeps}"] = {
+                "value": ws * args.smoother_steps / (mss / 1e3), "unit": "global_iters/s",
+                "ms_per_step": mss / args.smoother_steps, "steps": args.smoother_steps,
+                "warmup": args.smoother_warmup, "pcg_iters": rs["pcg"],
+                "true_rel_res": rs["true_res"], "clocks": rs["clocks"]}
+            rs["solver"].close()
+            del rs
+            torch.cuda.empty_cache()
     xpbd = None
     if not args.no_xpbd and ws == 1:  # a single-GPU comparison: not repeated per rank
         xpbd = xpbd_comparison()
@@ -690,6 +717,7 @@ def run_ours(args, ws, rank):
         "fp64": fp64,
         "assembled": assembled,
         "arap": arap,
+        "smoothers": smoothers,
         "xpbd_vs_mgpbd": xpbd,
         "serving": serve,
         "create_s": res["create_s"],

@@ -252,18 +252,19 @@ mgpbd_status mgpbd_get_lanes(mgpbd_handle_t *h, int level, int *csr32, int *csr6
  * down to the coarsest level, its dense solve, prolongation and smoothing back
  * up to level 1).  By default each step is its own launch.
  * mgpbd_set_coarse_tail(h, 1) runs them, where it applies (weighted-Jacobi
- * smoother, one near-kernel vector, a level between level 0 and the
- * coarsest), as one cooperative kernel over two blocks per SM with a grid
- * barrier between dependent steps; the results are the same bits either way
- * (no step of it sums across rows).  A cooperative launch needs every SM at
- * once, so it waits for other streams' kernels; it is slower on the
- * 1.65M-tet block than the separate launches inside a CUDA graph.  0 restores
- * the default.  No device work; MGPBD_E_INVALID for another value.
- * mgpbd_set_wait_limit bounds how many times a block of that kernel polls a
- * grid barrier (default 2^24, one to two seconds); when a wait runs out the
- * solve stops and returns MGPBD_E_DEVICE_TIMEOUT, and the next solve starts
- * from a reset barrier.  0 makes every waiting block give up at once (to test
- * that path).  MGPBD_E_INVALID for polls < 0. */
+ * smoother, one near-kernel vector, a level between level 0 and the coarsest)
+ * from the first level of at most 16,384 rows, as one cooperative kernel over
+ * two blocks per SM with a grid barrier between dependent steps; the results
+ * are the same bits either way (no step of it sums across rows).  A
+ * cooperative launch needs every SM at once, so it waits for other streams'
+ * kernels; on these workloads it is no faster than the separate launches
+ * inside a CUDA graph.  0 restores the default.  No device work;
+ * MGPBD_E_INVALID for another value.
+ * mgpbd_set_wait_limit bounds how many times a block of the cooperative kernel
+ * polls a grid barrier (default 2^24, one to two seconds); when a wait runs
+ * out the solve stops and returns MGPBD_E_DEVICE_TIMEOUT, and the next solve
+ * starts from a reset barrier.  0 makes every waiting block give up at once
+ * (to test that path).  MGPBD_E_INVALID for polls < 0. */
 mgpbd_status mgpbd_set_coarse_tail(mgpbd_handle_t *h, int enable);
 mgpbd_status mgpbd_set_wait_limit(mgpbd_handle_t *h, long long polls);
 /* CSR of level `level`: ptr [n+1] int64, col [nnz] int32, val [nnz] double

@@ -27,6 +27,7 @@
 // operation order as a plain sequential FP64 program, so aggregates, P, B and
 // colours are reproducible bit for bit.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -661,17 +662,42 @@ mgpbd_status level_precision_copies(Handle *h, int l) {
   return MGPBD_OK;
 }
 
+// The largest dynamic shared memory a Galerkin launch requests.  The limit a
+// kernel may request is one setting per kernel for the whole process, so it is
+// raised once to this bound (under a mutex, before the first launch), never
+// per launch: per launch, one thread could lower it between another thread's
+// setting and that thread's launch, which then fails.
+constexpr int kGalerkinSmemMax = 200 * 1024;
+
+__global__ void k_gal_values_k(int na, int k, const int64_t *mptr, const int32_t *mrow,
+                               const int64_t *ptr, const int32_t *col, const double *val,
+                               const int32_t *agg, const double *P, const int64_t *bptr,
+                               const int32_t *bcol, const int64_t *cptr, double *cval,
+                               int maxblk, double *acc_global);
+
+static mgpbd_status galerkin_smem_limits() {
+  static std::mutex mu;
+  static bool done = false;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done) return MGPBD_OK;
+  MG_CUDA(cudaFuncSetAttribute(k_gal_values, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kGalerkinSmemMax));
+  MG_CUDA(cudaFuncSetAttribute(k_gal_values_k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kGalerkinSmemMax));
+  done = true;
+  return MGPBD_OK;
+}
+
 static mgpbd_status galerkin_values(Handle *h, int l) {
   Level &L = h->lev[l], &Lc = h->lev[l + 1];
   int maxlen = std::max(L.max_coarse_row, 1);
   int warps = maxlen > 1536 ? 1 : (maxlen > 384 ? 2 : 4);
   size_t smem = (size_t)warps * maxlen * (sizeof(double) + sizeof(int));
-  if (smem > 200 * 1024) {
+  if (smem > (size_t)kGalerkinSmemMax) {
     set_error("Galerkin: coarse row too long for shared memory");
     return MGPBD_E_SETUP;
   }
-  MG_CUDA(cudaFuncSetAttribute(k_gal_values, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem));
+  MG_TRY(galerkin_smem_limits());
   int blocks = (int)std::min<int64_t>((L.n_agg + warps - 1) / warps, 1 << 20);
   k_gal_values<<<blocks, warps * 32, smem, h->stream>>>(L.n_agg, L.mptr, L.mrow, L.ptr, L.col,
                                                        L.val, L.agg, L.P, Lc.ptr, Lc.col, Lc.val,
@@ -1156,8 +1182,7 @@ static mgpbd_status galerkin_values_k(Handle *h, int l) {
     acc_global = (double *)h->tmp;
     smem = 0;
   }
-  MG_CUDA(cudaFuncSetAttribute(k_gal_values_k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem));
+  MG_TRY(galerkin_smem_limits());
   k_gal_values_k<<<blocks, warps * 32, smem, h->stream>>>(L.n_agg, k, L.mptr, L.mrow, L.ptr,
                                                          L.col, L.val, L.agg, L.P, L.gbptr,
                                                          L.gbcol, Lc.ptr, Lc.val, maxblk,

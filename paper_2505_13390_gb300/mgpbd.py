@@ -365,8 +365,8 @@ class Solver:
         _check(load().mgpbd_set_lanes(self.h, csr32, csr64, vert32, vert64), "set_lanes")
 
     def set_coarse_tail(self, enable: bool):
-        """The V-cycle below level 0 as one cooperative kernel (default) or as
-        separate launches; the same bits either way."""
+        """The V-cycle below level 0 as one cooperative kernel (True) or as
+        separate launches (False, the default); the same bits either way."""
         _check(load().mgpbd_set_coarse_tail(self.h, 1 if enable else 0), "set_coarse_tail")
 
     def set_wait_limit(self, polls: int):
