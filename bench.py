@@ -97,6 +97,11 @@ def parse():
     ap.add_argument("--arap-warmup", type=int, default=3)
     ap.add_argument("--assembled-steps", type=int, default=1)
     ap.add_argument("--assembled-warmup", type=int, default=1)
+    ap.add_argument("--ap-split", type=int, default=0, choices=[0, 1],
+                    help="the PCG recurrence's A.p from float-float pairs with residual "
+                         "replacement (1) or in FP64 (0)")
+    ap.add_argument("--no-ap-ab", action="store_true",
+                    help="skip the leg that times the headline with the other A.p form")
     return ap.parse_args()
 
 
@@ -235,6 +240,19 @@ def hbm_peak() -> float:
     return _measured_hbm() or 6800.0
 
 
+def ap_roofline(pr, split):
+    """Live CUDA-event figures of the recurrence's A.p (one launch = its
+    vertex and row pass) against the measured copy bandwidth."""
+    if not pr or not pr["launches"]:
+        return None
+    avg = pr["total_ms"] / pr["launches"]
+    ach = pr["bytes_per_launch"] / (avg / 1e3) / 1e9
+    return {"form": "float-float pairs, FP64 residual replacement" if split else "FP64",
+            "bound": "hbm", "achieved": ach, "peak": hbm_peak(), "unit": "GB/s",
+            "frac": ach / hbm_peak(), "bytes_per_launch": pr["bytes_per_launch"],
+            "avg_launch_ms": avg, "launches": pr["launches"]}
+
+
 def measure(mesh, params, steps, warmup, ws, profile=True):
     import torch
 
@@ -276,10 +294,12 @@ def measure(mesh, params, steps, warmup, ws, profile=True):
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     prof = g.profile_read() if profile else None
+    prof_ap = g.profile_read_ap() if profile else None
     if profile:
         g.profile(False)
     st = g.stats()
-    out = dict(ms=ms, launches=launches, clocks=ck, prof=prof, stats=st, create_s=create_s,
+    out = dict(ms=ms, launches=launches, clocks=ck, prof=prof, prof_ap=prof_ap, stats=st,
+               create_s=create_s,
                pcg=run.pcg[pcg0:], true_res=run.true_res[pcg0:], solver=g, runner=run)
     return out
 
@@ -549,7 +569,8 @@ def run_ours(args, ws, rank):
         ge.build()
     cpu = None
     mesh, params = workload(args.workload)
-    params = dict(params, precision=1, autotune=1, level0_op=args.level0_op, use_graphs=1)
+    params = dict(params, precision=1, autotune=1, level0_op=args.level0_op, use_graphs=1,
+                  ap_split=args.ap_split if args.level0_op == 1 else 0)
     res = measure(mesh, params, args.steps, args.warmup, ws)
     value, ms = job_rate(ws, args.steps, res["ms"])
     prof = res["prof"]
@@ -570,14 +591,29 @@ def run_ours(args, ws, rank):
         e2e_val, e2e_bytes = e2e(g, res["runner"], args.e2e_steps)
         e2e_val = e2e_val * ws
         e2e_pcg = list(res["runner"].pcg[pcg0:])
+    ap_prod = ap_roofline(res["prof_ap"], params["ap_split"])
     fp64 = None
     assembled = None
+    ap_ab = None
     levels = [g.level_info(l) for l in range(g.levels)]
     g.close()
     del res["solver"], res["runner"]
     torch.cuda.empty_cache()
+    if args.level0_op == 1 and not args.no_ap_ab:
+        # the same configuration with the other form of the recurrence's A.p,
+        # timed the same way from the same start
+        pb = dict(params, ap_split=1 - params["ap_split"])
+        rb = measure(mesh, pb, args.steps, args.warmup, ws)
+        msb = max_over_ranks(ws, rb["ms"])
+        ap_ab = {"ap_split": pb["ap_split"], "value": ws * args.steps / (msb / 1e3),
+                 "ms_per_step": msb / args.steps, "pcg_iters": rb["pcg"],
+                 "true_rel_res": rb["true_res"], "clocks": rb["clocks"],
+                 "ap_product": ap_roofline(rb["prof_ap"], pb["ap_split"])}
+        rb["solver"].close()
+        del rb
+        torch.cuda.empty_cache()
     if args.level0_op == 1 and not args.no_assembled:
-        pa = dict(params, level0_op=0)
+        pa = dict(params, level0_op=0, ap_split=0)
         ra = measure(mesh, pa, args.assembled_steps, args.assembled_warmup, ws)
         msa = max_over_ranks(ws, ra["ms"])
         pr = ra["prof"]
@@ -598,7 +634,7 @@ def run_ours(args, ws, rank):
         del ra
         torch.cuda.empty_cache()
     if not args.no_fp64:
-        p64 = dict(params, precision=0)
+        p64 = dict(params, precision=0, ap_split=0)
         r64 = measure(mesh, p64, args.fp64_steps, args.fp64_warmup, ws)
         ms64 = max_over_ranks(ws, r64["ms"])
         pr = r64["prof"]
@@ -608,7 +644,8 @@ def run_ours(args, ws, rank):
                 "steps": args.fp64_steps, "warmup": args.fp64_warmup,
                 "pcg_iters": r64["pcg"], "true_rel_res": r64["true_res"],
                 "clocks": r64["clocks"],
-                "smoother_sweep_gbs": a64, "smoother_sweep_frac": a64 / hbm}
+                "smoother_sweep_gbs": a64, "smoother_sweep_frac": a64 / hbm,
+                "ap_product": ap_roofline(r64["prof_ap"], 0)}
         r64["solver"].close()
     arap = None
     if not args.no_arap:
@@ -689,6 +726,9 @@ def run_ours(args, ws, rank):
         # FP64 |b - A dlambda| / |b| of each timed solve: the error statement
         # of the mixed-precision result (the oracle cannot run this size)
         "true_rel_res": res["true_res"],
+        # the PCG recurrence's A.p (vertex and row pass), timed live the same way
+        "ap_product": ap_prod,
+        "ap_other_form": ap_ab,
         "roofline": {"bound": "hbm",
                      "kernel": ("level-0 matrix-free weighted-Jacobi sweep, FP32 "
                                 "(k_mf_vertex + k_mf_row)") if args.level0_op == 1 else

@@ -118,6 +118,15 @@ typedef struct {
   int nk_vectors;       /* k near-kernel vectors (Sec. 4.3; the paper uses six), 1..8: P
                            has k columns per aggregate from a QR of each aggregate's
                            block of B, coarse levels have k unknowns per aggregate */
+  int ap_split;         /* 0: the PCG recurrence's A.p in FP64 (default); 1 (needs
+                           precision MGPBD_MIXED and level0_op 1): A.p matrix-free
+                           from float-float pairs (every FP64 operand stored as FP32
+                           high and low parts, products and sums by error-free
+                           transformations on the FP32 pipe, ~2^-46 relative per
+                           product), with the recursive residual replaced by an FP64
+                           b - A x whenever |r| has fallen tenfold since the solve's
+                           start or its last replacement.  x, r, p and the scalars
+                           stay FP64.  Instances with it set step outside a cohort. */
   uint64_t seed_nk, seed_agg, seed_col, seed_pow;
 } mgpbd_params;
 
@@ -129,6 +138,7 @@ typedef struct {
   double true_rel_res;  /* |b - A dlambda| / |b| recomputed in FP64 */
   double omega;         /* relaxation used for x (after backtracking) */
   double bnorm_after;   /* |b| at the updated state (backtracking only, else -1) */
+  int replacements;     /* residual replacements of the solve (params.ap_split) */
 } mgpbd_solve_info;
 
 typedef struct {
@@ -228,6 +238,16 @@ mgpbd_status mgpbd_solve(mgpbd_handle_t *h, const double *d_b, double *d_dl,
  * Sec. 4.4); device arrays of n_rows doubles. */
 mgpbd_status mgpbd_vcycle(mgpbd_handle_t *h, const double *d_r, double *d_z);
 
+/* y = A x with the level-0 matrix of eq. 3 (A = grad C M^-1 grad C^T +
+ * alpha~) at the last mgpbd_eval_assemble, in one of the forms the PCG
+ * recurrence's A.p takes (Sec. 4.4): form 0 the assembled CSR matrix in FP64;
+ * 1 matrix-free in FP64 (needs params.level0_op 1); 2 matrix-free from
+ * float-float pairs (needs params.ap_split).  d_x, d_y: device arrays of
+ * n_rows doubles, not overlapping.  MGPBD_E_INVALID when the form is not
+ * prepared on the instance (before the first mgpbd_eval_assemble, or its
+ * parameters off).  Synchronises. */
+mgpbd_status mgpbd_apply(mgpbd_handle_t *h, const double *d_x, double *d_y, int form);
+
 /* Counters and phase times.  Synchronises. */
 mgpbd_status mgpbd_stats(mgpbd_handle_t *h, mgpbd_stats_t *s);
 
@@ -305,6 +325,13 @@ mgpbd_status mgpbd_get_lambda(mgpbd_handle_t *h, double *lambda, double *dlambda
 mgpbd_status mgpbd_profile(mgpbd_handle_t *h, int enable);
 mgpbd_status mgpbd_profile_read(mgpbd_handle_t *h, double *total_ms, int64_t *launches,
                                 double *bytes_per_launch);
+/* The same for the A.p of the PCG recurrence (Sec. 4.4): one timed launch is
+ * the product of one iteration (matrix-free: its vertex and row passes, in
+ * FP64 or from float-float pairs per params.ap_split; assembled: the FP64 CSR
+ * product), its algorithmic bytes counted once per array (every value 8
+ * bytes in both matrix-free forms). */
+mgpbd_status mgpbd_profile_read_ap(mgpbd_handle_t *h, double *total_ms, int64_t *launches,
+                                   double *bytes_per_launch);
 unsigned long long mgpbd_launch_count(void);
 
 /* ---- serving: continuous batching of many instances ----

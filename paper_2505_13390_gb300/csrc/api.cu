@@ -31,69 +31,80 @@ static mgpbd_status grow_events(std::vector<cudaEvent_t> &ev, std::vector<int> &
   return MGPBD_OK;
 }
 
-// events for a chunk's graph are created before capture begins
+// events for a chunk's graph are created before capture begins (`pairs`
+// per channel)
 mgpbd_status prof_reserve_graph(Handle *h, int pairs) {
-  return grow_events(h->gev, h->gev_iter, pairs);
+  for (int ch = 0; ch < PROF_CH; ++ch) MG_TRY(grow_events(h->gev[ch], h->gev_iter[ch], pairs));
+  return MGPBD_OK;
 }
 
-mgpbd_status prof_begin(Handle *h) {
+mgpbd_status prof_begin(Handle *h, int ch) {
   if (!h->prof) return MGPBD_OK;
   if (h->capturing) {
-    if (h->gev_used + 1 > (int)h->gev.size() / 2) {
+    if (h->gev_used[ch] + 1 > (int)h->gev[ch].size() / 2) {
       set_error("profiling: event pool of the captured chunk is too small");
       return MGPBD_E_INVALID;
     }
-    MG_CUDA(cudaEventRecordWithFlags(h->gev[2 * h->gev_used], h->stream, cudaEventRecordExternal));
+    MG_CUDA(cudaEventRecordWithFlags(h->gev[ch][2 * h->gev_used[ch]], h->stream,
+                                     cudaEventRecordExternal));
     return MGPBD_OK;
   }
-  MG_TRY(grow_events(h->pev, h->pev_iter, h->pev_used + 1));
-  MG_CUDA(cudaEventRecord(h->pev[2 * h->pev_used], h->stream));
+  MG_TRY(grow_events(h->pev[ch], h->pev_iter[ch], h->pev_used[ch] + 1));
+  MG_CUDA(cudaEventRecord(h->pev[ch][2 * h->pev_used[ch]], h->stream));
   return MGPBD_OK;
 }
 
-mgpbd_status prof_end(Handle *h) {
+mgpbd_status prof_end(Handle *h, int ch) {
   if (!h->prof) return MGPBD_OK;
   if (h->capturing) {
-    MG_CUDA(cudaEventRecordWithFlags(h->gev[2 * h->gev_used + 1], h->stream,
+    MG_CUDA(cudaEventRecordWithFlags(h->gev[ch][2 * h->gev_used[ch] + 1], h->stream,
                                      cudaEventRecordExternal));
-    h->gev_iter[h->gev_used] = h->pcg_k;
-    h->gev_used++;
+    h->gev_iter[ch][h->gev_used[ch]] = h->pcg_k;
+    h->gev_used[ch]++;
     return MGPBD_OK;
   }
-  MG_CUDA(cudaEventRecord(h->pev[2 * h->pev_used + 1], h->stream));
-  h->pev_iter[h->pev_used] = h->pcg_k;
-  h->pev_used++;
+  MG_CUDA(cudaEventRecord(h->pev[ch][2 * h->pev_used[ch] + 1], h->stream));
+  h->pev_iter[ch][h->pev_used[ch]] = h->pcg_k;
+  h->pev_used[ch]++;
   return MGPBD_OK;
+}
+
+// Whether the timed launch of PCG iteration `it` ran in a solve that took
+// `iters` iterations: iteration k's A.p runs before its convergence test,
+// its V-cycle after it (kernels return at once after the solve has finished).
+static bool prof_ran(int ch, int it, int iters) {
+  return ch == PROF_AP ? it <= iters - 1 : it <= iters - 2;
 }
 
 // after a replay of the chunk that starts at PCG iteration first_iter (the
-// host has synchronised and copied the scalars): the V-cycle of iteration k
-// ran unless the solve had finished before it
+// host has synchronised and copied the scalars)
 mgpbd_status prof_harvest_graph(Handle *h, int first_iter) {
   const PcgScalars &s = *h->sc_host;
-  for (int k = 0; k < h->gev_used; ++k) {
-    const int it = first_iter + h->gev_iter[k];
-    if (s.done && it > s.iters - 2) continue;
-    float ms = 0.f;
-    MG_CUDA(cudaEventElapsedTime(&ms, h->gev[2 * k], h->gev[2 * k + 1]));
-    h->prof_ms += ms;
-    h->prof_n++;
-  }
+  for (int ch = 0; ch < PROF_CH; ++ch)
+    for (int k = 0; k < h->gev_used[ch]; ++k) {
+      const int it = first_iter + h->gev_iter[ch][k];
+      if (s.done && !prof_ran(ch, it, s.iters)) continue;
+      float ms = 0.f;
+      MG_CUDA(cudaEventElapsedTime(&ms, h->gev[ch][2 * k], h->gev[ch][2 * k + 1]));
+      h->prof_ms[ch] += ms;
+      h->prof_n[ch]++;
+    }
   return MGPBD_OK;
 }
 
 mgpbd_status prof_harvest(Handle *h, int iters) {
   if (!h->prof) return MGPBD_OK;
-  for (int k = 0; k < h->pev_used; ++k) {
-    // the V-cycle of PCG iteration k ran only if the solve had not finished
-    if (h->pev_iter[k] > iters - 2) continue;
-    float ms = 0.f;
-    MG_CUDA(cudaEventSynchronize(h->pev[2 * k + 1]));
-    MG_CUDA(cudaEventElapsedTime(&ms, h->pev[2 * k], h->pev[2 * k + 1]));
-    h->prof_ms += ms;
-    h->prof_n++;
+  for (int ch = 0; ch < PROF_CH; ++ch) {
+    for (int k = 0; k < h->pev_used[ch]; ++k) {
+      if (!prof_ran(ch, h->pev_iter[ch][k], iters)) continue;
+      float ms = 0.f;
+      MG_CUDA(cudaEventSynchronize(h->pev[ch][2 * k + 1]));
+      MG_CUDA(cudaEventElapsedTime(&ms, h->pev[ch][2 * k], h->pev[ch][2 * k + 1]));
+      h->prof_ms[ch] += ms;
+      h->prof_n[ch]++;
+    }
+    h->pev_used[ch] = 0;
   }
-  h->pev_used = 0;
   return MGPBD_OK;
 }
 
@@ -263,7 +274,8 @@ static mgpbd_status check_params(const mgpbd_params *p) {
       (p->autotune != 0 && p->autotune != 1) || (p->level0_op != 0 && p->level0_op != 1) ||
       (p->use_graphs != 0 && p->use_graphs != 1) ||
       (p->linear_solver != 0 && p->linear_solver != 1) || p->nk_vectors < 1 ||
-      p->nk_vectors > 8 ||
+      p->nk_vectors > 8 || (p->ap_split != 0 && p->ap_split != 1) ||
+      (p->ap_split == 1 && (p->precision != MGPBD_MIXED || p->level0_op != 1)) ||
       !(p->pcg_rtol >= 0.0) || !(p->power_safety > 0.0)) {
     set_error("invalid mgpbd_params");
     return MGPBD_E_INVALID;
@@ -278,8 +290,10 @@ static void destroy(Handle *h) {
   h->arena.release_all();
   if (h->sc_host) cudaFreeHost(h->sc_host);
   if (h->flag_host) cudaFreeHost(h->flag_host);
-  for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
-  for (cudaEvent_t e : h->gev) cudaEventDestroy(e);
+  for (int ch = 0; ch < PROF_CH; ++ch) {
+    for (cudaEvent_t e : h->pev[ch]) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->gev[ch]) cudaEventDestroy(e);
+  }
   if (h->pcg_graph) cudaGraphExecDestroy(h->pcg_graph);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
@@ -548,6 +562,7 @@ mgpbd_status mgpbd_default_params(mgpbd_params *p) {
   p->use_graphs = 0;
   p->linear_solver = 0;
   p->nk_vectors = 1;
+  p->ap_split = 0;
   p->seed_nk = 3;
   p->seed_agg = 4;
   p->seed_col = 5;
@@ -698,6 +713,20 @@ mgpbd_status mgpbd_vcycle(mgpbd_handle_t *hh, const double *d_r, double *d_z) {
   return MGPBD_OK;
 }
 
+mgpbd_status mgpbd_apply(mgpbd_handle_t *hh, const double *d_x, double *d_y, int form) {
+  Handle *h = H(hh);
+  if (!h || (h->m > 0 && (!d_x || !d_y)) || form < 0 || form > 2) return MGPBD_E_INVALID;
+  if (h->m == 0) return MGPBD_OK;
+  if (!h->lev[0].val || (form >= 1 && (h->p.level0_op != 1 || !h->vslot)) ||
+      (form == 2 && !h->p.ap_split)) {
+    set_error("mgpbd_apply: this form of A is not prepared on the instance");
+    return MGPBD_E_INVALID;
+  }
+  MG_TRY(apply_level0(h, form, d_x, d_y));
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  return MGPBD_OK;
+}
+
 mgpbd_status mgpbd_stats(mgpbd_handle_t *hh, mgpbd_stats_t *s) {
   Handle *h = H(hh);
   if (!h || !s) return MGPBD_E_INVALID;
@@ -730,9 +759,11 @@ mgpbd_status mgpbd_profile(mgpbd_handle_t *hh, int enable) {
   if (!h) return MGPBD_E_INVALID;
   MG_CUDA(cudaStreamSynchronize(h->stream));
   h->prof = enable != 0;
-  h->pev_used = 0;
-  h->prof_ms = 0.0;
-  h->prof_n = 0;
+  for (int ch = 0; ch < PROF_CH; ++ch) {
+    h->pev_used[ch] = 0;
+    h->prof_ms[ch] = 0.0;
+    h->prof_n[ch] = 0;
+  }
   return MGPBD_OK;
 }
 
@@ -741,8 +772,8 @@ mgpbd_status mgpbd_profile_read(mgpbd_handle_t *hh, double *total_ms, int64_t *l
   Handle *h = H(hh);
   if (!h) return MGPBD_E_INVALID;
   MG_CUDA(cudaStreamSynchronize(h->stream));
-  if (total_ms) *total_ms = h->prof_ms;
-  if (launches) *launches = h->prof_n;
+  if (total_ms) *total_ms = h->prof_ms[PROF_SWEEP];
+  if (launches) *launches = h->prof_n[PROF_SWEEP];
   if (bytes_per_launch) {
     const Level &L = h->lev[0];
     double vb = h->p.precision == MGPBD_MIXED ? 4.0 : 8.0;
@@ -758,6 +789,32 @@ mgpbd_status mgpbd_profile_read(mgpbd_handle_t *hh, double *total_ms, int64_t *l
       // CSR sweep: values and column indices once, row pointers, and four
       // vectors (x, b, 1/A_ii, x_new)
       *bytes_per_launch = (double)L.nnz * (vb + 4.0) + (double)L.n * (8.0 + 4.0 * vb);
+    }
+  }
+  return MGPBD_OK;
+}
+
+mgpbd_status mgpbd_profile_read_ap(mgpbd_handle_t *hh, double *total_ms, int64_t *launches,
+                                   double *bytes_per_launch) {
+  Handle *h = H(hh);
+  if (!h) return MGPBD_E_INVALID;
+  MG_CUDA(cudaStreamSynchronize(h->stream));
+  if (total_ms) *total_ms = h->prof_ms[PROF_AP];
+  if (launches) *launches = h->prof_n[PROF_AP];
+  if (bytes_per_launch) {
+    const Level &L = h->lev[0];
+    if (h->p.level0_op == 1) {
+      // vertex pass: per incidence a row id and an 8-byte value per gradient
+      // component (FP64, or FP32 high and low parts); row pointers, order, p
+      // and w once, u written.  Row pass: row gradients and vertex ids, u
+      // once, alpha~, p and q.  Every value is 8 bytes in both forms.
+      double ninc = 2.0 * h->E + 4.0 * h->T;
+      *bytes_per_launch = ninc * 28.0 + (h->N + 1.0) * 8.0 + h->N * 4.0 + (double)h->m * 8.0 +
+                          h->N * 8.0 + 3.0 * h->N * 8.0 + h->E * 32.0 + h->T * 112.0 +
+                          3.0 * h->N * 8.0 + 3.0 * h->m * 8.0;
+    } else {
+      // FP64 CSR product: values and columns once, row pointers, p once, q
+      *bytes_per_launch = (double)L.nnz * 12.0 + (double)L.n * 24.0;
     }
   }
   return MGPBD_OK;

@@ -138,6 +138,8 @@ struct Level {
   void *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
 };
 
+enum ProfChannel { PROF_SWEEP = 0, PROF_AP = 1, PROF_CH = 2 };
+
 struct Handle {
   cudaStream_t stream = nullptr;
   int device = 0;            // CUDA device that was current at create
@@ -162,6 +164,13 @@ struct Handle {
   double *ginc64 = nullptr, *u64 = nullptr;
   float4 *ginc4 = nullptr;  // FP32 gradient and row id (bits in .w) per incidence
   float *gd32 = nullptr, *gt32 = nullptr, *at32 = nullptr, *w32 = nullptr, *u32 = nullptr;
+  // float-float A.p (params.ap_split): low parts beside the FP32 high parts
+  // above (gradients in incidence and row order, alpha~, w), u's low part,
+  // and p as (high, low) pairs written by the p update
+  float *ginc_lo = nullptr, *gd_lo = nullptr, *gt_lo = nullptr, *at_lo = nullptr,
+        *w_lo = nullptr, *u_lo = nullptr;
+  float2 *p_df = nullptr;
+  int n_replace = 0;           // residual replacements of the current solve
   int mf_g32 = 8, mf_g64 = 4;  // lanes per vertex of the vertex pass (autotuned)
   // lanes forced by mgpbd_set_lanes (0 = autotuned or rule): CSR rows in FP32
   // and FP64, matrix-free vertices in FP32 and FP64
@@ -202,20 +211,21 @@ struct Handle {
   int last_pcg_iters = 0;
   bool want_colors = false;  // colour every level at setup even for Jacobi
   mgpbd_solve_info last{};
-  // optional event timing of the level-0 smoother sweeps (the dominant kernel)
+  // optional event timing, per channel (PROF_SWEEP: the level-0 smoother
+  // sweeps, the dominant kernel; PROF_AP: the PCG recurrence's A.p)
   bool prof = false;
-  std::vector<cudaEvent_t> pev;  // pairs
-  std::vector<int> pev_iter;     // PCG iteration of each pair (-1 = initial V-cycle)
-  int pev_used = 0;
-  int pcg_k = -1;                // PCG iteration being launched
-  double prof_ms = 0.0;
-  long long prof_n = 0;
+  std::vector<cudaEvent_t> pev[PROF_CH];  // pairs
+  std::vector<int> pev_iter[PROF_CH];     // PCG iteration of each pair (-1 = initial V-cycle)
+  int pev_used[PROF_CH] = {};
+  int pcg_k = -1;                         // PCG iteration being launched
+  double prof_ms[PROF_CH] = {};
+  long long prof_n[PROF_CH] = {};
   // the same timing inside a captured PCG chunk: event-record nodes of the
   // graph, read back after every replay
   bool capturing = false;
-  std::vector<cudaEvent_t> gev;  // pairs
-  std::vector<int> gev_iter;     // iteration within the chunk of each pair
-  int gev_used = 0;
+  std::vector<cudaEvent_t> gev[PROF_CH];  // pairs
+  std::vector<int> gev_iter[PROF_CH];     // iteration within the chunk of each pair
+  int gev_used[PROF_CH] = {};
   bool graph_prof = false;       // the captured graph records gev
   // CUDA graph of a chunk of PCG iterations, valid while `graph_gen` matches
   unsigned long long gen = 1;      // bumped whenever device pointers or setup change
@@ -229,8 +239,8 @@ struct Handle {
 // event pair around one launch of the profiled kernel (no-op when disabled)
 mgpbd_status prof_reserve_graph(Handle *h, int pairs);
 mgpbd_status prof_harvest_graph(Handle *h, int first_iter);
-mgpbd_status prof_begin(Handle *h);
-mgpbd_status prof_end(Handle *h);
+mgpbd_status prof_begin(Handle *h, int ch = PROF_SWEEP);
+mgpbd_status prof_end(Handle *h, int ch = PROF_SWEEP);
 // sums the pairs recorded during the last solve that belong to iterations that ran
 mgpbd_status prof_harvest(Handle *h, int iters);
 
@@ -292,6 +302,7 @@ mgpbd_status pcg_solve(Handle *h, const double *d_b, double *d_x, mgpbd_solve_in
 mgpbd_status pcg_begin(Handle *h, const double *d_b, double *d_x);
 mgpbd_status pcg_finish(Handle *h, const double *d_b, double *d_x, mgpbd_solve_info *info);
 mgpbd_status vcycle_apply(Handle *h, const double *d_r, double *d_z);
+mgpbd_status apply_level0(Handle *h, int form, const double *x, double *y);
 mgpbd_status dot_dd(Handle *h, const double *x, const double *y, int64_t n, double *d_out);
 mgpbd_status xpbd_step(Handle *h, mgpbd_solve_info *info);
 mgpbd_status power_method(Handle *h, int l);
@@ -378,6 +389,15 @@ template <>
 __device__ __forceinline__ double narrow<double>(double v) { return v; }
 __device__ __forceinline__ double widen(float v) { return f32_to_f64(v); }
 __device__ __forceinline__ double widen(double v) { return v; }
+
+// a binary64 value as a float-float pair (h, l): h = RN32(a), l = RN32(a - h).
+// a - h is exact in binary64 (a multiple of a's last place below half of h's,
+// at most 30 significant bits), so h + l carries 48 of a's 53 significant
+// bits inside the binary32 normal range; one FP64 subtraction.
+__device__ __forceinline__ float2 df_split(double a) {
+  const float h = f64_to_f32(a);
+  return make_float2(h, f64_to_f32(a - f32_to_f64(h)));
+}
 
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {

@@ -27,6 +27,9 @@
 namespace mg {
 
 constexpr int kMfVertexLanes = 8;
+// u = W J^T x holds four slots per vertex (x, y, z, unused), so that the pair
+// form's row pass gathers a vertex's components with one 16-byte load
+constexpr int kUStride = 4;
 
 // slot of vertex v in each incident row (create time)
 __global__ void k_vslot(int N, int E, const int32_t *edge, const int32_t *tet, const int64_t *vptr,
@@ -121,7 +124,7 @@ __device__ __forceinline__ void mf_vertex64_rows(int64_t w0, int64_t nw, int N,
     }
     double s = group_sum3<G>(a0, a1, a2, g);
     const int comp = group_sum3_component<G>(g);
-    if (valid && comp < 3 && (g & (G / 4 - 1)) == 0) u[3 * (int64_t)v + comp] = w[v] * s;
+    if (valid && comp < 3 && (g & (G / 4 - 1)) == 0) u[kUStride * (int64_t)v + comp] = w[v] * s;
   }
 }
 
@@ -168,7 +171,7 @@ __device__ __forceinline__ void mf_vertex32_rows(int64_t w0, int64_t nw, int N,
     }
     float s = group_sum3<G>(a0, a1, a2, g);
     const int comp = group_sum3_component<G>(g);
-    if (valid && comp < 3 && (g & (G / 4 - 1)) == 0) u[3 * (int64_t)v + comp] = w[v] * s;
+    if (valid && comp < 3 && (g & (G / 4 - 1)) == 0) u[kUStride * (int64_t)v + comp] = w[v] * s;
   }
 }
 
@@ -178,6 +181,230 @@ __global__ void __launch_bounds__(256, 8)
                   const float *w, const float *x, float *u, const PcgScalars *sc) {
   if (sc && is_done(sc)) return;
   mf_vertex32_rows<G>(HW_WARPS, N, vorder, vptr, ginc, w, x, u);
+}
+
+// 16-byte loads of the pair form's row pass (all arrays 256-byte aligned by
+// the arena): a vertex's three slots of u, and a tet row's twelve gradient
+// values.  (The FP32 and FP64 row passes keep scalar loads: with these, the
+// FP32 sweep needed more registers and ran slower.)
+__device__ __forceinline__ void ld_u(const float *u, int v, float &a, float &b, float &c) {
+  const float4 t = reinterpret_cast<const float4 *>(u)[v];
+  a = t.x;
+  b = t.y;
+  c = t.z;
+}
+__device__ __forceinline__ void ld_g12(const float *g, float *o) {
+  const float4 *q = reinterpret_cast<const float4 *>(g);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float4 t = q[k];
+    o[4 * k] = t.x;
+    o[4 * k + 1] = t.y;
+    o[4 * k + 2] = t.z;
+    o[4 * k + 3] = t.w;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A.p from float-float pairs (params.ap_split).  Every FP64 operand of the
+// product is held as a pair (h, l) of binary32 numbers with a = h + l to 48
+// bits (df_split).  A product of two pairs takes its rounding error from one
+// FMA (Dekker's product, the FMA form) and adds the two cross terms; sums
+// use Knuth's two-sum, whose error term is exact.  Every step issues on the
+// FP32 pipe; one product carries about 2^-46 relative error, a sum of n
+// terms about n 2^-47 of the sum of their magnitudes.
+// ---------------------------------------------------------------------------
+struct DF {
+  float h, l;
+};
+
+// s + e == a + b exactly (Knuth's two-sum, no ordering condition)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// acc += (gh + gl) (xh + xl); the term gl xl lies below 2^-47 of the product
+__device__ __forceinline__ void df_fma(DF &acc, float gh, float gl, float xh, float xl) {
+  const float p = __fmul_rn(gh, xh);
+  float e = __fmaf_rn(gh, xh, -p);  // gh xh - p, exactly
+  e = __fmaf_rn(gh, xl, e);
+  e = __fmaf_rn(gl, xh, e);
+  float s, t;
+  two_sum(acc.h, p, s, t);
+  acc.h = s;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(t, e));
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  float s, t;
+  two_sum(a.h, b.h, s, t);
+  return DF{s, __fadd_rn(__fadd_rn(a.l, b.l), t)};
+}
+
+// the pair with its low part below half a unit in the last place of h
+__device__ __forceinline__ DF df_norm(DF a) {
+  float s, t;
+  two_sum(a.h, a.l, s, t);
+  return DF{s, t};
+}
+
+__device__ __forceinline__ DF shfl_xor_df(DF v, int o) {
+  return DF{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+}
+
+// group_sum3 (reduce.cuh) for pairs: the same exchange pattern, with the
+// pairwise sums taken by df_add
+template <int G>
+__device__ __forceinline__ DF group_sum3_df(DF a0, DF a1, DF a2, int g) {
+  static_assert(G >= 4 && G <= 32, "group of 4..32 lanes");
+  constexpr int o1 = G / 2, o2 = G / 4;
+  const bool h1 = (g & o1) != 0, h2 = (g & o2) != 0;
+  const DF z{0.f, 0.f};
+  DF k0 = h1 ? a2 : a0, k1 = h1 ? z : a1;
+  const DF s0 = h1 ? a0 : a2, s1 = h1 ? a1 : z;
+  k0 = df_add(k0, shfl_xor_df(s0, o1));
+  k1 = df_add(k1, shfl_xor_df(s1, o1));
+  DF k = h2 ? k1 : k0;
+  const DF s = h2 ? k0 : k1;
+  k = df_add(k, shfl_xor_df(s, o2));
+#pragma unroll
+  for (int o = o2 / 2; o > 0; o >>= 1) k = df_add(k, shfl_xor_df(k, o));
+  return k;
+}
+
+// vertex pass of the pair product: u_v = w_v * sum_q g_q x_row(q) with the
+// high parts of g (and the row id) from the FP32 incidence records and the
+// low parts from `glo` (three per incidence); x and the result as pairs
+template <int G>
+__device__ __forceinline__ void mf_vertex_df_rows(int64_t w0, int64_t nw, int N,
+                                                  const int32_t *vorder, const int64_t *vptr,
+                                                  const float4 *ginc, const float *glo,
+                                                  const float *wh, const float *wl,
+                                                  const float2 *x, float *uh, float *ul) {
+  GROUP_ROWS_OVER(G, N, w0, nw) {
+    DF a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f};
+    const int v = valid ? vorder[i] : 0;
+    if (valid) {
+      int64_t q = vptr[v] + g;
+      const int64_t e = vptr[v + 1];
+      for (; q + 3 * G < e; q += 4 * G) {
+        float4 ev[4];
+        float2 xv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ev[k] = ginc[q + k * G];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) xv[k] = x[__float_as_int(ev[k].w)];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float *lo = glo + 3 * (q + k * G);
+          df_fma(a0, ev[k].x, lo[0], xv[k].x, xv[k].y);
+          df_fma(a1, ev[k].y, lo[1], xv[k].x, xv[k].y);
+          df_fma(a2, ev[k].z, lo[2], xv[k].x, xv[k].y);
+        }
+      }
+      for (; q < e; q += G) {
+        const float4 ea = ginc[q];
+        const float2 xa = x[__float_as_int(ea.w)];
+        const float *lo = glo + 3 * q;
+        df_fma(a0, ea.x, lo[0], xa.x, xa.y);
+        df_fma(a1, ea.y, lo[1], xa.x, xa.y);
+        df_fma(a2, ea.z, lo[2], xa.x, xa.y);
+      }
+    }
+    const DF s = group_sum3_df<G>(a0, a1, a2, g);
+    const int comp = group_sum3_component<G>(g);
+    if (valid && comp < 3 && (g & (G / 4 - 1)) == 0) {
+      DF r{0.f, 0.f};
+      df_fma(r, wh[v], wl[v], s.h, s.l);
+      r = df_norm(r);
+      uh[kUStride * (int64_t)v + comp] = r.h;
+      ul[kUStride * (int64_t)v + comp] = r.l;
+    }
+  }
+}
+
+template <int G>
+__global__ void k_mf_vertex_df(int N, const int32_t *vorder, const int64_t *vptr,
+                               const float4 *ginc, const float *glo, const float *wh,
+                               const float *wl, const float2 *x, float *uh, float *ul,
+                               const PcgScalars *sc) {
+  if (sc && is_done(sc)) return;
+  mf_vertex_df_rows<G>(HW_WARPS, N, vorder, vptr, ginc, glo, wh, wl, x, uh, ul);
+}
+
+// row pass of the pair product: q_i = sum_s g_{i,s}.u_{v_s} + alpha~_i p_i,
+// written in FP64 (h + l is exact there), with p.q folded into the PCG
+// scalars (each thread's share summed as a pair, the block sums in FP64)
+__global__ void __launch_bounds__(256, 4) k_mf_row_df(int E, int m, const int32_t *edge, const int32_t *tet,
+                            const float *gdh, const float *gdl, const float *gth,
+                            const float *gtl, const float *uh, const float *ul, const float *ath,
+                            const float *atl, const float2 *p, double *q, DotCtx c) {
+  if (is_done(c.sc)) return;
+  DF dot{0.f, 0.f};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    DF y{0.f, 0.f};
+    if (i < E) {
+      const int2 e = reinterpret_cast<const int2 *>(edge)[i];
+      float ah[3], al[3], bh[3], bl[3];
+      ld_u(uh, e.x, ah[0], ah[1], ah[2]);
+      ld_u(ul, e.x, al[0], al[1], al[2]);
+      ld_u(uh, e.y, bh[0], bh[1], bh[2]);
+      ld_u(ul, e.y, bl[0], bl[1], bl[2]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const DF d = df_add(DF{ah[k], al[k]}, DF{-bh[k], -bl[k]});
+        df_fma(y, gdh[3 * i + k], gdl[3 * i + k], d.h, d.l);
+      }
+    } else {
+      const int4 t4 = reinterpret_cast<const int4 *>(tet)[i - E];
+      const int t[4] = {t4.x, t4.y, t4.z, t4.w};
+      float gh[12], gl[12];
+      ld_g12(gth + 12 * (i - E), gh);
+      ld_g12(gtl + 12 * (i - E), gl);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        float h[3], l[3];
+        ld_u(uh, t[s], h[0], h[1], h[2]);
+        ld_u(ul, t[s], l[0], l[1], l[2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) df_fma(y, gh[3 * s + k], gl[3 * s + k], h[k], l[k]);
+      }
+    }
+    const float2 pi = p[i];
+    df_fma(y, ath[i], atl[i], pi.x, pi.y);
+    y = df_norm(y);
+    q[i] = f32_to_f64(y.h) + f32_to_f64(y.l);
+    df_fma(dot, pi.x, pi.y, y.h, y.l);
+  }
+  block_dot_finish(f32_to_f64(dot.h) + f32_to_f64(dot.l), c);
+}
+
+// low parts lo = RN32(a - hi) of FP64 values whose high parts are already
+// stored (hi = RN32(a)); incidence records hold theirs in .x .y .z
+__global__ void k_df_lo(int64_t n, const double *a, const float *hi, float *lo) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    lo[k] = f64_to_f32(a[k] - f32_to_f64(hi[k]));
+}
+
+__global__ void k_df_lo_inc(int64_t ninc, const double *g64, const float4 *g4, float *lo) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ninc;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const float4 h = g4[k];
+    lo[3 * k] = f64_to_f32(g64[3 * k] - f32_to_f64(h.x));
+    lo[3 * k + 1] = f64_to_f32(g64[3 * k + 1] - f32_to_f64(h.y));
+    lo[3 * k + 2] = f64_to_f32(g64[3 * k + 2] - f32_to_f64(h.z));
+  }
+}
+
+// p as pairs (the start of a solve; later the p update writes them)
+__global__ void k_df_split(int64_t n, const double *a, float2 *out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = df_split(a[k]);
 }
 
 enum {
@@ -207,8 +434,8 @@ __device__ __forceinline__ void mf_row_body(int vb, int vn, int E, int m, const 
     T y;
     if (i < E) {
       const T *n = gd + 3 * i;
-      const T *ua = u + 3 * (int64_t)edge[2 * i];
-      const T *ub = u + 3 * (int64_t)edge[2 * i + 1];
+      const T *ua = u + kUStride * (int64_t)edge[2 * i];
+      const T *ub = u + kUStride * (int64_t)edge[2 * i + 1];
       y = n[0] * (ua[0] - ub[0]);
       y = fma(n[1], ua[1] - ub[1], y);
       y = fma(n[2], ua[2] - ub[2], y);
@@ -218,7 +445,7 @@ __device__ __forceinline__ void mf_row_body(int vb, int vn, int E, int m, const 
       y = 0;
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
-        const T *uv = u + 3 * (int64_t)t[s];
+        const T *uv = u + kUStride * (int64_t)t[s];
         y = fma(gg[3 * s], uv[0], y);
         y = fma(gg[3 * s + 1], uv[1], y);
         y = fma(gg[3 * s + 2], uv[2], y);
@@ -258,18 +485,32 @@ mgpbd_status mf_create(Handle *h) {
   const bool mixed = h->p.precision == MGPBD_MIXED;
   MG_TRY(alloc_n(h->arena, &h->vslot, (size_t)ninc));
   MG_TRY(alloc_n(h->arena, &h->ginc64, 3 * (size_t)ninc));
-  MG_TRY(alloc_n(h->arena, &h->u64, 3 * (size_t)h->N));
+  MG_TRY(alloc_n(h->arena, &h->u64, kUStride * (size_t)h->N));
   if (mixed) {
     MG_TRY(alloc_n(h->arena, &h->ginc4, (size_t)ninc));
     MG_TRY(alloc_n(h->arena, &h->gd32, 3 * (size_t)h->E));
     MG_TRY(alloc_n(h->arena, &h->gt32, 12 * (size_t)h->T));
     MG_TRY(alloc_n(h->arena, &h->at32, (size_t)h->m));
     MG_TRY(alloc_n(h->arena, &h->w32, (size_t)h->N));
-    MG_TRY(alloc_n(h->arena, &h->u32, 3 * (size_t)h->N));
+    MG_TRY(alloc_n(h->arena, &h->u32, kUStride * (size_t)h->N));
     k_to_f32_mf<<<blocks_for(h->m, 256), 256, 0, h->stream>>>(h->m, h->alpha_t, h->at32);
     MG_LAUNCH("k_to_f32_mf(alpha)");
     k_to_f32_mf<<<blocks_for(h->N, 256), 256, 0, h->stream>>>(h->N, h->w, h->w32);
     MG_LAUNCH("k_to_f32_mf(w)");
+  }
+  if (h->p.ap_split) {
+    MG_TRY(alloc_n(h->arena, &h->ginc_lo, 3 * (size_t)ninc));
+    MG_TRY(alloc_n(h->arena, &h->gd_lo, 3 * (size_t)h->E));
+    MG_TRY(alloc_n(h->arena, &h->gt_lo, 12 * (size_t)h->T));
+    MG_TRY(alloc_n(h->arena, &h->at_lo, (size_t)h->m));
+    MG_TRY(alloc_n(h->arena, &h->w_lo, (size_t)h->N));
+    MG_TRY(alloc_n(h->arena, &h->u_lo, kUStride * (size_t)h->N));
+    MG_TRY(alloc_n(h->arena, &h->p_df, (size_t)h->m));
+    MG_CUDA(cudaMemsetAsync(h->p_df, 0, sizeof(float2) * (size_t)h->m, h->stream));
+    k_df_lo<<<blocks_for(h->m, 256), 256, 0, h->stream>>>(h->m, h->alpha_t, h->at32, h->at_lo);
+    MG_LAUNCH("k_df_lo(alpha)");
+    k_df_lo<<<blocks_for(h->N, 256), 256, 0, h->stream>>>(h->N, h->w, h->w32, h->w_lo);
+    MG_LAUNCH("k_df_lo(w)");
   }
   k_vslot<<<blocks_for(h->N, 128), 128, 0, h->stream>>>(h->N, h->E, h->edge, h->tet, h->vptr,
                                                        h->vrow, h->vslot);
@@ -321,6 +562,18 @@ mgpbd_status mf_prepare(Handle *h) {
     k_to_f32_mf<<<blocks_for(12 * (int64_t)h->T, 256), 256, 0, h->stream>>>(12 * (int64_t)h->T,
                                                                            h->gt, h->gt32);
     MG_LAUNCH("k_to_f32_mf(gt)");
+  }
+  if (h->p.ap_split) {
+    const int64_t ninc = 2 * (int64_t)h->E + 4 * (int64_t)h->T;
+    k_df_lo_inc<<<blocks_for(ninc, 256), 256, 0, h->stream>>>(ninc, h->ginc64, h->ginc4,
+                                                             h->ginc_lo);
+    MG_LAUNCH("k_df_lo_inc");
+    k_df_lo<<<blocks_for(3 * (int64_t)h->E, 256), 256, 0, h->stream>>>(3 * (int64_t)h->E, h->gd,
+                                                                      h->gd32, h->gd_lo);
+    MG_LAUNCH("k_df_lo(gd)");
+    k_df_lo<<<blocks_for(12 * (int64_t)h->T, 256), 256, 0, h->stream>>>(
+        12 * (int64_t)h->T, h->gt, h->gt32, h->gt_lo);
+    MG_LAUNCH("k_df_lo(gt)");
   }
   return MGPBD_OK;
 }
@@ -464,8 +717,22 @@ static mgpbd_status mf_vertex(Handle *h, const float *x, int G = 0, bool check_d
   return MGPBD_OK;
 }
 
+// u = W J^T x from pairs (params.ap_split): high parts into u32 (free
+// outside the V-cycle's sweeps), low parts into u_lo; the lanes of the FP64
+// vertex pass, whose place it takes
+static mgpbd_status mf_vertex(Handle *h, const float2 *x, int G = 0, bool check_done = true) {
+  if (G == 0) G = h->force_vert64 ? h->force_vert64 : h->mf_g64;
+  const PcgScalars *sc = check_done ? h->sc : nullptr;
+  MF_G_DISPATCH(G, (k_mf_vertex_df<GG><<<mf_vertex_blocks(h, GG), 256, 0, h->stream>>>(
+                       h->N, h->vorder, h->vptr, h->ginc4, h->ginc_lo, h->w32, h->w_lo, x,
+                       h->u32, h->u_lo, sc)));
+  MG_LAUNCH("k_mf_vertex_df");
+  return MGPBD_OK;
+}
+
 // Times the vertex pass with 4, 8 and 16 lanes per vertex in each precision
-// the solve uses and keeps the fastest (params.autotune).
+// the solve uses and keeps the fastest (params.autotune); with ap_split the
+// A.p's lanes are timed on its pair form.
 mgpbd_status mf_autotune(Handle *h) {
   if (h->m == 0 || !h->vslot) return MGPBD_OK;
   auto pick = [&](auto *x, int *out) -> mgpbd_status {
@@ -488,13 +755,28 @@ mgpbd_status mf_autotune(Handle *h) {
     }
     return MGPBD_OK;
   };
-  MG_TRY(pick((const double *)h->pr, &h->mf_g64));
+  if (h->p.ap_split)
+    MG_TRY(pick((const float2 *)h->p_df, &h->mf_g64));
+  else
+    MG_TRY(pick((const double *)h->pr, &h->mf_g64));
   if (h->p.precision == MGPBD_MIXED) MG_TRY(pick((const float *)h->lev[0].b, &h->mf_g32));
   return MGPBD_OK;
 }
 
-// A.p in FP64 with p.Ap folded into the PCG scalars
-mgpbd_status mf_apply_pq(Handle *h, const double *p, double *q, const DotCtx &c) {
+// A.p with p.Ap folded into the PCG scalars: in FP64, or (pairs) from the
+// pairs of p that the p update wrote beside it
+mgpbd_status mf_apply_pq_form(Handle *h, bool pairs, const double *p, double *q,
+                              const DotCtx &c) {
+  if (pairs) {
+    MG_TRY(mf_vertex(h, (const float2 *)h->p_df));
+    const int grid =
+        std::min(mf_grid(h->m, 256), wave_blocks((const void *)k_mf_row_df, 256));
+    k_mf_row_df<<<grid, 256, 0, h->stream>>>(h->E, h->m, h->edge, h->tet, h->gd32, h->gd_lo,
+                                             h->gt32, h->gt_lo, h->u32, h->u_lo, h->at32,
+                                             h->at_lo, h->p_df, q, c);
+    MG_LAUNCH("k_mf_row_df(A.p)");
+    return MGPBD_OK;
+  }
   MG_TRY(mf_vertex(h, p));
   const int grid = std::min(mf_grid(h->m, 256),
                             wave_blocks((const void *)k_mf_row<double, MF_APPLY_DOT>, 256));
@@ -502,6 +784,29 @@ mgpbd_status mf_apply_pq(Handle *h, const double *p, double *q, const DotCtx &c)
       h->E, h->m, h->edge, h->tet, h->gd, h->gt, h->u64, h->alpha_t, p, nullptr, nullptr, 0.0, q,
       c);
   MG_LAUNCH("k_mf_row(A.p)");
+  return MGPBD_OK;
+}
+
+mgpbd_status mf_apply_pq(Handle *h, const double *p, double *q, const DotCtx &c) {
+  return mf_apply_pq_form(h, h->p.ap_split != 0, p, q, c);
+}
+
+// r = b - A x in FP64 (the residual replacement that accompanies the pair
+// form of A.p)
+mgpbd_status mf_residual64(Handle *h, const double *x, const double *b, double *r) {
+  MG_TRY(mf_vertex(h, x, 0, false));
+  DotCtx c{};
+  c.sc = h->sc;
+  k_mf_row<double, MF_RESID><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
+      h->E, h->m, h->edge, h->tet, h->gd, h->gt, h->u64, h->alpha_t, x, b, nullptr, 0.0, r, c);
+  MG_LAUNCH("k_mf_row(b - A x)");
+  return MGPBD_OK;
+}
+
+// pairs of an FP64 vector (p at the start of a solve)
+mgpbd_status mf_split(Handle *h, const double *a, float2 *out, int64_t n) {
+  k_df_split<<<blocks_for(n, 256), 256, 0, h->stream>>>(n, a, out);
+  MG_LAUNCH("k_df_split");
   return MGPBD_OK;
 }
 

@@ -226,6 +226,10 @@ __device__ __forceinline__ AT row_dot(const int64_t *ptr, const int32_t *col, co
 
 // matrix-free level-0 products (mfree.cu)
 mgpbd_status mf_apply_pq(Handle *h, const double *p, double *q, const DotCtx &c);
+mgpbd_status mf_apply_pq_form(Handle *h, bool pairs, const double *p, double *q,
+                              const DotCtx &c);
+mgpbd_status mf_residual64(Handle *h, const double *x, const double *b, double *r);
+mgpbd_status mf_split(Handle *h, const double *a, float2 *out, int64_t n);
 template <class T>
 mgpbd_status mf_level0(Handle *h, int mode, const T *x, const T *b, const T *dinv, T omega,
                        T *out);

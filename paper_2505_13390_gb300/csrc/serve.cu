@@ -97,6 +97,9 @@ static size_t estimate_bytes_desc(const mgpbd_mesh_desc *d, const mgpbd_params *
   for (int64_t j = 0; j < 4 * (int64_t)T; ++j) nnz += (double)deg[d->tet[j]];
   double m = (double)E + T, ninc = 2.0 * E + 4.0 * T;
   double b = nnz * (4 + 8 + 4 + 2 + 1) + m * 400.0 + N * 200.0 + ninc * 48.0 + (2 << 20);
+  // float-float A.p: low parts of the gradients (incidence and row order),
+  // alpha~ and w, u's low part, p as pairs
+  if (p->ap_split) b += ninc * 12.0 + (double)E * 12.0 + (double)T * 48.0 + m * 12.0 + N * 16.0;
   const double nc = std::min(m, (double)std::max(p->coarse_max, 1));
   b += 24.0 * nc * nc;
   return (size_t)b;

@@ -147,9 +147,11 @@ __global__ void k_top_prep(int64_t n, const double *r, T *bl, const T *dinv, T o
 }
 
 // p = z + beta p, two entries per thread (16-byte loads; p and z are
-// 256-byte aligned)
+// 256-byte aligned); with pdf, p also as float-float pairs for the pair form
+// of A.p (params.ap_split)
 __device__ __forceinline__ void p_update_body(int vb, int vn, int64_t n, double *p,
-                                              const double *z, const PcgScalars *sc) {
+                                              const double *z, const PcgScalars *sc,
+                                              float2 *pdf = nullptr) {
   const double be = sc->beta;
   const int64_t n2 = n / 2, h2 = (n2 + 1) / 2;  // pairs k and k + h2 per thread
   double2 *p2 = reinterpret_cast<double2 *>(p);
@@ -166,18 +168,30 @@ __device__ __forceinline__ void p_update_body(int vb, int vn, int64_t n, double 
     pa.x = fma(be, pa.x, za.x);
     pa.y = fma(be, pa.y, za.y);
     p2[k] = pa;
+    if (pdf) {
+      const float2 s0 = df_split(pa.x), s1 = df_split(pa.y);
+      reinterpret_cast<float4 *>(pdf)[k] = make_float4(s0.x, s0.y, s1.x, s1.y);
+    }
     if (two) {
       pb.x = fma(be, pb.x, zb.x);
       pb.y = fma(be, pb.y, zb.y);
       p2[k2] = pb;
+      if (pdf) {
+        const float2 s0 = df_split(pb.x), s1 = df_split(pb.y);
+        reinterpret_cast<float4 *>(pdf)[k2] = make_float4(s0.x, s0.y, s1.x, s1.y);
+      }
     }
   }
-  if ((n & 1) && vb == 0 && threadIdx.x == 0) p[n - 1] = fma(be, p[n - 1], z[n - 1]);
+  if ((n & 1) && vb == 0 && threadIdx.x == 0) {
+    p[n - 1] = fma(be, p[n - 1], z[n - 1]);
+    if (pdf) pdf[n - 1] = df_split(p[n - 1]);
+  }
 }
 
-__global__ void k_p_update(int64_t n, double *p, const double *z, const PcgScalars *sc) {
+__global__ void k_p_update(int64_t n, double *p, const double *z, const PcgScalars *sc,
+                           float2 *pdf) {
   if (is_done(sc)) return;
-  p_update_body(blockIdx.x, gridDim.x, n, p, z, sc);
+  p_update_body(blockIdx.x, gridDim.x, n, p, z, sc, pdf);
 }
 
 __global__ void k_pcg_init(PcgScalars *sc, unsigned int *bar) {
@@ -989,7 +1003,8 @@ __global__ void kb_gather(const CohortMember *mem, int K, PcgScalars *out) {
 // ---- host side -------------------------------------------------------------
 bool cohort_eligible(const Handle *h) {
   const mgpbd_params &p = h->p;
-  return p.precision == MGPBD_MIXED && p.level0_op == 1 && p.smoother == MGPBD_SMOOTH_JACOBI &&
+  return p.precision == MGPBD_MIXED && p.level0_op == 1 && !p.ap_split &&
+         p.smoother == MGPBD_SMOOTH_JACOBI &&
          p.smooth_sweeps == 2 && p.nk_vectors == 1 && p.linear_solver == 0 && h->have_setup &&
          h->L >= 2 && h->m > 0;
 }
@@ -1448,6 +1463,27 @@ mgpbd_status vcycle_apply(Handle *h, const double *d_r, double *d_z) {
   return vcycle_top(h, d_r, d_z, false, -1);
 }
 
+// y = A x at level 0 in one of the forms of the PCG recurrence's product:
+// 0 FP64 CSR, 1 FP64 matrix-free, 2 matrix-free from float-float pairs
+mgpbd_status apply_level0(Handle *h, int form, const double *x, double *y) {
+  const int m = h->m;
+  const Level &L = h->lev[0];
+  k_pcg_init<<<1, 1, 0, h->stream>>>(h->sc, h->gbar);
+  MG_LAUNCH("k_pcg_init");
+  DotCtx c = make_ctx(h, DOT_STORE, &h->sc->tr2);  // x.Ax lands in a scratch scalar
+  if (form == 0) {
+    const int G = group_for(h, L, true);
+    DISPATCH_G(G, (k_spmv_pq<GG, double, double>
+                   <<<std::min(row_blocks(m, GG),
+                               wave_blocks((const void *)k_spmv_pq<GG, double, double>, 256)),
+                      256, 0, h->stream>>>(m, L.ptr, L.col, L.val, x, y, c)));
+    MG_LAUNCH("k_spmv_pq");
+    return MGPBD_OK;
+  }
+  if (form == 2) MG_TRY(mf_split(h, x, h->p_df, m));
+  return mf_apply_pq_form(h, form == 2, x, y, c);
+}
+
 mgpbd_status dot_dd(Handle *h, const double *x, const double *y, int64_t n, double *d_out) {
   return launch_dot(h, x, y, n, DOT_STORE, 0, d_out);
 }
@@ -1463,6 +1499,9 @@ static mgpbd_status pcg_iteration(Handle *h, double *x) {
   // FP64 in both modes: rounding A's values to FP32 perturbs entries of size
   // ~1e4 by ~1e-3, far above alpha~ (~1e-7), and the FP32 operator is then
   // numerically indefinite on the stiff workloads (p.Ap <= 0).
+  // (params.ap_split: the matrix-free product from float-float pairs, with
+  // residual replacement in pcg_solve)
+  MG_TRY(prof_begin(h, PROF_AP));
   if (h->p.level0_op == 1) {
     MG_TRY(mf_apply_pq(h, p, q, cpq));
   } else {
@@ -1472,6 +1511,7 @@ static mgpbd_status pcg_iteration(Handle *h, double *x) {
                       256, 0, h->stream>>>(m, L.ptr, L.col, L.val, p, q, cpq)));
     MG_LAUNCH("k_spmv_pq");
   }
+  MG_TRY(prof_end(h, PROF_AP));
   // the update also starts the V-cycle (right-hand side, first Jacobi sweep)
   const bool jac = top_jacobi(h);
   if (h->p.precision == MGPBD_MIXED)
@@ -1488,8 +1528,8 @@ static mgpbd_status pcg_iteration(Handle *h, double *x) {
         jac ? (double *)L.x : nullptr);
   MG_LAUNCH("k_xr_update");
   MG_TRY(vcycle_top(h, r, z, true, DOT_RZ));
-  k_p_update<<<blocks_for(std::max(1, (m / 2 + 1) / 2), 256), 256, 0, h->stream>>>(m, p, z,
-                                                                                 h->sc);
+  k_p_update<<<blocks_for(std::max(1, (m / 2 + 1) / 2), 256), 256, 0, h->stream>>>(
+      m, p, z, h->sc, h->p.ap_split ? h->p_df : nullptr);
   MG_LAUNCH("k_p_update");
   return MGPBD_OK;
 }
@@ -1500,7 +1540,7 @@ mgpbd_status pcg_begin(Handle *h, const double *b, double *x) {
   MG_CUDA(cudaEventRecord(h->ev0, h->stream));
   double *r = h->pr, *z = h->pz, *p = h->pp;
   h->pcg_k = -1;
-  h->pev_used = 0;
+  for (int ch = 0; ch < PROF_CH; ++ch) h->pev_used[ch] = 0;
   k_pcg_init<<<1, 1, 0, h->stream>>>(h->sc, h->gbar);
   MG_LAUNCH("k_pcg_init");
   MG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * m, h->stream));
@@ -1508,6 +1548,8 @@ mgpbd_status pcg_begin(Handle *h, const double *b, double *x) {
   MG_TRY(launch_dot(h, b, b, m, DOT_BNORM, 0));
   MG_TRY(vcycle_top(h, r, z, false, DOT_RZ0));
   MG_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->stream));
+  h->n_replace = 0;
+  if (h->p.ap_split) MG_TRY(mf_split(h, p, h->p_df, m));
   return MGPBD_OK;
 }
 
@@ -1526,6 +1568,15 @@ mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *
   // (the legacy default stream cannot be captured: graphs need the caller's own stream)
   const bool graphs = h->p.use_graphs && h->stream != nullptr &&
                       h->stream != cudaStreamLegacy && h->stream != cudaStreamPerThread;
+  // Residual replacement (params.ap_split): the recursive residual drifts
+  // from b - A x by the rounding of every A.p, ~2^-46 relative in the pair
+  // form against 2^-53 in FP64.  Whenever |r| has fallen tenfold since the
+  // start or the last replacement, r is recomputed as b - A x in FP64 between
+  // two chunks (the reliable-update scheme for CG: only r is replaced, the
+  // search direction and the scalars carry on), so the drift that remains at
+  // convergence is that of the iterations after the last replacement, made
+  // on residuals at most ten times the final one.
+  double rr_ref = -1.0;
   while (launched < h->p.pcg_maxiter) {
     int c = std::min(chunk, h->p.pcg_maxiter - launched);
     const bool replay = graphs && c == chunk;
@@ -1539,7 +1590,7 @@ mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *
         if (h->prof) MG_TRY(prof_reserve_graph(h, c * 2 * std::max(1, h->p.smooth_sweeps) + 8));
         cudaGraph_t gr = nullptr;
         unsigned long long n0 = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
-        h->gev_used = 0;
+        for (int ch = 0; ch < PROF_CH; ++ch) h->gev_used[ch] = 0;
         MG_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         h->capturing = true;
         mgpbd_status cs = MGPBD_OK;
@@ -1579,6 +1630,15 @@ mgpbd_status pcg_solve(Handle *h, const double *b, double *x, mgpbd_solve_info *
     MG_CUDA(cudaStreamSynchronize(h->stream));
     if (replay && h->graph_prof) MG_TRY(prof_harvest_graph(h, launched - c));
     if (h->sc_host->done) break;
+    if (h->p.ap_split && h->p.level0_op == 1) {
+      const double rr = h->sc_host->rr;
+      if (rr_ref < 0.0) rr_ref = h->sc_host->bnorm2;
+      if (rr <= 1e-2 * rr_ref) {
+        MG_TRY(mf_residual64(h, x, b, h->pr));
+        rr_ref = rr;
+        h->n_replace++;
+      }
+    }
   }
   return pcg_finish(h, b, x, info);
 }
@@ -1606,6 +1666,7 @@ mgpbd_status pcg_finish(Handle *h, const double *b, double *x, mgpbd_solve_info 
   info->bnorm = bn;
   info->rel_res = bn > 0 ? sqrt(s.rr) / bn : 0.0;
   info->true_rel_res = bn > 0 ? sqrt(s.tr2) / bn : 0.0;
+  info->replacements = h->n_replace;
   info->status = s.done ? s.status : MGPBD_W_NOT_CONVERGED;
   if (bn == 0.0) info->status = MGPBD_OK;
   h->last_pcg_iters = s.iters;

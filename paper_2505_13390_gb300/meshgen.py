@@ -103,7 +103,8 @@ def default_params(**over) -> Dict:
         level0_op=0,  # 1: matrix-free level-0 products through the constraint gradients
         use_graphs=0,  # 1: replay PCG iteration chunks from a captured CUDA graph
         linear_solver=0,  # 0: MGPCG; 1: XPBD's diagonal step (eq. 4), the baseline
-        precision=0,  # 0 = FP64, 1 = mixed (FP32 V-cycle / A.p)
+        precision=0,  # 0 = FP64, 1 = mixed (FP32 V-cycle, FP64 recurrences)
+        ap_split=0,  # 1: the recurrence's A.p from float-float pairs (mixed, matrix-free)
         seed_nk=3,
         seed_agg=4,
         seed_col=5,

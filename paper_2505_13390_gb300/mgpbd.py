@@ -38,7 +38,7 @@ class Params(C.Structure):
         ("power_safety", C.c_double), ("coarse_max", C.c_int), ("max_levels", C.c_int),
         ("precision", C.c_int), ("backtrack", C.c_int), ("autotune", C.c_int),
         ("level0_op", C.c_int), ("use_graphs", C.c_int), ("linear_solver", C.c_int),
-        ("nk_vectors", C.c_int), ("seed_nk", C.c_uint64), ("seed_agg", C.c_uint64), ("seed_col", C.c_uint64),
+        ("nk_vectors", C.c_int), ("ap_split", C.c_int), ("seed_nk", C.c_uint64), ("seed_agg", C.c_uint64), ("seed_col", C.c_uint64),
         ("seed_pow", C.c_uint64),
     ]
 
@@ -46,7 +46,7 @@ class Params(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("pcg_iters", C.c_int), ("status", C.c_int), ("bnorm", C.c_double),
                 ("rel_res", C.c_double), ("true_rel_res", C.c_double), ("omega", C.c_double),
-                ("bnorm_after", C.c_double)]
+                ("bnorm_after", C.c_double), ("replacements", C.c_int)]
 
     def as_dict(self) -> Dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -127,6 +127,9 @@ SIGNATURES = {
     "mgpbd_profile": (_i, [_vp, _i]),
     "mgpbd_profile_read": (_i, [_vp, C.POINTER(C.c_double), C.POINTER(_i64),
                                 C.POINTER(C.c_double)]),
+    "mgpbd_apply": (_i, [_vp, _vp, _vp, _i]),
+    "mgpbd_profile_read_ap": (_i, [_vp, C.POINTER(C.c_double), C.POINTER(_i64),
+                                   C.POINTER(C.c_double)]),
     "mgpbd_launch_count": (C.c_ulonglong, []),
     "mgpbd_true_residual_noalloc": (_i, [_vp, _vp, _vp, _vp]),
     "mgpbd_convert": (_i, [_vp, _vp, _vp, _vp, _i64, _vp]),
@@ -338,6 +341,13 @@ class Solver:
         _check(load().mgpbd_vcycle(self.h, _ptr(r), _ptr(z)), "vcycle")
         return z
 
+    def apply(self, x, form: int = 0):
+        """y = A x at level 0: form 0 FP64 CSR, 1 FP64 matrix-free, 2 float-float pairs."""
+        torch = self.torch
+        y = torch.zeros(self.m, dtype=torch.float64, device=x.device)
+        _check(load().mgpbd_apply(self.h, _ptr(x), _ptr(y), int(form)), "apply")
+        return y
+
     # ---- measurement ----------------------------------------------------
     def profile(self, enable: bool):
         _check(load().mgpbd_profile(self.h, 1 if enable else 0), "profile")
@@ -346,6 +356,13 @@ class Solver:
         ms, n, b = C.c_double(), C.c_int64(), C.c_double()
         _check(load().mgpbd_profile_read(self.h, C.byref(ms), C.byref(n), C.byref(b)),
                "profile_read")
+        return {"total_ms": ms.value, "launches": n.value, "bytes_per_launch": b.value}
+
+    def profile_read_ap(self) -> Dict:
+        """The same totals for the PCG recurrence's A.p."""
+        ms, n, b = C.c_double(), C.c_int64(), C.c_double()
+        _check(load().mgpbd_profile_read_ap(self.h, C.byref(ms), C.byref(n), C.byref(b)),
+               "profile_read_ap")
         return {"total_ms": ms.value, "launches": n.value, "bytes_per_launch": b.value}
 
     # ---- inspection -----------------------------------------------------

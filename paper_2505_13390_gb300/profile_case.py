@@ -1,13 +1,14 @@
 """Small cases of the benchmark's kernels for ncu captures.
 
-    python -m paper_2505_13390_gb300.profile_case AxBxC PREC PCG_ITERS [AUTOTUNE [OP]]
+    python -m paper_2505_13390_gb300.profile_case AxBxC PREC PCG_ITERS [AUTOTUNE [OP [SPLIT]]]
 
 builds a hex block of the bench recipe (0.005 m cells, 10% jitter, 5 tets
 per cell, alpha = 1e-10, bottom face pinned), runs the frame prologue, one
 evaluation/assembly, the AMG setup and one MGPCG solve capped at PCG_ITERS
 iterations, then exits 0.  PREC is 1 for mixed precision, 0 for FP64; OP is
 1 for the matrix-free level-0 operator, 0 (default) for the assembled CSR
-matrix.
+matrix; SPLIT 1 takes the recurrence's A.p from float-float pairs (needs PREC
+1 and OP 1).
 
     python -m paper_2505_13390_gb300.profile_case chainN [REPEATS]
 
@@ -34,9 +35,10 @@ def block(argv):
     prec, iters = int(argv[1]), int(argv[2])
     tune = int(argv[3]) if len(argv) > 3 else 0
     op = int(argv[4]) if len(argv) > 4 else 0
+    split = int(argv[5]) if len(argv) > 5 else 0
     mesh = hex_block(a, b, c, h=0.005, jitter=0.1, alpha=1e-10, pin="y0", seed=1)
     p = default_params(omega_x=0.1, precision=prec, pcg_maxiter=iters, autotune=tune,
-                       level0_op=op)
+                       level0_op=op, ap_split=split)
     g = Solver(mesh, p)
     g.begin_frame()
     g.eval_assemble()

@@ -178,3 +178,132 @@ def test_set_lanes_rejects_other_shapes():
     g.set_lanes()
     assert g.lanes(0)["csr32"] in (4, 8, 16, 32)
     g.close()
+
+
+# ---- A.p from float-float pairs (params.ap_split) ----------------------------
+# The recurrence's product from binary32 (high, low) pairs: ~2^-46 relative
+# per product, sums by two-sum, then residual replacement in FP64.
+
+
+def _magnitude(mesh, p, gd, gt, x):
+    """sum over the matrix-free terms of row i of their magnitudes:
+    (|J| W |J|^T |x|)_i + alpha~_i |x_i|, the scale of the rounding error of
+    any evaluation of (J W J^T + alpha~) x that forms those terms."""
+    N, E = mesh.n_verts, mesh.n_dist
+    w = np.asarray(mesh.inv_mass, float)
+    ax = np.abs(x)
+    u = np.zeros((N, 3))
+    dist = np.asarray(mesh.dist).reshape(-1, 2)
+    tet = np.asarray(mesh.tet).reshape(-1, 4)
+    for s in range(2):
+        np.add.at(u, dist[:, s], np.abs(gd) * ax[:E, None])
+    for s in range(4):
+        np.add.at(u, tet[:, s], np.abs(gt[:, s, :]) * ax[E:, None])
+    u *= w[:, None]
+    M = np.zeros(len(x))
+    M[:E] = (np.abs(gd) * (u[dist[:, 0]] + u[dist[:, 1]])).sum(1)
+    M[E:] = sum((np.abs(gt[:, s, :]) * u[tet[:, s]]).sum(1) for s in range(4))
+    at = np.asarray(mesh.alpha, float) / p["dt"] ** 2
+    return M + at * ax
+
+
+@pytest.mark.parametrize("name", ["cloth8", "hex3", "block6", "beam40"])
+def test_pair_product_elementwise(name):
+    """mgpbd_apply form 2 against the exact A x (the oracle's FP64 matrix of
+    eq. 3, at the same positions), row by row within 2^-40 of the magnitude
+    of the row's terms; the FP64 forms within 2^-47."""
+    import scipy.sparse as sp
+
+    from paper_2505_13390_gb300.mgpbd import Solver
+    mesh, p = CASES[name]()
+    p = dict(p, precision=1, level0_op=1, ap_split=1)
+    g = Solver(mesh, p)
+    g.begin_frame()
+    g.eval_assemble()
+    o = Oracle(mesh, p)
+    o.begin_frame()
+    o.eval_assemble()
+    ptr, col, val = o.matrix(0)
+    _, _, gd, gt = o.constraints()
+    m = len(ptr) - 1
+    A = sp.csr_matrix((val, col, ptr), shape=(m, m))
+    rng = np.random.default_rng(11)
+    for trial in range(3):
+        # signs mixed, magnitudes spread over six decades
+        x = rng.standard_normal(m) * 10.0 ** rng.uniform(-3, 3, m)
+        exact = A @ x
+        M = _magnitude(mesh, p, gd, gt, x)
+        xt = torch.from_numpy(x).cuda()
+        for form, bound in ((2, 2.0 ** -40), (1, 2.0 ** -47), (0, 2.0 ** -47)):
+            y = g.apply(xt, form).cpu().numpy()
+            rel = np.abs(y - exact) / np.maximum(M, 1e-300)
+            print(f"\n{name} trial {trial} form {form}: max |err| / magnitude {rel.max():.2e}")
+            assert rel.max() <= bound, (form, rel.max())
+    g.close()
+
+
+@pytest.mark.parametrize("name,iters", STIFF)
+def test_pair_form_vs_oracle(name, iters):
+    """The benchmark configuration with the pair form of A.p: the same bars as
+    with the FP64 product (error against the oracle within ten times that of
+    the FP64 path, FP64 true residuals within four times its), and the
+    residual replacement taking place."""
+    xo, _ = oracle_run(name, 1e-6, iters)
+    e64, t64 = fp64_default(name, iters)
+    from paper_2505_13390_gb300.mgpbd import Solver
+    mesh, p = CASES[name]()
+    p = dict(p, pcg_rtol=1e-6, pcg_maxiter=5000, precision=1, level0_op=1, use_graphs=1,
+             autotune=1, ap_split=1)
+    g = Solver(mesh, p, stream=torch.cuda.Stream())
+    g.begin_frame()
+    xg, tres, reps = [], [], []
+    for _ in range(iters):
+        d = g.iterate()
+        assert d["ret"] == 0, d
+        xg.append(g.get_state()[0].copy())
+        tres.append(d["true_rel_res"])
+        reps.append(d["replacements"])
+    g.close()
+    err = max_err(xg, xo, scale_of(name))
+    print(f"\n{name} pairs: err {err:.2e} (FP64 default {e64:.2e}); replacements {reps}; "
+          f"true residuals " + " ".join(f"{t:.1e}" for t in tres))
+    assert err <= max(10 * e64, 1e-9)
+    assert max(tres) <= 4 * max(max(t64), 1e-6)
+    assert min(reps) >= 1
+
+
+def test_pair_form_graphs_match_plain_launches():
+    """Replacement happens between chunks of eight iterations in both launch
+    modes, so a CUDA-graph replay and plain launches give the same bits."""
+    from paper_2505_13390_gb300.mgpbd import Solver
+    mesh, p = CASES["block6"]()
+    out = []
+    for graphs in (0, 1):
+        q = dict(p, precision=1, level0_op=1, ap_split=1, use_graphs=graphs)
+        g = Solver(mesh, q, stream=torch.cuda.Stream())
+        g.begin_frame()
+        ds = [g.iterate() for _ in range(2)]
+        out.append((g.get_state()[0].copy(), [d["pcg_iters"] for d in ds],
+                    [d["replacements"] for d in ds]))
+        g.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1:] == out[1][1:]
+
+
+def test_pair_form_parameters():
+    """ap_split needs mixed precision and the matrix-free level 0; form 2 of
+    mgpbd_apply needs ap_split."""
+    from paper_2505_13390_gb300 import mgpbd
+    mesh, p = CASES["cloth8"]()
+    for bad in (dict(ap_split=1, precision=0, level0_op=1),
+                dict(ap_split=1, precision=1, level0_op=0), dict(ap_split=2)):
+        with pytest.raises(mgpbd.MgpbdError):
+            mgpbd.Solver(mesh, dict(p, **bad))
+    g = mgpbd.Solver(mesh, dict(p, precision=1, level0_op=1))
+    g.begin_frame()
+    g.eval_assemble()
+    x = torch.ones(g.m, dtype=torch.float64, device="cuda")
+    g.apply(x, 1)
+    with pytest.raises(mgpbd.MgpbdError):
+        g.apply(x, 2)
+    g.close()
