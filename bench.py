@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--serve-arms", default="batched_streams,batched_cohort,serial_mixed,plain_fp64",
                     help="comma list of: " + ", ".join(SERVE_ARMS))
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving legs (e.g. --serve-requests 512) and print them")
     ap.add_argument("--no-serve-saturated", action="store_true",
                     help="skip the batched arms' run with every request at t = 0")
     ap.add_argument("--no-arap", action="store_true",
@@ -567,6 +569,11 @@ def run_ours(args, ws, rank):
     from paper_2505_13390_gb300.meshgen import workload
     if not os.path.exists(os.path.join(ROOT, "paper_2505_13390_gb300", "libmgpbd.so")):
         ge.build()
+    if args.serve_only:
+        if rank == 0:
+            print(json.dumps({"metric": "p50/p99 step latency and global XPBD iters/s, served",
+                              "serving": serving(args)}))
+        return
     cpu = None
     mesh, params = workload(args.workload)
     params = dict(params, precision=1, autotune=1, level0_op=args.level0_op, use_graphs=1,

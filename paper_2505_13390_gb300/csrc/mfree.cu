@@ -103,23 +103,18 @@ __device__ __forceinline__ void mf_vertex64_rows(int64_t w0, int64_t nw, int N,
     if (valid) {
       int64_t q = vptr[v] + g;
       const int64_t e = vptr[v + 1];
-      for (; q + 3 * G < e; q += 4 * G) {
+      for (; q < e; q += 4 * G) {  // batches of four, the last one guarded
         double xv[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) xv[k] = x[vrow[q + k * G]];
+        for (int k = 0; k < 4; ++k) xv[k] = q + k * G < e ? x[vrow[q + k * G]] : 0.0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const double *gq = ginc + 3 * (q + k * G);
-          a0 = fma(gq[0], xv[k], a0);
-          a1 = fma(gq[1], xv[k], a1);
-          a2 = fma(gq[2], xv[k], a2);
-        }
-      }
-      for (; q < e; q += G) {
-        const double xa = x[vrow[q]];
-        a0 = fma(ginc[3 * q], xa, a0);
-        a1 = fma(ginc[3 * q + 1], xa, a1);
-        a2 = fma(ginc[3 * q + 2], xa, a2);
+        for (int k = 0; k < 4; ++k)
+          if (q + k * G < e) {
+            const double *gq = ginc + 3 * (q + k * G);
+            a0 = fma(gq[0], xv[k], a0);
+            a1 = fma(gq[1], xv[k], a1);
+            a2 = fma(gq[2], xv[k], a2);
+          }
       }
     }
     double s = group_sum3<G>(a0, a1, a2, g);
@@ -147,26 +142,23 @@ __device__ __forceinline__ void mf_vertex32_rows(int64_t w0, int64_t nw, int N,
     if (valid) {
       int64_t q = vptr[v] + g;
       const int64_t e = vptr[v + 1];
-      for (; q + 3 * G < e; q += 4 * G) {
+      // batches of four incidences per lane, the last one guarded, so that
+      // a ragged tail costs one round of loads and gathers, not one per entry
+      for (; q < e; q += 4 * G) {
         float4 ev[4];
         float xv[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) ev[k] = ginc[q + k * G];
+        for (int k = 0; k < 4; ++k)
+          ev[k] = q + k * G < e ? ginc[q + k * G] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) xv[k] = x[__float_as_int(ev[k].w)];
+        for (int k = 0; k < 4; ++k) xv[k] = q + k * G < e ? x[__float_as_int(ev[k].w)] : 0.f;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          a0 = fmaf(ev[k].x, xv[k], a0);
-          a1 = fmaf(ev[k].y, xv[k], a1);
-          a2 = fmaf(ev[k].z, xv[k], a2);
-        }
-      }
-      for (; q < e; q += G) {
-        const float4 ea = ginc[q];
-        const float xa = x[__float_as_int(ea.w)];
-        a0 = fmaf(ea.x, xa, a0);
-        a1 = fmaf(ea.y, xa, a1);
-        a2 = fmaf(ea.z, xa, a2);
+        for (int k = 0; k < 4; ++k)
+          if (q + k * G < e) {
+            a0 = fmaf(ev[k].x, xv[k], a0);
+            a1 = fmaf(ev[k].y, xv[k], a1);
+            a2 = fmaf(ev[k].z, xv[k], a2);
+          }
       }
     }
     float s = group_sum3<G>(a0, a1, a2, g);
@@ -289,28 +281,23 @@ __device__ __forceinline__ void mf_vertex_df_rows(int64_t w0, int64_t nw, int N,
     if (valid) {
       int64_t q = vptr[v] + g;
       const int64_t e = vptr[v + 1];
-      for (; q + 3 * G < e; q += 4 * G) {
+      for (; q < e; q += 4 * G) {  // batches of four, the last one guarded
         float4 ev[4];
         float2 xv[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) ev[k] = ginc[q + k * G];
+        for (int k = 0; k < 4; ++k)
+          ev[k] = q + k * G < e ? ginc[q + k * G] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) xv[k] = x[__float_as_int(ev[k].w)];
+        for (int k = 0; k < 4; ++k)
+          xv[k] = q + k * G < e ? x[__float_as_int(ev[k].w)] : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float *lo = glo + 3 * (q + k * G);
-          df_fma(a0, ev[k].x, lo[0], xv[k].x, xv[k].y);
-          df_fma(a1, ev[k].y, lo[1], xv[k].x, xv[k].y);
-          df_fma(a2, ev[k].z, lo[2], xv[k].x, xv[k].y);
-        }
-      }
-      for (; q < e; q += G) {
-        const float4 ea = ginc[q];
-        const float2 xa = x[__float_as_int(ea.w)];
-        const float *lo = glo + 3 * q;
-        df_fma(a0, ea.x, lo[0], xa.x, xa.y);
-        df_fma(a1, ea.y, lo[1], xa.x, xa.y);
-        df_fma(a2, ea.z, lo[2], xa.x, xa.y);
+        for (int k = 0; k < 4; ++k)
+          if (q + k * G < e) {
+            const float *lo = glo + 3 * (q + k * G);
+            df_fma(a0, ev[k].x, lo[0], xv[k].x, xv[k].y);
+            df_fma(a1, ev[k].y, lo[1], xv[k].x, xv[k].y);
+            df_fma(a2, ev[k].z, lo[2], xv[k].x, xv[k].y);
+          }
       }
     }
     const DF s = group_sum3_df<G>(a0, a1, a2, g);
