@@ -120,6 +120,12 @@ struct Level {
   double *B = nullptr;       // near-kernel of this level
   int64_t *mptr = nullptr;   // members of each aggregate (ascending rows)
   int32_t *mrow = nullptr;
+  // level 0 with the matrix-free operator and one column of P: each row's
+  // position in the member list (-1: in no aggregate) and P in member order
+  // (the V-cycle's precision), so that the residual is written and the
+  // restriction reads it in member order
+  int32_t *mpos = nullptr;
+  void *Pm = nullptr;
   int max_members = 0;
   int max_coarse_row = 0;    // longest row of level+1 (Galerkin smem size), in aggregates
   // k > 1 near-kernel vectors: dead columns of P and the aggregate-level

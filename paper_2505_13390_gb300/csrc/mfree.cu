@@ -103,18 +103,23 @@ __device__ __forceinline__ void mf_vertex64_rows(int64_t w0, int64_t nw, int N,
     if (valid) {
       int64_t q = vptr[v] + g;
       const int64_t e = vptr[v + 1];
-      for (; q < e; q += 4 * G) {  // batches of four, the last one guarded
+      for (; q + 3 * G < e; q += 4 * G) {
         double xv[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) xv[k] = q + k * G < e ? x[vrow[q + k * G]] : 0.0;
+        for (int k = 0; k < 4; ++k) xv[k] = x[vrow[q + k * G]];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (q + k * G < e) {
-            const double *gq = ginc + 3 * (q + k * G);
-            a0 = fma(gq[0], xv[k], a0);
-            a1 = fma(gq[1], xv[k], a1);
-            a2 = fma(gq[2], xv[k], a2);
-          }
+        for (int k = 0; k < 4; ++k) {
+          const double *gq = ginc + 3 * (q + k * G);
+          a0 = fma(gq[0], xv[k], a0);
+          a1 = fma(gq[1], xv[k], a1);
+          a2 = fma(gq[2], xv[k], a2);
+        }
+      }
+      for (; q < e; q += G) {
+        const double xa = x[vrow[q]];
+        a0 = fma(ginc[3 * q], xa, a0);
+        a1 = fma(ginc[3 * q + 1], xa, a1);
+        a2 = fma(ginc[3 * q + 2], xa, a2);
       }
     }
     double s = group_sum3<G>(a0, a1, a2, g);
@@ -142,23 +147,26 @@ __device__ __forceinline__ void mf_vertex32_rows(int64_t w0, int64_t nw, int N,
     if (valid) {
       int64_t q = vptr[v] + g;
       const int64_t e = vptr[v + 1];
-      // batches of four incidences per lane, the last one guarded, so that
-      // a ragged tail costs one round of loads and gathers, not one per entry
-      for (; q < e; q += 4 * G) {
+      for (; q + 3 * G < e; q += 4 * G) {
         float4 ev[4];
         float xv[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          ev[k] = q + k * G < e ? ginc[q + k * G] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < 4; ++k) ev[k] = ginc[q + k * G];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) xv[k] = q + k * G < e ? x[__float_as_int(ev[k].w)] : 0.f;
+        for (int k = 0; k < 4; ++k) xv[k] = x[__float_as_int(ev[k].w)];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (q + k * G < e) {
-            a0 = fmaf(ev[k].x, xv[k], a0);
-            a1 = fmaf(ev[k].y, xv[k], a1);
-            a2 = fmaf(ev[k].z, xv[k], a2);
-          }
+        for (int k = 0; k < 4; ++k) {
+          a0 = fmaf(ev[k].x, xv[k], a0);
+          a1 = fmaf(ev[k].y, xv[k], a1);
+          a2 = fmaf(ev[k].z, xv[k], a2);
+        }
+      }
+      for (; q < e; q += G) {
+        const float4 ea = ginc[q];
+        const float xa = x[__float_as_int(ea.w)];
+        a0 = fmaf(ea.x, xa, a0);
+        a1 = fmaf(ea.y, xa, a1);
+        a2 = fmaf(ea.z, xa, a2);
       }
     }
     float s = group_sum3<G>(a0, a1, a2, g);
@@ -281,23 +289,28 @@ __device__ __forceinline__ void mf_vertex_df_rows(int64_t w0, int64_t nw, int N,
     if (valid) {
       int64_t q = vptr[v] + g;
       const int64_t e = vptr[v + 1];
-      for (; q < e; q += 4 * G) {  // batches of four, the last one guarded
+      for (; q + 3 * G < e; q += 4 * G) {
         float4 ev[4];
         float2 xv[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          ev[k] = q + k * G < e ? ginc[q + k * G] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < 4; ++k) ev[k] = ginc[q + k * G];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          xv[k] = q + k * G < e ? x[__float_as_int(ev[k].w)] : make_float2(0.f, 0.f);
+        for (int k = 0; k < 4; ++k) xv[k] = x[__float_as_int(ev[k].w)];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (q + k * G < e) {
-            const float *lo = glo + 3 * (q + k * G);
-            df_fma(a0, ev[k].x, lo[0], xv[k].x, xv[k].y);
-            df_fma(a1, ev[k].y, lo[1], xv[k].x, xv[k].y);
-            df_fma(a2, ev[k].z, lo[2], xv[k].x, xv[k].y);
-          }
+        for (int k = 0; k < 4; ++k) {
+          const float *lo = glo + 3 * (q + k * G);
+          df_fma(a0, ev[k].x, lo[0], xv[k].x, xv[k].y);
+          df_fma(a1, ev[k].y, lo[1], xv[k].x, xv[k].y);
+          df_fma(a2, ev[k].z, lo[2], xv[k].x, xv[k].y);
+        }
+      }
+      for (; q < e; q += G) {
+        const float4 ea = ginc[q];
+        const float2 xa = x[__float_as_int(ea.w)];
+        const float *lo = glo + 3 * q;
+        df_fma(a0, ea.x, lo[0], xa.x, xa.y);
+        df_fma(a1, ea.y, lo[1], xa.x, xa.y);
+        df_fma(a2, ea.z, lo[2], xa.x, xa.y);
       }
     }
     const DF s = group_sum3_df<G>(a0, a1, a2, g);
@@ -400,7 +413,8 @@ enum {
   MF_APPLY_DOT = 2,
   MF_APPLY = kMfApply,
   MF_SWEEP_Z = 4,
-  MF_SWEEP_ZDOT = 5
+  MF_SWEEP_ZDOT = 5,
+  MF_RESID_MEMBER = kMfResidMember
 };
 
 // row pass: y_i = sum_s g_{i,s}.u_{v_s} + alpha~_i x_i, then
@@ -409,12 +423,15 @@ enum {
 //   MF_APPLY_DOT  out = y, with x.y folded into the PCG scalars (DOT_PQ)
 //   MF_SWEEP_Z    z = x + omega D^-1 (b - y) widened to FP64
 //   MF_SWEEP_ZDOT the same, with r.z folded into the PCG scalars
+//   MF_RESID_MEMBER out[pos_i] = b - y for rows in an aggregate (the
+//                 residual in member order, for the restriction)
 template <class T, int MODE>
 __device__ __forceinline__ void mf_row_body(int vb, int vn, int E, int m, const int32_t *edge,
                                             const int32_t *tet, const T *gd, const T *gt,
                                             const T *u, const T *at, const T *x, const T *b,
                                             const T *dinv, T omega, T *out, const DotCtx &c,
-                                            double *z, const double *rr) {
+                                            double *z, const double *rr,
+                                            const int32_t *pos = nullptr) {
   double acc = 0.0;
   for (int64_t i = vb * (int64_t)blockDim.x + threadIdx.x; i < m;
        i += (int64_t)vn * blockDim.x) {
@@ -442,6 +459,10 @@ __device__ __forceinline__ void mf_row_body(int vb, int vn, int E, int m, const 
     y = fma(at[i], xi, y);
     if (MODE == MF_SWEEP) out[i] = fma(omega, (b[i] - y) * dinv[i], xi);
     else if (MODE == MF_RESID) out[i] = b[i] - y;
+    else if (MODE == MF_RESID_MEMBER) {
+      const int32_t q = pos[i];
+      if (q >= 0) out[q] = b[i] - y;
+    }
     else if (MODE == MF_APPLY) out[i] = y;
     else if (MODE == MF_APPLY_DOT) {
       out[i] = y;
@@ -459,10 +480,10 @@ template <class T, int MODE>
 __global__ void k_mf_row(int E, int m, const int32_t *edge, const int32_t *tet, const T *gd,
                          const T *gt, const T *u, const T *at, const T *x, const T *b,
                          const T *dinv, T omega, T *out, DotCtx c, double *z = nullptr,
-                         const double *rr = nullptr) {
+                         const double *rr = nullptr, const int32_t *pos = nullptr) {
   if (is_done(c.sc)) return;
   mf_row_body<T, MODE>(blockIdx.x, gridDim.x, E, m, edge, tet, gd, gt, u, at, x, b, dinv, omega,
-                       out, c, z, rr);
+                       out, c, z, rr, pos);
 }
 
 // ---------------------------------------------------------------------------
@@ -814,6 +835,10 @@ mgpbd_status mf_level0<float>(Handle *h, int mode, const float *x, const float *
   else if (mode == MF_APPLY)
     k_mf_row<float, MF_APPLY><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
         h->E, h->m, h->edge, h->tet, h->gd32, h->gt32, h->u32, h->at32, x, b, dinv, omega, out, c);
+  else if (mode == MF_RESID_MEMBER)
+    k_mf_row<float, MF_RESID_MEMBER><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
+        h->E, h->m, h->edge, h->tet, h->gd32, h->gt32, h->u32, h->at32, x, b, dinv, omega, out, c,
+        nullptr, nullptr, h->lev[0].mpos);
   else
     k_mf_row<float, MF_RESID><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
         h->E, h->m, h->edge, h->tet, h->gd32, h->gt32, h->u32, h->at32, x, b, dinv, omega, out, c);
@@ -833,6 +858,10 @@ mgpbd_status mf_level0<double>(Handle *h, int mode, const double *x, const doubl
   else if (mode == MF_APPLY)
     k_mf_row<double, MF_APPLY><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
         h->E, h->m, h->edge, h->tet, h->gd, h->gt, h->u64, h->alpha_t, x, b, dinv, omega, out, c);
+  else if (mode == MF_RESID_MEMBER)
+    k_mf_row<double, MF_RESID_MEMBER><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
+        h->E, h->m, h->edge, h->tet, h->gd, h->gt, h->u64, h->alpha_t, x, b, dinv, omega, out, c,
+        nullptr, nullptr, h->lev[0].mpos);
   else
     k_mf_row<double, MF_RESID><<<mf_grid(h->m, 256), 256, 0, h->stream>>>(
         h->E, h->m, h->edge, h->tet, h->gd, h->gt, h->u64, h->alpha_t, x, b, dinv, omega, out, c);

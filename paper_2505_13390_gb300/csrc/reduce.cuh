@@ -233,7 +233,7 @@ mgpbd_status mf_split(Handle *h, const double *a, float2 *out, int64_t n);
 template <class T>
 mgpbd_status mf_level0(Handle *h, int mode, const T *x, const T *b, const T *dinv, T omega,
                        T *out);
-constexpr int kMfSweep = 0, kMfResid = 1, kMfApply = 3;
+constexpr int kMfSweep = 0, kMfResid = 1, kMfApply = 3, kMfResidMember = 6;
 mgpbd_status mf_autotune(Handle *h);
 
 // The last level-0 sweep of a top V-cycle can write the preconditioned

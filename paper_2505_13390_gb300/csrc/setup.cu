@@ -592,6 +592,38 @@ static mgpbd_status read_int(Handle *h, const int *d, int *out) {
 
 static size_t tsize(const Handle *h) { return h->p.precision == MGPBD_MIXED ? 4 : 8; }
 
+// Level 0's member order (matrix-free operator, one column of P): pos_i =
+// the position of row i in the member list (-1 before: rows in no
+// aggregate), and P in member order in the V-cycle's precision.  The
+// level-0 residual is then written, and restricted, in member order: the
+// restriction streams P and r instead of gathering them row by row, with
+// the same products summed in the same order.
+__global__ void k_member_order(int na, const int64_t *mptr, const int32_t *mrow, const double *P,
+                               const float *P32, double *Pm64, float *Pm32, int32_t *pos) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < na; a += gridDim.x * blockDim.x)
+    for (int64_t q = mptr[a]; q < mptr[a + 1]; ++q) {
+      const int i = mrow[q];
+      pos[i] = (int32_t)q;
+      if (Pm64) Pm64[q] = P[i];
+      else Pm32[q] = P32[i];
+    }
+}
+
+static mgpbd_status member_order_level0(Handle *h) {
+  Level &L = h->lev[0];
+  const bool mixed = h->p.precision == MGPBD_MIXED;
+  if (!L.mpos) {
+    MG_TRY(alloc_n(h->arena, &L.mpos, (size_t)L.n));
+    MG_TRY(h->arena.alloc(&L.Pm, tsize(h) * (size_t)L.n));
+  }
+  MG_CUDA(cudaMemsetAsync(L.mpos, 0xff, sizeof(int32_t) * (size_t)L.n, h->stream));
+  k_member_order<<<blocks_for(L.n_agg, 128), 128, 0, h->stream>>>(
+      L.n_agg, L.mptr, L.mrow, L.P, L.P32, mixed ? nullptr : (double *)L.Pm,
+      mixed ? (float *)L.Pm : nullptr, L.mpos);
+  MG_LAUNCH("k_member_order");
+  return MGPBD_OK;
+}
+
 // n-sized and nnz-sized buffers of a level, grown on demand
 static mgpbd_status ensure_level(Handle *h, int l, int n, int64_t nnz) {
   Level &L = h->lev[l];
@@ -1264,6 +1296,7 @@ mgpbd_status amg_setup(Handle *h) {
                                                                        L.P32);
       MG_LAUNCH("k_to_f32(P)");
     }
+    if (l == 0 && k == 1 && h->p.level0_op == 1) MG_TRY(member_order_level0(h));
     MG_TRY(k == 1 ? galerkin_values(h, l) : galerkin_values_k(h, l));
     ++l;
   }

@@ -385,69 +385,23 @@ __device__ __forceinline__ void restrict_aggs(int64_t w, int64_t nw, int na, int
   }
 }
 
-// The residual and the restriction in one pass: a warp per aggregate
-// computes the residuals of its member rows itself (G lanes per row, the
-// row_dot and group sum of resid_rows), hands member j's residual to lane j
-// of the 32-member chunk, and sums P_ic r_i in restrict_aggs' order.  Every
-// rounding is that of resid_rows followed by restrict_aggs; the residual
-// vector is neither written nor read back, and no launch or grid barrier
-// separates the two steps.
-constexpr int kMaxNearKernel = 8;
-template <int G, class T>
-__device__ __forceinline__ void resid_restrict_aggs(int64_t w, int64_t nw, int na, int k,
-                                                    const int64_t *mptr, const int32_t *mrow,
-                                                    const T *P, const int64_t *ptr,
-                                                    const int32_t *col, const T *val, const T *b,
-                                                    const T *x, T *bc, const T *dinv_c, T om_c,
-                                                    T *xc) {
-  constexpr int R = 32 / G;  // member rows per round
-  const int lane = threadIdx.x & 31, gi = lane / G, g = lane % G;
-  for (int64_t a = w; a < na; a += nw) {
-    const int64_t q0 = mptr[a], q1 = mptr[a + 1];
-    T acc[kMaxNearKernel];
-#pragma unroll
-    for (int c = 0; c < kMaxNearKernel; ++c) acc[c] = 0;
-    for (int64_t base = q0; base < q1; base += 32) {
-      T rm = 0;  // residual of member base + lane
-      for (int j = 0; j < 32 && base + j < q1; j += R) {
-        const int64_t qm = base + j + gi;
-        const bool valid = qm < q1;
-        const int i = valid ? mrow[qm] : 0;
-        T s = valid ? row_dot<G, T, T, T>(ptr, col, val, x, i, g) : (T)0;
-        s = group_sum<G>(s);
-        const T ri = valid ? b[i] - s : (T)0;
-        const int from = lane - j;  // the group that computed this lane's member
-        const T got = __shfl_sync(0xffffffffu, ri, (from >= 0 && from < R) ? from * G : 0);
-        if (from >= 0 && from < R) rm = got;
-      }
-      if (base + lane < q1) {
-        const int i = mrow[base + lane];
-#pragma unroll
-        for (int c = 0; c < kMaxNearKernel; ++c)
-          if (c < k) acc[c] = fma(P[(int64_t)i * k + c], rm, acc[c]);
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < kMaxNearKernel; ++c) {
-      if (c >= k) break;
-      const T t = warp_sum(acc[c]);
-      if (lane == 0) {
-        const int64_t ac = a * k + c;
-        bc[ac] = t;
-        if (xc) xc[ac] = om_c * (t * dinv_c[ac]);
-      }
+// restrict_aggs with one column of P, on P and r stored in member order
+// (level 0, matrix-free): the same products in the same order, streamed
+template <class T>
+__global__ void k_restrict_member(int na, const int64_t *mptr, const T *Pm, const T *rm, T *bc,
+                                  const PcgScalars *sc, const T *dinv_c, T om_c, T *xc) {
+  if (is_done(sc)) return;
+  const int lane = threadIdx.x & 31;
+  for (int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; a < na;
+       a += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    T acc = 0;
+    for (int64_t q = mptr[a] + lane; q < mptr[a + 1]; q += 32) acc = fma(Pm[q], rm[q], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      bc[a] = acc;
+      if (xc) xc[a] = om_c * (acc * dinv_c[a]);
     }
   }
-}
-
-template <int G, class T>
-__global__ void k_resid_restrict(int na, int k, const int64_t *mptr, const int32_t *mrow,
-                                 const T *P, const int64_t *ptr, const int32_t *col,
-                                 const T *val, const T *b, const T *x, T *bc,
-                                 const PcgScalars *sc, const T *dinv_c, T om_c, T *xc) {
-  if (is_done(sc)) return;
-  resid_restrict_aggs<G, T>(HW_WARPS, na, k, mptr, mrow, P, ptr, col, val, b, x, bc, dinv_c,
-                            om_c, xc);
 }
 
 template <class T>
@@ -857,12 +811,12 @@ __global__ void __launch_bounds__(256) k_coarse_tail(TailDesc<T> d, unsigned int
       x = x2;
       x2 = t;
     }
+    DISPATCH_G(L.G, (resid_rows<GG, T>(w0, nw, L.n, L.ptr, L.col, L.val, L.b, x, L.r)));
+    if (!sync()) return;
     const TailLevel<T> &Lc = d.lev[l + 1];
     const bool c_jac = l + 1 < d.coarsest;  // the coarse level's first sweep rides along
-    DISPATCH_G(L.G, (resid_restrict_aggs<GG, T>(w0, nw, L.n_agg, 1, L.mptr, L.mrow, L.P, L.ptr,
-                                                L.col, L.val, L.b, x, Lc.b,
-                                                c_jac ? Lc.dinv : nullptr, Lc.omega,
-                                                c_jac ? Lc.x : nullptr)));
+    restrict_aggs<T>(w0, nw, L.n_agg, 1, L.mptr, L.mrow, L.P, L.r, Lc.b,
+                     c_jac ? Lc.dinv : nullptr, Lc.omega, c_jac ? Lc.x : nullptr);
     if (!sync()) return;
     cur[l] = x;
   }
@@ -1030,15 +984,19 @@ __global__ void __launch_bounds__(256) kb_tail(const CohortMember *mem, int K, i
   for (int d = 1; d <= maxc; ++d) {
     if (mine && d < ck) jacobi(T.lev[d], T.lev[d].x, T.lev[d].x2);  // the pre-sweep after the first
     if (!sync()) return;
-    if (mine && d < ck) {  // residual and restriction in one pass
-      const TailLevel<float> &L = T.lev[d], &Lc = T.lev[d + 1];
-      const bool c_jac = d + 1 < ck;
-      DISPATCH_G(L.G, (resid_restrict_aggs<GG, float>(lw, nlw, L.n_agg, 1, L.mptr, L.mrow, L.P,
-                                                      L.ptr, L.col, L.val, L.b, L.x2, Lc.b,
-                                                      c_jac ? Lc.dinv : nullptr, Lc.omega,
-                                                      c_jac ? Lc.x : nullptr)));
+    if (mine && d < ck) {
+      const TailLevel<float> &L = T.lev[d];
+      DISPATCH_G(L.G, (resid_rows<GG, float>(lw, nlw, L.n, L.ptr, L.col, L.val, L.b, L.x2, L.r)));
     } else if (mine && d == ck) {
       coarse_rows<float>(lw, nlw, T.lev[d].n, T.cinv, T.lev[d].b, T.lev[d].x);
+    }
+    if (!sync()) return;
+    if (d == maxc) break;
+    if (mine && d < ck) {
+      const TailLevel<float> &L = T.lev[d], &Lc = T.lev[d + 1];
+      const bool c_jac = d + 1 < ck;
+      restrict_aggs<float>(lw, nlw, L.n_agg, 1, L.mptr, L.mrow, L.P, L.r, Lc.b,
+                           c_jac ? Lc.dinv : nullptr, Lc.omega, c_jac ? Lc.x : nullptr);
     }
     if (!sync()) return;
   }
@@ -1408,20 +1366,27 @@ static mgpbd_status vcycle_level(Handle *h, int l, const T *b_in, bool x0_ready 
   // the coarse level's first Jacobi sweep from zero rides on the restriction
   const bool c_jac = !gs && !cheb && l + 2 < h->L;
   const int nk = h->p.nk_vectors;
-  if (mf) {
+  if (mf && L.mpos && nk == 1) {
+    // the residual written in member order, the restriction streaming it
+    MG_TRY(mf_level0<T>(h, kMfResidMember, x, b_in, dinv, om, r));
+    k_restrict_member<T><<<blocks_for((int64_t)L.n_agg * 32, 256), 256, 0, h->stream>>>(
+        L.n_agg, L.mptr, (const T *)L.Pm, r, (T *)Lc.b, sc, c_jac ? dinvs<T>(Lc) : nullptr,
+        (T)Lc.omega, c_jac ? (T *)Lc.x : nullptr);
+    MG_LAUNCH("k_restrict_member");
+  } else if (mf) {
     MG_TRY(mf_level0<T>(h, kMfResid, x, b_in, dinv, om, r));
     k_restrict<T><<<blocks_for((int64_t)L.n_agg * 32, 256), 256, 0, h->stream>>>(
         L.n_agg, nk, L.mptr, L.mrow, Ps<T>(L), r, (T *)Lc.b, sc, c_jac ? dinvs<T>(Lc) : nullptr,
         (T)Lc.omega, c_jac ? (T *)Lc.x : nullptr);
     MG_LAUNCH("k_restrict");
   } else {
-    // CSR levels: residual and restriction in one pass (no residual vector)
-    DISPATCH_G(G, (k_resid_restrict<GG, T><<<blocks_for((int64_t)L.n_agg * 32, 256), 256, 0,
-                                              h->stream>>>(
-                      L.n_agg, nk, L.mptr, L.mrow, Ps<T>(L), L.ptr, L.col, val, b_in, x,
-                      (T *)Lc.b, sc, c_jac ? dinvs<T>(Lc) : nullptr, (T)Lc.omega,
-                      c_jac ? (T *)Lc.x : nullptr)));
-    MG_LAUNCH("k_resid_restrict");
+    DISPATCH_G(G, (k_resid<GG, T><<<row_blocks(n, GG), 256, 0, h->stream>>>(n, L.ptr, L.col, val,
+                                                                           b_in, x, r, sc)));
+    MG_LAUNCH("k_resid");
+    k_restrict<T><<<blocks_for((int64_t)L.n_agg * 32, 256), 256, 0, h->stream>>>(
+        L.n_agg, nk, L.mptr, L.mrow, Ps<T>(L), r, (T *)Lc.b, sc, c_jac ? dinvs<T>(Lc) : nullptr,
+        (T)Lc.omega, c_jac ? (T *)Lc.x : nullptr);
+    MG_LAUNCH("k_restrict");
   }
   const T *xc = (const T *)Lc.x;  // where the coarser level leaves its result
   if (tail_applies(h, l + 1)) {
