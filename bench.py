@@ -74,13 +74,15 @@ def parse():
                     help="1: matrix-free level-0 products (headline); 0: assembled CSR")
     ap.add_argument("--no-assembled", action="store_true",
                     help="skip the assembled-CSR comparison line")
-    ap.add_argument("--serve-requests", type=int, default=64,
+    # the default run keeps the serving legs to a few minutes; the 64- and
+    # 512-request traces and the other arms run with these flags
+    ap.add_argument("--serve-requests", type=int, default=24,
                     help="step requests of the serving trace (the full trace has 512)")
-    ap.add_argument("--serve-instances", type=int, default=64,
+    ap.add_argument("--serve-instances", type=int, default=24,
                     help="instances the requests draw from uniformly")
     ap.add_argument("--serve-rate", type=float, default=1.0, help="arrivals per second")
     ap.add_argument("--serve-active", type=int, default=8)
-    ap.add_argument("--serve-arms", default="batched_streams,batched_cohort,serial_mixed,plain_fp64",
+    ap.add_argument("--serve-arms", default="batched_streams,plain_fp64",
                     help="comma list of: " + ", ".join(SERVE_ARMS))
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-only", action="store_true",
@@ -93,8 +95,8 @@ def parse():
                     help="skip the XPBD-versus-MGPBD frame on cloth512")
     ap.add_argument("--no-smoothers", action="store_true",
                     help="skip the Chebyshev-smoother leg on the same block")
-    ap.add_argument("--smoother-steps", type=int, default=3)
-    ap.add_argument("--smoother-warmup", type=int, default=3)
+    ap.add_argument("--smoother-steps", type=int, default=2)
+    ap.add_argument("--smoother-warmup", type=int, default=2)
     ap.add_argument("--arap-steps", type=int, default=3)
     ap.add_argument("--arap-warmup", type=int, default=3)
     ap.add_argument("--assembled-steps", type=int, default=1)
@@ -102,6 +104,8 @@ def parse():
     ap.add_argument("--ap-split", type=int, default=0, choices=[0, 1],
                     help="the PCG recurrence's A.p from float-float pairs with residual "
                          "replacement (1) or in FP64 (0)")
+    ap.add_argument("--ap-ab-steps", type=int, default=2)
+    ap.add_argument("--ap-ab-warmup", type=int, default=1)
     ap.add_argument("--no-ap-ab", action="store_true",
                     help="skip the leg that times the headline with the other A.p form")
     return ap.parse_args()
@@ -385,8 +389,8 @@ SERVE_ARMS = {
 def serving(args):
     """Serving load: step requests of uneven instances with Poisson arrivals,
     driven through the request loop with wall-clock arrivals, all at PCG rtol
-    1e-6 on the same seeded trace (by default every request has an instance
-    of its own).  Arms (--serve-arms):
+    1e-6 on the same seeded trace (each request's instance drawn uniformly
+    from --serve-instances).  Arms (--serve-arms):
       batched_streams  the served form: mixed precision, matrix-free level 0,
                        up to --serve-active requests at once, each on its own
                        stream and worker thread with CUDA graphs;
@@ -610,10 +614,11 @@ def run_ours(args, ws, rank):
         # the same configuration with the other form of the recurrence's A.p,
         # timed the same way from the same start
         pb = dict(params, ap_split=1 - params["ap_split"])
-        rb = measure(mesh, pb, args.steps, args.warmup, ws)
+        rb = measure(mesh, pb, args.ap_ab_steps, args.ap_ab_warmup, ws)
         msb = max_over_ranks(ws, rb["ms"])
-        ap_ab = {"ap_split": pb["ap_split"], "value": ws * args.steps / (msb / 1e3),
-                 "ms_per_step": msb / args.steps, "pcg_iters": rb["pcg"],
+        ap_ab = {"ap_split": pb["ap_split"], "value": ws * args.ap_ab_steps / (msb / 1e3),
+                 "ms_per_step": msb / args.ap_ab_steps, "steps": args.ap_ab_steps,
+                 "warmup": args.ap_ab_warmup, "pcg_iters": rb["pcg"],
                  "true_rel_res": rb["true_res"], "clocks": rb["clocks"],
                  "ap_product": ap_roofline(rb["prof_ap"], pb["ap_split"])}
         rb["solver"].close()
