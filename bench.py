@@ -50,7 +50,7 @@ SWEEP_TRAFFIC_PER_NNZ = (489.342720e6 + 5.179904e6) / 59_625_809
 # + k_mf_row<float,0> 33.68 MB) per constraint row, from ncu captures of the
 # two passes on a 40x33x40 block of the same recipe (593,633 rows); the passes
 # stream per-row and per-incidence arrays, so traffic scales with the rows
-MF_SWEEP_TRAFFIC_PER_ROW = (30.742016e6 + 33.679104e6) / 593_633
+MF_SWEEP_TRAFFIC_PER_ROW = (30.742272e6 + 33.907456e6) / 593_633
 SAMPLE = (4, 33, 4)     # oracle sample: cells along x, y (vertical), z
 SAMPLE_PCG = 500        # PCG iterations per sampled global iteration (cost is linear in them)
 
