@@ -50,7 +50,7 @@ SWEEP_TRAFFIC_PER_NNZ = (489.342720e6 + 5.179904e6) / 59_625_809
 # + k_mf_row<float,0> 33.68 MB) per constraint row, from ncu captures of the
 # two passes on a 40x33x40 block of the same recipe (593,633 rows); the passes
 # stream per-row and per-incidence arrays, so traffic scales with the rows
-MF_SWEEP_TRAFFIC_PER_ROW = (30.742272e6 + 33.907456e6) / 593_633
+MF_SWEEP_TRAFFIC_PER_ROW = (30.742016e6 + 33.679104e6) / 593_633
 SAMPLE = (4, 33, 4)     # oracle sample: cells along x, y (vertical), z
 SAMPLE_PCG = 500        # PCG iterations per sampled global iteration (cost is linear in them)
 
@@ -259,7 +259,7 @@ def ap_roofline(pr, split):
             "avg_launch_ms": avg, "launches": pr["launches"]}
 
 
-def measure(mesh, params, steps, warmup, ws, profile=True):
+def measure(mesh, params, steps, warmup, ws, profile=True, profile_ap=False):
     import torch
 
     from paper_2505_13390_gb300.mgpbd import Solver, launch_count
@@ -275,7 +275,7 @@ def measure(mesh, params, steps, warmup, ws, profile=True):
     barrier(ws)
     torch.cuda.synchronize()
     if profile:
-        g.profile(True)
+        g.profile(True, ap=profile_ap)
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
@@ -300,7 +300,7 @@ def measure(mesh, params, steps, warmup, ws, profile=True):
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     prof = g.profile_read() if profile else None
-    prof_ap = g.profile_read_ap() if profile else None
+    prof_ap = g.profile_read_ap() if profile and profile_ap else None
     if profile:
         g.profile(False)
     st = g.stats()
@@ -582,7 +582,11 @@ def run_ours(args, ws, rank):
     mesh, params = workload(args.workload)
     params = dict(params, precision=1, autotune=1, level0_op=args.level0_op, use_graphs=1,
                   ap_split=args.ap_split if args.level0_op == 1 else 0)
-    res = measure(mesh, params, args.steps, args.warmup, ws)
+    # the headline records the sweeps' event pairs (the roofline), and the
+    # A.p's only when it is the pair form (the FP64 form is timed in the
+    # fp64 leg, on the same kernels)
+    res = measure(mesh, params, args.steps, args.warmup, ws,
+                  profile_ap=bool(params["ap_split"]))
     value, ms = job_rate(ws, args.steps, res["ms"])
     prof = res["prof"]
     g = res["solver"]
@@ -602,7 +606,7 @@ def run_ours(args, ws, rank):
         e2e_val, e2e_bytes = e2e(g, res["runner"], args.e2e_steps)
         e2e_val = e2e_val * ws
         e2e_pcg = list(res["runner"].pcg[pcg0:])
-    ap_prod = ap_roofline(res["prof_ap"], params["ap_split"])
+    ap_prod = ap_roofline(res["prof_ap"], 1) if params["ap_split"] else None
     fp64 = None
     assembled = None
     ap_ab = None
@@ -614,7 +618,7 @@ def run_ours(args, ws, rank):
         # the same configuration with the other form of the recurrence's A.p,
         # timed the same way from the same start
         pb = dict(params, ap_split=1 - params["ap_split"])
-        rb = measure(mesh, pb, args.ap_ab_steps, args.ap_ab_warmup, ws)
+        rb = measure(mesh, pb, args.ap_ab_steps, args.ap_ab_warmup, ws, profile_ap=True)
         msb = max_over_ranks(ws, rb["ms"])
         ap_ab = {"ap_split": pb["ap_split"], "value": ws * args.ap_ab_steps / (msb / 1e3),
                  "ms_per_step": msb / args.ap_ab_steps, "steps": args.ap_ab_steps,
@@ -647,7 +651,9 @@ def run_ours(args, ws, rank):
         torch.cuda.empty_cache()
     if not args.no_fp64:
         p64 = dict(params, precision=0, ap_split=0)
-        r64 = measure(mesh, p64, args.fp64_steps, args.fp64_warmup, ws)
+        # the FP64 A.p kernels are the headline's: they are timed here, so that
+        # the headline's timed region carries only the sweeps' event pairs
+        r64 = measure(mesh, p64, args.fp64_steps, args.fp64_warmup, ws, profile_ap=True)
         ms64 = max_over_ranks(ws, r64["ms"])
         pr = r64["prof"]
         a64 = pr["bytes_per_launch"] / (pr["total_ms"] / max(pr["launches"], 1) / 1e3) / 1e9
@@ -658,6 +664,11 @@ def run_ours(args, ws, rank):
                 "clocks": r64["clocks"],
                 "smoother_sweep_gbs": a64, "smoother_sweep_frac": a64 / hbm,
                 "ap_product": ap_roofline(r64["prof_ap"], 0)}
+        if ap_prod is None and fp64["ap_product"]:
+            ap_prod = dict(fp64["ap_product"],
+                           measured_in="fp64 leg: the same FP64 A.p kernels on the same "
+                                       "workload, so that the headline's timed region carries "
+                                       "only the sweeps' event pairs")
         r64["solver"].close()
     arap = None
     if not args.no_arap:

@@ -312,12 +312,15 @@ mgpbd_status mgpbd_get_constraints(mgpbd_handle_t *h, double *C, double *b, doub
 mgpbd_status mgpbd_get_lambda(mgpbd_handle_t *h, double *lambda, double *dlambda, int mem);
 
 /* ---- measurement ----
- * mgpbd_profile(h, 1) starts recording a CUDA event pair around every
- * level-0 smoother sweep (one CSR launch, or the vertex and row passes of the
- * matrix-free sweep) (the dominant kernel of the V-cycle, Sec. 5.2
- * of the paper: the V-cycle takes most of an iteration and the smoother most
- * of the V-cycle); mgpbd_profile(h, 0) stops.  Both reset the totals and
- * synchronise.  mgpbd_profile_read returns the summed kernel time, the number
+ * mgpbd_profile(h, enable) with enable a mask: bit 0 (1) records a CUDA event
+ * pair around every level-0 smoother sweep (one CSR launch, or the vertex and
+ * row passes of the matrix-free sweep) (the dominant kernel of the V-cycle,
+ * Sec. 5.2 of the paper: the V-cycle takes most of an iteration and the
+ * smoother most of the V-cycle); bit 1 (2) around every A.p of the PCG
+ * recurrence (read with mgpbd_profile_read_ap); 0 stops.  Each event pair
+ * costs a few microseconds of the iteration, so record only what is read.
+ * Other values are MGPBD_E_INVALID.  Every call resets the totals and
+ * synchronises.  mgpbd_profile_read returns the summed kernel time, the number
  * of timed launches (launches skipped after PCG convergence are excluded)
  * and the algorithmic bytes of one launch (CSR values and columns once, row
  * pointers, and four row vectors).  mgpbd_launch_count is the number of

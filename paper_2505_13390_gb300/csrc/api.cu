@@ -39,7 +39,7 @@ mgpbd_status prof_reserve_graph(Handle *h, int pairs) {
 }
 
 mgpbd_status prof_begin(Handle *h, int ch) {
-  if (!h->prof) return MGPBD_OK;
+  if (!h->prof || !(h->prof_mask & (1 << ch))) return MGPBD_OK;
   if (h->capturing) {
     if (h->gev_used[ch] + 1 > (int)h->gev[ch].size() / 2) {
       set_error("profiling: event pool of the captured chunk is too small");
@@ -55,7 +55,7 @@ mgpbd_status prof_begin(Handle *h, int ch) {
 }
 
 mgpbd_status prof_end(Handle *h, int ch) {
-  if (!h->prof) return MGPBD_OK;
+  if (!h->prof || !(h->prof_mask & (1 << ch))) return MGPBD_OK;
   if (h->capturing) {
     MG_CUDA(cudaEventRecordWithFlags(h->gev[ch][2 * h->gev_used[ch] + 1], h->stream,
                                      cudaEventRecordExternal));
@@ -758,7 +758,10 @@ mgpbd_status mgpbd_profile(mgpbd_handle_t *hh, int enable) {
   Handle *h = H(hh);
   if (!h) return MGPBD_E_INVALID;
   MG_CUDA(cudaStreamSynchronize(h->stream));
+  if (enable < 0 || enable > 3) return MGPBD_E_INVALID;
   h->prof = enable != 0;
+  h->prof_mask = enable;
+  h->gen++;  // a captured graph records the channels of its capture
   for (int ch = 0; ch < PROF_CH; ++ch) {
     h->pev_used[ch] = 0;
     h->prof_ms[ch] = 0.0;

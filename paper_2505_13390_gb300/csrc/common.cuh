@@ -171,10 +171,11 @@ struct Handle {
   float4 *ginc4 = nullptr;  // FP32 gradient and row id (bits in .w) per incidence
   float *gd32 = nullptr, *gt32 = nullptr, *at32 = nullptr, *w32 = nullptr, *u32 = nullptr;
   // float-float A.p (params.ap_split): low parts beside the FP32 high parts
-  // above (gradients in incidence and row order, alpha~, w), u's low part,
-  // and p as (high, low) pairs written by the p update
+  // above (gradients in incidence and row order, alpha~, w), u as high and
+  // low parts (four slots per vertex), and p as (high, low) pairs written by
+  // the p update
   float *ginc_lo = nullptr, *gd_lo = nullptr, *gt_lo = nullptr, *at_lo = nullptr,
-        *w_lo = nullptr, *u_lo = nullptr;
+        *w_lo = nullptr, *u_hi = nullptr, *u_lo = nullptr;
   float2 *p_df = nullptr;
   int n_replace = 0;           // residual replacements of the current solve
   int mf_g32 = 8, mf_g64 = 4;  // lanes per vertex of the vertex pass (autotuned)
@@ -220,6 +221,7 @@ struct Handle {
   // optional event timing, per channel (PROF_SWEEP: the level-0 smoother
   // sweeps, the dominant kernel; PROF_AP: the PCG recurrence's A.p)
   bool prof = false;
+  int prof_mask = 0;  // channels recorded: bit PROF_SWEEP, bit PROF_AP
   std::vector<cudaEvent_t> pev[PROF_CH];  // pairs
   std::vector<int> pev_iter[PROF_CH];     // PCG iteration of each pair (-1 = initial V-cycle)
   int pev_used[PROF_CH] = {};

@@ -99,7 +99,7 @@ static size_t estimate_bytes_desc(const mgpbd_mesh_desc *d, const mgpbd_params *
   double b = nnz * (4 + 8 + 4 + 2 + 1) + m * 400.0 + N * 200.0 + ninc * 48.0 + (2 << 20);
   // float-float A.p: low parts of the gradients (incidence and row order),
   // alpha~ and w, u's low part, p as pairs
-  if (p->ap_split) b += ninc * 12.0 + (double)E * 12.0 + (double)T * 48.0 + m * 12.0 + N * 16.0;
+  if (p->ap_split) b += ninc * 12.0 + (double)E * 12.0 + (double)T * 48.0 + m * 12.0 + N * 40.0;
   const double nc = std::min(m, (double)std::max(p->coarse_max, 1));
   b += 24.0 * nc * nc;
   return (size_t)b;

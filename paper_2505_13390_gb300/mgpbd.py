@@ -349,8 +349,11 @@ class Solver:
         return y
 
     # ---- measurement ----------------------------------------------------
-    def profile(self, enable: bool):
-        _check(load().mgpbd_profile(self.h, 1 if enable else 0), "profile")
+    def profile(self, enable: bool, ap: bool = False):
+        """Event timing of the level-0 sweeps (enable) and of the recurrence's
+        A.p (ap); each recorded pair costs a few microseconds per iteration."""
+        mask = (1 if enable else 0) | (2 if ap else 0)
+        _check(load().mgpbd_profile(self.h, mask), "profile")
 
     def profile_read(self) -> Dict:
         ms, n, b = C.c_double(), C.c_int64(), C.c_double()
