@@ -307,3 +307,30 @@ def test_pair_form_parameters():
     with pytest.raises(mgpbd.MgpbdError):
         g.apply(x, 2)
     g.close()
+
+
+def test_profile_channels():
+    """mgpbd_profile's mask selects the timed kernels: the level-0 sweeps
+    (1), the recurrence's A.p (2), both (3); other values are rejected."""
+    from paper_2505_13390_gb300 import mgpbd
+    mesh, p = CASES["block6"]()
+    g = mgpbd.Solver(mesh, dict(p, precision=1, level0_op=1, use_graphs=1),
+                     stream=torch.cuda.Stream())
+    g.begin_frame()
+    g.iterate()
+    seen = {}
+    for sweeps, ap in ((True, False), (False, True), (True, True)):
+        g.profile(sweeps, ap=ap)
+        d = g.iterate()
+        seen[(sweeps, ap)] = (g.profile_read()["launches"], g.profile_read_ap()["launches"],
+                              d["pcg_iters"])
+        g.profile(False)
+    sw, ap_, it = seen[(True, False)]
+    assert sw > 0 and ap_ == 0
+    sw, ap_, it = seen[(False, True)]
+    assert sw == 0 and ap_ == it  # one product per PCG iteration
+    sw, ap_, it = seen[(True, True)]
+    assert sw > 0 and ap_ == it
+    with pytest.raises(mgpbd.MgpbdError):
+        mgpbd._check(mgpbd.load().mgpbd_profile(g.h, 4), "profile")
+    g.close()
