@@ -70,3 +70,35 @@ def test_reference_arm_line_carries_every_key():
     assert "4x33x4" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_ap_roofline_figures():
+    """The A.p line: algorithmic bytes per launch over the mean event time,
+    against the measured copy bandwidth; nothing when nothing was timed."""
+    import bench
+    pr = {"total_ms": 3.5, "launches": 20, "bytes_per_launch": 689588680.0}
+    d = bench.ap_roofline(pr, 0)
+    assert d["form"] == "FP64" and d["launches"] == 20
+    assert d["avg_launch_ms"] == pytest.approx(0.175)
+    assert d["achieved"] == pytest.approx(689588680.0 / 0.175e-3 / 1e9)
+    assert d["frac"] == pytest.approx(d["achieved"] / bench.hbm_peak())
+    assert bench.ap_roofline(pr, 1)["form"].startswith("float-float")
+    assert bench.ap_roofline(None, 0) is None
+    assert bench.ap_roofline({"total_ms": 0.0, "launches": 0, "bytes_per_launch": 1.0}, 0) is None
+
+
+def test_default_run_stays_short():
+    """The default serving legs (what the driver's run includes) are the
+    24-request trace with the streams and plain FP64 arms; the larger
+    traces and other arms take flags."""
+    import bench
+    old = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        a = bench.parse()
+    finally:
+        sys.argv = old
+    assert a.serve_requests == 24 and a.serve_instances == 24
+    assert a.serve_arms.split(",") == ["batched_streams", "plain_fp64"]
+    assert all(n in bench.SERVE_ARMS for n in a.serve_arms.split(","))
+    assert a.ap_split == 0 and not a.serve_only
